@@ -1,0 +1,212 @@
+/*
+ * wt.h - C ABI of the GB300 (sm_103a) hybrid-spectral wave-tank library.
+ *
+ * The library solves, on one GPU, the hot path of the sigma-transformed
+ * incompressible Navier-Stokes free-surface model of Melander, Bitsch, Chen
+ * and Engsig-Karup ("A High-Order Hybrid-Spectral Incompressible Navier-Stokes
+ * Model For Nonlinear Water Waves"): the mixed-stage pressure Poisson problem
+ * (Sec. 3.2-3.3, Eq. poissonp with boundary rows Eq. bcpd / bcpdneu),
+ * discretised with a Fourier basis in x (and y) and Chebyshev-Gauss-Lobatto
+ * nodes in sigma (Sec. 3.4-3.5), solved by GMRES preconditioned with one
+ * geometric p-multigrid V-cycle (Sec. 4, Algorithm 1), inside the
+ * low-storage explicit Runge-Kutta stage (Eq. LSERK) together with the
+ * kinematic free-surface update (Eq. kinematicFS).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Return value: WT_OK (0) or one of the WT_E* codes below; the text of the
+ *    last error of the calling thread is available from wt_last_error().
+ *  - Arrays are float64 and owned by the caller; the library copies what it
+ *    needs and never keeps a caller pointer after the call returns.  Each
+ *    array may live in host memory or in device memory of the tank's GPU;
+ *    the library inspects every pointer (cudaPointerGetAttributes) and copies
+ *    host data through its own device buffers on the tank's stream.
+ *  - Field layout: [Nz+1][Ny][Nx] (x fastest), sigma index 0 = free surface
+ *    (sigma = 1), index Nz = bottom (sigma = 0).  Surface / bathymetry
+ *    layout: [Ny][Nx].  A 2D (vertical-plane) tank has Ny = 1.
+ *  - Grid: x_j = j L / Nx, y_j = j L / Ny (periodic, domain [0,L) x [0,L)),
+ *    sigma_m = (cos(m pi / Nz) + 1) / 2.
+ *  - Nx is a power of two in [4, 4096]; Ny is 1 or a power of two in
+ *    [4, 1024]; 2 <= Nz <= 32.
+ *  - Every call is stream-ordered on the tank's stream (wt_set_stream,
+ *    default: the legacy default stream) and returns after the results are
+ *    complete, except where stated.
+ *  - A tank handle must not be used by two threads at the same time.
+ */
+#ifndef WT_H
+#define WT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum wt_status {
+  WT_OK = 0,
+  WT_EINVAL = 1,    /* invalid argument (sizes, pointers, options)            */
+  WT_ENOMEM = 2,    /* device or host allocation failed                       */
+  WT_ENOCONV = 3,   /* solve stopped at max_it / max_ir above its tolerance;
+                       the best iterate is still written                      */
+  WT_EBREAK = 4,    /* water depth d = h + eta <= 0 or a non-finite value:
+                       the sigma map is invalid (e.g. a breaking wave)        */
+  WT_ECUDA = 5,     /* a CUDA runtime call or kernel launch failed            */
+  WT_ETIMEOUT = 6,  /* a bounded device-side wait gave up                     */
+  WT_ENOTSUP = 7    /* valid request that this build does not support        */
+};
+
+enum wt_precision { WT_FP64 = 0, WT_MIXED = 1, WT_FP32 = 2 };
+
+typedef struct wt_tank wt_tank;
+
+/* Solver and model options (wt_default_options fills the defaults shown). */
+typedef struct wt_options {
+  int mode;          /* WT_FP64: FP64 GMRES + FP64 V-cycle.  WT_MIXED: FP64
+                        iterative refinement around FP32 FGMRES + FP32
+                        V-cycle (default WT_MIXED)                           */
+  double tol;        /* relative residual ||b - A p||_2 / ||b||_2 (1e-10)   */
+  int restart;       /* GMRES restart length m (30)                          */
+  int nu1, nu2;      /* pre- / post-smoothing sweeps (2, 2)                  */
+  double omega;      /* block-Jacobi damping (0.4)                           */
+  int max_it;        /* Krylov iterations per solve (FP64) or per refinement
+                        step (mixed) (200)                                   */
+  int max_ir;        /* refinement steps in WT_MIXED (30)                    */
+  double inner_tol;  /* relative reduction asked of each FP32 inner solve
+                        in WT_MIXED (1e-4)                                   */
+  int filter;        /* exponential cut-off filter every stage (0)           */
+  int linear;        /* linearised model, Sec. 5.3 (0)                       */
+  int coarsest_max;  /* a level with at most this many unknowns is solved
+                        directly by FP64 LU (64, at most 128)               */
+  int bc_transfer;   /* 0: surface/bottom residual rows injected into the
+                        coarse boundary rows (default); 1: whole column
+                        through the Chebyshev truncation as printed          */
+} wt_options;
+
+typedef struct wt_solve_info {
+  int iterations;        /* Krylov iterations (all refinement steps)         */
+  int ir_steps;          /* FP64 refinement steps (WT_MIXED), else 0         */
+  double rel_residual;   /* final ||b - A p||_2 / ||b||_2, FP64 operator     */
+  int status;            /* same code as the call's return value             */
+} wt_solve_info;
+
+/* Fill *opt with the defaults listed above.  Never fails for opt != NULL. */
+int wt_default_options(wt_options* opt);
+
+/*
+ * Create a tank on the current CUDA device.  Sec. 2 (geometry), Sec. 3.4
+ * (grids), Sec. 4.1 (level hierarchy).  bathymetry: h(x, y) > 0, [Ny][Nx].
+ * g: gravity (9.81 in the paper), nu: kinematic viscosity (only nu = 0 is
+ * supported by this build: WT_ENOTSUP otherwise).  On success *out owns all
+ * device memory of the tank until wt_destroy.
+ */
+int wt_create(int Nx, int Ny, int Nz, double L, double g, double nu,
+              const double* bathymetry, wt_tank** out);
+
+/* Replace the options.  Rebuilds the level hierarchy when coarsest_max
+ * changes.  WT_EINVAL for out-of-range values. */
+int wt_set_options(wt_tank* t, const wt_options* opt);
+int wt_get_options(const wt_tank* t, wt_options* opt);
+
+/* Use the given cudaStream_t (passed as void*) for all later calls. */
+int wt_set_stream(wt_tank* t, void* stream);
+
+/* Grid coordinates: x [Nx], y [Ny], sigma [Nz+1] (any may be NULL). */
+int wt_get_grid(const wt_tank* t, double* x, double* y, double* sigma);
+
+/* Multigrid hierarchy: *nlevels and, if dims != NULL, dims[3*l+0..2] =
+ * (Nx, Ny, Nz) of level l, finest first (capacity >= 3 * 16). */
+int wt_get_levels(const wt_tank* t, int* nlevels, int* dims);
+
+/*
+ * Model state: eta [Ny][Nx], u, v, w [Nz+1][Ny][Nx] (v ignored / returned as
+ * zero when Ny = 1), time t.  wt_set_state also clears the 2N Runge-Kutta
+ * registers K (Eq. LSERK, K^0 = 0) and the pressure warm start.
+ */
+int wt_set_state(wt_tank* t, const double* eta, const double* u, const double* v,
+                 const double* w, double time);
+int wt_get_state(const wt_tank* t, double* eta, double* u, double* v, double* w,
+                 double* time);
+/* Last pressure p_D [Nz+1][Ny][Nx] computed by wt_rk_stage / wt_step. */
+int wt_get_pressure(const wt_tank* t, double* p);
+
+/*
+ * Ap = A_{a,b} p, the mixed-stage operator (Eq. poissonp: divergence with the
+ * geometry of eta_a, gradient with that of eta_b; surface rows p, Eq. bcpd;
+ * bottom rows n . Grad_b p with n = (h_x, h_y, 1), Eq. bcpdneu).
+ * precision: WT_FP64 or WT_FP32 (inputs rounded to float, result widened).
+ */
+int wt_apply_operator(wt_tank* t, const double* eta_a, const double* eta_b,
+                      const double* p, double* Ap, int precision);
+
+/*
+ * z = M^{-1} r: one p-multigrid V-cycle (Algorithm 1) from a zero initial
+ * state, damped block-Jacobi smoothing, spectral transfers (Sec. 4.2-4.3).
+ * precision: WT_FP64 or WT_FP32.  Test hook for the preconditioner.
+ */
+int wt_precondition(wt_tank* t, const double* eta_a, const double* eta_b,
+                    const double* r, double* z, int precision);
+
+/*
+ * Solve A_{a,b} p = rhs to ||rhs - A p|| <= tol ||rhs|| (Sec. 4.4): rhs
+ * carries the interior right-hand side and the surface (Dirichlet) and bottom
+ * (Neumann) rows.  p is the initial guess on entry and the solution on exit.
+ * tol <= 0 uses the option's tol.  info may be NULL.  WT_ENOCONV leaves the
+ * best iterate in p.
+ */
+int wt_poisson_solve(wt_tank* t, const double* eta_a, const double* eta_b,
+                     const double* rhs, double* p, double tol, wt_solve_info* info);
+
+/*
+ * One stage k = 1..5 of the five-stage fourth-order 2N-storage Runge-Kutta
+ * scheme (Eq. LSERK, coefficients of Carpenter & Kennedy) with step dt:
+ * free-surface update (Eq. kinematicFS), forcing (Eq. forc1), mixed-stage
+ * Poisson solve and projection (Eq. rkforc1, poissonp).  Advances the time
+ * by dt after stage 5.  WT_EBREAK when d <= 0 or a value is not finite.
+ */
+int wt_rk_stage(wt_tank* t, int k, double dt);
+
+/* nsteps full steps (5 stages each). */
+int wt_step(wt_tank* t, double dt, int nsteps);
+
+/* Statistics of the last wt_rk_stage / wt_step: total Krylov iterations and
+ * solves since the last wt_set_state. */
+int wt_get_stats(const wt_tank* t, long* solves, long* iterations);
+
+/*
+ * Launch accounting and kernel timing (no counterpart in the paper; used to
+ * measure the kernels against the GB300 roofline).  Kernel classes:
+ *   WT_K_ROWPASS  spectral x-row / y-line passes (FFT derivative, resampling,
+ *                 filter) with fused epilogues
+ *   WT_K_OPCOLS   sigma part of the operator, WT_K_SMOOTH block-Jacobi update
+ *                 (+ Nyquist coefficients), WT_K_COLMAT sigma transfers and
+ *                 sigma derivatives, WT_K_BLOCKINV column-block inverses,
+ *                 WT_K_COARSE coarsest LU, WT_K_KRYLOV GMRES vector kernels,
+ *                 WT_K_STAGE metric and Runge-Kutta pointwise kernels.
+ * wt_profile(t, mask) starts a timing window: every later launch of a class
+ * whose bit is set in mask is bracketed by CUDA events on the tank's stream
+ * (mask = 0 stops timing).  wt_profile_read sums the window for one class:
+ * total device milliseconds, launches, and the algorithmic bytes and flops
+ * of those launches.  wt_get_launches: all kernel launches of the tank since
+ * wt_create (counted whether or not timing is on).
+ */
+enum wt_kernel_class {
+  WT_K_ROWPASS = 0, WT_K_OPCOLS = 1, WT_K_SMOOTH = 2, WT_K_COLMAT = 3,
+  WT_K_BLOCKINV = 4, WT_K_COARSE = 5, WT_K_KRYLOV = 6, WT_K_STAGE = 7, WT_K_COUNT = 8
+};
+int wt_profile(wt_tank* t, unsigned mask);
+int wt_profile_read(wt_tank* t, int kernel_class, double* ms, long* launches, double* bytes,
+                    double* flops);
+int wt_get_launches(const wt_tank* t, long* launches);
+
+/* Release every resource of the tank.  t may be NULL. */
+int wt_destroy(wt_tank* t);
+
+/* Copy the calling thread's last error text into buf (always terminated).
+ * Returns the status code that produced it. */
+int wt_last_error(char* buf, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WT_H */

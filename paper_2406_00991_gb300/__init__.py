@@ -1,0 +1,356 @@
+"""Python binding of libwt, the GB300 (sm_103a) CUDA library for the
+hybrid-spectral free-surface Navier-Stokes wave tank (C ABI: include/wt.h).
+
+Only argument marshalling happens here: every step of the computation runs in
+the CUDA kernels of ``csrc/``.  Arrays may be numpy float64 arrays (host
+memory) or contiguous float64 torch CUDA tensors (device memory); the library
+detects which.  Importing fails loudly when libwt.so has not been built
+(``paper_2406_00991_gb300.build.build()``); there is no CPU fallback.
+
+The functions keep the C names (``wt_create``, ``wt_poisson_solve``,
+``wt_rk_stage``, ``wt_step`` ...) and return the status code; ``Tank`` wraps
+them and raises ``WtError`` on a non-zero status.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH
+
+WT_OK, WT_EINVAL, WT_ENOMEM, WT_ENOCONV, WT_EBREAK, WT_ECUDA, WT_ETIMEOUT, WT_ENOTSUP = range(8)
+WT_FP64, WT_MIXED, WT_FP32 = 0, 1, 2
+STATUS_NAMES = {0: "WT_OK", 1: "WT_EINVAL", 2: "WT_ENOMEM", 3: "WT_ENOCONV", 4: "WT_EBREAK",
+                5: "WT_ECUDA", 6: "WT_ETIMEOUT", 7: "WT_ENOTSUP"}
+
+
+class wt_options(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("tol", ctypes.c_double), ("restart", ctypes.c_int),
+                ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
+                ("max_it", ctypes.c_int), ("max_ir", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("filter", ctypes.c_int), ("linear", ctypes.c_int), ("coarsest_max", ctypes.c_int),
+                ("bc_transfer", ctypes.c_int)]
+
+
+class wt_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("ir_steps", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError("libwt.so is not built (run paper_2406_00991_gb300.build.build()); "
+                          "this package has no CPU fallback")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P = ctypes.c_void_p
+    D = ctypes.c_double
+    I = ctypes.c_int
+    sig = {
+        "wt_default_options": [ctypes.POINTER(wt_options)],
+        "wt_create": [I, I, I, D, D, D, P, ctypes.POINTER(P)],
+        "wt_set_options": [P, ctypes.POINTER(wt_options)],
+        "wt_get_options": [P, ctypes.POINTER(wt_options)],
+        "wt_set_stream": [P, P],
+        "wt_get_grid": [P, P, P, P],
+        "wt_get_levels": [P, ctypes.POINTER(I), P],
+        "wt_set_state": [P, P, P, P, P, D],
+        "wt_get_state": [P, P, P, P, P, ctypes.POINTER(D)],
+        "wt_get_pressure": [P, P],
+        "wt_apply_operator": [P, P, P, P, P, I],
+        "wt_precondition": [P, P, P, P, P, I],
+        "wt_poisson_solve": [P, P, P, P, P, D, ctypes.POINTER(wt_solve_info)],
+        "wt_rk_stage": [P, I, D],
+        "wt_step": [P, D, I],
+        "wt_get_stats": [P, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long)],
+        "wt_destroy": [P],
+        "wt_profile": [P, ctypes.c_uint],
+        "wt_profile_read": [P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long),
+                            ctypes.POINTER(D), ctypes.POINTER(D)],
+        "wt_get_launches": [P, ctypes.POINTER(ctypes.c_long)],
+        "wt_last_error": [ctypes.c_char_p, ctypes.c_size_t],
+    }
+    for name, args in sig.items():
+        try:
+            f = getattr(lib, name)
+        except AttributeError as e:
+            raise ImportError("libwt.so is stale (missing %s): rebuild it" % name) from e
+        f.argtypes = args
+        f.restype = I
+    return lib
+
+
+class _Missing:
+    """Stand-in while libwt.so is absent: any use raises the load error."""
+
+    def __init__(self, err):
+        self._err = err
+
+    def __getattr__(self, name):
+        raise self._err
+
+
+def _reload():
+    """(Re)load libwt.so after a build; returns the ctypes library."""
+    global _lib, lib
+    _lib = _load()
+    lib = _lib
+    return _lib
+
+
+try:
+    _lib = _load()
+except ImportError as _e:          # not built yet: fail loudly at the first call
+    _lib = _Missing(_e)
+lib = _lib
+
+
+def _ptr(a):
+    """Device pointer of a float64 CUDA tensor or host pointer of a float64 numpy array."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if a.dtype.__repr__() != "torch.float64" or not a.is_contiguous():
+            raise TypeError("torch tensors passed to libwt must be contiguous float64")
+        return ctypes.c_void_p(a.data_ptr())
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]):
+        raise TypeError("numpy arrays passed to libwt must be C-contiguous float64")
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def wt_last_error():
+    buf = ctypes.create_string_buffer(512)
+    code = _lib.wt_last_error(buf, 512)
+    return code, buf.value.decode()
+
+
+def wt_default_options():
+    o = wt_options()
+    _lib.wt_default_options(ctypes.byref(o))
+    return o
+
+
+def wt_create(Nx, Ny, Nz, L, g, nu, bathymetry):
+    h = ctypes.c_void_p()
+    st = _lib.wt_create(int(Nx), int(Ny), int(Nz), float(L), float(g), float(nu), _ptr(bathymetry),
+                        ctypes.byref(h))
+    return st, h
+
+
+def wt_set_options(t, opt):
+    return _lib.wt_set_options(t, ctypes.byref(opt))
+
+
+def wt_get_options(t):
+    o = wt_options()
+    st = _lib.wt_get_options(t, ctypes.byref(o))
+    return st, o
+
+
+def wt_set_stream(t, stream_handle):
+    return _lib.wt_set_stream(t, ctypes.c_void_p(int(stream_handle)))
+
+
+def wt_get_grid(t, x, y, sigma):
+    return _lib.wt_get_grid(t, _ptr(x), _ptr(y), _ptr(sigma))
+
+
+def wt_get_levels(t):
+    n = ctypes.c_int()
+    dims = (ctypes.c_int * 48)()
+    st = _lib.wt_get_levels(t, ctypes.byref(n), dims)
+    return st, [tuple(dims[3 * l: 3 * l + 3]) for l in range(n.value)]
+
+
+def wt_set_state(t, eta, u, v, w, time=0.0):
+    return _lib.wt_set_state(t, _ptr(eta), _ptr(u), _ptr(v), _ptr(w), float(time))
+
+
+def wt_get_state(t, eta, u, v, w):
+    tm = ctypes.c_double()
+    st = _lib.wt_get_state(t, _ptr(eta), _ptr(u), _ptr(v), _ptr(w), ctypes.byref(tm))
+    return st, tm.value
+
+
+def wt_get_pressure(t, p):
+    return _lib.wt_get_pressure(t, _ptr(p))
+
+
+def wt_apply_operator(t, eta_a, eta_b, p, Ap, precision=WT_FP64):
+    return _lib.wt_apply_operator(t, _ptr(eta_a), _ptr(eta_b), _ptr(p), _ptr(Ap), int(precision))
+
+
+def wt_precondition(t, eta_a, eta_b, r, z, precision=WT_FP64):
+    return _lib.wt_precondition(t, _ptr(eta_a), _ptr(eta_b), _ptr(r), _ptr(z), int(precision))
+
+
+def wt_poisson_solve(t, eta_a, eta_b, rhs, p, tol=0.0):
+    info = wt_solve_info()
+    st = _lib.wt_poisson_solve(t, _ptr(eta_a), _ptr(eta_b), _ptr(rhs), _ptr(p), float(tol),
+                               ctypes.byref(info))
+    return st, info
+
+
+def wt_rk_stage(t, k, dt):
+    return _lib.wt_rk_stage(t, int(k), float(dt))
+
+
+def wt_step(t, dt, nsteps):
+    return _lib.wt_step(t, float(dt), int(nsteps))
+
+
+def wt_get_stats(t):
+    s, i = ctypes.c_long(), ctypes.c_long()
+    st = _lib.wt_get_stats(t, ctypes.byref(s), ctypes.byref(i))
+    return st, s.value, i.value
+
+
+def wt_destroy(t):
+    return _lib.wt_destroy(t)
+
+
+KERNEL_CLASSES = ["rowpass", "opcols", "smooth", "colmat", "blockinv", "coarse", "krylov", "stage"]
+
+
+def wt_profile(t, mask):
+    return _lib.wt_profile(t, ctypes.c_uint(mask))
+
+
+def wt_profile_read(t, kernel_class):
+    ms, b, f = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    n = ctypes.c_long()
+    st = _lib.wt_profile_read(t, int(kernel_class), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b),
+                              ctypes.byref(f))
+    return st, ms.value, n.value, b.value, f.value
+
+
+def wt_get_launches(t):
+    n = ctypes.c_long()
+    st = _lib.wt_get_launches(t, ctypes.byref(n))
+    return st, n.value
+
+
+class WtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(code, code), msg))
+        self.code = code
+
+
+def _check(st):
+    if st != WT_OK:
+        code, msg = wt_last_error()
+        raise WtError(st, msg)
+
+
+class Tank:
+    """Owning wrapper of a wt_tank handle; methods raise WtError on failure."""
+
+    def __init__(self, Nx, Ny, Nz, L, bathymetry, g=9.81, nu=0.0, **options):
+        self.Nx, self.Ny, self.Nz, self.L = int(Nx), int(Ny), int(Nz), float(L)
+        self.M1 = self.Nz + 1
+        st, h = wt_create(Nx, Ny, Nz, L, g, nu, np.ascontiguousarray(bathymetry, dtype=np.float64)
+                          if not hasattr(bathymetry, "data_ptr") else bathymetry)
+        _check(st)
+        self.handle = h
+        if options:
+            self.set_options(**options)
+
+    @property
+    def shape(self):
+        return (self.M1, self.Ny, self.Nx)
+
+    def options(self):
+        st, o = wt_get_options(self.handle)
+        _check(st)
+        return {k: getattr(o, k) for k, _ in wt_options._fields_}
+
+    def set_options(self, **kw):
+        st, o = wt_get_options(self.handle)
+        _check(st)
+        for k, v in kw.items():
+            if k not in dict(wt_options._fields_):
+                raise KeyError(k)
+            setattr(o, k, v)
+        _check(wt_set_options(self.handle, o))
+
+    def set_stream(self, stream_handle):
+        _check(wt_set_stream(self.handle, stream_handle))
+
+    def grid(self):
+        x = np.zeros(self.Nx)
+        y = np.zeros(self.Ny)
+        s = np.zeros(self.M1)
+        _check(wt_get_grid(self.handle, x, y, s))
+        return x, y, s
+
+    def levels(self):
+        st, lv = wt_get_levels(self.handle)
+        _check(st)
+        return lv
+
+    def set_state(self, eta, u, v, w, time=0.0):
+        _check(wt_set_state(self.handle, eta, u, v, w, time))
+
+    def get_state(self):
+        eta = np.zeros((self.Ny, self.Nx))
+        u, v, w = (np.zeros(self.shape) for _ in range(3))
+        st, tm = wt_get_state(self.handle, eta, u, v, w)
+        _check(st)
+        return eta, u, v, w, tm
+
+    def pressure(self):
+        p = np.zeros(self.shape)
+        _check(wt_get_pressure(self.handle, p))
+        return p
+
+    def apply_operator(self, eta_a, eta_b, p, precision=WT_FP64, out=None):
+        out = np.zeros(self.shape) if out is None else out
+        _check(wt_apply_operator(self.handle, eta_a, eta_b, p, out, precision))
+        return out
+
+    def precondition(self, eta_a, eta_b, r, precision=WT_FP64, out=None):
+        out = np.zeros(self.shape) if out is None else out
+        _check(wt_precondition(self.handle, eta_a, eta_b, r, out, precision))
+        return out
+
+    def poisson_solve(self, eta_a, eta_b, rhs, p=None, tol=0.0, raise_noconv=True):
+        p = np.zeros(self.shape) if p is None else p
+        st, info = wt_poisson_solve(self.handle, eta_a, eta_b, rhs, p, tol)
+        if st != WT_OK and (st != WT_ENOCONV or raise_noconv):
+            _check(st)
+        return p, info
+
+    def rk_stage(self, k, dt):
+        _check(wt_rk_stage(self.handle, k, dt))
+
+    def step(self, dt, nsteps=1):
+        _check(wt_step(self.handle, dt, nsteps))
+
+    def stats(self):
+        st, s, i = wt_get_stats(self.handle)
+        _check(st)
+        return s, i
+
+    def profile(self, mask):
+        _check(wt_profile(self.handle, mask))
+
+    def profile_read(self, kernel_class):
+        st, ms, n, b, f = wt_profile_read(self.handle, kernel_class)
+        _check(st)
+        return dict(ms=ms, launches=n, bytes=b, flops=f)
+
+    def launches(self):
+        st, n = wt_get_launches(self.handle)
+        _check(st)
+        return n
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            wt_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,796 @@
+// C ABI of libwt (declared in include/wt.h): tank creation (grids, level
+// hierarchy, Chebyshev matrices and twiddles built on the host in FP64),
+// options, state transfer, the solve / operator test hooks and the
+// low-storage Runge-Kutta stage (paper Sec. 3.1-3.3).
+#include "wt_host.h"
+#include "wt_solver.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+
+using namespace wt;
+
+namespace {
+
+thread_local std::string g_err;
+thread_local int g_code = WT_OK;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  g_code = code;
+  return code;
+}
+
+int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// ------------------------------------------------------------ host matrices
+// CGL nodes xi_m = cos(m pi / Nz); sigma = (xi + 1) / 2 (m = 0: surface).
+std::vector<double> cgl_xi(int Nz) {
+  std::vector<double> x(Nz + 1);
+  for (int m = 0; m <= Nz; ++m) x[m] = std::cos(M_PI * m / Nz);
+  return x;
+}
+// d/dsigma on the CGL nodes: 2 x the textbook CGL matrix on [-1, 1]
+// (c_0 = c_Nz = 2; off-diagonal c_i (-1)^(i+j) / (c_j (xi_i - xi_j)); diagonal = -row sum).
+std::vector<double> cheb_D(int Nz) {
+  const int M1 = Nz + 1;
+  auto x = cgl_xi(Nz);
+  std::vector<double> D(M1 * M1, 0.0);
+  for (int i = 0; i < M1; ++i) {
+    double rs = 0.0;
+    for (int j = 0; j < M1; ++j) {
+      if (i == j) continue;
+      const double ci = (i == 0 || i == Nz) ? 2.0 : 1.0;
+      const double cj = (j == 0 || j == Nz) ? 2.0 : 1.0;
+      const double sgn = ((i + j) & 1) ? -1.0 : 1.0;
+      const double v = ci / cj * sgn / (x[i] - x[j]);
+      D[i * M1 + j] = 2.0 * v;
+      rs += v;
+    }
+    D[i * M1 + i] = -2.0 * rs;
+  }
+  return D;
+}
+std::vector<double> matmul(const std::vector<double>& A, const std::vector<double>& B, int n, int k, int m) {
+  std::vector<double> C((size_t)n * m, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int l = 0; l < k; ++l)
+      for (int j = 0; j < m; ++j) C[(size_t)i * m + j] += A[(size_t)i * k + l] * B[(size_t)l * m + j];
+  return C;
+}
+// nodal -> modal Chebyshev coefficients on the CGL nodes (discrete Chebyshev
+// transform): a_k = 2/(Nz c_k) sum_j f_j cos(k j pi / Nz) / c_j.
+std::vector<double> cheb_modal(int Nz) {
+  const int M1 = Nz + 1;
+  std::vector<double> W(M1 * M1);
+  for (int k = 0; k <= Nz; ++k)
+    for (int j = 0; j <= Nz; ++j) {
+      const double ck = (k == 0 || k == Nz) ? 2.0 : 1.0;
+      const double cj = (j == 0 || j == Nz) ? 2.0 : 1.0;
+      W[k * M1 + j] = 2.0 / (Nz * ck * cj) * std::cos(M_PI * k * j / Nz);
+    }
+  return W;
+}
+double chebT(int k, double xi) { return std::cos(k * std::acos(std::max(-1.0, std::min(1.0, xi)))); }
+// Chebyshev truncation Nzf -> Nzc evaluated at the coarse nodes (Sec. 4.2).
+std::vector<double> cheb_restrict(int Nzf, int Nzc, bool inject) {
+  auto Wf = cheb_modal(Nzf);
+  auto xc = cgl_xi(Nzc);
+  const int Mf = Nzf + 1, Mc = Nzc + 1;
+  std::vector<double> R(Mc * Mf, 0.0);
+  for (int i = 0; i < Mc; ++i)
+    for (int j = 0; j < Mf; ++j) {
+      double s = 0.0;
+      for (int k = 0; k <= Nzc; ++k) s += chebT(k, xc[i]) * Wf[k * Mf + j];
+      R[i * Mf + j] = s;
+    }
+  if (inject) {
+    for (int j = 0; j < Mf; ++j) {
+      R[0 * Mf + j] = (j == 0) ? 1.0 : 0.0;
+      R[(Mc - 1) * Mf + j] = (j == Mf - 1) ? 1.0 : 0.0;
+    }
+  }
+  return R;
+}
+// Interpolation of the degree-Nzc polynomial at the fine nodes (Sec. 4.2).
+std::vector<double> cheb_prolong(int Nzc, int Nzf) {
+  auto Wc = cheb_modal(Nzc);
+  auto xf = cgl_xi(Nzf);
+  const int Mf = Nzf + 1, Mc = Nzc + 1;
+  std::vector<double> P(Mf * Mc, 0.0);
+  for (int i = 0; i < Mf; ++i)
+    for (int j = 0; j < Mc; ++j) {
+      double s = 0.0;
+      for (int k = 0; k <= Nzc; ++k) s += chebT(k, xf[i]) * Wc[k * Mc + j];
+      P[i * Mc + j] = s;
+    }
+  return P;
+}
+// Exponential cut-off F_S(i, Nc, alpha = 36, s = 2) with the damping sign (Sec. 3.6).
+double filter_resp(int i, int N, int Nc) {
+  if (i <= Nc) return 1.0;
+  const double r = double(i - Nc) / double(N + 1 - Nc);
+  return std::exp(-36.0 * r * r);
+}
+// Dense periodic first derivative (Nyquist coefficient zero) and its square.
+std::vector<double> fourier_D_and_DD(int N, double L) {
+  std::vector<double> D(N * N, 0.0);
+  if (N > 1) {
+    const double h = 2.0 * M_PI / N;
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) {
+        if (i == j) continue;
+        const int k = i - j;
+        const double sgn = (k & 1) ? -1.0 : 1.0;
+        D[i * N + j] = 0.5 * sgn / std::tan(k * h / 2.0) * (2.0 * M_PI / L);
+      }
+  }
+  auto DD = matmul(D, D, N, N, N);
+  std::vector<double> out(D);
+  out.insert(out.end(), DD.begin(), DD.end());
+  return out;
+}
+// Diagonal of the composite second derivative: -(1/N) sum_{n != N/2} kappa_n^2.
+double second_diag(int N, double L) {
+  if (N <= 1) return 0.0;
+  double s = 0.0;
+  for (int n = -N / 2 + 1; n < N / 2; ++n) {
+    const double k = 2.0 * M_PI * n / L;
+    s += k * k;
+  }
+  return -s / N;
+}
+
+// p-multigrid hierarchy (Sec. 4.1, reading in the oracle): halve Nx (and Ny)
+// if Nx > Nz, halve Nz if Nz > Nx, both if equal; stop at <= coarsest_max
+// unknowns or when Nx < 4 / Nz < 2 would follow.
+std::vector<std::array<int, 3>> hierarchy(int Nx, int Ny, int Nz, int coarsest_max) {
+  std::vector<std::array<int, 3>> lv{{Nx, Ny, Nz}};
+  for (;;) {
+    auto [nx, ny, nz] = lv.back();
+    if ((long)nx * ny * (nz + 1) <= coarsest_max) break;
+    int cx = nx, cy = ny, cz = nz;
+    if (nx > nz) { cx = nx / 2; cy = ny > 1 ? ny / 2 : 1; }
+    else if (nz > nx) { cz = std::max(2, (nz + 1) / 2); }
+    else { cx = nx / 2; cy = ny > 1 ? ny / 2 : 1; cz = std::max(2, (nz + 1) / 2); }
+    if (cx < 4 || cz < 2 || (Ny > 1 && cy < 4) || (cx == nx && cy == ny && cz == nz)) break;
+    lv.push_back({cx, cy, cz});
+  }
+  return lv;
+}
+
+template <typename T>
+T* upload(Arena& ar, const std::vector<double>& h) {
+  std::vector<T> tmp(h.begin(), h.end());
+  T* d = ar.alloc<T>(h.size());
+  WT_CK(cudaMemcpy(d, tmp.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+  return d;
+}
+
+template <typename T>
+void alloc_level(Arena& ar, Level<T>& L, int Nx, int Ny, int Nz, double Ldom, bool coarsest) {
+  L.Nx = Nx; L.Ny = Ny; L.Nz = Nz; L.M1 = Nz + 1; L.ncols = Nx * Ny; L.n = (long)L.M1 * L.ncols;
+  L.logNx = ilog2(Nx); L.logNy = ilog2(Ny);
+  auto x = cgl_xi(Nz);
+  std::vector<double> sig(L.M1);
+  for (int m = 0; m < L.M1; ++m) sig[m] = 0.5 * (x[m] + 1.0);
+  auto D = cheb_D(Nz);
+  auto D2 = matmul(D, D, L.M1, L.M1, L.M1);
+  std::vector<double> SD(D);
+  for (int i = 0; i < L.M1; ++i)
+    for (int j = 0; j < L.M1; ++j) SD[i * L.M1 + j] *= sig[i];
+  auto DSD = matmul(D, SD, L.M1, L.M1, L.M1);
+  L.sigma = upload<T>(ar, sig);
+  L.D = upload<T>(ar, D);
+  L.D2 = upload<T>(ar, D2);
+  L.DSD = upload<T>(ar, DSD);
+  L.meta = ar.alloc<T>((size_t)kMeta * L.ncols);
+  L.x = ar.alloc<T>(L.n); L.f = ar.alloc<T>(L.n); L.r = ar.alloc<T>(L.n);
+  L.t1 = ar.alloc<T>(L.n); L.t2 = ar.alloc<T>(L.n); L.t3 = ar.alloc<T>(L.n);
+  L.t4 = ar.alloc<T>(L.n); L.t5 = ar.alloc<T>(L.n); L.t6 = ar.alloc<T>(L.n);
+  L.rhoX = ar.alloc<T>((size_t)L.M1 * Ny);
+  L.rhoY = ar.alloc<T>((size_t)L.M1 * Nx);
+  L.rhoXY = ar.alloc<T>(L.M1);
+  L.nclass = Ny > 1 ? 4 : 2;
+  L.cxx = (T)second_diag(Nx, Ldom);
+  L.cyy = (T)second_diag(Ny, Ldom);
+  if (!coarsest) L.Binv = ar.alloc<T>((size_t)L.nclass * L.M1 * L.M1 * L.ncols);
+}
+
+void build_hierarchy(wt_tank& t) {
+  t.har.release();
+  t.L64.clear();
+  t.L32.clear();
+  t.S.clear();
+  t.dims = hierarchy(t.Nx, t.Ny, t.Nz, t.opt.coarsest_max);
+  const int nl = (int)t.dims.size();
+  if (nl > kMaxLevels) throw WtError{WT_EINVAL, "too many multigrid levels"};
+  t.L64.resize(nl);
+  t.L32.resize(nl);
+  t.S.resize(nl);
+  for (int l = 0; l < nl; ++l) {
+    auto [nx, ny, nz] = t.dims[l];
+    alloc_level<double>(t.har, t.L64[l], nx, ny, nz, t.L, l == nl - 1);
+    alloc_level<float>(t.har, t.L32[l], nx, ny, nz, t.L, l == nl - 1);
+    auto& S = t.S[l];
+    const size_t nc = (size_t)nx * ny;
+    S.h = t.har.alloc<double>(nc); S.hx = t.har.alloc<double>(nc); S.hy = t.har.alloc<double>(nc);
+    S.ea = t.har.alloc<double>(nc); S.eax = t.har.alloc<double>(nc); S.eay = t.har.alloc<double>(nc);
+    S.eb = t.har.alloc<double>(nc); S.ebx = t.har.alloc<double>(nc); S.eby = t.har.alloc<double>(nc);
+    S.tmp = t.har.alloc<double>((size_t)t.Ny * nx);
+  }
+  const bool inject = t.opt.bc_transfer == 0;
+  for (int l = 0; l + 1 < nl; ++l) {
+    const int Nzf = t.dims[l][2], Nzc = t.dims[l + 1][2];
+    auto R = cheb_restrict(Nzf, Nzc, inject);
+    auto P = cheb_prolong(Nzc, Nzf);
+    t.L64[l].Rsig = upload<double>(t.har, R);
+    t.L64[l].Psig = upload<double>(t.har, P);
+    t.L32[l].Rsig = upload<float>(t.har, R);
+    t.L32[l].Psig = upload<float>(t.har, P);
+  }
+  auto [cx, cy, cz] = t.dims.back();
+  t.ncoarse = cx * cy * (cz + 1);
+  if (t.ncoarse > 128)
+    throw WtError{WT_ENOTSUP, "coarsest level has " + std::to_string(t.ncoarse) +
+                                  " unknowns; the dense FP64 solve takes at most 128"};
+  t.cLU = t.har.alloc<double>((size_t)t.ncoarse * t.ncoarse);
+  t.cpiv = t.har.alloc<int>(t.ncoarse);
+  t.cDx = upload<double>(t.har, fourier_D_and_DD(cx, t.L));
+  t.cDy = upload<double>(t.har, fourier_D_and_DD(cy, t.L));
+}
+
+const double* in_dev(wt_tank& t, const double* user, double* staging, size_t count) {
+  cudaPointerAttributes at{};
+  cudaError_t e = cudaPointerGetAttributes(&at, user);
+  if (e != cudaSuccess) cudaGetLastError();
+  if (e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged))
+    return user;
+  WT_CK(cudaMemcpyAsync(staging, user, sizeof(double) * count, cudaMemcpyHostToDevice, t.s));
+  return staging;
+}
+void out_copy(wt_tank& t, double* user, const double* dev, size_t count) {
+  WT_CK(cudaMemcpyAsync(user, dev, sizeof(double) * count, cudaMemcpyDefault, t.s));
+}
+
+int check_options(const wt_options& o) {
+  if (o.mode != WT_FP64 && o.mode != WT_MIXED) return fail(WT_EINVAL, "mode must be WT_FP64 or WT_MIXED");
+  if (!(o.tol > 0) || !(o.tol < 1)) return fail(WT_EINVAL, "tol must be in (0, 1)");
+  if (o.restart < 1 || o.restart > 31) return fail(WT_EINVAL, "restart must be in [1, 31]");
+  if (o.nu1 < 0 || o.nu1 > 8 || o.nu2 < 0 || o.nu2 > 8 || o.nu1 + o.nu2 == 0)
+    return fail(WT_EINVAL, "nu1, nu2 must be in [0, 8], not both 0");
+  if (!(o.omega > 0) || !(o.omega < 2)) return fail(WT_EINVAL, "omega must be in (0, 2)");
+  if (o.max_it < 1 || o.max_ir < 1) return fail(WT_EINVAL, "max_it and max_ir must be >= 1");
+  if (!(o.inner_tol > 0) || !(o.inner_tol < 1)) return fail(WT_EINVAL, "inner_tol must be in (0, 1)");
+  if (o.coarsest_max < 1 || o.coarsest_max > 128) return fail(WT_EINVAL, "coarsest_max must be in [1, 128]");
+  if ((o.filter != 0 && o.filter != 1) || (o.linear != 0 && o.linear != 1) ||
+      (o.bc_transfer != 0 && o.bc_transfer != 1))
+    return fail(WT_EINVAL, "filter, linear, bc_transfer are 0 or 1");
+  return WT_OK;
+}
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    return f();
+  } catch (const WtError& e) {
+    return fail(e.code, e.msg);
+  } catch (const std::exception& e) {
+    return fail(WT_ENOMEM, e.what());
+  }
+}
+
+int read_flags(wt_tank& t) {
+  WT_CK(cudaMemcpyAsync(t.hflag, t.dflag, sizeof(int), cudaMemcpyDeviceToHost, t.s));
+  WT_CK(cudaStreamSynchronize(t.s));
+  WT_CK(cudaGetLastError());
+  const int f = *t.hflag;
+  if (f) {
+    WT_CK(cudaMemsetAsync(t.dflag, 0, sizeof(int), t.s));
+    WT_CK(cudaStreamSynchronize(t.s));
+  }
+  return f;
+}
+
+// Carpenter-Kennedy five-stage fourth-order 2N-storage coefficients.
+const double kAlpha[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                          -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+const double kBeta[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                         1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                         2277821191437.0 / 14882151754819.0};
+
+RowPass<double> dpass(wt_tank& t, const double* in, double* out, int nrows, int N, int op) {
+  RowPass<double> a;
+  a.in = in; a.out = out; a.nrows = nrows; a.Nin = N; a.Nout = N;
+  a.logNin = ilog2(N); a.logNout = ilog2(N); a.op = op;
+  a.kscale = 2.0 * M_PI / t.L; a.tw = t.tw64; a.logNtw = t.logNtw;
+  return a;
+}
+// d/dx of a field with `planes` sigma levels (planes = 1: a surface)
+void ddx(wt_tank& t, const double* in, double* out, int planes) {
+  run_rowpass(t, dpass(t, in, out, planes * t.Ny, t.Nx, XOP_DERIV));
+}
+void ddy(wt_tank& t, const double* in, double* out, int planes) {
+  RowPass<double> a = dpass(t, in, out, planes * t.Nx, t.Ny, XOP_DERIV);
+  a.ylines = 1;
+  a.Nxl = t.Nx;
+  run_rowpass(t, a);
+}
+void dds(wt_tank& t, const double* in, double* out) {
+  run_col_matrix<double>(t, t.L64[0].D, t.M1, t.M1, in, out, t.ncols, 0);
+}
+void filter_field(wt_tank& t, double* q, int planes, bool cheb) {
+  RowPass<double> a = dpass(t, q, q, planes * t.Ny, t.Nx, XOP_FILTER);
+  a.filt = t.filt_x;
+  run_rowpass(t, a);
+  if (t.Ny > 1) {
+    RowPass<double> b = dpass(t, q, q, planes * t.Nx, t.Ny, XOP_FILTER);
+    b.ylines = 1;
+    b.Nxl = t.Nx;
+    b.filt = t.filt_y;
+    run_rowpass(t, b);
+  }
+  if (cheb) run_col_matrix<double>(t, t.Fcheb, t.M1, t.M1, q, q, t.ncols, 0);
+}
+
+int rk_stage(wt_tank& t, int k, double dt) {
+  const double a = kAlpha[k - 1], b = kBeta[k - 1];
+  const bool y = t.Ny > 1;
+  const int M1 = t.M1;
+  auto& W = t.work;
+  if (t.opt.filter) {
+    filter_field(t, t.eta, 1, false);
+    filter_field(t, t.u, M1, true);
+    if (y) filter_field(t, t.v, M1, true);
+    filter_field(t, t.w, M1, true);
+  }
+  // free-surface update (Eq. kinematicFS), independent of p_D
+  ddx(t, t.eta, t.eta_x, 1);
+  if (y) ddy(t, t.eta, t.eta_y, 1);
+  WT_LAUNCH(t, K_STAGE, 8.0 * t.ncols * 9, 8.0 * t.ncols, launch_stage_eta(t.ncols, M1, t.opt.linear, a, b, dt, t.u, y ? t.v : nullptr, t.w, t.eta_x,
+                         y ? t.eta_y : t.zero_s, t.Keta, t.eta, t.eta_new, t.f_eta, t.dflag, t.s));
+  // geometry a = eta^(k), b = eta^(k-1) (still water for the linear model)
+  const int prec = t.opt.mode == WT_FP64 ? WT_FP64 : WT_FP32;
+  setup_geometry(t, t.opt.linear ? t.zero_s : t.eta_new, t.opt.linear ? t.zero_s : t.eta, prec, true, true);
+  StageArgs sa;
+  sa.Nx = t.Nx; sa.Ny = t.Ny; sa.M1 = M1; sa.ncols = t.ncols;
+  sa.g = t.g; sa.alpha = a; sa.beta = b; sa.dt = dt; sa.linear = t.opt.linear;
+  sa.sigma = t.L64[0].sigma; sa.D = t.L64[0].D; sa.meta = t.L64[0].meta;
+  double *ux = W[0], *uy = W[1], *vx = W[2], *vy = W[3], *wx = W[4], *wy = W[5];
+  double *us = W[6], *vs = W[7], *ws = W[8], *usx = W[9], *vsy = W[10], *Dus = W[11], *Dvs = W[12],
+         *Dws = W[13], *rhs = W[14], *px = W[15], *py = W[16], *Dp = W[17];
+  // forcing without p_D (Eq. forc1), 2N registers and u* = u + beta (alpha K + dt F)
+  ddx(t, t.u, ux, M1);
+  ddx(t, t.w, wx, M1);
+  if (y) {
+    ddx(t, t.v, vx, M1);
+    ddy(t, t.u, uy, M1);
+    ddy(t, t.v, vy, M1);
+    ddy(t, t.w, wy, M1);
+  }
+  dds(t, t.u, us);
+  dds(t, t.w, ws);
+  if (y) dds(t, t.v, vs);
+  WT_LAUNCH(t, K_STAGE, 8.0 * t.n * (y ? 24 : 14), 30.0 * t.n, launch_stage_forcing(sa, t.u, y ? t.v : nullptr, t.w, ux, uy, vx, vy, wx, wy, t.eta_x,
+                             y ? t.eta_y : t.zero_s, t.f_eta, t.Ku, t.Kv, t.Kw, us, vs, ws, t.s));
+  // right-hand side of the mixed-stage Poisson problem (Eq. poissonp, bcpdneu)
+  ddx(t, us, usx, M1);
+  if (y) ddy(t, vs, vsy, M1);
+  dds(t, us, Dus);
+  dds(t, ws, Dws);
+  if (y) dds(t, vs, Dvs);
+  WT_LAUNCH(t, K_STAGE, 8.0 * t.n * (y ? 9 : 6), 10.0 * t.n, launch_stage_rhs(sa, us, y ? vs : nullptr, ws, usx, vsy, Dus, Dvs, Dws, rhs, t.s));
+  // solve with the previous stage's p_D as the initial guess
+  wt_solve_info info{};
+  int st = poisson_solve_device(t, rhs, t.p, t.opt.tol, &info);
+  if (st != WT_OK && st != WT_ENOCONV) return fail(st, "pressure solve failed (depth <= 0 or non-finite)");
+  // projection (Eq. rkforc1)
+  ddx(t, t.p, px, M1);
+  if (y) ddy(t, t.p, py, M1);
+  dds(t, t.p, Dp);
+  WT_LAUNCH(t, K_STAGE, 8.0 * t.n * (y ? 12 : 9), 16.0 * t.n, launch_stage_project(sa, px, py, Dp, t.Ku, t.Kv, t.Kw, t.u, y ? t.v : nullptr, t.w, t.dflag, t.s));
+  std::swap(t.eta, t.eta_new);
+  if (k == 5) t.time += dt;
+  const int fl = read_flags(t);
+  if (fl) return fail(WT_EBREAK, "water depth d <= 0 or non-finite state after stage " + std::to_string(k));
+  if (st == WT_ENOCONV) return fail(WT_ENOCONV, "pressure solve did not reach its tolerance");
+  return WT_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+int wt_default_options(wt_options* o) {
+  if (!o) return fail(WT_EINVAL, "options pointer is NULL");
+  o->mode = WT_MIXED;
+  o->tol = 1e-10;
+  o->restart = 30;
+  o->nu1 = 2;
+  o->nu2 = 2;
+  o->omega = 0.4;
+  o->max_it = 200;
+  o->max_ir = 30;
+  o->inner_tol = 1e-4;
+  o->filter = 0;
+  o->linear = 0;
+  o->coarsest_max = 64;
+  o->bc_transfer = 0;
+  return WT_OK;
+}
+
+int wt_create(int Nx, int Ny, int Nz, double L, double g, double nu, const double* bathymetry,
+              wt_tank** out) {
+  if (!out) return fail(WT_EINVAL, "out pointer is NULL");
+  *out = nullptr;
+  if (!pow2(Nx) || Nx < 4 || Nx > 4096) return fail(WT_EINVAL, "Nx must be a power of two in [4, 4096]");
+  if (!(Ny == 1 || (pow2(Ny) && Ny >= 4 && Ny <= 1024)))
+    return fail(WT_EINVAL, "Ny must be 1 or a power of two in [4, 1024]");
+  if (Nz < 2 || Nz > 32) return fail(WT_EINVAL, "Nz must be in [2, 32]");
+  if (!(L > 0) || !std::isfinite(L)) return fail(WT_EINVAL, "L must be positive");
+  if (!(g > 0) || !std::isfinite(g)) return fail(WT_EINVAL, "g must be positive");
+  if (nu != 0.0) return fail(WT_ENOTSUP, "viscosity nu != 0 is not supported by this build");
+  if (!bathymetry) return fail(WT_EINVAL, "bathymetry pointer is NULL");
+  return guarded([&]() -> int {
+    std::unique_ptr<wt_tank> t(new wt_tank());
+    WT_CK(cudaGetDevice(&t->device));
+    t->Nx = Nx; t->Ny = Ny; t->Nz = Nz; t->M1 = Nz + 1; t->ncols = Nx * Ny; t->n = (long)t->M1 * t->ncols;
+    t->L = L; t->g = g; t->nu = nu;
+    wt_default_options(&t->opt);
+    auto& ar = t->ar;
+    const long n = t->n;
+    const int nc = t->ncols;
+    // twiddles exp(-2 pi i j / Ntw), host FP64
+    const int Ntw = std::max(Nx, Ny);
+    t->logNtw = ilog2(Ntw);
+    {
+      std::vector<double2> tw(Ntw / 2);
+      std::vector<float2> tf(Ntw / 2);
+      for (int j = 0; j < Ntw / 2; ++j) {
+        const double ang = 2.0 * M_PI * j / Ntw;
+        tw[j] = make_double2(std::cos(ang), -std::sin(ang));
+        tf[j] = make_float2((float)tw[j].x, (float)tw[j].y);
+      }
+      t->tw64 = ar.alloc<double2>(Ntw / 2);
+      t->tw32 = ar.alloc<float2>(Ntw / 2);
+      WT_CK(cudaMemcpy(t->tw64, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice));
+      WT_CK(cudaMemcpy(t->tw32, tf.data(), sizeof(float2) * tf.size(), cudaMemcpyHostToDevice));
+    }
+    {
+      std::vector<double> fx(Nx / 2 + 1), fy(std::max(1, Ny / 2 + 1), 1.0);
+      for (int i = 0; i <= Nx / 2; ++i) fx[i] = filter_resp(i, Nx / 2, Nx / 4);
+      if (Ny > 1)
+        for (int i = 0; i <= Ny / 2; ++i) fy[i] = filter_resp(i, Ny / 2, Ny / 4);
+      t->filt_x = upload<double>(ar, fx);
+      t->filt_y = upload<double>(ar, fy);
+      const int M1 = Nz + 1;
+      auto W = cheb_modal(Nz);
+      auto x = cgl_xi(Nz);
+      const int Nc = (int)std::floor(0.9 * Nz);
+      std::vector<double> VF(M1 * M1);
+      for (int i = 0; i < M1; ++i)
+        for (int k = 0; k < M1; ++k) VF[i * M1 + k] = chebT(k, x[i]) * filter_resp(k, Nz, Nc);
+      t->Fcheb = upload<double>(ar, matmul(VF, W, M1, M1, M1));
+    }
+    // Krylov storage for restart <= 31, state and stage arrays
+    t->V64 = ar.alloc<double>((size_t)32 * n);
+    t->Z64 = ar.alloc<double>((size_t)31 * n);
+    t->V32 = ar.alloc<float>((size_t)32 * n);
+    t->Z32 = ar.alloc<float>((size_t)31 * n);
+    t->nblk = (int)std::min<long>(148, std::max<long>(1, (n + 2047) / 2048));
+    t->partial = ar.alloc<double>((size_t)t->nblk * 40);
+    t->st = ar.alloc<double>(4608);
+    t->stN = ar.alloc<double>(4608);
+    t->x64 = ar.alloc<double>(n); t->r64 = ar.alloc<double>(n); t->b64 = ar.alloc<double>(n);
+    t->b32 = ar.alloc<float>(n); t->e32 = ar.alloc<float>(n);
+    t->eta = ar.alloc<double>(nc); t->eta_new = ar.alloc<double>(nc); t->Keta = ar.alloc<double>(nc);
+    t->f_eta = ar.alloc<double>(nc); t->eta_x = ar.alloc<double>(nc); t->eta_y = ar.alloc<double>(nc);
+    t->zero_s = ar.alloc<double>(nc);
+    t->u = ar.alloc<double>(n); t->v = ar.alloc<double>(n); t->w = ar.alloc<double>(n);
+    t->Ku = ar.alloc<double>(n); t->Kv = ar.alloc<double>(n); t->Kw = ar.alloc<double>(n);
+    t->p = ar.alloc<double>(n);
+    for (int i = 0; i < 18; ++i) t->work.push_back(ar.alloc<double>(n));
+    t->io_s1 = ar.alloc<double>(nc); t->io_s2 = ar.alloc<double>(nc);
+    t->io_f1 = ar.alloc<double>(n); t->io_f2 = ar.alloc<double>(n);
+    t->dflag = ar.alloc<int>(4);
+    WT_CK(cudaMallocHost(&t->hflag, sizeof(int) * 4));
+    WT_CK(cudaMallocHost(&t->hst, sizeof(double) * 16));
+    build_hierarchy(*t);
+    // bathymetry
+    const double* hd = in_dev(*t, bathymetry, t->io_s1, nc);
+    std::vector<double> hh(nc);
+    WT_CK(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * nc, cudaMemcpyDefault, t->s));
+    WT_CK(cudaStreamSynchronize(t->s));
+    for (double v : hh)
+      if (!(v > 0) || !std::isfinite(v)) return fail(WT_EINVAL, "bathymetry must be positive and finite");
+    WT_CK(cudaMemcpyAsync(t->io_s2, hh.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, t->s));
+    setup_bathymetry(*t, t->io_s2);
+    WT_CK(cudaStreamSynchronize(t->s));
+    WT_CK(cudaGetLastError());
+    *out = t.release();
+    return WT_OK;
+  });
+}
+
+int wt_set_options(wt_tank* t, const wt_options* o) {
+  if (!t || !o) return fail(WT_EINVAL, "NULL argument");
+  int st = check_options(*o);
+  if (st != WT_OK) return st;
+  return guarded([&]() -> int {
+    const bool rebuild = o->coarsest_max != t->opt.coarsest_max || o->bc_transfer != t->opt.bc_transfer;
+    t->opt = *o;
+    if (rebuild) {
+      WT_CK(cudaStreamSynchronize(t->s));
+      // keep the fine-level bathymetry across the rebuild
+      std::vector<double> hh(t->ncols);
+      WT_CK(cudaMemcpy(hh.data(), t->S[0].h, sizeof(double) * t->ncols, cudaMemcpyDeviceToHost));
+      build_hierarchy(*t);
+      WT_CK(cudaMemcpy(t->io_s2, hh.data(), sizeof(double) * t->ncols, cudaMemcpyHostToDevice));
+      setup_bathymetry(*t, t->io_s2);
+      WT_CK(cudaStreamSynchronize(t->s));
+    }
+    return WT_OK;
+  });
+}
+
+int wt_get_options(const wt_tank* t, wt_options* o) {
+  if (!t || !o) return fail(WT_EINVAL, "NULL argument");
+  *o = t->opt;
+  return WT_OK;
+}
+
+int wt_set_stream(wt_tank* t, void* stream) {
+  if (!t) return fail(WT_EINVAL, "NULL tank");
+  t->s = static_cast<cudaStream_t>(stream);
+  return WT_OK;
+}
+
+int wt_get_grid(const wt_tank* t, double* x, double* y, double* sigma) {
+  if (!t) return fail(WT_EINVAL, "NULL tank");
+  if (x)
+    for (int j = 0; j < t->Nx; ++j) x[j] = j * t->L / t->Nx;
+  if (y)
+    for (int j = 0; j < t->Ny; ++j) y[j] = t->Ny > 1 ? j * t->L / t->Ny : 0.0;
+  if (sigma) {
+    auto xi = cgl_xi(t->Nz);
+    for (int m = 0; m <= t->Nz; ++m) sigma[m] = 0.5 * (xi[m] + 1.0);
+  }
+  return WT_OK;
+}
+
+int wt_get_levels(const wt_tank* t, int* nlevels, int* dims) {
+  if (!t || !nlevels) return fail(WT_EINVAL, "NULL argument");
+  *nlevels = (int)t->dims.size();
+  if (dims)
+    for (size_t l = 0; l < t->dims.size(); ++l)
+      for (int k = 0; k < 3; ++k) dims[3 * l + k] = t->dims[l][k];
+  return WT_OK;
+}
+
+int wt_set_state(wt_tank* t, const double* eta, const double* u, const double* v, const double* w,
+                 double time) {
+  if (!t || !eta || !u || !w || (t->Ny > 1 && !v)) return fail(WT_EINVAL, "NULL state array");
+  return guarded([&]() -> int {
+    const long n = t->n;
+    const int nc = t->ncols;
+    const double* e = in_dev(*t, eta, t->io_s1, nc);
+    WT_CK(cudaMemcpyAsync(t->eta, e, sizeof(double) * nc, cudaMemcpyDeviceToDevice, t->s));
+    const double* uu = in_dev(*t, u, t->io_f1, n);
+    WT_CK(cudaMemcpyAsync(t->u, uu, sizeof(double) * n, cudaMemcpyDeviceToDevice, t->s));
+    const double* ww = in_dev(*t, w, t->io_f2, n);
+    WT_CK(cudaMemcpyAsync(t->w, ww, sizeof(double) * n, cudaMemcpyDeviceToDevice, t->s));
+    if (t->Ny > 1) {
+      const double* vv = in_dev(*t, v, t->io_f1, n);
+      WT_CK(cudaMemcpyAsync(t->v, vv, sizeof(double) * n, cudaMemcpyDeviceToDevice, t->s));
+    } else {
+      WT_CK(cudaMemsetAsync(t->v, 0, sizeof(double) * n, t->s));
+    }
+    WT_CK(cudaMemsetAsync(t->Keta, 0, sizeof(double) * nc, t->s));
+    WT_CK(cudaMemsetAsync(t->Ku, 0, sizeof(double) * n, t->s));
+    WT_CK(cudaMemsetAsync(t->Kv, 0, sizeof(double) * n, t->s));
+    WT_CK(cudaMemsetAsync(t->Kw, 0, sizeof(double) * n, t->s));
+    WT_CK(cudaMemsetAsync(t->p, 0, sizeof(double) * n, t->s));
+    WT_CK(cudaStreamSynchronize(t->s));
+    t->time = time;
+    t->have_state = true;
+    t->solves = 0;
+    t->iterations = 0;
+    return WT_OK;
+  });
+}
+
+int wt_get_state(const wt_tank* tc, double* eta, double* u, double* v, double* w, double* time) {
+  if (!tc) return fail(WT_EINVAL, "NULL tank");
+  wt_tank* t = const_cast<wt_tank*>(tc);
+  return guarded([&]() -> int {
+    if (eta) out_copy(*t, eta, t->eta, t->ncols);
+    if (u) out_copy(*t, u, t->u, t->n);
+    if (v) out_copy(*t, v, t->v, t->n);
+    if (w) out_copy(*t, w, t->w, t->n);
+    WT_CK(cudaStreamSynchronize(t->s));
+    if (time) *time = t->time;
+    return WT_OK;
+  });
+}
+
+int wt_get_pressure(const wt_tank* tc, double* p) {
+  if (!tc || !p) return fail(WT_EINVAL, "NULL argument");
+  wt_tank* t = const_cast<wt_tank*>(tc);
+  return guarded([&]() -> int {
+    out_copy(*t, p, t->p, t->n);
+    WT_CK(cudaStreamSynchronize(t->s));
+    return WT_OK;
+  });
+}
+
+int wt_apply_operator(wt_tank* t, const double* eta_a, const double* eta_b, const double* p, double* Ap,
+                      int precision) {
+  if (!t || !eta_a || !eta_b || !p || !Ap) return fail(WT_EINVAL, "NULL argument");
+  if (precision != WT_FP64 && precision != WT_FP32) return fail(WT_EINVAL, "precision must be WT_FP64 or WT_FP32");
+  return guarded([&]() -> int {
+    const long n = t->n;
+    const double* ea = in_dev(*t, eta_a, t->io_s1, t->ncols);
+    const double* eb = in_dev(*t, eta_b, t->io_s2, t->ncols);
+    setup_geometry(*t, ea, eb, precision, false, false);
+    const double* pd = in_dev(*t, p, t->io_f1, n);
+    if (precision == WT_FP64) {
+      apply_op<double>(*t, 0, pd, t->io_f2, nullptr, false);
+    } else {
+      auto& L = t->L32[0];
+      WT_LAUNCH(*t, K_KRYLOV, 12.0 * n, 0.0, (launch_convert<double, float>(pd, L.x, n, nullptr, 0, t->s)));
+      apply_op<float>(*t, 0, L.x, L.f, nullptr, false);
+      WT_LAUNCH(*t, K_KRYLOV, 12.0 * n, 0.0, (launch_convert<float, double>(L.f, t->io_f2, n, nullptr, 0, t->s)));
+    }
+    out_copy(*t, Ap, t->io_f2, n);
+    const int fl = read_flags(*t);
+    if (fl) return fail(WT_EBREAK, "water depth d <= 0 or non-finite surface");
+    return WT_OK;
+  });
+}
+
+int wt_precondition(wt_tank* t, const double* eta_a, const double* eta_b, const double* r, double* z,
+                    int precision) {
+  if (!t || !eta_a || !eta_b || !r || !z) return fail(WT_EINVAL, "NULL argument");
+  if (precision != WT_FP64 && precision != WT_FP32) return fail(WT_EINVAL, "precision must be WT_FP64 or WT_FP32");
+  return guarded([&]() -> int {
+    const long n = t->n;
+    const double* ea = in_dev(*t, eta_a, t->io_s1, t->ncols);
+    const double* eb = in_dev(*t, eta_b, t->io_s2, t->ncols);
+    setup_geometry(*t, ea, eb, precision, true, true);
+    const double* rd = in_dev(*t, r, t->io_f1, n);
+    if (precision == WT_FP64) {
+      WT_CK(cudaMemcpyAsync(t->b64, rd, sizeof(double) * n, cudaMemcpyDeviceToDevice, t->s));
+      vcycle<double>(*t, 0, t->b64, t->x64);
+      out_copy(*t, z, t->x64, n);
+    } else {
+      WT_LAUNCH(*t, K_KRYLOV, 12.0 * n, 0.0, (launch_convert<double, float>(rd, t->b32, n, nullptr, 0, t->s)));
+      vcycle<float>(*t, 0, t->b32, t->e32);
+      WT_LAUNCH(*t, K_KRYLOV, 12.0 * n, 0.0, (launch_convert<float, double>(t->e32, t->io_f2, n, nullptr, 0, t->s)));
+      out_copy(*t, z, t->io_f2, n);
+    }
+    const int fl = read_flags(*t);
+    if (fl) return fail(WT_EBREAK, "water depth d <= 0, non-finite surface or singular block");
+    return WT_OK;
+  });
+}
+
+int wt_poisson_solve(wt_tank* t, const double* eta_a, const double* eta_b, const double* rhs, double* p,
+                     double tol, wt_solve_info* info) {
+  if (!t || !eta_a || !eta_b || !rhs || !p) return fail(WT_EINVAL, "NULL argument");
+  if (tol <= 0) tol = t->opt.tol;
+  return guarded([&]() -> int {
+    const long n = t->n;
+    const double* ea = in_dev(*t, eta_a, t->io_s1, t->ncols);
+    const double* eb = in_dev(*t, eta_b, t->io_s2, t->ncols);
+    const int prec = t->opt.mode == WT_FP64 ? WT_FP64 : WT_FP32;
+    setup_geometry(*t, ea, eb, prec, true, true);
+    const double* bd = in_dev(*t, rhs, t->io_f1, n);
+    WT_CK(cudaMemcpyAsync(t->b64, bd, sizeof(double) * n, cudaMemcpyDeviceToDevice, t->s));
+    const double* p0 = in_dev(*t, p, t->io_f2, n);
+    WT_CK(cudaMemcpyAsync(t->x64, p0, sizeof(double) * n, cudaMemcpyDeviceToDevice, t->s));
+    wt_solve_info inf{};
+    int st = poisson_solve_device(*t, t->b64, t->x64, tol, &inf);
+    out_copy(*t, p, t->x64, n);
+    WT_CK(cudaStreamSynchronize(t->s));
+    if (info) *info = inf;
+    if (st == WT_ENOCONV) return fail(st, "solve stopped above its tolerance");
+    if (st != WT_OK) return fail(st, "depth <= 0, singular block or non-finite value in the solve");
+    return WT_OK;
+  });
+}
+
+int wt_rk_stage(wt_tank* t, int k, double dt) {
+  if (!t) return fail(WT_EINVAL, "NULL tank");
+  if (k < 1 || k > 5) return fail(WT_EINVAL, "stage k must be in [1, 5]");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(WT_EINVAL, "dt must be positive");
+  if (!t->have_state) return fail(WT_EINVAL, "no state: call wt_set_state first");
+  return guarded([&]() -> int { return rk_stage(*t, k, dt); });
+}
+
+int wt_step(wt_tank* t, double dt, int nsteps) {
+  if (!t) return fail(WT_EINVAL, "NULL tank");
+  if (nsteps < 0) return fail(WT_EINVAL, "nsteps must be >= 0");
+  for (int s = 0; s < nsteps; ++s)
+    for (int k = 1; k <= 5; ++k) {
+      const int st = wt_rk_stage(t, k, dt);
+      if (st != WT_OK) return st;
+    }
+  return WT_OK;
+}
+
+int wt_get_stats(const wt_tank* t, long* solves, long* iterations) {
+  if (!t) return fail(WT_EINVAL, "NULL tank");
+  if (solves) *solves = t->solves;
+  if (iterations) *iterations = t->iterations;
+  return WT_OK;
+}
+
+int wt_profile(wt_tank* t, unsigned mask) {
+  if (!t) return fail(WT_EINVAL, "NULL tank");
+  return guarded([&]() -> int {
+    WT_CK(cudaStreamSynchronize(t->s));
+    t->prof.rec.clear();
+    t->prof.used = 0;
+    t->prof.mask = mask;
+    return WT_OK;
+  });
+}
+
+int wt_profile_read(wt_tank* t, int k, double* ms, long* launches, double* bytes, double* flops) {
+  if (!t) return fail(WT_EINVAL, "NULL tank");
+  if (k < 0 || k >= K_NCAT) return fail(WT_EINVAL, "kernel class out of range");
+  return guarded([&]() -> int {
+    WT_CK(cudaStreamSynchronize(t->s));
+    double tot = 0.0, b = 0.0, f = 0.0;
+    long cnt = 0;
+    for (const auto& r : t->prof.rec) {
+      if (r.cat != k) continue;
+      float e = 0.f;
+      WT_CK(cudaEventElapsedTime(&e, t->prof.pool[r.ev0], t->prof.pool[r.ev1]));
+      tot += e;
+      b += r.bytes;
+      f += r.flops;
+      ++cnt;
+    }
+    if (ms) *ms = tot;
+    if (launches) *launches = cnt;
+    if (bytes) *bytes = b;
+    if (flops) *flops = f;
+    return WT_OK;
+  });
+}
+
+int wt_get_launches(const wt_tank* t, long* launches) {
+  if (!t || !launches) return fail(WT_EINVAL, "NULL argument");
+  *launches = t->prof.launches;
+  return WT_OK;
+}
+
+int wt_destroy(wt_tank* t) {
+  if (!t) return WT_OK;
+  cudaStreamSynchronize(t->s);
+  if (t->hflag) cudaFreeHost(t->hflag);
+  if (t->hst) cudaFreeHost(t->hst);
+  delete t;
+  return WT_OK;
+}
+
+int wt_last_error(char* buf, size_t n) {
+  if (buf && n) {
+    const size_t k = std::min(n - 1, g_err.size());
+    std::memcpy(buf, g_err.data(), k);
+    buf[k] = '\0';
+  }
+  return g_code;
+}
+
+}  // extern "C"

@@ -1,0 +1,150 @@
+// Host-side data of a tank (shared by wt_capi.cu and wt_solver.cu).
+#pragma once
+
+#include "../../include/wt.h"
+#include "wt_internal.h"
+
+#include <array>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+namespace wt {
+
+struct WtError {
+  int code;
+  std::string msg;
+};
+
+#define WT_CK(call)                                                                         \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      throw ::wt::WtError{WT_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};   \
+  } while (0)
+
+// Device allocations released together.
+struct Arena {
+  std::vector<void*> ptrs;
+  Arena() = default;
+  Arena(const Arena&) = delete;
+  Arena& operator=(const Arena&) = delete;
+  ~Arena() { release(); }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+  template <typename T>
+  T* alloc(size_t n) {
+    if (n == 0) n = 1;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw WtError{WT_ENOMEM, "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed"};
+    }
+    ptrs.push_back(p);
+    WT_CK(cudaMemset(p, 0, n * sizeof(T)));
+    return static_cast<T*>(p);
+  }
+};
+
+template <typename T>
+struct Level {
+  int Nx = 0, Ny = 0, Nz = 0, M1 = 0, ncols = 0, logNx = 0, logNy = 0;
+  long n = 0;
+  T *sigma = nullptr, *D = nullptr, *D2 = nullptr, *DSD = nullptr, *meta = nullptr;
+  T *x = nullptr, *f = nullptr, *r = nullptr;
+  T *t1 = nullptr, *t2 = nullptr, *t3 = nullptr, *t4 = nullptr, *t5 = nullptr, *t6 = nullptr;
+  T *Binv = nullptr;
+  int nclass = 0;
+  T cxx = 0, cyy = 0;
+  T *rhoX = nullptr, *rhoY = nullptr, *rhoXY = nullptr;
+  T *Rsig = nullptr, *Psig = nullptr;   // to / from the next coarser level
+  LevelView<T> view(const c2_t<T>* tw, int logNtw, double Ld) const {
+    LevelView<T> v;
+    v.Nx = Nx; v.Ny = Ny; v.Nz = Nz; v.M1 = M1; v.logNx = logNx; v.logNy = logNy;
+    v.ncols = ncols; v.n = n; v.L = (T)Ld;
+    v.sigma = sigma; v.D = D; v.D2 = D2; v.DSD = DSD; v.meta = meta;
+    v.tw = tw; v.logNtw = logNtw;
+    return v;
+  }
+};
+
+// FP64 surface data of one level: bathymetry and the two free surfaces.
+struct SurfLevel {
+  double *h = nullptr, *hx = nullptr, *hy = nullptr;
+  double *ea = nullptr, *eax = nullptr, *eay = nullptr;
+  double *eb = nullptr, *ebx = nullptr, *eby = nullptr;
+  double *tmp = nullptr;
+};
+
+// Kernel classes of the optional per-launch CUDA-event profiler.
+enum KCat { K_ROWPASS = 0, K_OPCOLS, K_SMOOTH, K_COLMAT, K_BLOCKINV, K_COARSE, K_KRYLOV, K_STAGE,
+            K_NCAT };
+
+struct ProfRec {
+  int ev0, ev1, cat;
+  double bytes, flops;
+};
+
+struct Prof {
+  unsigned mask = 0;                 // bit k: time kernel class k with events
+  std::vector<cudaEvent_t> pool;     // reused between profiling windows
+  size_t used = 0;
+  std::vector<ProfRec> rec;
+  long launches = 0;                 // every kernel launch since creation
+  ~Prof() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
+}  // namespace wt
+
+struct wt_tank {
+  wt::Prof prof;
+  int Nx = 0, Ny = 0, Nz = 0, M1 = 0, ncols = 0;
+  long n = 0;
+  double L = 0, g = 9.81, nu = 0;
+  wt_options opt{};
+  cudaStream_t s = nullptr;
+  int device = 0;
+
+  wt::Arena ar;       // sizes fixed at creation
+  wt::Arena har;      // level hierarchy (rebuilt when coarsest_max changes)
+
+  std::vector<std::array<int, 3>> dims;
+  std::vector<wt::Level<double>> L64;
+  std::vector<wt::Level<float>> L32;
+  std::vector<wt::SurfLevel> S;
+  double2* tw64 = nullptr;
+  float2* tw32 = nullptr;
+  int logNtw = 0;
+  double *cLU = nullptr, *cDx = nullptr, *cDy = nullptr;
+  int* cpiv = nullptr;
+  int ncoarse = 0;
+  double *filt_x = nullptr, *filt_y = nullptr, *Fcheb = nullptr;
+  float* zeros32 = nullptr;
+
+  // Krylov storage (finest level)
+  double *V64 = nullptr, *Z64 = nullptr;
+  float *V32 = nullptr, *Z32 = nullptr;
+  double *st = nullptr, *stN = nullptr, *partial = nullptr;
+  int nblk = 1;
+  double *x64 = nullptr, *r64 = nullptr, *b64 = nullptr;
+  float *b32 = nullptr, *e32 = nullptr;
+
+  // model state and stage work arrays (finest level, FP64)
+  double *eta = nullptr, *eta_new = nullptr, *Keta = nullptr, *f_eta = nullptr;
+  double *eta_x = nullptr, *eta_y = nullptr, *zero_s = nullptr;
+  double *u = nullptr, *v = nullptr, *w = nullptr, *Ku = nullptr, *Kv = nullptr, *Kw = nullptr;
+  double *p = nullptr;
+  std::vector<double*> work;       // fine-level FP64 temporaries
+  double *io_s1 = nullptr, *io_s2 = nullptr, *io_f1 = nullptr, *io_f2 = nullptr;
+  double time = 0;
+  bool have_state = false;
+  int* dflag = nullptr;
+  int* hflag = nullptr;            // pinned
+  double* hst = nullptr;           // pinned
+  long solves = 0, iterations = 0;
+};

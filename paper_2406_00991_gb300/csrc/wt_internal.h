@@ -1,0 +1,186 @@
+// Internal declarations shared by the CUDA translation units of libwt.
+//
+// Device data of one multigrid level is described by LevelView<T>, passed by
+// value to kernels.  Field arrays are [M1][Ny][Nx] (x fastest), M1 = Nz + 1,
+// sigma index 0 = free surface.  Per-column metric data is struct-of-arrays:
+// meta[f * ncols + c] for field f of column c = jy * Nx + jx.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace wt {
+
+// ------------------------------------------------------------ metric fields
+// sigma_x^g(m) = AX_g - sigma_m BX_g, sigma_y^g(m) = AY_g - sigma_m BY_g and
+// sigma_z^g = Z_g (Eq. 1_Scoef) with AX = h_x/d, BX = d_x/d, AY = h_y/d,
+// BY = d_y/d, Z = 1/d for geometry g in {a, b}; HX, HY = bottom slope.
+enum MetaField {
+  M_AXa = 0, M_BXa, M_AYa, M_BYa, M_Za,
+  M_AXb, M_BXb, M_AYb, M_BYb, M_Zb,
+  M_HX, M_HY, M_D_A, M_D_B,   // d^a, d^b (for sigma_t and checks)
+  kMeta
+};
+
+constexpr int kMaxLevels = 16;
+constexpr int kMaxM1 = 33;      // Nz <= 32
+
+template <typename T> struct C2;
+template <> struct C2<float> { using type = float2; };
+template <> struct C2<double> { using type = double2; };
+template <typename T> using c2_t = typename C2<T>::type;
+
+template <typename T>
+struct LevelView {
+  int Nx, Ny, Nz, M1;
+  int logNx, logNy;
+  int ncols;          // Nx * Ny
+  long n;             // M1 * ncols
+  T L;
+  const T* sigma;     // [M1]
+  const T* D;         // [M1*M1] d/dsigma on the CGL nodes
+  const T* D2;        // [M1*M1] D*D
+  const T* DSD;       // [M1*M1] D*diag(sigma)*D
+  const T* meta;      // [kMeta * ncols]
+  const c2_t<T>* tw;  // twiddles exp(-2 pi i t / Ntw), t < Ntw/2
+  int logNtw;
+};
+
+// Nyquist classes of the column-block smoother: 2D uses {00, N0}; 3D uses
+// {00, N0, 0N, NN} (x-Nyquist, y-Nyquist, both).
+constexpr int kMaxClasses = 4;
+
+// ------------------------------------------------------------------ launchers
+// All launchers enqueue on `s` and return cudaGetLastError().
+
+// Spectral x-row / y-line passes (wt_fft.cu).
+enum XEpi { EPI_STORE = 0, EPI_ADD = 1, EPI_RESID = 2, EPI_ACC = 3 };
+enum XOp { XOP_DERIV = 0, XOP_RESAMPLE = 1, XOP_FILTER = 2, XOP_NONE = 3 };
+
+template <typename T>
+struct RowPass {
+  // rows of length Nin read from `in` (row stride Nin), written with length
+  // Nout to `out` (row stride Nout).  Row r of a field is (m, jy) = (r / Ny, r % Ny)
+  // for x-rows; for y-lines the pass runs along y with x as the batch index.
+  const T* in = nullptr;
+  T* out = nullptr;
+  const T* add = nullptr;      // EPI_ADD / EPI_RESID addend
+  const T* rhs = nullptr;      // EPI_RESID: out = rhs - (add + D in)
+  int nrows = 0;               // rows (x) or planes*Nx (y)
+  int Nin = 0, Nout = 0;       // transform sizes
+  int logNin = 0, logNout = 0;
+  int Ny = 1;                  // for the sigma index of a row (skip_bc)
+  int M1 = 0;                  // sigma levels (skip_bc)
+  int skip_bc = 0;             // derivative term is zero on sigma rows 0 and M1-1
+  int op = XOP_DERIV;
+  int epi = EPI_STORE;
+  T kscale = 1;                // 2 pi / L
+  T scale = 1;                 // extra factor on the transformed term
+  const T* filt = nullptr;     // XOP_FILTER: response per |n|, size Nin/2+1
+  T* nyq = nullptr;            // optional per-row Nyquist coefficient of the output
+  const c2_t<T>* tw = nullptr;
+  int logNtw = 0;
+  // y-line geometry (ylines = 1): lines along y of a [planes][Ny][Nx] array
+  int ylines = 0, Nxl = 0;     // x extent of each plane
+};
+
+template <typename T> cudaError_t launch_rowpass(const RowPass<T>& a, cudaStream_t s);
+
+// Column kernels (wt_col.cu).
+template <typename T>
+cudaError_t launch_op_cols(const LevelView<T>& L, const T* p, const T* Px, const T* Py,
+                           T* Gx, T* Gy, T* part, cudaStream_t s);
+template <typename T>
+cudaError_t launch_smooth_cols(const LevelView<T>& L, const T* r, const T* rhoX, const T* rhoY,
+                               const T* rhoXY, const T* Binv, int nclass, T* x, T omega,
+                               int first, cudaStream_t s);
+// out[mo][c] = sum_mi M[mo][mi] in[mi][c] for c < ncols (sigma transfers, filter)
+template <typename T>
+cudaError_t launch_col_matrix(const T* M, int Mo, int Mi, const T* in, T* out, int ncols,
+                              int accumulate, cudaStream_t s);
+template <typename T>
+cudaError_t launch_block_inverse(const LevelView<T>& L, T* Binv, int nclass, T cxx, T cyy,
+                                 int* flag, cudaStream_t s);
+
+// Dense coarsest level (wt_coarse.cu), always FP64 arithmetic.
+cudaError_t launch_coarse_factor(const LevelView<double>& L, const double* Dx, const double* Dy,
+                                 double* LU, int* piv, int* flag, cudaStream_t s);
+template <typename T>
+cudaError_t launch_coarse_solve(int n, const double* LU, const int* piv, const T* f, T* x,
+                                cudaStream_t s);
+
+// Vector / Krylov kernels (wt_krylov.cu).
+template <typename T>
+cudaError_t launch_dots(const T* w, const T* V, long ldv, int nvec, long n, double* partial,
+                        int nblk, int with_norm, cudaStream_t s);
+cudaError_t launch_reduce_partials(const double* partial, int nblk, int nvals, double* out,
+                                   cudaStream_t s);
+template <typename T>
+cudaError_t launch_update_dots(T* w, const T* V, long ldv, int nvec, long n, const double* h,
+                               double* partial, int nblk, cudaStream_t s);
+template <typename T>
+cudaError_t launch_update_normalize(T* w, const T* V, long ldv, int nvec, long n,
+                                    const double* h, const double* inv_norm, T* vout,
+                                    cudaStream_t s);
+template <typename T>
+cudaError_t launch_lincomb(T* x, const T* Z, long ldz, int nvec, long n, const double* y,
+                           cudaStream_t s);
+template <typename T>
+cudaError_t launch_scale_copy(const T* in, T* out, long n, const double* scale, int invert,
+                              cudaStream_t s);
+template <typename Ti, typename To>
+cudaError_t launch_convert(const Ti* in, To* out, long n, const double* scale, int invert,
+                           cudaStream_t s);
+template <typename T>
+cudaError_t launch_axpy_from(double* x, const T* e, long n, const double* scale, cudaStream_t s);
+cudaError_t launch_nyquist_coef(const void* r, int is_double, int nrows, int Nx, int logNx,
+                                void* rho, cudaStream_t s);
+// GMRES small dense part on one thread: see wt_krylov.cu for the state layout.
+cudaError_t launch_gmres_init(double* st, const double* partial, int nblk, int m, double bnorm,
+                              cudaStream_t s);
+cudaError_t launch_gmres_arnoldi(double* st, const double* partial1, const double* partial2,
+                                 int nblk, int j, int m, double bnorm, double tol,
+                                 cudaStream_t s);
+cudaError_t launch_gmres_solve_y(double* st, int k, int m, cudaStream_t s);
+
+// Surface metric (wt_metric.cu).
+cudaError_t launch_metric_fill(int ncols, const double* h, const double* hx, const double* hy,
+                               const double* ea, const double* eax, const double* eay,
+                               const double* eb, const double* ebx, const double* eby,
+                               double* meta, int* flag, cudaStream_t s);
+template <typename Ti, typename To>
+cudaError_t launch_cast(const Ti* in, To* out, long n, cudaStream_t s);
+
+// Runge-Kutta stage kernels (wt_rk.cu).
+struct StageArgs {
+  int Nx, Ny, M1, ncols;
+  double g, alpha, beta, dt;
+  int linear;
+  const double* sigma;
+  const double* D;        // d/dsigma [M1*M1]
+  const double* meta;     // finest-level metric (a = new, b = old)
+};
+cudaError_t launch_stage_forcing(const StageArgs& a, const double* u, const double* v,
+                                 const double* w, const double* ux, const double* uy,
+                                 const double* vx, const double* vy, const double* wx,
+                                 const double* wy, const double* eta_x, const double* eta_y,
+                                 const double* f_eta, double* Ku, double* Kv, double* Kw,
+                                 double* us, double* vs, double* ws, cudaStream_t s);
+cudaError_t launch_stage_eta(int ncols, int M1, int linear, double alpha, double beta, double dt,
+                             const double* u, const double* v, const double* w,
+                             const double* eta_x, const double* eta_y, double* Keta,
+                             const double* eta, double* eta_new, double* f_eta, int* flag,
+                             cudaStream_t s);
+cudaError_t launch_stage_rhs(const StageArgs& a, const double* us, const double* vs,
+                             const double* ws, const double* usx, const double* vsy,
+                             const double* Dus, const double* Dvs, const double* Dws, double* rhs,
+                             cudaStream_t s);
+cudaError_t launch_stage_project(const StageArgs& a, const double* px, const double* py,
+                                 const double* Dp, double* Ku, double* Kv, double* Kw, double* u,
+                                 double* v, double* w, int* flag, cudaStream_t s);
+
+}  // namespace wt

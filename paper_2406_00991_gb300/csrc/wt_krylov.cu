@@ -1,0 +1,344 @@
+// Krylov kernels of the outer iteration (Sec. 4.4): flexible GMRES(m) with
+// classical Gram-Schmidt applied twice (two block dot products per Arnoldi
+// step instead of j sequential ones), warp-shuffle + shared-memory
+// reductions accumulated in FP64, and the small Hessenberg / Givens update on
+// the device so the host only reads one residual estimate per iteration.
+//
+// GMRES state vector st (FP64, device), offsets in wt_internal.h users:
+//   st[0] beta, st[1] |g_{j+1}|, st[2] 1/h_{j+1,j}, st[3] done flag,
+//   st[4] ||b||, st[5] h_{j+1,j}, then h1, h2, cs, sn, g, y and H (column-major).
+#include "wt_internal.h"
+
+#include <algorithm>
+
+namespace wt {
+
+constexpr int OFF_H1 = 8, OFF_H2 = 72, OFF_CS = 136, OFF_SN = 200, OFF_G = 264, OFF_Y = 328,
+              OFF_H = 392;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_dots(const T* __restrict__ w, const T* __restrict__ V,
+                                             long ldv, int nvec, long n, double* __restrict__ partial,
+                                             int with_norm) {
+  __shared__ double red[8][33];
+  T acc[33];
+#pragma unroll
+  for (int i = 0; i < 33; ++i) acc[i] = T(0);
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    const T wv = w[e];
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < nvec) acc[i] += wv * V[i * ldv + e];
+    acc[32] += wv * wv;
+  }
+  const int nvals = nvec + with_norm;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 33; ++i) {
+    const bool used = (i < nvec) || (i == 32 && with_norm);
+    if (!used) continue;
+    double v = (double)acc[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][i] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
+    const int src = (i < nvec) ? i : 32;
+    double s = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k][src];
+    partial[(long)blockIdx.x * nvals + i] = s;
+  }
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ partial, int nblk, int nvals,
+                                  double* __restrict__ out) {
+  for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
+    double s = 0;
+    for (int b = 0; b < nblk; ++b) s += partial[(long)b * nvals + i];
+    out[i] = s;
+  }
+}
+
+// w -= V h (h = st[OFF_H1..]); then partial2 = (V^T w, ||w||^2).
+template <typename T>
+__global__ void __launch_bounds__(256) k_update_dots(T* __restrict__ w, const T* __restrict__ V,
+                                                    long ldv, int nvec, long n,
+                                                    const double* __restrict__ h,
+                                                    double* __restrict__ partial) {
+  __shared__ double red[8][33];
+  __shared__ T sh[32];
+  for (int i = threadIdx.x; i < 32; i += blockDim.x) sh[i] = i < nvec ? (T)h[i] : T(0);
+  __syncthreads();
+  T acc[33];
+#pragma unroll
+  for (int i = 0; i < 33; ++i) acc[i] = T(0);
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    T v[32];
+    T wv = w[e];
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < nvec) { v[i] = V[i * ldv + e]; wv -= sh[i] * v[i]; }
+    w[e] = wv;
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < nvec) acc[i] += wv * v[i];
+    acc[32] += wv * wv;
+  }
+  const int nvals = nvec + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 33; ++i) {
+    if (!(i < nvec || i == 32)) continue;
+    double v = (double)acc[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][i] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
+    const int src = (i < nvec) ? i : 32;
+    double s = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k][src];
+    partial[(long)blockIdx.x * nvals + i] = s;
+  }
+}
+
+// vout = (w - V h) * inv_norm, h = st[OFF_H2..], inv_norm = st[2]
+template <typename T>
+__global__ void __launch_bounds__(256) k_update_normalize(T* __restrict__ w, const T* __restrict__ V,
+                                                         long ldv, int nvec, long n,
+                                                         const double* __restrict__ h,
+                                                         const double* __restrict__ inv_norm,
+                                                         T* __restrict__ vout) {
+  __shared__ T sh[32];
+  for (int i = threadIdx.x; i < 32; i += blockDim.x) sh[i] = i < nvec ? (T)h[i] : T(0);
+  __syncthreads();
+  const T s = (T)(*inv_norm);
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    T wv = w[e];
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < nvec) wv -= sh[i] * V[i * ldv + e];
+    vout[e] = wv * s;
+  }
+}
+
+// x += sum_i y_i Z_i, y = st[OFF_Y..]
+template <typename T>
+__global__ void __launch_bounds__(256) k_lincomb(T* __restrict__ x, const T* __restrict__ Z, long ldz,
+                                                int nvec, long n, const double* __restrict__ y) {
+  __shared__ T sy[32];
+  for (int i = threadIdx.x; i < 32; i += blockDim.x) sy[i] = i < nvec ? (T)y[i] : T(0);
+  __syncthreads();
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    T acc = x[e];
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < nvec) acc += sy[i] * Z[i * ldz + e];
+    x[e] = acc;
+  }
+}
+
+template <typename Ti, typename To>
+__global__ void k_convert(const Ti* __restrict__ in, To* __restrict__ out, long n,
+                          const double* __restrict__ scale, int invert) {
+  double s = 1.0;
+  if (scale) s = invert ? 1.0 / *scale : *scale;
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+    out[e] = (To)((double)in[e] * s);
+}
+
+template <typename T>
+__global__ void k_axpy_from(double* __restrict__ x, const T* __restrict__ e, long n,
+                            const double* __restrict__ scale) {
+  const double s = *scale;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    x[i] += s * (double)e[i];
+}
+
+__global__ void k_nyquist_coef_f(const float* __restrict__ r, int nrows, int N, float* __restrict__ rho) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= nrows) return;
+  float s = 0;
+  for (int j = lane; j < N; j += 32) s += ((j & 1) ? -1.f : 1.f) * r[(long)warp * N + j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) rho[warp] = s / (float)N;
+}
+__global__ void k_nyquist_coef_d(const double* __restrict__ r, int nrows, int N, double* __restrict__ rho) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= nrows) return;
+  double s = 0;
+  for (int j = lane; j < N; j += 32) s += ((j & 1) ? -1.0 : 1.0) * r[(long)warp * N + j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) rho[warp] = s / (double)N;
+}
+
+// ---- small dense GMRES part (one CTA)
+__device__ double block_sum_partial(const double* partial, int nblk, int nvals, int i) {
+  double s = 0;
+  for (int b = 0; b < nblk; ++b) s += partial[(long)b * nvals + i];
+  return s;
+}
+
+__global__ void k_gmres_init(double* st, const double* __restrict__ partial, int nblk, int m,
+                             double bnorm, double tol) {
+  if (threadIdx.x != 0) return;
+  const double ww = block_sum_partial(partial, nblk, 1, 0);
+  const double beta = sqrt(ww);
+  st[0] = beta;
+  st[1] = beta;
+  st[2] = beta > 0 ? 1.0 / beta : 0.0;
+  st[3] = (beta <= tol * bnorm) ? 1.0 : 0.0;
+  st[4] = bnorm;
+  for (int i = 0; i <= m; ++i) st[OFF_G + i] = 0.0;
+  st[OFF_G] = beta;
+}
+
+__global__ void k_gmres_arnoldi(double* st, const double* __restrict__ partial2, int nblk, int j,
+                                int m, double tol) {
+  __shared__ double h2[64];
+  __shared__ double ww;
+  const int nvals = j + 2;    // j+1 dots and ||w||^2
+  for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
+    const double s = block_sum_partial(partial2, nblk, nvals, i);
+    if (i < j + 1) h2[i] = s; else ww = s;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double* H = st + OFF_H + (long)j * (m + 1);
+  double hh = ww;
+  for (int i = 0; i <= j; ++i) {
+    H[i] = st[OFF_H1 + i] + h2[i];
+    st[OFF_H2 + i] = h2[i];
+    hh -= h2[i] * h2[i];
+  }
+  const double hn = hh > 0 ? sqrt(hh) : 0.0;
+  for (int i = 0; i < j; ++i) {
+    const double c = st[OFF_CS + i], s = st[OFF_SN + i];
+    const double t = c * H[i] + s * H[i + 1];
+    H[i + 1] = -s * H[i] + c * H[i + 1];
+    H[i] = t;
+  }
+  const double den = hypot(H[j], hn);
+  const double c = den > 0 ? H[j] / den : 1.0, s = den > 0 ? hn / den : 0.0;
+  st[OFF_CS + j] = c;
+  st[OFF_SN + j] = s;
+  H[j] = den;
+  const double gj = st[OFF_G + j];
+  st[OFF_G + j + 1] = -s * gj;
+  st[OFF_G + j] = c * gj;
+  const double res = fabs(st[OFF_G + j + 1]);
+  st[1] = res;
+  st[5] = hn;
+  // a numerically negligible new direction ends the cycle (lucky breakdown)
+  const bool breakdown = !(hn > 1e-14 * den);
+  st[2] = breakdown ? 0.0 : 1.0 / hn;
+  st[3] = (res <= tol * st[4] || breakdown) ? 1.0 : 0.0;
+}
+
+__global__ void k_gmres_solve_y(double* st, int k, int m) {
+  if (threadIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = st[OFF_G + i];
+    for (int l = i + 1; l < k; ++l) s -= st[OFF_H + (long)l * (m + 1) + i] * st[OFF_Y + l];
+    st[OFF_Y + i] = s / st[OFF_H + (long)i * (m + 1) + i];
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+static inline int blocks_for(long n) {
+  return (int)std::min<long>(std::max<long>(1, (n + 255) / 256), 152 * 4);
+}
+
+template <typename T>
+cudaError_t launch_dots(const T* w, const T* V, long ldv, int nvec, long n, double* partial, int nblk,
+                        int with_norm, cudaStream_t s) {
+  k_dots<T><<<nblk, 256, 0, s>>>(w, V, ldv, nvec, n, partial, with_norm);
+  return cudaGetLastError();
+}
+cudaError_t launch_reduce_partials(const double* partial, int nblk, int nvals, double* out,
+                                   cudaStream_t s) {
+  k_reduce_partials<<<1, 64, 0, s>>>(partial, nblk, nvals, out);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_update_dots(T* w, const T* V, long ldv, int nvec, long n, const double* h,
+                               double* partial, int nblk, cudaStream_t s) {
+  k_update_dots<T><<<nblk, 256, 0, s>>>(w, V, ldv, nvec, n, h, partial);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_update_normalize(T* w, const T* V, long ldv, int nvec, long n, const double* h,
+                                    const double* inv_norm, T* vout, cudaStream_t s) {
+  k_update_normalize<T><<<blocks_for(n), 256, 0, s>>>(w, V, ldv, nvec, n, h, inv_norm, vout);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_lincomb(T* x, const T* Z, long ldz, int nvec, long n, const double* y,
+                           cudaStream_t s) {
+  k_lincomb<T><<<blocks_for(n), 256, 0, s>>>(x, Z, ldz, nvec, n, y);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_scale_copy(const T* in, T* out, long n, const double* scale, int invert,
+                              cudaStream_t s) {
+  k_convert<T, T><<<blocks_for(n), 256, 0, s>>>(in, out, n, scale, invert);
+  return cudaGetLastError();
+}
+template <typename Ti, typename To>
+cudaError_t launch_convert(const Ti* in, To* out, long n, const double* scale, int invert,
+                           cudaStream_t s) {
+  k_convert<Ti, To><<<blocks_for(n), 256, 0, s>>>(in, out, n, scale, invert);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_axpy_from(double* x, const T* e, long n, const double* scale, cudaStream_t s) {
+  k_axpy_from<T><<<blocks_for(n), 256, 0, s>>>(x, e, n, scale);
+  return cudaGetLastError();
+}
+cudaError_t launch_nyquist_coef(const void* r, int is_double, int nrows, int Nx, int logNx, void* rho,
+                                cudaStream_t s) {
+  (void)logNx;
+  const int threads = 256;
+  const int blocks = (nrows * 32 + threads - 1) / threads;
+  if (is_double)
+    k_nyquist_coef_d<<<blocks, threads, 0, s>>>((const double*)r, nrows, Nx, (double*)rho);
+  else
+    k_nyquist_coef_f<<<blocks, threads, 0, s>>>((const float*)r, nrows, Nx, (float*)rho);
+  return cudaGetLastError();
+}
+cudaError_t launch_gmres_init(double* st, const double* partial, int nblk, int m, double bnorm,
+                              cudaStream_t s) {
+  // tol is applied by the arnoldi kernel and the host; init only records beta
+  k_gmres_init<<<1, 32, 0, s>>>(st, partial, nblk, m, bnorm, 0.0);
+  return cudaGetLastError();
+}
+cudaError_t launch_gmres_arnoldi(double* st, const double* partial1, const double* partial2, int nblk,
+                                 int j, int m, double bnorm, double tol, cudaStream_t s) {
+  (void)partial1;
+  (void)bnorm;
+  k_gmres_arnoldi<<<1, 64, 0, s>>>(st, partial2, nblk, j, m, tol);
+  return cudaGetLastError();
+}
+cudaError_t launch_gmres_solve_y(double* st, int k, int m, cudaStream_t s) {
+  k_gmres_solve_y<<<1, 32, 0, s>>>(st, k, m);
+  return cudaGetLastError();
+}
+
+#define WT_KINST(T)                                                                                  \
+  template cudaError_t launch_dots<T>(const T*, const T*, long, int, long, double*, int, int,         \
+                                      cudaStream_t);                                                 \
+  template cudaError_t launch_update_dots<T>(T*, const T*, long, int, long, const double*, double*,   \
+                                             int, cudaStream_t);                                     \
+  template cudaError_t launch_update_normalize<T>(T*, const T*, long, int, long, const double*,       \
+                                                  const double*, T*, cudaStream_t);                  \
+  template cudaError_t launch_lincomb<T>(T*, const T*, long, int, long, const double*, cudaStream_t); \
+  template cudaError_t launch_scale_copy<T>(const T*, T*, long, const double*, int, cudaStream_t);    \
+  template cudaError_t launch_axpy_from<T>(double*, const T*, long, const double*, cudaStream_t);
+WT_KINST(float)
+WT_KINST(double)
+template cudaError_t launch_convert<double, float>(const double*, float*, long, const double*, int,
+                                                   cudaStream_t);
+template cudaError_t launch_convert<float, double>(const float*, double*, long, const double*, int,
+                                                   cudaStream_t);
+
+}  // namespace wt

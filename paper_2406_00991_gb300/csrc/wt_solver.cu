@@ -1,0 +1,370 @@
+// Host orchestration of the pressure solve (paper Sec. 4): geometry set-up of
+// every level, the matrix-free operator, the p-multigrid V-cycle
+// (Algorithm 1), flexible GMRES (Sec. 4.4) and the FP64 iterative
+// refinement wrapped around the FP32 solver.  Every step runs in the kernels
+// of wt_fft.cu / wt_col.cu / wt_coarse.cu / wt_krylov.cu / wt_rk.cu; the host
+// only sequences launches and reads one scalar per Krylov iteration.
+#include "wt_host.h"
+#include "wt_solver.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace wt {
+
+template <> std::vector<Level<double>>& levels<double>(wt_tank& t) { return t.L64; }
+template <> std::vector<Level<float>>& levels<float>(wt_tank& t) { return t.L32; }
+template <> const c2_t<double>* twiddles<double>(wt_tank& t) { return t.tw64; }
+template <> const c2_t<float>* twiddles<float>(wt_tank& t) { return t.tw32; }
+
+static int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+template <typename T>
+static RowPass<T> xpass(wt_tank& t, const T* in, T* out, int nrows, int Nin, int Nout, int op) {
+  RowPass<T> a;
+  a.in = in;
+  a.out = out;
+  a.nrows = nrows;
+  a.Nin = Nin;
+  a.Nout = Nout;
+  a.logNin = ilog2(Nin);
+  a.logNout = ilog2(Nout);
+  a.op = op;
+  a.kscale = (T)(2.0 * M_PI / t.L);
+  a.tw = twiddles<T>(t);
+  a.logNtw = t.logNtw;
+  return a;
+}
+
+template <typename T>
+static RowPass<T> ypass(wt_tank& t, const T* in, T* out, int planes, int Nxl, int Nin, int Nout, int op) {
+  RowPass<T> a = xpass<T>(t, in, out, planes * Nxl, Nin, Nout, op);
+  a.ylines = 1;
+  a.Nxl = Nxl;
+  return a;
+}
+
+// ------------------------------------------------------------------ geometry
+// Fourier truncation of a fine surface array to level l plus its derivatives.
+static void surface_level(wt_tank& t, int l, const double* fine, double* out, double* outx,
+                          double* outy) {
+  cudaStream_t s = t.s;
+  const auto& Lf = t.L64[0];
+  const auto& Ll = t.L64[l];
+  double* tmp = t.S[l].tmp;
+  if (l == 0) {
+    WT_CK(cudaMemcpyAsync(out, fine, sizeof(double) * Lf.ncols, cudaMemcpyDeviceToDevice, s));
+  } else if (Ll.Ny == 1) {
+    run_rowpass(t, xpass<double>(t, fine, out, 1, Lf.Nx, Ll.Nx, XOP_RESAMPLE));
+  } else {
+    run_rowpass(t, xpass<double>(t, fine, tmp, Lf.Ny, Lf.Nx, Ll.Nx, XOP_RESAMPLE));
+    run_rowpass(t, ypass<double>(t, tmp, out, 1, Ll.Nx, Lf.Ny, Ll.Ny, XOP_RESAMPLE));
+  }
+  if (outx) run_rowpass(t, xpass<double>(t, out, outx, Ll.Ny, Ll.Nx, Ll.Nx, XOP_DERIV));
+  if (outy && Ll.Ny > 1)
+    run_rowpass(t, ypass<double>(t, out, outy, 1, Ll.Nx, Ll.Ny, Ll.Ny, XOP_DERIV));
+}
+
+void setup_bathymetry(wt_tank& t, const double* h_fine) {
+  for (size_t l = 0; l < t.L64.size(); ++l)
+    surface_level(t, (int)l, h_fine, t.S[l].h, t.S[l].hx, t.L64[l].Ny > 1 ? t.S[l].hy : nullptr);
+}
+
+void setup_geometry(wt_tank& t, const double* ea, const double* eb, int precision, bool blocks,
+                    bool coarse) {
+  const int nl = (int)t.L64.size();
+  for (int l = 0; l < nl; ++l) {
+    auto& S = t.S[l];
+    auto& L = t.L64[l];
+    const bool y = L.Ny > 1;
+    surface_level(t, l, ea, S.ea, S.eax, y ? S.eay : nullptr);
+    surface_level(t, l, eb, S.eb, S.ebx, y ? S.eby : nullptr);
+    WT_LAUNCH(t, K_STAGE, 8.0 * L.ncols * 23, 20.0 * L.ncols, launch_metric_fill(L.ncols, S.h, S.hx, y ? S.hy : nullptr, S.ea, S.eax, y ? S.eay : nullptr,
+                             S.eb, S.ebx, y ? S.eby : nullptr, L.meta, t.dflag, t.s));
+    if (precision == WT_FP32)
+      WT_LAUNCH(t, K_STAGE, 12.0 * kMeta * L.ncols, 0.0, (launch_cast<double, float>(L.meta, t.L32[l].meta, (long)kMeta * L.ncols, t.s)));
+  }
+  if (blocks) {
+    for (int l = 0; l < nl - 1; ++l) {
+      if (precision == WT_FP32) {
+        auto& L = t.L32[l];
+        WT_LAUNCH(t, K_BLOCKINV, 4.0 * L.ncols * (L.nclass * L.M1 * L.M1 + kMeta), 2.0 * L.nclass * L.ncols * L.M1 * L.M1 * L.M1, launch_block_inverse<float>(L.view(t.tw32, t.logNtw, t.L), L.Binv, L.nclass, L.cxx, L.cyy,
+                                          t.dflag, t.s));
+      } else {
+        auto& L = t.L64[l];
+        WT_LAUNCH(t, K_BLOCKINV, 8.0 * L.ncols * (L.nclass * L.M1 * L.M1 + kMeta), 2.0 * L.nclass * L.ncols * L.M1 * L.M1 * L.M1, launch_block_inverse<double>(L.view(t.tw64, t.logNtw, t.L), L.Binv, L.nclass, L.cxx, L.cyy,
+                                           t.dflag, t.s));
+      }
+    }
+  }
+  if (coarse) {
+    auto& C = t.L64[nl - 1];
+    WT_LAUNCH(t, K_COARSE, 8.0 * t.ncoarse * t.ncoarse, 2.0 / 3.0 * t.ncoarse * t.ncoarse * t.ncoarse, launch_coarse_factor(C.view(t.tw64, t.logNtw, t.L), t.cDx, t.cDy, t.cLU, t.cpiv, t.dflag, t.s));
+  }
+}
+
+// ------------------------------------------------------------------ operator
+// out = A x (f == nullptr) or out = f - A x; nyq: Nyquist coefficients of out.
+template <typename T>
+void apply_op(wt_tank& t, int l, const T* x, T* out, const T* f, bool nyq) {
+  auto& L = levels<T>(t)[l];
+  cudaStream_t s = t.s;
+  const auto V = L.view(twiddles<T>(t), t.logNtw, t.L);
+  if (L.Ny == 1) {
+    run_rowpass(t, xpass<T>(t, x, L.t1, L.M1, L.Nx, L.Nx, XOP_DERIV));
+    WT_LAUNCH(t, K_OPCOLS, sizeof(T) * (4.0 * L.n + 7.0 * L.ncols), 6.0 * L.M1 * L.M1 * L.ncols, launch_op_cols<T>(V, x, L.t1, nullptr, L.t2, nullptr, L.t3, s));
+    RowPass<T> a = xpass<T>(t, L.t2, out, L.M1, L.Nx, L.Nx, XOP_DERIV);
+    a.skip_bc = 1;
+    a.Ny = 1;
+    a.M1 = L.M1;
+    a.add = L.t3;
+    a.rhs = f;
+    a.epi = f ? EPI_RESID : EPI_ADD;
+    a.nyq = nyq ? L.rhoX : nullptr;
+    run_rowpass(t, a);
+  } else {
+    run_rowpass(t, xpass<T>(t, x, L.t1, L.M1 * L.Ny, L.Nx, L.Nx, XOP_DERIV));
+    run_rowpass(t, ypass<T>(t, x, L.t4, L.M1, L.Nx, L.Ny, L.Ny, XOP_DERIV));
+    WT_LAUNCH(t, K_OPCOLS, sizeof(T) * (6.0 * L.n + 12.0 * L.ncols), 8.0 * L.M1 * L.M1 * L.ncols, launch_op_cols<T>(V, x, L.t1, L.t4, L.t2, L.t5, L.t3, s));
+    RowPass<T> a = xpass<T>(t, L.t2, L.t6, L.M1 * L.Ny, L.Nx, L.Nx, XOP_DERIV);
+    a.skip_bc = 1;
+    a.Ny = L.Ny;
+    a.M1 = L.M1;
+    a.add = L.t3;
+    a.epi = EPI_ADD;
+    run_rowpass(t, a);
+    RowPass<T> b = ypass<T>(t, L.t5, out, L.M1, L.Nx, L.Ny, L.Ny, XOP_DERIV);
+    b.skip_bc = 1;
+    b.M1 = L.M1;
+    b.add = L.t6;
+    b.rhs = f;
+    b.epi = f ? EPI_RESID : EPI_ADD;
+    b.nyq = nyq ? L.rhoY : nullptr;
+    run_rowpass(t, b);
+    if (nyq) {
+      WT_LAUNCH(t, K_SMOOTH, sizeof(T) * (double)(L.M1 * L.Ny) * (L.Nx), 2.0 * (L.M1 * L.Ny) * (L.Nx), launch_nyquist_coef(out, sizeof(T) == 8, L.M1 * L.Ny, L.Nx, L.logNx, L.rhoX, s));
+      WT_LAUNCH(t, K_SMOOTH, sizeof(T) * (double)(L.M1) * (L.Ny), 2.0 * (L.M1) * (L.Ny), launch_nyquist_coef(L.rhoX, sizeof(T) == 8, L.M1, L.Ny, L.logNy, L.rhoXY, s));
+    }
+  }
+}
+
+// Nyquist coefficients of an arbitrary field (first sweep on the finest level).
+template <typename T>
+static void nyquist_of(wt_tank& t, Level<T>& L, const T* f) {
+  cudaStream_t s = t.s;
+  if (L.Ny == 1) {
+    WT_LAUNCH(t, K_SMOOTH, sizeof(T) * (double)(L.M1) * (L.Nx), 2.0 * (L.M1) * (L.Nx), launch_nyquist_coef(f, sizeof(T) == 8, L.M1, L.Nx, L.logNx, L.rhoX, s));
+  } else {
+    // y-Nyquist per (m, jx) line via a y-pass with an identity spectrum
+    RowPass<T> b = ypass<T>(t, f, L.t6, L.M1, L.Nx, L.Ny, L.Ny, XOP_NONE);
+    b.nyq = L.rhoY;
+    run_rowpass(t, b);
+    WT_LAUNCH(t, K_SMOOTH, sizeof(T) * (double)(L.M1 * L.Ny) * (L.Nx), 2.0 * (L.M1 * L.Ny) * (L.Nx), launch_nyquist_coef(f, sizeof(T) == 8, L.M1 * L.Ny, L.Nx, L.logNx, L.rhoX, s));
+    WT_LAUNCH(t, K_SMOOTH, sizeof(T) * (double)(L.M1) * (L.Ny), 2.0 * (L.M1) * (L.Ny), launch_nyquist_coef(L.rhoX, sizeof(T) == 8, L.M1, L.Ny, L.logNy, L.rhoXY, s));
+  }
+}
+
+// ------------------------------------------------------------------ V-cycle
+template <typename T>
+static void smooth(wt_tank& t, int l, T* x, const T* f, bool first, bool f_has_nyq) {
+  auto& L = levels<T>(t)[l];
+  const auto V = L.view(twiddles<T>(t), t.logNtw, t.L);
+  const T om = (T)t.opt.omega;
+  if (first) {
+    const bool y = L.Ny > 1;
+    if (f_has_nyq) nyquist_of<T>(t, L, f);
+    WT_LAUNCH(t, K_SMOOTH, sizeof(T) * (2.0 * L.n + (double)L.nclass * L.M1 * L.M1 * L.ncols), 2.0 * L.nclass * L.M1 * L.M1 * L.ncols, launch_smooth_cols<T>(V, f, f_has_nyq ? L.rhoX : nullptr, (f_has_nyq && y) ? L.rhoY : nullptr,
+                                (f_has_nyq && y) ? L.rhoXY : nullptr, L.Binv, L.nclass, x, om, 1, t.s));
+  } else {
+    apply_op<T>(t, l, x, L.r, f, true);
+    WT_LAUNCH(t, K_SMOOTH, sizeof(T) * (3.0 * L.n + (double)L.nclass * L.M1 * L.M1 * L.ncols), 2.0 * L.nclass * L.M1 * L.M1 * L.ncols, launch_smooth_cols<T>(V, L.r, L.rhoX, L.Ny > 1 ? L.rhoY : nullptr, L.Ny > 1 ? L.rhoXY : nullptr,
+                                L.Binv, L.nclass, x, om, 0, t.s));
+  }
+}
+
+template <typename T>
+static void restrict_to(wt_tank& t, int l, const T* r) {
+  auto& F = levels<T>(t)[l];
+  auto& C = levels<T>(t)[l + 1];
+  cudaStream_t s = t.s;
+  const T* cur = r;
+  if (C.Nx != F.Nx) {
+    run_rowpass(t, xpass<T>(t, cur, F.t4, F.M1 * F.Ny, F.Nx, C.Nx, XOP_RESAMPLE));
+    cur = F.t4;
+    if (F.Ny > 1) {
+      run_rowpass(t, ypass<T>(t, cur, F.t5, F.M1, C.Nx, F.Ny, C.Ny, XOP_RESAMPLE));
+      cur = F.t5;
+    }
+  }
+  run_col_matrix<T>(t, F.Rsig, C.M1, F.M1, cur, C.f, C.ncols, 0);
+}
+
+template <typename T>
+static void prolong_add(wt_tank& t, int l, T* x) {
+  auto& F = levels<T>(t)[l];
+  auto& C = levels<T>(t)[l + 1];
+  cudaStream_t s = t.s;
+  if (C.Nx == F.Nx) {
+    run_col_matrix<T>(t, F.Psig, F.M1, C.M1, C.x, x, F.ncols, 1);
+    return;
+  }
+  run_col_matrix<T>(t, F.Psig, F.M1, C.M1, C.x, F.t4, C.ncols, 0);
+  const T* cur = F.t4;
+  if (F.Ny > 1) {
+    run_rowpass(t, ypass<T>(t, cur, F.t5, F.M1, C.Nx, C.Ny, F.Ny, XOP_RESAMPLE));
+    cur = F.t5;
+  }
+  RowPass<T> a = xpass<T>(t, cur, x, F.M1 * F.Ny, C.Nx, F.Nx, XOP_RESAMPLE);
+  a.epi = EPI_ACC;
+  run_rowpass(t, a);
+}
+
+template <typename T>
+void vcycle(wt_tank& t, int l, const T* f, T* x) {
+  auto& lev = levels<T>(t);
+  const int nl = (int)lev.size();
+  auto& L = lev[l];
+  if (l == nl - 1) {
+    WT_LAUNCH(t, K_COARSE, 8.0 * L.n * L.n + 2.0 * sizeof(T) * L.n, 2.0 * L.n * L.n, launch_coarse_solve<T>((int)L.n, t.cLU, t.cpiv, f, x, t.s));
+    return;
+  }
+  // pre-smoothing (nu1 sweeps from a zero initial state).  A right-hand side
+  // that arrived through a Fourier truncation has no x- (y-) Nyquist content;
+  // the finest level and levels reached by sigma-only coarsening may have some.
+  const bool f_nyq = (l == 0) || (lev[l - 1].Nx == L.Nx);
+  if (t.opt.nu1 > 0) {
+    smooth<T>(t, l, x, f, true, f_nyq);
+    for (int i = 1; i < t.opt.nu1; ++i) smooth<T>(t, l, x, f, false, false);
+    apply_op<T>(t, l, x, L.r, f, false);      // r = f - A u
+    restrict_to<T>(t, l, L.r);
+  } else {
+    WT_CK(cudaMemsetAsync(x, 0, sizeof(T) * L.n, t.s));
+    restrict_to<T>(t, l, f);
+  }
+  vcycle<T>(t, l + 1, lev[l + 1].f, lev[l + 1].x);
+  prolong_add<T>(t, l, x);                     // u = u + P e_c
+  for (int i = 0; i < t.opt.nu2; ++i) smooth<T>(t, l, x, f, false, false);
+}
+
+// ------------------------------------------------------------------ norms
+template <typename T>
+static double norm2(wt_tank& t, const T* v, long n) {
+  WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * ((0) + 1), 2.0 * n * ((0) + 1), launch_dots<T>(v, nullptr, 0, 0, n, t.partial, t.nblk, 1, t.s));
+  WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk, 0.0, launch_gmres_init(t.stN, t.partial, t.nblk, 1, 1.0, t.s));
+  WT_CK(cudaMemcpyAsync(t.hst, t.stN, sizeof(double) * 4, cudaMemcpyDeviceToHost, t.s));
+  WT_CK(cudaStreamSynchronize(t.s));
+  return t.hst[0];
+}
+
+// ------------------------------------------------------------------ FGMRES
+template <typename T> static T* Vbuf(wt_tank& t);
+template <> double* Vbuf<double>(wt_tank& t) { return t.V64; }
+template <> float* Vbuf<float>(wt_tank& t) { return t.V32; }
+template <typename T> static T* Zbuf(wt_tank& t);
+template <> double* Zbuf<double>(wt_tank& t) { return t.Z64; }
+template <> float* Zbuf<float>(wt_tank& t) { return t.Z32; }
+
+// Right-preconditioned flexible GMRES(m) on the finest level of precision T:
+// x is the initial guess and the result; returns the last true relative
+// residual ||b - A x|| / bnorm computed in precision T.
+template <typename T>
+double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit, int* its_out) {
+  auto& L0 = levels<T>(t)[0];
+  const long n = L0.n;
+  const int m = t.opt.restart;
+  T* V = Vbuf<T>(t);
+  T* Z = Zbuf<T>(t);
+  int its = 0;
+  double rel = 1.0;
+  for (;;) {
+    apply_op<T>(t, 0, x, V, b, false);                       // r = b - A x -> V_0
+    WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * ((0) + 1), 2.0 * n * ((0) + 1), launch_dots<T>(V, nullptr, 0, 0, n, t.partial, t.nblk, 1, t.s));
+    WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk, 0.0, launch_gmres_init(t.st, t.partial, t.nblk, m, bnorm, t.s));
+    WT_CK(cudaMemcpyAsync(t.hst, t.st, sizeof(double) * 6, cudaMemcpyDeviceToHost, t.s));
+    WT_CK(cudaStreamSynchronize(t.s));
+    rel = bnorm > 0 ? t.hst[0] / bnorm : 0.0;
+    if (rel <= tol || its >= maxit || t.hst[0] == 0.0) break;
+    WT_LAUNCH(t, K_KRYLOV, 2.0 * sizeof(T) * n, (double)n, launch_scale_copy<T>(V, V, n, t.st + 2, 0, t.s));  // v_0 = r / beta
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      T* vj = V + (long)j * n;
+      T* zj = Z + (long)j * n;
+      T* w = V + (long)(j + 1) * n;
+      vcycle<T>(t, 0, vj, zj);                               // z_j = M^{-1} v_j
+      apply_op<T>(t, 0, zj, w, nullptr, false);              // w = A z_j
+      WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * ((j + 1) + 1), 2.0 * n * ((j + 1) + 1), launch_dots<T>(w, V, n, j + 1, n, t.partial, t.nblk, 0, t.s));
+      WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk * (j + 1), 0.0, launch_reduce_partials(t.partial, t.nblk, j + 1, t.st + 8, t.s));
+      WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (j + 3), 4.0 * n * (j + 2), launch_update_dots<T>(w, V, n, j + 1, n, t.st + 8, t.partial, t.nblk, t.s));
+      WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk * (j + 2), 0.0, launch_gmres_arnoldi(t.st, nullptr, t.partial, t.nblk, j, m, bnorm, tol, t.s));
+      WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (j + 3), 2.0 * n * (j + 2), launch_update_normalize<T>(w, V, n, j + 1, n, t.st + 72, t.st + 2, w, t.s));
+      WT_CK(cudaMemcpyAsync(t.hst, t.st, sizeof(double) * 6, cudaMemcpyDeviceToHost, t.s));
+      WT_CK(cudaStreamSynchronize(t.s));
+      ++its;
+      k = j + 1;
+      if (t.hst[3] != 0.0 || its >= maxit) break;
+    }
+    WT_LAUNCH(t, K_KRYLOV, 8.0 * k * k, (double)k * k, launch_gmres_solve_y(t.st, k, m, t.s));
+    WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (k + 2), 2.0 * n * k, launch_lincomb<T>(x, Z, n, k, n, t.st + 328, t.s));
+  }
+  if (its_out) *its_out = its;
+  return rel;
+}
+
+// ------------------------------------------------------------------ solves
+int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_solve_info* info) {
+  const long n = t.n;
+  const double bn = norm2<double>(t, b, n);
+  int its_total = 0, ir = 0;
+  double rel = 0.0;
+  int status = WT_OK;
+  if (bn == 0.0) {
+    WT_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, t.s));
+    rel = 0.0;
+  } else if (t.opt.mode == WT_FP64) {
+    int its = 0;
+    rel = fgmres<double>(t, b, x, bn, tol, t.opt.max_it, &its);
+    its_total = its;
+    if (!(rel <= tol)) status = WT_ENOCONV;
+  } else {
+    // FP64 iterative refinement around the FP32 solver
+    for (;;) {
+      apply_op<double>(t, 0, x, t.r64, b, false);            // r = b - A64 x
+      const double rn = norm2<double>(t, t.r64, n);
+      rel = rn / bn;
+      if (rel <= tol) break;
+      if (ir >= t.opt.max_ir || !std::isfinite(rel)) { status = WT_ENOCONV; break; }
+      WT_LAUNCH(t, K_KRYLOV, 12.0 * n, (double)n, (launch_convert<double, float>(t.r64, t.b32, n, t.stN + 2, 0, t.s)));  // r / ||r||
+      WT_CK(cudaMemsetAsync(t.e32, 0, sizeof(float) * n, t.s));
+      int its = 0;
+      fgmres<float>(t, t.b32, t.e32, 1.0, t.opt.inner_tol, t.opt.max_it, &its);
+      its_total += its;
+      WT_LAUNCH(t, K_KRYLOV, 20.0 * n, 2.0 * n, launch_axpy_from<float>(x, t.e32, n, t.stN + 0, t.s));  // x += ||r|| e
+      ++ir;
+    }
+  }
+  WT_CK(cudaMemcpyAsync(t.hflag, t.dflag, sizeof(int), cudaMemcpyDeviceToHost, t.s));
+  WT_CK(cudaStreamSynchronize(t.s));
+  if (*t.hflag & 7) status = WT_EBREAK;
+  if (!std::isfinite(rel)) status = WT_EBREAK;
+  t.solves += 1;
+  t.iterations += its_total;
+  if (info) {
+    info->iterations = its_total;
+    info->ir_steps = ir;
+    info->rel_residual = rel;
+    info->status = status;
+  }
+  return status;
+}
+
+template void apply_op<double>(wt_tank&, int, const double*, double*, const double*, bool);
+template void apply_op<float>(wt_tank&, int, const float*, float*, const float*, bool);
+template void vcycle<double>(wt_tank&, int, const double*, double*);
+template void vcycle<float>(wt_tank&, int, const float*, float*);
+
+}  // namespace wt

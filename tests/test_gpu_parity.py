@@ -1,0 +1,210 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle on the
+same seeded inputs.  Tolerances are derived in the design doc (operator: rounding
+of the FFT and sigma contractions relative to max |A p|; solves: the
+spec bounds 1e-10 FP64 / 1e-9 mixed on the relative residual measured
+with the oracle's own operator)."""
+
+import math
+
+import numpy as np
+import pytest
+
+import seeded_inputs as si
+from oracle import krylov, pmg, rk
+from oracle import operator as op
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2406_00991_gb300 as w
+    return w
+
+
+def curved(Nx, Ny, Nz, L, seed=0, amp=0.05, bump=0.3):
+    g = op.Grid(Nx, Ny, Nz, L)
+    X, Y = np.meshgrid(g.x, g.y, indexing="xy")
+    h = 1.0 - bump * np.exp(-((X - L / 2) / (L / 8)) ** 2)
+    if Ny > 1:
+        h = h + 0.05 * np.cos(2 * np.pi * Y / L)
+    r = np.random.default_rng(seed)
+    ea = amp * np.cos(2 * np.pi * X / L) + (0.3 * amp * np.sin(2 * np.pi * Y / L) if Ny > 1 else 0)
+    eb = ea + 0.01 * amp * r.standard_normal(ea.shape)
+    return g, np.ascontiguousarray(h), np.ascontiguousarray(ea), np.ascontiguousarray(eb)
+
+
+CASES_2D = [(8, 4, 2 * math.pi), (64, 16, 2 * math.pi), (256, 24, 32.0), (1024, 24, 32.0)]
+
+
+@pytest.mark.parametrize("Nx,Nz,L", CASES_2D)
+def test_operator_parity_2d(wt, Nx, Nz, L):
+    g, h, ea, eb = curved(Nx, 1, Nz, L)
+    p = np.random.default_rng(1).standard_normal(g.shape)
+    ref = op.apply_A(g, op.Geometry(g, h, ea), op.Geometry(g, h, eb), p)
+    T = wt.Tank(Nx, 1, Nz, L, h)
+    got = T.apply_operator(ea, eb, p, wt.WT_FP64)
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-11 * scale
+    got32 = T.apply_operator(ea, eb, p, wt.WT_FP32)
+    assert np.abs(got32 - ref).max() <= 2e-4 * scale
+
+
+@pytest.mark.parametrize("Nx,Ny,Nz", [(8, 8, 4), (32, 32, 8), (64, 64, 16)])
+def test_operator_parity_3d(wt, Nx, Ny, Nz):
+    L = 2 * math.pi
+    g, h, ea, eb = curved(Nx, Ny, Nz, L)
+    p = np.random.default_rng(2).standard_normal(g.shape)
+    ref = op.apply_A(g, op.Geometry(g, h, ea), op.Geometry(g, h, eb), p)
+    T = wt.Tank(Nx, Ny, Nz, L, h)
+    got = T.apply_operator(ea, eb, p, wt.WT_FP64)
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-11 * scale
+    got32 = T.apply_operator(ea, eb, p, wt.WT_FP32)
+    assert np.abs(got32 - ref).max() <= 2e-4 * scale
+
+
+def test_levels_match_oracle_hierarchy(wt):
+    for (Nx, Ny, Nz) in [(1024, 1, 24), (64, 1, 16), (256, 256, 16), (2048, 1, 32)]:
+        T = wt.Tank(Nx, Ny, Nz, 1.0, np.ones((Ny, Nx)))
+        assert T.levels() == pmg.hierarchy(Nx, Ny, Nz, coarsest_max=64)
+
+
+@pytest.mark.parametrize("Nx,Ny,Nz", [(64, 1, 16), (256, 1, 24), (16, 16, 8)])
+def test_vcycle_parity(wt, Nx, Ny, Nz):
+    # same algorithm on both sides (block Jacobi with Nyquist split, omega 0.4,
+    # nu1 = nu2 = 2, injected boundary rows, coarsest <= 64 unknowns): the
+    # preconditioned vectors agree to rounding.
+    L = 2 * math.pi
+    g, h, ea, eb = curved(Nx, Ny, Nz, L)
+    r = np.random.default_rng(3).standard_normal(g.shape)
+    levels = pmg.build_levels(Nx, Ny, Nz, L, h, ea, eb, coarsest_max=64)
+    ref = pmg.vcycle(levels, 0, np.zeros(g.shape), r, 2, 2, "jacobi", 0.4, "inject")
+    T = wt.Tank(Nx, Ny, Nz, L, h)
+    got = T.precondition(ea, eb, r, wt.WT_FP64)
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-9 * scale
+    got32 = T.precondition(ea, eb, r, wt.WT_FP32)
+    assert np.abs(got32 - ref).max() <= 5e-3 * scale
+
+
+def manufactured_rhs():
+    Nx, Nz, L = 64, 16, 2 * math.pi
+    g = op.Grid(Nx, 1, Nz, L)
+    geo = op.Geometry(g, np.ones(Nx), np.zeros(Nx))
+    z = geo.z_nodes(g)
+    X = np.broadcast_to(g.x[None, None, :], g.shape)
+    ms = si.Manufactured(seed=0)
+    b = ms.laplacian(X, z)
+    b[0] = ms.p(X[0], z[0])
+    b[-1] = ms.dpdz(X[-1], z[-1])
+    return g, np.ascontiguousarray(b), ms.p(X, z)
+
+
+@pytest.mark.parametrize("mode,tol,bound", [(0, 1e-12, 1e-10), (1, 1e-12, 1e-9)])
+def test_manufactured_solve(wt, mode, tol, bound):
+    g, b, pe = manufactured_rhs()
+    T = wt.Tank(64, 1, 16, 2 * math.pi, np.ones((1, 64)), mode=mode, tol=tol)
+    z = np.zeros((1, 64))
+    p, info = T.poisson_solve(z, z, b)
+    assert info.rel_residual <= tol
+    assert np.abs(p - pe).max() <= bound * np.abs(pe).max()
+    geo = op.Geometry(g, np.ones(64), np.zeros(64))
+    r = b - op.apply_A(g, geo, geo, p)
+    assert np.linalg.norm(r) <= max(tol, 1e-13) * 10 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("Nx,Ny,Nz,L", [(1024, 1, 24, 32.0), (128, 1, 12, 8.0), (32, 32, 8, 2 * math.pi)])
+def test_curved_solve_residual_in_oracle_operator(wt, mode, Nx, Ny, Nz, L):
+    g, h, ea, eb = curved(Nx, Ny, Nz, L)
+    b = np.random.default_rng(4).standard_normal(g.shape)
+    T = wt.Tank(Nx, Ny, Nz, L, h, mode=mode, tol=1e-10, max_it=300)
+    p, info = T.poisson_solve(ea, eb, b)
+    assert info.rel_residual <= 1e-10
+    r = b - op.apply_A(g, op.Geometry(g, h, ea), op.Geometry(g, h, eb), p)
+    bound = 1e-10 if mode == 0 else 1e-9
+    assert np.linalg.norm(r) <= bound * np.linalg.norm(b) * 1.5
+
+
+def test_solve_matches_oracle_dense_lu(wt):
+    Nx, Nz, L = 32, 10, 2 * math.pi
+    g, h, ea, eb = curved(Nx, 1, Nz, L)
+    b = np.random.default_rng(5).standard_normal(g.shape)
+    lev = pmg.Level(Nx, 1, Nz, L, h, ea, eb)
+    ref = krylov.solve_dense(lev, b)
+    for mode, bound in ((0, 1e-9), (1, 1e-8)):
+        T = wt.Tank(Nx, 1, Nz, L, h, mode=mode, tol=1e-12)
+        p, info = T.poisson_solve(ea, eb, b)
+        assert np.abs(p - ref).max() <= bound * np.abs(ref).max()
+
+
+def test_zero_rhs_and_invalid_geometry(wt):
+    Nx, Nz, L = 32, 8, 2 * math.pi
+    h = np.ones((1, Nx))
+    T = wt.Tank(Nx, 1, Nz, L, h)
+    z = np.zeros((1, Nx))
+    p, info = T.poisson_solve(z, z, np.zeros(T.shape), p=np.ones(T.shape))
+    assert np.all(p == 0.0)
+    bad = np.full((1, Nx), -2.0)                 # d = h + eta <= 0
+    with pytest.raises(wt.WtError) as e:
+        T.apply_operator(bad, z, np.ones(T.shape))
+    assert e.value.code == wt.WT_EBREAK
+    # the tank stays usable after the error
+    T.apply_operator(z, z, np.ones(T.shape))
+
+
+def _oracle_state(g, tank_o, eta, u, w):
+    st = rk.State(g, eta, u, np.zeros_like(u), w)
+    return st
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_rk_stages_parity(wt, mode):
+    # five stages of a nonlinear wave over a bump: GPU vs oracle, both solving
+    # each Poisson problem to 1e-12
+    Nx, Nz, L = 64, 12, 2 * math.pi
+    x = np.arange(Nx) * L / Nx
+    h = (1.0 - 0.3 * np.exp(-((x - L / 2) / 1.0) ** 2))[None]
+    g = op.Grid(Nx, 1, Nz, L)
+    eta0 = si.stokes2_eta(x, 0.03, 1.0, 1.0)[None]
+    geo = op.Geometry(g, h, eta0)
+    u0, w0 = si.linear_velocity(x[None, None, :], geo.z_nodes(g), 0.03, 1.0, 1.0)
+    tank_o = rk.Tank(Nx, 1, Nz, L, h, tol=1e-13, coarsest_max=64)
+    st = rk.State(g, eta0, u0, np.zeros_like(u0), w0)
+    dt = 0.01
+    T = wt.Tank(Nx, 1, Nz, L, h, mode=mode, tol=1e-12)
+    T.set_state(np.ascontiguousarray(eta0), np.ascontiguousarray(u0), np.zeros_like(u0),
+                np.ascontiguousarray(w0))
+    for k in range(1, 6):
+        rk.stage(tank_o, st, k, dt)
+        T.rk_stage(k, dt)
+    eta, u, v, w, tm = T.get_state()
+    assert abs(tm - dt) < 1e-15
+    assert np.abs(eta - st.eta).max() <= 1e-10 * np.abs(st.eta).max()
+    assert np.abs(u - st.u).max() <= 1e-8 * np.abs(st.u).max()
+    assert np.abs(w - st.w).max() <= 1e-8 * np.abs(st.w).max()
+    # the projected velocity is discretely divergence-free in the oracle's operator
+    dv, bot = rk.divergence_residual(tank_o, rk.State(g, eta, u, v, w))
+    assert np.abs(dv).max() < 1e-7 and np.abs(bot).max() < 1e-9
+
+
+def test_airy_period_on_gpu(wt):
+    # linear model, k = 1, h = 1: eta returns to A cos x after one period
+    Nx, Nz, L = 64, 16, 2 * math.pi
+    T = wt.Tank(Nx, 1, Nz, L, np.ones((1, Nx)), mode=0, tol=1e-12, linear=1)
+    g = op.Grid(Nx, 1, Nz, L)
+    A = 0.005
+    eta0 = si.airy(g.x, None, A=A)[None]
+    geo = op.Geometry(g, np.ones(Nx), np.zeros(Nx))
+    _, u, w = si.airy(g.x[None, None, :], geo.z_nodes(g), A=A)
+    T.set_state(np.ascontiguousarray(eta0), np.ascontiguousarray(u), np.zeros_like(u),
+                np.ascontiguousarray(w))
+    Tp = 2 * math.pi / si.omega(1.0, 1.0)
+    T.step(Tp / 100, 100)
+    eta = T.get_state()[0]
+    assert np.abs(eta - eta0).max() / A < 2e-5
+    assert abs(eta.mean()) < 1e-12
