@@ -1,0 +1,365 @@
+#!/usr/bin/env python3
+"""Benchmark of the wave-tank hot path on GB300.
+
+Workload: the 2D nonlinear wave over a Gaussian bar (periodic x in [0, 32),
+Nx = 1024, Nz = 24, h = 1 - 0.5 exp(-((x-16)/2)^2), second-order Stokes wave
+with H/L = 0.04 and kh = 0.98 at the deep end, linear-theory velocity,
+dt = 0.5 dx / sqrt(g h_max), exponential filter on, Poisson tolerance 1e-10
+at every stage).  One step = one full five-stage low-storage Runge-Kutta step
+(five mixed-stage Poisson solves plus the free-surface and stage updates).
+
+Metric: RK4 DOF-updates/s = 5 stages x Nx x Ny x (Nz+1) / step time (the
+headline, mixed FP32/FP64 solver) with Poisson solves/s, and the same for the
+plain FP64 solver on the same GPU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (numpy float64, one thread) on a
+bounded sample of the same workload (one Runge-Kutta stage per step).
+"""
+
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import math
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import seeded_inputs as si  # noqa: E402
+
+METRIC = "RK4 DOF-updates/s (mixed FP32/FP64 p-MG Poisson solves at 1e-10 residual)"
+UNIT = "DOF-updates/s"
+STAGES = 5
+
+
+def workload():
+    p = si.nonlinear_2d_tank()
+    x = np.arange(p["Nx"]) * p["L"] / p["Nx"]
+    h = si.bump(x, p["L"], p["bump_A"], p["bump_w"])[None, :]
+    return p, x, np.ascontiguousarray(h)
+
+
+def config(p, extra=None):
+    c = {"workload": "2D nonlinear Stokes-2 wave over a Gaussian bar (Nx=1024, Nz=24, L=32, "
+                     "H/L=0.04, kh=0.98, CFL 0.5, filter on, tol 1e-10 per stage)",
+         "Nx": p["Nx"], "Ny": 1, "Nz": p["Nz"], "L": p["L"], "dt": p["dt"],
+         "dof_per_stage": p["Nx"] * (p["Nz"] + 1), "stages_per_step": STAGES,
+         "poisson_tol": 1e-10, "l2": "flushed between timed steps (256 MiB device write)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def initial_state(p, x, h, sigma):
+    eta = si.nonlinear_2d_initial(x, None, p)
+    d = h[0] + eta
+    z = sigma[:, None] * d[None, :] - h[0][None, :]
+    _, u, w = si.nonlinear_2d_initial(x[None, :], z, p)
+    M1 = p["Nz"] + 1
+    return (np.ascontiguousarray(eta[None, :]), np.ascontiguousarray(u.reshape(M1, 1, -1)),
+            np.zeros((M1, 1, p["Nx"])), np.ascontiguousarray(w.reshape(M1, 1, -1)))
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import paper_2406_00991_gb300 as w
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    p, x, h = workload()
+    T = w.Tank(p["Nx"], 1, p["Nz"], p["L"], h, mode=w.WT_MIXED, tol=1e-10, filter=1)
+    T.set_stream(stream.cuda_stream)
+    _, _, sigma = T.grid()
+    st0 = initial_state(p, x, h, sigma)
+    dof_step = STAGES * p["Nx"] * (p["Nz"] + 1)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed_steps(K, prof_mask=0):
+        """K steps, each timed by CUDA events on the tank's stream, L2 flushed before each."""
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(K)]
+        T.profile(prof_mask)
+        l0 = T.launches()
+        s0, i0 = T.stats()
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(K):
+            flush.zero_()
+            evs[k][0].record(stream)
+            T.step(p["dt"], 1)
+            evs[k][1].record(stream)
+        barrier()
+        wall = time.perf_counter() - t0
+        ms = [a.elapsed_time(b) for a, b in evs]
+        s1, i1 = T.stats()
+        return ms, wall, T.launches() - l0, (s1 - s0, i1 - i0)
+
+    # ---------------- mixed (headline)
+    T.set_state(*st0)
+    # the first warm-up step times every kernel class to find the dominant one
+    T.profile(0xFF)
+    T.step(p["dt"], 1)
+    cls_ms = []
+    for c in range(len(w.KERNEL_CLASSES)):
+        cls_ms.append(T.profile_read(c))
+    T.profile(0)
+    dom = int(np.argmax([c["ms"] for c in cls_ms]))
+    for _ in range(max(0, args.warmup - 1)):
+        T.step(p["dt"], 1)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ms, wall, launches, (solves, iters) = timed_steps(args.steps, prof_mask=1 << dom)
+    ck = clocks.stop()
+    kern = T.profile_read(dom)
+    T.profile(0)
+    step_ms = max_over_ranks(float(np.mean(ms)))
+    value = sum_over_ranks(dof_step) / (step_ms / 1e3)
+    solves_s = sum_over_ranks(STAGES) / (step_ms / 1e3)
+
+    # ---------------- end to end through the C ABI with pinned host buffers
+    host = [torch.from_numpy(a.copy()).pin_memory().numpy() for a in st0]
+    out_eta = torch.zeros(host[0].shape, dtype=torch.float64).pin_memory().numpy()
+    out_u = torch.zeros(host[1].shape, dtype=torch.float64).pin_memory().numpy()
+    out_w = torch.zeros(host[3].shape, dtype=torch.float64).pin_memory().numpy()
+    Ke = max(1, min(args.steps, 3))
+    barrier()
+    e2e_ms = []
+    for k in range(Ke):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        w.wt_set_state(T.handle, host[0], host[1], host[2], host[3], 0.0)
+        T.step(p["dt"], 1)
+        w.wt_get_state(T.handle, out_eta, out_u, None, out_w)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_step = max_over_ranks(float(np.mean(e2e_ms)))
+    bytes_io = 8 * (host[0].size + host[1].size + host[3].size)
+
+    # ---------------- plain FP64 solver on the same GPU
+    T.set_options(mode=w.WT_FP64)
+    T.set_state(*st0)
+    T.step(p["dt"], 1)
+    Kf = max(1, min(args.steps, 3))
+    ms64, _, _, (s64, it64) = timed_steps(Kf)
+    step64 = max_over_ranks(float(np.mean(ms64)))
+
+    if rank != 0:
+        return
+    hbm, peak_src = peaks()
+    achieved = kern["bytes"] / (kern["ms"] / 1e3) / 1e9 if kern["ms"] > 0 else 0.0
+    per_launch = kern["bytes"] / max(1, kern["launches"])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+        "config": config(p, {"parallelism": "replicas" if world > 1 else "single-gpu",
+                             "solver": "mixed: FP64 refinement, FP32 FGMRES(30) + p-MG V-cycle"}),
+        "solves_per_s": solves_s,
+        "krylov_iterations_per_solve": iters / max(1, solves),
+        "fp64": {"value": dof_step * world / (step64 / 1e3),
+                 "unit": UNIT, "ms_per_step": step64, "solves_per_s": STAGES * world / (step64 / 1e3),
+                 "krylov_iterations_per_solve": it64 / max(1, s64), "steps": Kf},
+        "mixed_over_fp64": step64 / step_ms,
+        "e2e": {"value": dof_step * world / (e2e_step / 1e3), "unit": UNIT,
+                "ms_per_step": e2e_step, "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io,
+                "note": "wt_set_state(host) + wt_step + wt_get_state(host), pinned buffers"},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": w.KERNEL_CLASSES[dom], "achieved": achieved,
+                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+                     "algorithmic_bytes_per_launch": per_launch,
+                     "avg_launch_us": kern["ms"] * 1e3 / max(1, kern["launches"]),
+                     "launches": kern["launches"]},
+        "kernel_share_first_warmup_step": {w.KERNEL_CLASSES[c]: round(cls_ms[c]["ms"], 3)
+                                           for c in range(len(cls_ms))},
+        "clocks": ck,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, x, h, budget_s=args.cpu_budget)
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ oracle (CPU)
+def oracle_tank(p, h):
+    from oracle import rk
+    return rk.Tank(p["Nx"], 1, p["Nz"], p["L"], h, tol=1e-10, coarsest_max=64, filter=True)
+
+
+def oracle_state(p, x, h):
+    from oracle import rk
+    from oracle import spectral as sp
+    sigma = sp.cgl_sigma(p["Nz"])
+    st = initial_state(p, x, h, sigma)
+    g = oracle_tank(p, h).grid
+    return rk.State(g, st[0], st[1], st[2], st[3])
+
+
+def cpu_baseline(p, x, h, budget_s=15.0):
+    """Oracle Runge-Kutta stages of the same workload until ~budget_s of CPU work."""
+    from oracle import rk
+    tank = oracle_tank(p, h)
+    st = oracle_state(p, x, h)
+    n = 0
+    t0 = time.perf_counter()
+    while n < STAGES:
+        rk.stage(tank, st, n + 1, p["dt"])
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    dof = p["Nx"] * (p["Nz"] + 1)
+    return {"value": n * dof / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d Runge-Kutta stage(s) of the first step (%.1f s, numpy float64, one thread)"
+                      % (n, el)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import rk
+    p, x, h = workload()
+    tank = oracle_tank(p, h)
+    st = oracle_state(p, x, h)
+    dof = p["Nx"] * (p["Nz"] + 1)
+    k = 0
+    for _ in range(args.warmup):
+        rk.stage(tank, st, k % STAGES + 1, p["dt"])
+        k += 1
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        rk.stage(tank, st, k % STAGES + 1, p["dt"])
+        times.append(time.perf_counter() - t0)
+        k += 1
+    ms = float(np.mean(times)) * 1e3
+    value = dof / (ms / 1e3)
+    sample = "one Runge-Kutta stage per step (a fifth of a full step), numpy float64, one thread"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": config(p, {"step": "one RK stage"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

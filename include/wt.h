@@ -46,7 +46,7 @@ enum wt_status {
   WT_OK = 0,
   WT_EINVAL = 1,    /* invalid argument (sizes, pointers, options)            */
   WT_ENOMEM = 2,    /* device or host allocation failed                       */
-  WT_ENOCONV = 3,   /* solve stopped at max_it / max_ir above its tolerance;
+  WT_ENOCONV = 3,   /* solve stopped at max_it above its tolerance;       
                        the best iterate is still written                      */
   WT_EBREAK = 4,    /* water depth d = h + eta <= 0 or a non-finite value:
                        the sigma map is invalid (e.g. a breaking wave)        */
@@ -61,18 +61,16 @@ typedef struct wt_tank wt_tank;
 
 /* Solver and model options (wt_default_options fills the defaults shown). */
 typedef struct wt_options {
-  int mode;          /* WT_FP64: FP64 GMRES + FP64 V-cycle.  WT_MIXED: FP64
-                        iterative refinement around FP32 FGMRES + FP32
-                        V-cycle (default WT_MIXED)                           */
+  int mode;          /* WT_FP64: FP64 flexible GMRES + FP64 V-cycle.
+                        WT_MIXED: FP64 flexible GMRES (FP64 residuals and
+                        Krylov basis) whose preconditioner is the FP32
+                        V-cycle, so every iteration refines the FP64 iterate
+                        with an FP32 correction (default WT_MIXED)           */
   double tol;        /* relative residual ||b - A p||_2 / ||b||_2 (1e-10)   */
   int restart;       /* GMRES restart length m (30)                          */
   int nu1, nu2;      /* pre- / post-smoothing sweeps (2, 2)                  */
   double omega;      /* block-Jacobi damping (0.4)                           */
-  int max_it;        /* Krylov iterations per solve (FP64) or per refinement
-                        step (mixed) (200)                                   */
-  int max_ir;        /* refinement steps in WT_MIXED (30)                    */
-  double inner_tol;  /* relative reduction asked of each FP32 inner solve
-                        in WT_MIXED (1e-4)                                   */
+  int max_it;        /* Krylov iterations per solve (200)                    */
   int filter;        /* exponential cut-off filter every stage (0)           */
   int linear;        /* linearised model, Sec. 5.3 (0)                       */
   int coarsest_max;  /* a level with at most this many unknowns is solved
@@ -83,8 +81,7 @@ typedef struct wt_options {
 } wt_options;
 
 typedef struct wt_solve_info {
-  int iterations;        /* Krylov iterations (all refinement steps)         */
-  int ir_steps;          /* FP64 refinement steps (WT_MIXED), else 0         */
+  int iterations;        /* Krylov iterations (= preconditioner applications) */
   double rel_residual;   /* final ||b - A p||_2 / ||b||_2, FP64 operator     */
   int status;            /* same code as the call's return value             */
 } wt_solve_info;

@@ -28,14 +28,14 @@ STATUS_NAMES = {0: "WT_OK", 1: "WT_EINVAL", 2: "WT_ENOMEM", 3: "WT_ENOCONV", 4: 
 class wt_options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("tol", ctypes.c_double), ("restart", ctypes.c_int),
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
-                ("max_it", ctypes.c_int), ("max_ir", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("max_it", ctypes.c_int),
                 ("filter", ctypes.c_int), ("linear", ctypes.c_int), ("coarsest_max", ctypes.c_int),
                 ("bc_transfer", ctypes.c_int)]
 
 
 class wt_solve_info(ctypes.Structure):
-    _fields_ = [("iterations", ctypes.c_int), ("ir_steps", ctypes.c_int),
-                ("rel_residual", ctypes.c_double), ("status", ctypes.c_int)]
+    _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("status", ctypes.c_int)]
 
 
 def _load():

@@ -268,8 +268,7 @@ int check_options(const wt_options& o) {
   if (o.nu1 < 0 || o.nu1 > 8 || o.nu2 < 0 || o.nu2 > 8 || o.nu1 + o.nu2 == 0)
     return fail(WT_EINVAL, "nu1, nu2 must be in [0, 8], not both 0");
   if (!(o.omega > 0) || !(o.omega < 2)) return fail(WT_EINVAL, "omega must be in (0, 2)");
-  if (o.max_it < 1 || o.max_ir < 1) return fail(WT_EINVAL, "max_it and max_ir must be >= 1");
-  if (!(o.inner_tol > 0) || !(o.inner_tol < 1)) return fail(WT_EINVAL, "inner_tol must be in (0, 1)");
+  if (o.max_it < 1) return fail(WT_EINVAL, "max_it must be >= 1");
   if (o.coarsest_max < 1 || o.coarsest_max > 128) return fail(WT_EINVAL, "coarsest_max must be in [1, 128]");
   if ((o.filter != 0 && o.filter != 1) || (o.linear != 0 && o.linear != 1) ||
       (o.bc_transfer != 0 && o.bc_transfer != 1))
@@ -419,8 +418,6 @@ int wt_default_options(wt_options* o) {
   o->nu2 = 2;
   o->omega = 0.4;
   o->max_it = 200;
-  o->max_ir = 30;
-  o->inner_tol = 1e-4;
   o->filter = 0;
   o->linear = 0;
   o->coarsest_max = 64;

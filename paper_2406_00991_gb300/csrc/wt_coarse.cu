@@ -1,8 +1,8 @@
 // Coarsest p-multigrid level: direct solve u = A^{-1} f (Algorithm 1, p = 1),
 // in FP64 for both solver modes.  The dense A_{a,b} of the level is assembled
-// on the device entry by entry from the composite operator, then factored by
-// LU with partial pivoting in shared memory by one CTA; every V-cycle then
-// runs one forward / backward substitution on one warp.
+// on the device entry by entry from the composite operator and inverted in
+// shared memory by one CTA (Gauss-Jordan with partial pivoting, once per
+// geometry); every V-cycle then applies the inverse with one thread per row.
 //
 // Entry of A_{a,b} for row i = (m, y, x) and column j = (m', y', x'), with
 // dense per-level D_x, D_y (zero diagonal) and D (d/dsigma):
@@ -83,7 +83,9 @@ __global__ void __launch_bounds__(256) k_coarse_factor(LevelView<double> L, cons
     A[i * ld + j] = v;
   }
   __syncthreads();
-  // LU with partial pivoting, in place
+  // in-place Gauss-Jordan inversion with row pivoting (the pivot column is
+  // overwritten by the inverse's column; row swaps become column swaps at the end)
+  __shared__ int perm[128];
   for (int k = 0; k < n; ++k) {
     if (threadIdx.x < 32) {
       double best = -1.0;
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(256) k_coarse_factor(LevelView<double> L, cons
       }
       if (threadIdx.x == 0) {
         spiv = bi;
-        piv[k] = bi;
+        perm[k] = bi;
         if (!(best > 0.0) || !isfinite(best)) atomicOr(flag, 2);
       }
     }
@@ -114,49 +116,55 @@ __global__ void __launch_bounds__(256) k_coarse_factor(LevelView<double> L, cons
       __syncthreads();
     }
     const double inv = 1.0 / A[k * ld + k];
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[i * ld + k] *= inv;
     __syncthreads();
-    const int rem = n - k - 1;
-    for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
-      const int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
-      A[i * ld + j] -= A[i * ld + k] * A[k * ld + j];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) A[k * ld + j] = (j == k ? 1.0 : A[k * ld + j]) * inv;
+    __syncthreads();
+    // eliminate column k from every other row; column k of those rows becomes -f * inv
+    for (int idx = threadIdx.x; idx < (n - 1) * n; idx += blockDim.x) {
+      int i = idx / n;
+      const int j = idx - i * n;
+      if (i >= k) ++i;
+      const double f = A[i * ld + k];
+      if (j != k) A[i * ld + j] -= f * A[k * ld + j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (i != k) A[i * ld + k] = -A[i * ld + k] * A[k * ld + k];
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double t0 = A[i * ld + k];
+        A[i * ld + k] = A[i * ld + p];
+        A[i * ld + p] = t0;
+      }
     }
     __syncthreads();
   }
+  // store the inverse transposed: LUout[j * n + i] = Ainv[i][j] (coalesced solve)
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const int i = idx / n, j = idx - i * n;
-    LUout[idx] = A[i * ld + j];
+    LUout[j * n + i] = A[i * ld + j];
   }
 }
 
+// x = A^{-1} f with the stored (transposed) inverse: one thread per row.
 template <typename T>
-__global__ void __launch_bounds__(32) k_coarse_solve(int n, const double* __restrict__ LU,
-                                                    const int* __restrict__ piv,
-                                                    const T* __restrict__ f, T* __restrict__ x) {
+__global__ void __launch_bounds__(128) k_coarse_solve(int n, const double* __restrict__ AinvT,
+                                                     const int* __restrict__ piv,
+                                                     const T* __restrict__ f, T* __restrict__ x) {
   __shared__ double b[128];
-  const int lane = threadIdx.x;
-  for (int i = lane; i < n; i += 32) b[i] = (double)f[i];
-  __syncwarp();
-  if (lane == 0) {
-    for (int k = 0; k < n; ++k) {
-      const int p = piv[k];
-      if (p != k) { const double t0 = b[k]; b[k] = b[p]; b[p] = t0; }
-    }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) b[i] = (double)f[i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double acc = 0.0;
+#pragma unroll 8
+    for (int j = 0; j < n; ++j) acc += AinvT[j * n + i] * b[j];
+    x[i] = (T)acc;
   }
-  __syncwarp();
-  for (int k = 0; k < n; ++k) {          // L y = P f (unit lower)
-    const double bk = b[k];
-    for (int i = k + 1 + lane; i < n; i += 32) b[i] -= LU[i * n + k] * bk;
-    __syncwarp();
-  }
-  for (int k = n - 1; k >= 0; --k) {     // U x = y
-    if (lane == 0) b[k] /= LU[k * n + k];
-    __syncwarp();
-    const double bk = b[k];
-    for (int i = lane; i < k; i += 32) b[i] -= LU[i * n + k] * bk;
-    __syncwarp();
-  }
-  for (int i = lane; i < n; i += 32) x[i] = (T)b[i];
+  (void)piv;
 }
 
 cudaError_t launch_coarse_factor(const LevelView<double>& L, const double* Dx, const double* Dy,
@@ -178,7 +186,7 @@ cudaError_t launch_coarse_factor(const LevelView<double>& L, const double* Dx, c
 template <typename T>
 cudaError_t launch_coarse_solve(int n, const double* LU, const int* piv, const T* f, T* x,
                                 cudaStream_t s) {
-  k_coarse_solve<T><<<1, 32, 0, s>>>(n, LU, piv, f, x);
+  k_coarse_solve<T><<<1, 128, 0, s>>>(n, LU, piv, f, x);
   return cudaGetLastError();
 }
 

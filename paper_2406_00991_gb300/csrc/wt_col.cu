@@ -1,6 +1,5 @@
-// Column (sigma-direction) kernels: one thread owns one vertical column and
-// keeps it in registers; the Chebyshev matrices sit in shared memory padded
-// to MAXM x MAXM with zeros, so every loop has compile-time bounds.
+// Column (sigma-direction) kernels on shared-memory tiles of 16 columns x all
+// sigma rows (see TC / RG below).
 //
 //  k_op_cols      the sigma part of A_{a,b} (Eq. 1_chain, poissonp, bcpdneu):
 //                 P_s = D p, G = (P_x + sx_b P_s, P_y + sy_b P_s, Z_b P_s),
@@ -17,192 +16,176 @@
 
 namespace wt {
 
-template <typename T, int MAXM>
-__device__ __forceinline__ void load_padded(T* sM, const T* __restrict__ M, int M1) {
-  for (int i = threadIdx.x; i < MAXM * MAXM; i += blockDim.x) {
-    const int r = i / MAXM, c = i - r * MAXM;
-    sM[i] = (r < M1 && c < M1) ? M[r * M1 + c] : T(0);
-  }
-}
+// Column kernels work on tiles of TC consecutive columns x all M1 sigma rows
+// held in shared memory ([row][column-in-tile]); thread (rg, tc) of a
+// 128-thread CTA owns column tc of the tile and the rows rg, rg+8, rg+16, ...
+// so every sigma contraction has M1 x TC independent outputs per CTA and the
+// global loads of a warp cover 16 consecutive columns.
+constexpr int TC = 16;
+constexpr int RG = 8;                 // row groups: 128 threads = RG x TC
 
-// Every thread keeps the input column of a contraction in registers (static
-// indices, inner loop unrolled) and walks the output rows with a rolled loop;
-// intermediate columns go through shared memory laid out [row][thread].
-template <typename T, int MAXM, int DIM>
+template <typename T, int DIM>
 __global__ void __launch_bounds__(128) k_op_cols(LevelView<T> L, const T* __restrict__ p,
                                                  const T* __restrict__ Px, const T* __restrict__ Py,
                                                  T* __restrict__ Gx, T* __restrict__ Gy,
                                                  T* __restrict__ part) {
-  __shared__ T sD[MAXM * MAXM];
-  __shared__ T ssig[MAXM];
-  __shared__ T sPs[MAXM * 128];
+  extern __shared__ __align__(16) unsigned char smraw[];
   const int M1 = L.M1;
-  load_padded<T, MAXM>(sD, L.D, M1);
-  for (int i = threadIdx.x; i < MAXM; i += blockDim.x) ssig[i] = i < M1 ? L.sigma[i] : T(0);
-  __syncthreads();
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= L.ncols) return;
-  const int t = threadIdx.x;
+  T* sD = reinterpret_cast<T*>(smraw);            // M1*M1
+  T* sP = sD + M1 * M1;                          // p tile
+  T* sPs = sP + M1 * TC;                         // D p
+  T* sGx = sPs + M1 * TC;                        // G_x (Px on entry)
+  T* sGy = sGx + M1 * TC;                        // G_y (Py on entry), 3D only
+  const int tc = threadIdx.x % TC, rg = threadIdx.x / TC;
   const long nc = L.ncols;
+  const long c0 = (long)blockIdx.x * TC;
+  const long c = c0 + tc;
+  const bool live = c < nc;
+  for (int i = threadIdx.x; i < M1 * M1; i += blockDim.x) sD[i] = L.D[i];
+  for (int i = threadIdx.x; i < M1 * TC; i += blockDim.x) {
+    const int m = i / TC, cc = i % TC;
+    const long col = c0 + cc;
+    const bool ok = col < nc;
+    sP[i] = ok ? p[m * nc + col] : T(0);
+    sGx[i] = ok ? Px[m * nc + col] : T(0);
+    if constexpr (DIM == 3) sGy[i] = ok ? Py[m * nc + col] : T(0);
+  }
+  __syncthreads();
+  // P_s = D p
+  for (int m = rg; m < M1; m += RG) {
+    T acc = 0;
+    for (int k = 0; k < M1; ++k) acc += sD[m * M1 + k] * sP[k * TC + tc];
+    sPs[m * TC + tc] = acc;
+  }
+  __syncthreads();
   const T* meta = L.meta;
-  T p0;
-  {
-    T v[MAXM];
-#pragma unroll
-    for (int k = 0; k < MAXM; ++k) v[k] = (k < M1) ? p[k * nc + c] : T(0);
-    p0 = v[0];
-#pragma unroll 1
-    for (int m = 0; m < M1; ++m) {
-      T acc = 0;
-#pragma unroll
-      for (int k = 0; k < MAXM; ++k) acc += sD[m * MAXM + k] * v[k];
-      sPs[m * 128 + t] = acc;                        // P_s = D p
-    }
-  }
-  const T AXb = meta[M_AXb * nc + c], BXb = meta[M_BXb * nc + c];
-  const T AXa = meta[M_AXa * nc + c], BXa = meta[M_BXa * nc + c];
-  const T Za = meta[M_Za * nc + c], Zb = meta[M_Zb * nc + c];
-  const T HX = meta[M_HX * nc + c];
-  T ps[MAXM], gx[MAXM];
-#pragma unroll
-  for (int k = 0; k < MAXM; ++k) {
-    if (k < M1) {
-      ps[k] = sPs[k * 128 + t];
-      gx[k] = Px[k * nc + c] + (AXb - ssig[k] * BXb) * ps[k];   // G_x
-      Gx[k * nc + c] = gx[k];
-    } else {
-      ps[k] = T(0);
-      gx[k] = T(0);
-    }
-  }
-  T gy[DIM == 3 ? MAXM : 1];
-  T AYa = 0, BYa = 0, HY = 0;
+  const long cm = live ? c : 0;
+  const T AXb = meta[M_AXb * nc + cm], BXb = meta[M_BXb * nc + cm];
+  const T AXa = meta[M_AXa * nc + cm], BXa = meta[M_BXa * nc + cm];
+  const T Za = meta[M_Za * nc + cm], Zb = meta[M_Zb * nc + cm];
+  const T HX = meta[M_HX * nc + cm];
+  T AYa = 0, BYa = 0, AYb = 0, BYb = 0, HY = 0;
   if constexpr (DIM == 3) {
-    const T AYb = meta[M_AYb * nc + c], BYb = meta[M_BYb * nc + c];
-    AYa = meta[M_AYa * nc + c];
-    BYa = meta[M_BYa * nc + c];
-    HY = meta[M_HY * nc + c];
-#pragma unroll
-    for (int k = 0; k < MAXM; ++k) {
-      if (k < M1) {
-        gy[k] = Py[k * nc + c] + (AYb - ssig[k] * BYb) * ps[k];  // G_y
-        Gy[k * nc + c] = gy[k];
-      } else {
-        gy[k] = T(0);
-      }
+    AYa = meta[M_AYa * nc + cm]; BYa = meta[M_BYa * nc + cm];
+    AYb = meta[M_AYb * nc + cm]; BYb = meta[M_BYb * nc + cm];
+    HY = meta[M_HY * nc + cm];
+  }
+  // G = (P_x + sx_b P_s, P_y + sy_b P_s, .)
+  for (int m = rg; m < M1; m += RG) {
+    const T s = L.sigma[m];
+    const T ps = sPs[m * TC + tc];
+    const T gx = sGx[m * TC + tc] + (AXb - s * BXb) * ps;
+    sGx[m * TC + tc] = gx;
+    if (live) Gx[m * nc + c] = gx;
+    if constexpr (DIM == 3) {
+      const T gy = sGy[m * TC + tc] + (AYb - s * BYb) * ps;
+      sGy[m * TC + tc] = gy;
+      if (live) Gy[m * nc + c] = gy;
     }
   }
+  __syncthreads();
   const T ZZ = Za * Zb;
-  part[c] = p0;                                                  // surface row
-  {
-    // bottom row n . Grad_b p; indexed through shared / global memory so that
-    // the register arrays keep static indices only
-    const int mb = M1 - 1;
-    const T psb = sPs[mb * 128 + t];
-    const T sb = ssig[mb];
-    T bot = HX * (Px[mb * nc + c] + (AXb - sb * BXb) * psb) + Zb * psb;
-    if constexpr (DIM == 3)
-      bot += HY * (Py[mb * nc + c] + (meta[M_AYb * nc + c] - sb * meta[M_BYb * nc + c]) * psb);
-    part[mb * nc + c] = bot;                                     // bottom row
-  }
-#pragma unroll 1
-  for (int m = 1; m < M1 - 1; ++m) {
-    T q = 0, s = 0, qy = 0;
-#pragma unroll
-    for (int k = 0; k < MAXM; ++k) {
-      const T d = sD[m * MAXM + k];
-      q += d * gx[k];
-      s += d * ps[k];
-      if constexpr (DIM == 3) qy += d * gy[k];
+  for (int m = rg; m < M1; m += RG) {
+    T out;
+    if (m == 0) {
+      out = sP[tc];                                         // surface row: p
+    } else if (m == M1 - 1) {                               // bottom row: n . Grad_b p
+      out = HX * sGx[m * TC + tc] + Zb * sPs[m * TC + tc];
+      if constexpr (DIM == 3) out += HY * sGy[m * TC + tc];
+    } else {
+      T q = 0, sum = 0, qy = 0;
+      for (int k = 0; k < M1; ++k) {
+        const T d = sD[m * M1 + k];
+        q += d * sGx[k * TC + tc];
+        sum += d * sPs[k * TC + tc];
+        if constexpr (DIM == 3) qy += d * sGy[k * TC + tc];
+      }
+      const T s = L.sigma[m];
+      out = (AXa - s * BXa) * q + ZZ * sum;
+      if constexpr (DIM == 3) out += (AYa - s * BYa) * qy;
     }
-    T out = (AXa - ssig[m] * BXa) * q + ZZ * s;
-    if constexpr (DIM == 3) out += (AYa - ssig[m] * BYa) * qy;
-    part[m * nc + c] = out;
+    if (live) part[m * nc + c] = out;
   }
 }
 
-template <typename T, int MAXM, int DIM>
+template <typename T, int DIM>
 __global__ void __launch_bounds__(128) k_smooth_cols(LevelView<T> L, const T* __restrict__ r,
                                                      const T* __restrict__ rhoX,
                                                      const T* __restrict__ rhoY,
                                                      const T* __restrict__ rhoXY,
-                                                     const T* __restrict__ Binv, int nclass,
+                                                     const T* __restrict__ Binv,
                                                      T* __restrict__ x, T omega, int first) {
-  __shared__ T sE[MAXM * 128];
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= L.ncols) return;
-  const int t = threadIdx.x;
-  const int M1 = L.M1;
-  const long nc = L.ncols;
-  const int jx = c % L.Nx, jy = c / L.Nx;
-  const T sx = (jx & 1) ? T(-1) : T(1);
-  const T sy = (jy & 1) ? T(-1) : T(1);
-  const long blk = (long)M1 * M1;
-  // residual split by Nyquist class: 0 regular, 1 x-Nyquist, 2 y-Nyquist, 3 both
+  extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int NC = DIM == 2 ? 2 : 4;
-#pragma unroll 1
-  for (int cls = 0; cls < NC; ++cls) {
-    T v[MAXM];
-#pragma unroll
-    for (int k = 0; k < MAXM; ++k) {
-      T val = 0;
-      if (k < M1) {
-        T rNx = 0, rNy = 0, rNN = 0;
-        if constexpr (DIM == 2) {
-          if (rhoX) rNx = rhoX[k] * sx;
-        } else {
-          const T cxy = rhoXY ? rhoXY[k] : T(0);
-          rNN = cxy * sx * sy;
-          if (rhoX) rNx = (rhoX[k * L.Ny + jy] - cxy * sy) * sx;
-          if (rhoY) rNy = (rhoY[k * L.Nx + jx] - cxy * sx) * sy;
-        }
-        if (cls == 0) val = r[k * nc + c] - rNx - rNy - rNN;
-        else if (cls == 1) val = rNx;
-        else if (cls == 2) val = rNy;
-        else val = rNN;
+  const int M1 = L.M1;
+  T* sR = reinterpret_cast<T*>(smraw);            // [NC][M1][TC] residual parts
+  const int tc = threadIdx.x % TC, rg = threadIdx.x / TC;
+  const long nc = L.ncols;
+  const long c0 = (long)blockIdx.x * TC;
+  for (int i = threadIdx.x; i < M1 * TC; i += blockDim.x) {
+    const int m = i / TC, cc = i % TC;
+    const long col = c0 + cc;
+    T rr = 0, rNx = 0, rNy = 0, rNN = 0;
+    if (col < nc) {
+      rr = r[m * nc + col];
+      const int jx = (int)(col % L.Nx), jy = (int)(col / L.Nx);
+      const T sx = (jx & 1) ? T(-1) : T(1), sy = (jy & 1) ? T(-1) : T(1);
+      if constexpr (DIM == 2) {
+        if (rhoX) rNx = rhoX[m] * sx;
+      } else {
+        const T cxy = rhoXY ? rhoXY[m] : T(0);
+        rNN = cxy * sx * sy;
+        if (rhoX) rNx = (rhoX[m * L.Ny + jy] - cxy * sy) * sx;
+        if (rhoY) rNy = (rhoY[m * L.Nx + jx] - cxy * sx) * sy;
       }
-      v[k] = val;
     }
-    const T* B = Binv + cls * blk * nc + c;
-#pragma unroll 1
-    for (int m = 0; m < M1; ++m) {
-      T e = 0;
-      const T* Bm = B + (long)m * M1 * nc;
+    sR[(0 * M1 + m) * TC + cc] = rr - rNx - rNy - rNN;
+    sR[(1 * M1 + m) * TC + cc] = rNx;
+    if constexpr (DIM == 3) {
+      sR[(2 * M1 + m) * TC + cc] = rNy;
+      sR[(3 * M1 + m) * TC + cc] = rNN;
+    }
+  }
+  __syncthreads();
+  const long c = c0 + tc;
+  if (c >= nc) return;
+  const long blk = (long)M1 * M1;
+  for (int m = rg; m < M1; m += RG) {
+    T e = 0;
 #pragma unroll
-      for (int k = 0; k < MAXM; ++k)
-        if (k < M1) e += Bm[(long)k * nc] * v[k];
-      sE[m * 128 + t] = (cls == 0 ? T(0) : sE[m * 128 + t]) + e;
+    for (int cls = 0; cls < NC; ++cls) {
+      const T* B = Binv + (cls * blk + (long)m * M1) * nc + c;
+      const T* R = sR + cls * M1 * TC + tc;
+#pragma unroll 5
+      for (int k = 0; k < M1; ++k) e += B[(long)k * nc] * R[k * TC];
     }
-  }
-#pragma unroll 1
-  for (int m = 0; m < M1; ++m) {
     const T xo = first ? T(0) : x[m * nc + c];
-    x[m * nc + c] = xo + omega * sE[m * 128 + t];
+    x[m * nc + c] = xo + omega * e;
   }
-  (void)nclass;
 }
 
-template <typename T, int MAXM>
+template <typename T>
 __global__ void __launch_bounds__(128) k_col_matrix(const T* __restrict__ M, int Mo, int Mi,
                                                     const T* __restrict__ in, T* __restrict__ out,
                                                     int ncols, int accumulate) {
-  __shared__ T sM[MAXM * MAXM];
-  for (int i = threadIdx.x; i < MAXM * MAXM; i += blockDim.x) {
-    const int r = i / MAXM, k = i - r * MAXM;
-    sM[i] = (r < Mo && k < Mi) ? M[r * Mi + k] : T(0);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sM = reinterpret_cast<T*>(smraw);            // Mo*Mi
+  T* sIn = sM + Mo * Mi;                          // [Mi][TC]
+  const int tc = threadIdx.x % TC, rg = threadIdx.x / TC;
+  const long nc = ncols;
+  const long c0 = (long)blockIdx.x * TC;
+  for (int i = threadIdx.x; i < Mo * Mi; i += blockDim.x) sM[i] = M[i];
+  for (int i = threadIdx.x; i < Mi * TC; i += blockDim.x) {
+    const int k = i / TC, cc = i % TC;
+    const long col = c0 + cc;
+    sIn[i] = col < nc ? in[k * nc + col] : T(0);
   }
   __syncthreads();
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncols) return;
-  const long nc = ncols;
-  T v[MAXM];
-#pragma unroll
-  for (int k = 0; k < MAXM; ++k) v[k] = (k < Mi) ? in[k * nc + c] : T(0);
-#pragma unroll 1
-  for (int m = 0; m < Mo; ++m) {
+  const long c = c0 + tc;
+  if (c >= nc) return;
+  for (int m = rg; m < Mo; m += RG) {
     T acc = 0;
-#pragma unroll
-    for (int k = 0; k < MAXM; ++k) acc += sM[m * MAXM + k] * v[k];
+    for (int k = 0; k < Mi; ++k) acc += sM[m * Mi + k] * sIn[k * TC + tc];
     if (accumulate) acc += out[m * nc + c];
     out[m * nc + c] = acc;
   }
@@ -305,22 +288,25 @@ __global__ void __launch_bounds__(128) k_block_inverse(LevelView<T> L, T* __rest
 // ------------------------------------------------------------------ launchers
 static inline int grid_for(long n, int bs) { return (int)std::max<long>(1, (n + bs - 1) / bs); }
 
-#define WT_MAXM_DISPATCH(M1, CALL)              \
-  do {                                          \
-    if ((M1) <= 9) { constexpr int MM = 9; CALL; } \
-    else if ((M1) <= 17) { constexpr int MM = 17; CALL; } \
-    else if ((M1) <= 25) { constexpr int MM = 25; CALL; } \
-    else { constexpr int MM = 33; CALL; }       \
-  } while (0)
+template <typename T>
+static cudaError_t set_smem(const void* fn, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
 
 template <typename T>
 cudaError_t launch_op_cols(const LevelView<T>& L, const T* p, const T* Px, const T* Py, T* Gx,
                            T* Gy, T* part, cudaStream_t s) {
-  const int g = grid_for(L.ncols, 128);
+  const int g = grid_for(L.ncols, TC);
+  const size_t smem = sizeof(T) * ((size_t)L.M1 * L.M1 + 4 * (size_t)L.M1 * TC);
   if (L.Ny == 1) {
-    WT_MAXM_DISPATCH(L.M1, (k_op_cols<T, MM, 2><<<g, 128, 0, s>>>(L, p, Px, Py, Gx, Gy, part)));
+    cudaError_t e = set_smem<T>((const void*)k_op_cols<T, 2>, smem);
+    if (e != cudaSuccess) return e;
+    k_op_cols<T, 2><<<g, 128, smem, s>>>(L, p, Px, Py, Gx, Gy, part);
   } else {
-    WT_MAXM_DISPATCH(L.M1, (k_op_cols<T, MM, 3><<<g, 128, 0, s>>>(L, p, Px, Py, Gx, Gy, part)));
+    cudaError_t e = set_smem<T>((const void*)k_op_cols<T, 3>, smem);
+    if (e != cudaSuccess) return e;
+    k_op_cols<T, 3><<<g, 128, smem, s>>>(L, p, Px, Py, Gx, Gy, part);
   }
   return cudaGetLastError();
 }
@@ -329,23 +315,21 @@ template <typename T>
 cudaError_t launch_smooth_cols(const LevelView<T>& L, const T* r, const T* rhoX, const T* rhoY,
                                const T* rhoXY, const T* Binv, int nclass, T* x, T omega, int first,
                                cudaStream_t s) {
-  const int g = grid_for(L.ncols, 128);
-  if (L.Ny == 1) {
-    WT_MAXM_DISPATCH(L.M1, (k_smooth_cols<T, MM, 2><<<g, 128, 0, s>>>(L, r, rhoX, rhoY, rhoXY,
-                                                                        Binv, nclass, x, omega, first)));
-  } else {
-    WT_MAXM_DISPATCH(L.M1, (k_smooth_cols<T, MM, 3><<<g, 128, 0, s>>>(L, r, rhoX, rhoY, rhoXY,
-                                                                        Binv, nclass, x, omega, first)));
-  }
+  const int g = grid_for(L.ncols, TC);
+  const size_t smem = sizeof(T) * (size_t)nclass * L.M1 * TC;
+  if (L.Ny == 1)
+    k_smooth_cols<T, 2><<<g, 128, smem, s>>>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
+  else
+    k_smooth_cols<T, 3><<<g, 128, smem, s>>>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_col_matrix(const T* M, int Mo, int Mi, const T* in, T* out, int ncols,
                               int accumulate, cudaStream_t s) {
-  const int g = grid_for(ncols, 128);
-  const int mm = std::max(Mo, Mi);
-  WT_MAXM_DISPATCH(mm, (k_col_matrix<T, MM><<<g, 128, 0, s>>>(M, Mo, Mi, in, out, ncols, accumulate)));
+  const int g = grid_for(ncols, TC);
+  const size_t smem = sizeof(T) * ((size_t)Mo * Mi + (size_t)Mi * TC);
+  k_col_matrix<T><<<g, 128, smem, s>>>(M, Mo, Mi, in, out, ncols, accumulate);
   return cudaGetLastError();
 }
 

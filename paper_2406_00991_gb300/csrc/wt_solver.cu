@@ -269,11 +269,35 @@ template <typename T> static T* Zbuf(wt_tank& t);
 template <> double* Zbuf<double>(wt_tank& t) { return t.Z64; }
 template <> float* Zbuf<float>(wt_tank& t) { return t.Z32; }
 
+// Preconditioner z = M^{-1} v: one V-cycle in the precision of the Krylov
+// vectors, or (pre32 with T = double) an FP32 V-cycle on the rounded vector
+// with the correction widened back to FP64.
+template <typename T>
+static void precondition(wt_tank& t, const T* v, T* z, bool pre32);
+template <>
+void precondition<float>(wt_tank& t, const float* v, float* z, bool) {
+  vcycle<float>(t, 0, v, z);
+}
+template <>
+void precondition<double>(wt_tank& t, const double* v, double* z, bool pre32) {
+  if (!pre32) {
+    vcycle<double>(t, 0, v, z);
+    return;
+  }
+  const long n = t.n;
+  WT_LAUNCH(t, K_KRYLOV, 12.0 * n, 0.0, (launch_convert<double, float>(v, t.b32, n, nullptr, 0, t.s)));
+  vcycle<float>(t, 0, t.b32, t.e32);
+  WT_LAUNCH(t, K_KRYLOV, 12.0 * n, 0.0, (launch_convert<float, double>(t.e32, z, n, nullptr, 0, t.s)));
+}
+
 // Right-preconditioned flexible GMRES(m) on the finest level of precision T:
 // x is the initial guess and the result; returns the last true relative
-// residual ||b - A x|| / bnorm computed in precision T.
+// residual ||b - A x|| / bnorm computed in precision T.  With pre32 the
+// preconditioner is the FP32 V-cycle: every Arnoldi step then refines the
+// FP64 iterate with an FP32 correction (flexible Krylov iterative refinement).
 template <typename T>
-double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit, int* its_out) {
+double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit, int* its_out,
+              bool pre32) {
   auto& L0 = levels<T>(t)[0];
   const long n = L0.n;
   const int m = t.opt.restart;
@@ -283,25 +307,31 @@ double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit,
   double rel = 1.0;
   for (;;) {
     apply_op<T>(t, 0, x, V, b, false);                       // r = b - A x -> V_0
-    WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * ((0) + 1), 2.0 * n * ((0) + 1), launch_dots<T>(V, nullptr, 0, 0, n, t.partial, t.nblk, 1, t.s));
+    WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n, 2.0 * n,
+              launch_dots<T>(V, nullptr, 0, 0, n, t.partial, t.nblk, 1, t.s));
     WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk, 0.0, launch_gmres_init(t.st, t.partial, t.nblk, m, bnorm, t.s));
     WT_CK(cudaMemcpyAsync(t.hst, t.st, sizeof(double) * 6, cudaMemcpyDeviceToHost, t.s));
     WT_CK(cudaStreamSynchronize(t.s));
     rel = bnorm > 0 ? t.hst[0] / bnorm : 0.0;
     if (rel <= tol || its >= maxit || t.hst[0] == 0.0) break;
-    WT_LAUNCH(t, K_KRYLOV, 2.0 * sizeof(T) * n, (double)n, launch_scale_copy<T>(V, V, n, t.st + 2, 0, t.s));  // v_0 = r / beta
+    WT_LAUNCH(t, K_KRYLOV, 2.0 * sizeof(T) * n, (double)n, launch_scale_copy<T>(V, V, n, t.st + 2, 0, t.s));
     int k = 0;
     for (int j = 0; j < m; ++j) {
       T* vj = V + (long)j * n;
       T* zj = Z + (long)j * n;
       T* w = V + (long)(j + 1) * n;
-      vcycle<T>(t, 0, vj, zj);                               // z_j = M^{-1} v_j
+      precondition<T>(t, vj, zj, pre32);                     // z_j = M^{-1} v_j
       apply_op<T>(t, 0, zj, w, nullptr, false);              // w = A z_j
-      WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * ((j + 1) + 1), 2.0 * n * ((j + 1) + 1), launch_dots<T>(w, V, n, j + 1, n, t.partial, t.nblk, 0, t.s));
-      WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk * (j + 1), 0.0, launch_reduce_partials(t.partial, t.nblk, j + 1, t.st + 8, t.s));
-      WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (j + 3), 4.0 * n * (j + 2), launch_update_dots<T>(w, V, n, j + 1, n, t.st + 8, t.partial, t.nblk, t.s));
-      WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk * (j + 2), 0.0, launch_gmres_arnoldi(t.st, nullptr, t.partial, t.nblk, j, m, bnorm, tol, t.s));
-      WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (j + 3), 2.0 * n * (j + 2), launch_update_normalize<T>(w, V, n, j + 1, n, t.st + 72, t.st + 2, w, t.s));
+      WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (j + 2), 2.0 * n * (j + 1),
+                launch_dots<T>(w, V, n, j + 1, n, t.partial, t.nblk, 0, t.s));
+      WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk * (j + 1), 0.0,
+                launch_reduce_partials(t.partial, t.nblk, j + 1, t.st + 8, t.s));
+      WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (j + 3), 4.0 * n * (j + 2),
+                launch_update_dots<T>(w, V, n, j + 1, n, t.st + 8, t.partial, t.nblk, t.s));
+      WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk * (j + 2), 0.0,
+                launch_gmres_arnoldi(t.st, nullptr, t.partial, t.nblk, j, m, bnorm, tol, t.s));
+      WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (j + 3), 2.0 * n * (j + 2),
+                launch_update_normalize<T>(w, V, n, j + 1, n, t.st + 72, t.st + 2, w, t.s));
       WT_CK(cudaMemcpyAsync(t.hst, t.st, sizeof(double) * 6, cudaMemcpyDeviceToHost, t.s));
       WT_CK(cudaStreamSynchronize(t.s));
       ++its;
@@ -309,7 +339,8 @@ double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit,
       if (t.hst[3] != 0.0 || its >= maxit) break;
     }
     WT_LAUNCH(t, K_KRYLOV, 8.0 * k * k, (double)k * k, launch_gmres_solve_y(t.st, k, m, t.s));
-    WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (k + 2), 2.0 * n * k, launch_lincomb<T>(x, Z, n, k, n, t.st + 328, t.s));
+    WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (k + 2), 2.0 * n * k,
+              launch_lincomb<T>(x, Z, n, k, n, t.st + 328, t.s));
   }
   if (its_out) *its_out = its;
   return rel;
@@ -319,33 +350,19 @@ double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit,
 int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_solve_info* info) {
   const long n = t.n;
   const double bn = norm2<double>(t, b, n);
-  int its_total = 0, ir = 0;
+  int its_total = 0;
   double rel = 0.0;
   int status = WT_OK;
   if (bn == 0.0) {
     WT_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, t.s));
     rel = 0.0;
-  } else if (t.opt.mode == WT_FP64) {
+  } else {
+    // WT_FP64: FP64 V-cycle.  WT_MIXED: FP32 V-cycle inside the FP64 flexible
+    // GMRES, i.e. FP64 residuals and Krylov basis, FP32 preconditioner.
     int its = 0;
-    rel = fgmres<double>(t, b, x, bn, tol, t.opt.max_it, &its);
+    rel = fgmres<double>(t, b, x, bn, tol, t.opt.max_it, &its, t.opt.mode == WT_MIXED);
     its_total = its;
     if (!(rel <= tol)) status = WT_ENOCONV;
-  } else {
-    // FP64 iterative refinement around the FP32 solver
-    for (;;) {
-      apply_op<double>(t, 0, x, t.r64, b, false);            // r = b - A64 x
-      const double rn = norm2<double>(t, t.r64, n);
-      rel = rn / bn;
-      if (rel <= tol) break;
-      if (ir >= t.opt.max_ir || !std::isfinite(rel)) { status = WT_ENOCONV; break; }
-      WT_LAUNCH(t, K_KRYLOV, 12.0 * n, (double)n, (launch_convert<double, float>(t.r64, t.b32, n, t.stN + 2, 0, t.s)));  // r / ||r||
-      WT_CK(cudaMemsetAsync(t.e32, 0, sizeof(float) * n, t.s));
-      int its = 0;
-      fgmres<float>(t, t.b32, t.e32, 1.0, t.opt.inner_tol, t.opt.max_it, &its);
-      its_total += its;
-      WT_LAUNCH(t, K_KRYLOV, 20.0 * n, 2.0 * n, launch_axpy_from<float>(x, t.e32, n, t.stN + 0, t.s));  // x += ||r|| e
-      ++ir;
-    }
   }
   WT_CK(cudaMemcpyAsync(t.hflag, t.dflag, sizeof(int), cudaMemcpyDeviceToHost, t.s));
   WT_CK(cudaStreamSynchronize(t.s));
@@ -355,7 +372,6 @@ int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_
   t.iterations += its_total;
   if (info) {
     info->iterations = its_total;
-    info->ir_steps = ir;
     info->rel_residual = rel;
     info->status = status;
   }

@@ -78,7 +78,8 @@ void setup_geometry(wt_tank& t, const double* ea, const double* eb, int precisio
 template <typename T> void apply_op(wt_tank& t, int l, const T* x, T* out, const T* f, bool nyq);
 template <typename T> void vcycle(wt_tank& t, int l, const T* f, T* x);
 template <typename T>
-double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit, int* its_out);
+double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit, int* its_out,
+              bool pre32);
 
 // Solve A p = b on the finest level (device pointers, FP64) with the tank's
 // options; x holds the initial guess.  Geometry must be set up already.
