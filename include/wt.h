@@ -28,9 +28,12 @@
  *    sigma_m = (cos(m pi / Nz) + 1) / 2.
  *  - Nx is a power of two in [4, 4096]; Ny is 1 or a power of two in
  *    [4, 1024]; 2 <= Nz <= 32.
- *  - Every call is stream-ordered on the tank's stream (wt_set_stream,
- *    default: the legacy default stream) and returns after the results are
- *    complete, except where stated.
+ *  - Every call is stream-ordered on the tank's stream and returns after the
+ *    results are complete.  By default the tank owns a non-blocking stream
+ *    and orders each call after the work already queued on the legacy
+ *    default stream; wt_set_stream selects a caller's stream instead.
+ *  - The per-iteration kernels of the Krylov solver are captured as CUDA
+ *    graphs at first use and replayed (not while kernel timing is on).
  *  - A tank handle must not be used by two threads at the same time.
  */
 #ifndef WT_H
@@ -78,6 +81,10 @@ typedef struct wt_options {
   int bc_transfer;   /* 0: surface/bottom residual rows injected into the
                         coarse boundary rows (default); 1: whole column
                         through the Chebyshev truncation as printed          */
+  int tail_max;      /* levels with at most this many unknowns run in one
+                        single-CTA V-cycle launch (0: never, the
+                        default; graph replay of the multi-CTA levels is
+                        faster at the sizes measured so far)          */
 } wt_options;
 
 typedef struct wt_solve_info {
@@ -104,7 +111,9 @@ int wt_create(int Nx, int Ny, int Nz, double L, double g, double nu,
 int wt_set_options(wt_tank* t, const wt_options* opt);
 int wt_get_options(const wt_tank* t, wt_options* opt);
 
-/* Use the given cudaStream_t (passed as void*) for all later calls. */
+/* Use the given cudaStream_t (passed as void*) for all later calls; NULL
+ * returns to the tank's own stream.  The stream must not be the legacy
+ * default stream (graph capture). */
 int wt_set_stream(wt_tank* t, void* stream);
 
 /* Grid coordinates: x [Nx], y [Ny], sigma [Nz+1] (any may be NULL). */
@@ -178,7 +187,8 @@ int wt_get_stats(const wt_tank* t, long* solves, long* iterations);
  *                 (+ Nyquist coefficients), WT_K_COLMAT sigma transfers and
  *                 sigma derivatives, WT_K_BLOCKINV column-block inverses,
  *                 WT_K_COARSE coarsest LU, WT_K_KRYLOV GMRES vector kernels,
- *                 WT_K_STAGE metric and Runge-Kutta pointwise kernels.
+ *                 WT_K_STAGE metric and Runge-Kutta pointwise kernels,
+ *                 WT_K_TAIL the single-CTA lower V-cycle.
  * wt_profile(t, mask) starts a timing window: every later launch of a class
  * whose bit is set in mask is bracketed by CUDA events on the tank's stream
  * (mask = 0 stops timing).  wt_profile_read sums the window for one class:
@@ -188,7 +198,8 @@ int wt_get_stats(const wt_tank* t, long* solves, long* iterations);
  */
 enum wt_kernel_class {
   WT_K_ROWPASS = 0, WT_K_OPCOLS = 1, WT_K_SMOOTH = 2, WT_K_COLMAT = 3,
-  WT_K_BLOCKINV = 4, WT_K_COARSE = 5, WT_K_KRYLOV = 6, WT_K_STAGE = 7, WT_K_COUNT = 8
+  WT_K_BLOCKINV = 4, WT_K_COARSE = 5, WT_K_KRYLOV = 6, WT_K_STAGE = 7, WT_K_TAIL = 8,
+  WT_K_COUNT = 9
 };
 int wt_profile(wt_tank* t, unsigned mask);
 int wt_profile_read(wt_tank* t, int kernel_class, double* ms, long* launches, double* bytes,

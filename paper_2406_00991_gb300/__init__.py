@@ -30,7 +30,7 @@ class wt_options(ctypes.Structure):
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("max_it", ctypes.c_int),
                 ("filter", ctypes.c_int), ("linear", ctypes.c_int), ("coarsest_max", ctypes.c_int),
-                ("bc_transfer", ctypes.c_int)]
+                ("bc_transfer", ctypes.c_int), ("tail_max", ctypes.c_int)]
 
 
 class wt_solve_info(ctypes.Structure):
@@ -209,7 +209,8 @@ def wt_destroy(t):
     return _lib.wt_destroy(t)
 
 
-KERNEL_CLASSES = ["rowpass", "opcols", "smooth", "colmat", "blockinv", "coarse", "krylov", "stage"]
+KERNEL_CLASSES = ["rowpass", "opcols", "smooth", "colmat", "blockinv", "coarse", "krylov", "stage",
+                  "tail"]
 
 
 def wt_profile(t, mask):

@@ -237,6 +237,28 @@ void build_hierarchy(wt_tank& t) {
     t.L32[l].Rsig = upload<float>(t.har, R);
     t.L32[l].Psig = upload<float>(t.har, P);
   }
+  // level descriptors for the single-CTA V-cycle kernel
+  {
+    std::vector<TailLevel<double>> d64(nl);
+    std::vector<TailLevel<float>> d32(nl);
+    auto fill = [&](auto& v, auto& Lv, auto* tw) {
+      for (int l = 0; l < nl; ++l) {
+        auto& L = Lv[l];
+        v[l].V = L.view(tw, t.logNtw, t.L);
+        v[l].x = L.x; v[l].f = L.f; v[l].r = L.r;
+        v[l].t1 = L.t1; v[l].t2 = L.t2; v[l].t3 = L.t3; v[l].t4 = L.t4; v[l].t5 = L.t5; v[l].t6 = L.t6;
+        v[l].Binv = L.Binv;
+        v[l].rhoX = L.rhoX; v[l].rhoY = L.rhoY; v[l].rhoXY = L.rhoXY;
+        v[l].Rsig = L.Rsig; v[l].Psig = L.Psig;
+      }
+    };
+    fill(d64, t.L64, t.tw64);
+    fill(d32, t.L32, t.tw32);
+    t.tl64 = t.har.alloc<TailLevel<double>>(nl);
+    t.tl32 = t.har.alloc<TailLevel<float>>(nl);
+    WT_CK(cudaMemcpy(t.tl64, d64.data(), sizeof(TailLevel<double>) * nl, cudaMemcpyHostToDevice));
+    WT_CK(cudaMemcpy(t.tl32, d32.data(), sizeof(TailLevel<float>) * nl, cudaMemcpyHostToDevice));
+  }
   auto [cx, cy, cz] = t.dims.back();
   t.ncoarse = cx * cy * (cz + 1);
   if (t.ncoarse > 128)
@@ -270,6 +292,7 @@ int check_options(const wt_options& o) {
   if (!(o.omega > 0) || !(o.omega < 2)) return fail(WT_EINVAL, "omega must be in (0, 2)");
   if (o.max_it < 1) return fail(WT_EINVAL, "max_it must be >= 1");
   if (o.coarsest_max < 1 || o.coarsest_max > 128) return fail(WT_EINVAL, "coarsest_max must be in [1, 128]");
+  if (o.tail_max < 0) return fail(WT_EINVAL, "tail_max must be >= 0");
   if ((o.filter != 0 && o.filter != 1) || (o.linear != 0 && o.linear != 1) ||
       (o.bc_transfer != 0 && o.bc_transfer != 1))
     return fail(WT_EINVAL, "filter, linear, bc_transfer are 0 or 1");
@@ -285,6 +308,14 @@ int guarded(F&& f) {
   } catch (const std::exception& e) {
     return fail(WT_ENOMEM, e.what());
   }
+}
+
+// Order the tank's own stream after work already queued on the legacy
+// default stream (where callers usually produce their device inputs).
+void enter(wt_tank& t) {
+  if (t.s != t.own_stream) return;
+  WT_CK(cudaEventRecord(t.order_ev, 0));
+  WT_CK(cudaStreamWaitEvent(t.s, t.order_ev, 0));
 }
 
 int read_flags(wt_tank& t) {
@@ -341,6 +372,7 @@ void filter_field(wt_tank& t, double* q, int planes, bool cheb) {
 }
 
 int rk_stage(wt_tank& t, int k, double dt) {
+  enter(t);
   const double a = kAlpha[k - 1], b = kBeta[k - 1];
   const bool y = t.Ny > 1;
   const int M1 = t.M1;
@@ -422,6 +454,7 @@ int wt_default_options(wt_options* o) {
   o->linear = 0;
   o->coarsest_max = 64;
   o->bc_transfer = 0;
+  o->tail_max = 0;
   return WT_OK;
 }
 
@@ -440,6 +473,11 @@ int wt_create(int Nx, int Ny, int Nz, double L, double g, double nu, const doubl
   return guarded([&]() -> int {
     std::unique_ptr<wt_tank> t(new wt_tank());
     WT_CK(cudaGetDevice(&t->device));
+    // a stream of its own (graph capture needs a non-legacy stream); every call
+    // first orders itself after the work already queued on the legacy stream
+    WT_CK(cudaStreamCreateWithFlags(&t->own_stream, cudaStreamNonBlocking));
+    WT_CK(cudaEventCreateWithFlags(&t->order_ev, cudaEventDisableTiming));
+    t->s = t->own_stream;
     t->Nx = Nx; t->Ny = Ny; t->Nz = Nz; t->M1 = Nz + 1; t->ncols = Nx * Ny; t->n = (long)t->M1 * t->ncols;
     t->L = L; t->g = g; t->nu = nu;
     wt_default_options(&t->opt);
@@ -483,7 +521,7 @@ int wt_create(int Nx, int Ny, int Nz, double L, double g, double nu, const doubl
     t->Z64 = ar.alloc<double>((size_t)31 * n);
     t->V32 = ar.alloc<float>((size_t)32 * n);
     t->Z32 = ar.alloc<float>((size_t)31 * n);
-    t->nblk = (int)std::min<long>(148, std::max<long>(1, (n + 2047) / 2048));
+    t->nblk = (int)std::min<long>(296, std::max<long>(1, (n + 511) / 512));
     t->partial = ar.alloc<double>((size_t)t->nblk * 40);
     t->st = ar.alloc<double>(4608);
     t->stN = ar.alloc<double>(4608);
@@ -524,6 +562,8 @@ int wt_set_options(wt_tank* t, const wt_options* o) {
   if (st != WT_OK) return st;
   return guarded([&]() -> int {
     const bool rebuild = o->coarsest_max != t->opt.coarsest_max || o->bc_transfer != t->opt.bc_transfer;
+    WT_CK(cudaStreamSynchronize(t->s));
+    destroy_graphs(*t);
     t->opt = *o;
     if (rebuild) {
       WT_CK(cudaStreamSynchronize(t->s));
@@ -547,8 +587,11 @@ int wt_get_options(const wt_tank* t, wt_options* o) {
 
 int wt_set_stream(wt_tank* t, void* stream) {
   if (!t) return fail(WT_EINVAL, "NULL tank");
-  t->s = static_cast<cudaStream_t>(stream);
-  return WT_OK;
+  return guarded([&]() -> int {
+    WT_CK(cudaStreamSynchronize(t->s));
+    t->s = stream ? static_cast<cudaStream_t>(stream) : t->own_stream;
+    return WT_OK;
+  });
 }
 
 int wt_get_grid(const wt_tank* t, double* x, double* y, double* sigma) {
@@ -577,6 +620,7 @@ int wt_set_state(wt_tank* t, const double* eta, const double* u, const double* v
                  double time) {
   if (!t || !eta || !u || !w || (t->Ny > 1 && !v)) return fail(WT_EINVAL, "NULL state array");
   return guarded([&]() -> int {
+    enter(*t);
     const long n = t->n;
     const int nc = t->ncols;
     const double* e = in_dev(*t, eta, t->io_s1, nc);
@@ -609,6 +653,7 @@ int wt_get_state(const wt_tank* tc, double* eta, double* u, double* v, double* w
   if (!tc) return fail(WT_EINVAL, "NULL tank");
   wt_tank* t = const_cast<wt_tank*>(tc);
   return guarded([&]() -> int {
+    enter(*t);
     if (eta) out_copy(*t, eta, t->eta, t->ncols);
     if (u) out_copy(*t, u, t->u, t->n);
     if (v) out_copy(*t, v, t->v, t->n);
@@ -623,6 +668,7 @@ int wt_get_pressure(const wt_tank* tc, double* p) {
   if (!tc || !p) return fail(WT_EINVAL, "NULL argument");
   wt_tank* t = const_cast<wt_tank*>(tc);
   return guarded([&]() -> int {
+    enter(*t);
     out_copy(*t, p, t->p, t->n);
     WT_CK(cudaStreamSynchronize(t->s));
     return WT_OK;
@@ -634,6 +680,7 @@ int wt_apply_operator(wt_tank* t, const double* eta_a, const double* eta_b, cons
   if (!t || !eta_a || !eta_b || !p || !Ap) return fail(WT_EINVAL, "NULL argument");
   if (precision != WT_FP64 && precision != WT_FP32) return fail(WT_EINVAL, "precision must be WT_FP64 or WT_FP32");
   return guarded([&]() -> int {
+    enter(*t);
     const long n = t->n;
     const double* ea = in_dev(*t, eta_a, t->io_s1, t->ncols);
     const double* eb = in_dev(*t, eta_b, t->io_s2, t->ncols);
@@ -659,6 +706,7 @@ int wt_precondition(wt_tank* t, const double* eta_a, const double* eta_b, const 
   if (!t || !eta_a || !eta_b || !r || !z) return fail(WT_EINVAL, "NULL argument");
   if (precision != WT_FP64 && precision != WT_FP32) return fail(WT_EINVAL, "precision must be WT_FP64 or WT_FP32");
   return guarded([&]() -> int {
+    enter(*t);
     const long n = t->n;
     const double* ea = in_dev(*t, eta_a, t->io_s1, t->ncols);
     const double* eb = in_dev(*t, eta_b, t->io_s2, t->ncols);
@@ -685,6 +733,7 @@ int wt_poisson_solve(wt_tank* t, const double* eta_a, const double* eta_b, const
   if (!t || !eta_a || !eta_b || !rhs || !p) return fail(WT_EINVAL, "NULL argument");
   if (tol <= 0) tol = t->opt.tol;
   return guarded([&]() -> int {
+    enter(*t);
     const long n = t->n;
     const double* ea = in_dev(*t, eta_a, t->io_s1, t->ncols);
     const double* eb = in_dev(*t, eta_b, t->io_s2, t->ncols);
@@ -775,6 +824,9 @@ int wt_get_launches(const wt_tank* t, long* launches) {
 int wt_destroy(wt_tank* t) {
   if (!t) return WT_OK;
   cudaStreamSynchronize(t->s);
+  destroy_graphs(*t);
+  if (t->order_ev) cudaEventDestroy(t->order_ev);
+  if (t->own_stream) cudaStreamDestroy(t->own_stream);
   if (t->hflag) cudaFreeHost(t->hflag);
   if (t->hst) cudaFreeHost(t->hst);
   delete t;

@@ -1,5 +1,5 @@
-// Column (sigma-direction) kernels on shared-memory tiles of 16 columns x all
-// sigma rows (see TC / RG below).
+// Column (sigma-direction) kernels, one warp per vertical column (bodies in
+// wt_dev.cuh).
 //
 //  k_op_cols      the sigma part of A_{a,b} (Eq. 1_chain, poissonp, bcpdneu):
 //                 P_s = D p, G = (P_x + sx_b P_s, P_y + sy_b P_s, Z_b P_s),
@@ -10,185 +10,38 @@
 //  k_col_matrix   out = M in along sigma (Chebyshev transfers of Sec. 4.2, filter).
 //  k_block_inverse  builds and inverts the (Nz+1)^2 diagonal block of every
 //                 column by Gauss-Jordan with partial pivoting, one warp per column.
-#include "wt_internal.h"
+#include "wt_dev.cuh"
 
 #include <algorithm>
 
 namespace wt {
 
-// Column kernels work on tiles of TC consecutive columns x all M1 sigma rows
-// held in shared memory ([row][column-in-tile]); thread (rg, tc) of a
-// 128-thread CTA owns column tc of the tile and the rows rg, rg+8, rg+16, ...
-// so every sigma contraction has M1 x TC independent outputs per CTA and the
-// global loads of a warp cover 16 consecutive columns.
-constexpr int TC = 16;
-constexpr int RG = 8;                 // row groups: 128 threads = RG x TC
-
 template <typename T, int DIM>
-__global__ void __launch_bounds__(128) k_op_cols(LevelView<T> L, const T* __restrict__ p,
+__global__ void __launch_bounds__(256) k_op_cols(LevelView<T> L, const T* __restrict__ p,
                                                  const T* __restrict__ Px, const T* __restrict__ Py,
                                                  T* __restrict__ Gx, T* __restrict__ Gy,
                                                  T* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int M1 = L.M1;
-  T* sD = reinterpret_cast<T*>(smraw);            // M1*M1
-  T* sP = sD + M1 * M1;                          // p tile
-  T* sPs = sP + M1 * TC;                         // D p
-  T* sGx = sPs + M1 * TC;                        // G_x (Px on entry)
-  T* sGy = sGx + M1 * TC;                        // G_y (Py on entry), 3D only
-  const int tc = threadIdx.x % TC, rg = threadIdx.x / TC;
-  const long nc = L.ncols;
-  const long c0 = (long)blockIdx.x * TC;
-  const long c = c0 + tc;
-  const bool live = c < nc;
-  for (int i = threadIdx.x; i < M1 * M1; i += blockDim.x) sD[i] = L.D[i];
-  for (int i = threadIdx.x; i < M1 * TC; i += blockDim.x) {
-    const int m = i / TC, cc = i % TC;
-    const long col = c0 + cc;
-    const bool ok = col < nc;
-    sP[i] = ok ? p[m * nc + col] : T(0);
-    sGx[i] = ok ? Px[m * nc + col] : T(0);
-    if constexpr (DIM == 3) sGy[i] = ok ? Py[m * nc + col] : T(0);
-  }
-  __syncthreads();
-  // P_s = D p
-  for (int m = rg; m < M1; m += RG) {
-    T acc = 0;
-    for (int k = 0; k < M1; ++k) acc += sD[m * M1 + k] * sP[k * TC + tc];
-    sPs[m * TC + tc] = acc;
-  }
-  __syncthreads();
-  const T* meta = L.meta;
-  const long cm = live ? c : 0;
-  const T AXb = meta[M_AXb * nc + cm], BXb = meta[M_BXb * nc + cm];
-  const T AXa = meta[M_AXa * nc + cm], BXa = meta[M_BXa * nc + cm];
-  const T Za = meta[M_Za * nc + cm], Zb = meta[M_Zb * nc + cm];
-  const T HX = meta[M_HX * nc + cm];
-  T AYa = 0, BYa = 0, AYb = 0, BYb = 0, HY = 0;
-  if constexpr (DIM == 3) {
-    AYa = meta[M_AYa * nc + cm]; BYa = meta[M_BYa * nc + cm];
-    AYb = meta[M_AYb * nc + cm]; BYb = meta[M_BYb * nc + cm];
-    HY = meta[M_HY * nc + cm];
-  }
-  // G = (P_x + sx_b P_s, P_y + sy_b P_s, .)
-  for (int m = rg; m < M1; m += RG) {
-    const T s = L.sigma[m];
-    const T ps = sPs[m * TC + tc];
-    const T gx = sGx[m * TC + tc] + (AXb - s * BXb) * ps;
-    sGx[m * TC + tc] = gx;
-    if (live) Gx[m * nc + c] = gx;
-    if constexpr (DIM == 3) {
-      const T gy = sGy[m * TC + tc] + (AYb - s * BYb) * ps;
-      sGy[m * TC + tc] = gy;
-      if (live) Gy[m * nc + c] = gy;
-    }
-  }
-  __syncthreads();
-  const T ZZ = Za * Zb;
-  for (int m = rg; m < M1; m += RG) {
-    T out;
-    if (m == 0) {
-      out = sP[tc];                                         // surface row: p
-    } else if (m == M1 - 1) {                               // bottom row: n . Grad_b p
-      out = HX * sGx[m * TC + tc] + Zb * sPs[m * TC + tc];
-      if constexpr (DIM == 3) out += HY * sGy[m * TC + tc];
-    } else {
-      T q = 0, sum = 0, qy = 0;
-      for (int k = 0; k < M1; ++k) {
-        const T d = sD[m * M1 + k];
-        q += d * sGx[k * TC + tc];
-        sum += d * sPs[k * TC + tc];
-        if constexpr (DIM == 3) qy += d * sGy[k * TC + tc];
-      }
-      const T s = L.sigma[m];
-      out = (AXa - s * BXa) * q + ZZ * sum;
-      if constexpr (DIM == 3) out += (AYa - s * BYa) * qy;
-    }
-    if (live) part[m * nc + c] = out;
-  }
+  opcols_body<T, DIM>(L, p, Px, Py, Gx, Gy, part, blockIdx.x, gridDim.x, smraw);
 }
 
 template <typename T, int DIM>
-__global__ void __launch_bounds__(128) k_smooth_cols(LevelView<T> L, const T* __restrict__ r,
+__global__ void __launch_bounds__(256) k_smooth_cols(LevelView<T> L, const T* __restrict__ r,
                                                      const T* __restrict__ rhoX,
                                                      const T* __restrict__ rhoY,
                                                      const T* __restrict__ rhoXY,
                                                      const T* __restrict__ Binv,
                                                      T* __restrict__ x, T omega, int first) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  constexpr int NC = DIM == 2 ? 2 : 4;
-  const int M1 = L.M1;
-  T* sR = reinterpret_cast<T*>(smraw);            // [NC][M1][TC] residual parts
-  const int tc = threadIdx.x % TC, rg = threadIdx.x / TC;
-  const long nc = L.ncols;
-  const long c0 = (long)blockIdx.x * TC;
-  for (int i = threadIdx.x; i < M1 * TC; i += blockDim.x) {
-    const int m = i / TC, cc = i % TC;
-    const long col = c0 + cc;
-    T rr = 0, rNx = 0, rNy = 0, rNN = 0;
-    if (col < nc) {
-      rr = r[m * nc + col];
-      const int jx = (int)(col % L.Nx), jy = (int)(col / L.Nx);
-      const T sx = (jx & 1) ? T(-1) : T(1), sy = (jy & 1) ? T(-1) : T(1);
-      if constexpr (DIM == 2) {
-        if (rhoX) rNx = rhoX[m] * sx;
-      } else {
-        const T cxy = rhoXY ? rhoXY[m] : T(0);
-        rNN = cxy * sx * sy;
-        if (rhoX) rNx = (rhoX[m * L.Ny + jy] - cxy * sy) * sx;
-        if (rhoY) rNy = (rhoY[m * L.Nx + jx] - cxy * sx) * sy;
-      }
-    }
-    sR[(0 * M1 + m) * TC + cc] = rr - rNx - rNy - rNN;
-    sR[(1 * M1 + m) * TC + cc] = rNx;
-    if constexpr (DIM == 3) {
-      sR[(2 * M1 + m) * TC + cc] = rNy;
-      sR[(3 * M1 + m) * TC + cc] = rNN;
-    }
-  }
-  __syncthreads();
-  const long c = c0 + tc;
-  if (c >= nc) return;
-  const long blk = (long)M1 * M1;
-  for (int m = rg; m < M1; m += RG) {
-    T e = 0;
-#pragma unroll
-    for (int cls = 0; cls < NC; ++cls) {
-      const T* B = Binv + (cls * blk + (long)m * M1) * nc + c;
-      const T* R = sR + cls * M1 * TC + tc;
-#pragma unroll 5
-      for (int k = 0; k < M1; ++k) e += B[(long)k * nc] * R[k * TC];
-    }
-    const T xo = first ? T(0) : x[m * nc + c];
-    x[m * nc + c] = xo + omega * e;
-  }
+  smooth_any<T, DIM>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first, blockIdx.x, gridDim.x, smraw);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_col_matrix(const T* __restrict__ M, int Mo, int Mi,
+__global__ void __launch_bounds__(256) k_col_matrix(const T* __restrict__ M, int Mo, int Mi,
                                                     const T* __restrict__ in, T* __restrict__ out,
                                                     int ncols, int accumulate) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* sM = reinterpret_cast<T*>(smraw);            // Mo*Mi
-  T* sIn = sM + Mo * Mi;                          // [Mi][TC]
-  const int tc = threadIdx.x % TC, rg = threadIdx.x / TC;
-  const long nc = ncols;
-  const long c0 = (long)blockIdx.x * TC;
-  for (int i = threadIdx.x; i < Mo * Mi; i += blockDim.x) sM[i] = M[i];
-  for (int i = threadIdx.x; i < Mi * TC; i += blockDim.x) {
-    const int k = i / TC, cc = i % TC;
-    const long col = c0 + cc;
-    sIn[i] = col < nc ? in[k * nc + col] : T(0);
-  }
-  __syncthreads();
-  const long c = c0 + tc;
-  if (c >= nc) return;
-  for (int m = rg; m < Mo; m += RG) {
-    T acc = 0;
-    for (int k = 0; k < Mi; ++k) acc += sM[m * Mi + k] * sIn[k * TC + tc];
-    if (accumulate) acc += out[m * nc + c];
-    out[m * nc + c] = acc;
-  }
+  colmat_body<T>(M, Mo, Mi, in, out, ncols, accumulate, blockIdx.x, gridDim.x, smraw);
 }
 
 // Diagonal column block of A_{a,b} (the same expression the oracle pins
@@ -277,9 +130,9 @@ __global__ void __launch_bounds__(128) k_block_inverse(LevelView<T> L, T* __rest
     if (bad) {
       if (lane == 0) atomicOr(flag, 1);
     }
-    for (int i = lane; i < M1 * M1; i += 32) {
-      const int m = i / M1, k = i - m * M1;
-      Binv[(cls * blk + i) * nc + c] = bad ? T(0) : A[m * W + M1 + k];
+    for (int i = lane; i < M1 * M1; i += 32) {   // i = k * M1 + m: coalesced stores
+      const int k = i / M1, m = i - k * M1;
+      Binv[((long)c * nclass + cls) * blk + i] = bad ? T(0) : A[m * W + M1 + k];
     }
     __syncwarp();
   }
@@ -294,20 +147,20 @@ static cudaError_t set_smem(const void* fn, size_t smem) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+static inline int grid_cols(long ncols, int threads) {
+  const long w = threads / 32;
+  return (int)std::min<long>(std::max<long>(1, (ncols + w - 1) / w), 152L * 64);
+}
+
 template <typename T>
 cudaError_t launch_op_cols(const LevelView<T>& L, const T* p, const T* Px, const T* Py, T* Gx,
                            T* Gy, T* part, cudaStream_t s) {
-  const int g = grid_for(L.ncols, TC);
-  const size_t smem = sizeof(T) * ((size_t)L.M1 * L.M1 + 4 * (size_t)L.M1 * TC);
-  if (L.Ny == 1) {
-    cudaError_t e = set_smem<T>((const void*)k_op_cols<T, 2>, smem);
-    if (e != cudaSuccess) return e;
-    k_op_cols<T, 2><<<g, 128, smem, s>>>(L, p, Px, Py, Gx, Gy, part);
-  } else {
-    cudaError_t e = set_smem<T>((const void*)k_op_cols<T, 3>, smem);
-    if (e != cudaSuccess) return e;
-    k_op_cols<T, 3><<<g, 128, smem, s>>>(L, p, Px, Py, Gx, Gy, part);
-  }
+  const int g = grid_cols(L.ncols, 256);
+  const size_t smem = opcols_smem<T>(L.M1);
+  if (L.Ny == 1)
+    k_op_cols<T, 2><<<g, 256, smem, s>>>(L, p, Px, Py, Gx, Gy, part);
+  else
+    k_op_cols<T, 3><<<g, 256, smem, s>>>(L, p, Px, Py, Gx, Gy, part);
   return cudaGetLastError();
 }
 
@@ -315,21 +168,21 @@ template <typename T>
 cudaError_t launch_smooth_cols(const LevelView<T>& L, const T* r, const T* rhoX, const T* rhoY,
                                const T* rhoXY, const T* Binv, int nclass, T* x, T omega, int first,
                                cudaStream_t s) {
-  const int g = grid_for(L.ncols, TC);
-  const size_t smem = sizeof(T) * (size_t)nclass * L.M1 * TC;
+  (void)nclass;
+  const int g = grid_cols(L.ncols, 256);
   if (L.Ny == 1)
-    k_smooth_cols<T, 2><<<g, 128, smem, s>>>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
+    k_smooth_cols<T, 2><<<g, 256, 0, s>>>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
   else
-    k_smooth_cols<T, 3><<<g, 128, smem, s>>>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
+    k_smooth_cols<T, 3><<<g, 256, 0, s>>>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_col_matrix(const T* M, int Mo, int Mi, const T* in, T* out, int ncols,
                               int accumulate, cudaStream_t s) {
-  const int g = grid_for(ncols, TC);
-  const size_t smem = sizeof(T) * ((size_t)Mo * Mi + (size_t)Mi * TC);
-  k_col_matrix<T><<<g, 128, smem, s>>>(M, Mo, Mi, in, out, ncols, accumulate);
+  const int g = grid_cols(ncols, 256);
+  const size_t smem = sizeof(T) * (size_t)Mo * Mi;
+  k_col_matrix<T><<<g, 256, smem, s>>>(M, Mo, Mi, in, out, ncols, accumulate);
   return cudaGetLastError();
 }
 

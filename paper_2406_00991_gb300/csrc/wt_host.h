@@ -81,7 +81,7 @@ struct SurfLevel {
 
 // Kernel classes of the optional per-launch CUDA-event profiler.
 enum KCat { K_ROWPASS = 0, K_OPCOLS, K_SMOOTH, K_COLMAT, K_BLOCKINV, K_COARSE, K_KRYLOV, K_STAGE,
-            K_NCAT };
+            K_TAIL, K_NCAT };
 
 struct ProfRec {
   int ev0, ev1, cat;
@@ -99,10 +99,23 @@ struct Prof {
   }
 };
 
+// One captured FGMRES Arnoldi step (preconditioner, operator, CGS2 and
+// Givens kernels for basis index j), replayed with a single graph launch.
+struct IterGraph {
+  cudaGraphExec_t exec = nullptr;
+  long kernels = 0;
+};
+
 }  // namespace wt
 
 struct wt_tank {
   wt::Prof prof;
+  // graphs[key][j], key = 0: FP64 V-cycle, 1: FP32 V-cycle in FP64 FGMRES,
+  // 2: FP32 FGMRES; rebuilt after any option or hierarchy change
+  std::vector<wt::IterGraph> graphs[3];
+  bool use_graphs = true;
+  cudaStream_t own_stream = nullptr;
+  cudaEvent_t order_ev = nullptr;
   int Nx = 0, Ny = 0, Nz = 0, M1 = 0, ncols = 0;
   long n = 0;
   double L = 0, g = 9.81, nu = 0;
@@ -120,6 +133,8 @@ struct wt_tank {
   double2* tw64 = nullptr;
   float2* tw32 = nullptr;
   int logNtw = 0;
+  wt::TailLevel<double>* tl64 = nullptr;   // device descriptors of every level
+  wt::TailLevel<float>* tl32 = nullptr;
   double *cLU = nullptr, *cDx = nullptr, *cDy = nullptr;
   int* cpiv = nullptr;
   int ncoarse = 0;

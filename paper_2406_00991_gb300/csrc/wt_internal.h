@@ -106,6 +106,30 @@ template <typename T>
 cudaError_t launch_block_inverse(const LevelView<T>& L, T* Binv, int nclass, T cxx, T cyy,
                                  int* flag, cudaStream_t s);
 
+// Single-CTA V-cycle over the levels l0..nl-1 (wt_tail.cu): all small levels
+// run in one launch with __syncthreads between the phases.
+template <typename T>
+struct TailLevel {
+  LevelView<T> V;
+  T *x, *f, *r, *t1, *t2, *t3, *t4, *t5, *t6;
+  const T* Binv;
+  T *rhoX, *rhoY, *rhoXY;
+  const T *Rsig, *Psig;     // to / from the next coarser level
+};
+template <typename T>
+struct TailArgs {
+  const TailLevel<T>* lv;   // device array, all levels of the hierarchy
+  int l0, nl;
+  const T* f0;              // right-hand side of level l0
+  T* x0;                    // result of level l0
+  int f0_nyq;               // f0 may carry x- (y-) Nyquist content
+  T omega;
+  int nu1, nu2;
+  const double* AinvT;      // coarsest inverse, transposed, FP64
+  int smem;                 // dynamic shared memory of the launch
+};
+template <typename T> cudaError_t launch_vcycle_tail(const TailArgs<T>& a, int dim, cudaStream_t s);
+
 // Dense coarsest level (wt_coarse.cu), always FP64 arithmetic.
 cudaError_t launch_coarse_factor(const LevelView<double>& L, const double* Dx, const double* Dy,
                                  double* LU, int* piv, int* flag, cudaStream_t s);
@@ -141,7 +165,7 @@ cudaError_t launch_nyquist_coef(const void* r, int is_double, int nrows, int Nx,
                                 void* rho, cudaStream_t s);
 // GMRES small dense part on one thread: see wt_krylov.cu for the state layout.
 cudaError_t launch_gmres_init(double* st, const double* partial, int nblk, int m, double bnorm,
-                              cudaStream_t s);
+                              double tol, cudaStream_t s);
 cudaError_t launch_gmres_arnoldi(double* st, const double* partial1, const double* partial2,
                                  int nblk, int j, int m, double bnorm, double tol,
                                  cudaStream_t s);

@@ -6,7 +6,9 @@
 //
 // GMRES state vector st (FP64, device), offsets in wt_internal.h users:
 //   st[0] beta, st[1] |g_{j+1}|, st[2] 1/h_{j+1,j}, st[3] done flag,
-//   st[4] ||b||, st[5] h_{j+1,j}, then h1, h2, cs, sn, g, y and H (column-major).
+//   st[4] ||b||, st[5] h_{j+1,j}, st[6] tolerance, then h1, h2, cs, sn, g, y
+//   and H (column-major).  The tolerance and ||b|| live on the device so a
+//   captured Arnoldi step stays valid across solves.
 #include "wt_internal.h"
 
 #include <algorithm>
@@ -189,12 +191,14 @@ __global__ void k_gmres_init(double* st, const double* __restrict__ partial, int
   st[2] = beta > 0 ? 1.0 / beta : 0.0;
   st[3] = (beta <= tol * bnorm) ? 1.0 : 0.0;
   st[4] = bnorm;
+  st[6] = tol;
   for (int i = 0; i <= m; ++i) st[OFF_G + i] = 0.0;
   st[OFF_G] = beta;
 }
 
 __global__ void k_gmres_arnoldi(double* st, const double* __restrict__ partial2, int nblk, int j,
-                                int m, double tol) {
+                                int m) {
+  const double tol = st[6];
   __shared__ double h2[64];
   __shared__ double ww;
   const int nvals = j + 2;    // j+1 dots and ||w||^2
@@ -307,16 +311,16 @@ cudaError_t launch_nyquist_coef(const void* r, int is_double, int nrows, int Nx,
   return cudaGetLastError();
 }
 cudaError_t launch_gmres_init(double* st, const double* partial, int nblk, int m, double bnorm,
-                              cudaStream_t s) {
-  // tol is applied by the arnoldi kernel and the host; init only records beta
-  k_gmres_init<<<1, 32, 0, s>>>(st, partial, nblk, m, bnorm, 0.0);
+                              double tol, cudaStream_t s) {
+  k_gmres_init<<<1, 32, 0, s>>>(st, partial, nblk, m, bnorm, tol);
   return cudaGetLastError();
 }
 cudaError_t launch_gmres_arnoldi(double* st, const double* partial1, const double* partial2, int nblk,
                                  int j, int m, double bnorm, double tol, cudaStream_t s) {
   (void)partial1;
   (void)bnorm;
-  k_gmres_arnoldi<<<1, 64, 0, s>>>(st, partial2, nblk, j, m, tol);
+  (void)tol;
+  k_gmres_arnoldi<<<1, 64, 0, s>>>(st, partial2, nblk, j, m);
   return cudaGetLastError();
 }
 cudaError_t launch_gmres_solve_y(double* st, int k, int m, cudaStream_t s) {

@@ -224,11 +224,46 @@ static void prolong_add(wt_tank& t, int l, T* x) {
   run_rowpass(t, a);
 }
 
+template <typename T> static TailLevel<T>* tail_desc(wt_tank& t);
+template <> TailLevel<double>* tail_desc<double>(wt_tank& t) { return t.tl64; }
+template <> TailLevel<float>* tail_desc<float>(wt_tank& t) { return t.tl32; }
+
+// First level handled by the single-CTA V-cycle kernel (-1: none).
+template <typename T>
+static int tail_level(wt_tank& t) {
+  if (t.opt.tail_max <= 0) return -1;
+  auto& lev = levels<T>(t);
+  for (size_t l = 0; l < lev.size(); ++l)
+    if (lev[l].n <= t.opt.tail_max) return (int)l;
+  return -1;
+}
+
 template <typename T>
 void vcycle(wt_tank& t, int l, const T* f, T* x) {
   auto& lev = levels<T>(t);
   const int nl = (int)lev.size();
   auto& L = lev[l];
+  if (l == tail_level<T>(t)) {
+    TailArgs<T> a;
+    a.lv = tail_desc<T>(t);
+    a.l0 = l;
+    a.nl = nl;
+    a.f0 = f;
+    a.x0 = x;
+    a.f0_nyq = (l == 0) || (lev[l - 1].Nx == L.Nx);
+    a.omega = (T)t.opt.omega;
+    a.nu1 = t.opt.nu1;
+    a.nu2 = t.opt.nu2;
+    a.AinvT = t.cLU;
+    a.smem = 96 * 1024;
+    double bytes = 0.0;
+    for (int k = l; k < nl; ++k)
+      bytes += sizeof(T) * (double)lev[k].n * (14.0 * (t.opt.nu1 + t.opt.nu2) + 16.0) +
+               sizeof(T) * (double)lev[k].nclass * lev[k].M1 * lev[k].M1 * lev[k].ncols *
+                   (t.opt.nu1 + t.opt.nu2);
+    WT_LAUNCH(t, K_TAIL, bytes, 0.0, launch_vcycle_tail<T>(a, L.Ny > 1 ? 3 : 2, t.s));
+    return;
+  }
   if (l == nl - 1) {
     WT_LAUNCH(t, K_COARSE, 8.0 * L.n * L.n + 2.0 * sizeof(T) * L.n, 2.0 * L.n * L.n, launch_coarse_solve<T>((int)L.n, t.cLU, t.cpiv, f, x, t.s));
     return;
@@ -255,7 +290,7 @@ void vcycle(wt_tank& t, int l, const T* f, T* x) {
 template <typename T>
 static double norm2(wt_tank& t, const T* v, long n) {
   WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * ((0) + 1), 2.0 * n * ((0) + 1), launch_dots<T>(v, nullptr, 0, 0, n, t.partial, t.nblk, 1, t.s));
-  WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk, 0.0, launch_gmres_init(t.stN, t.partial, t.nblk, 1, 1.0, t.s));
+  WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk, 0.0, launch_gmres_init(t.stN, t.partial, t.nblk, 1, 1.0, 0.0, t.s));
   WT_CK(cudaMemcpyAsync(t.hst, t.stN, sizeof(double) * 4, cudaMemcpyDeviceToHost, t.s));
   WT_CK(cudaStreamSynchronize(t.s));
   return t.hst[0];
@@ -295,6 +330,78 @@ void precondition<double>(wt_tank& t, const double* v, double* z, bool pre32) {
 // residual ||b - A x|| / bnorm computed in precision T.  With pre32 the
 // preconditioner is the FP32 V-cycle: every Arnoldi step then refines the
 // FP64 iterate with an FP32 correction (flexible Krylov iterative refinement).
+void destroy_graphs(wt_tank& t) {
+  for (auto& v : t.graphs) {
+    for (auto& g : v)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    v.clear();
+  }
+}
+
+// Arnoldi step j: z_j = M^{-1} v_j, w = A z_j, CGS2 against v_0..v_j,
+// Givens update, v_{j+1} = w / h_{j+1,j}.  Device-only: capturable.
+template <typename T>
+static void arnoldi_step(wt_tank& t, int j, bool pre32) {
+  const long n = levels<T>(t)[0].n;
+  const int m = t.opt.restart;
+  T* V = Vbuf<T>(t);
+  T* Z = Zbuf<T>(t);
+  T* vj = V + (long)j * n;
+  T* zj = Z + (long)j * n;
+  T* w = V + (long)(j + 1) * n;
+  precondition<T>(t, vj, zj, pre32);                     // z_j = M^{-1} v_j
+  apply_op<T>(t, 0, zj, w, nullptr, false);              // w = A z_j
+  WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (j + 2), 2.0 * n * (j + 1),
+            launch_dots<T>(w, V, n, j + 1, n, t.partial, t.nblk, 0, t.s));
+  WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk * (j + 1), 0.0,
+            launch_reduce_partials(t.partial, t.nblk, j + 1, t.st + 8, t.s));
+  WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (j + 3), 4.0 * n * (j + 2),
+            launch_update_dots<T>(w, V, n, j + 1, n, t.st + 8, t.partial, t.nblk, t.s));
+  WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk * (j + 2), 0.0,
+            launch_gmres_arnoldi(t.st, nullptr, t.partial, t.nblk, j, m, 0.0, 0.0, t.s));
+  WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (j + 3), 2.0 * n * (j + 2),
+            launch_update_normalize<T>(w, V, n, j + 1, n, t.st + 72, t.st + 2, w, t.s));
+}
+
+// Run Arnoldi step j, replaying its CUDA graph (captured at first use) unless
+// per-launch timing is on.
+template <typename T>
+static void arnoldi_step_graph(wt_tank& t, int j, bool pre32) {
+  const int key = sizeof(T) == 4 ? 2 : (pre32 ? 1 : 0);
+  if (!t.use_graphs || t.prof.mask != 0) {
+    arnoldi_step<T>(t, j, pre32);
+    return;
+  }
+  auto& gv = t.graphs[key];
+  if ((int)gv.size() < t.opt.restart) gv.resize(t.opt.restart);
+  IterGraph& g = gv[j];
+  if (!g.exec) {
+    const long l0 = t.prof.launches;
+    cudaGraph_t graph = nullptr;
+    WT_CK(cudaStreamBeginCapture(t.s, cudaStreamCaptureModeThreadLocal));
+    try {
+      arnoldi_step<T>(t, j, pre32);
+    } catch (...) {
+      cudaStreamEndCapture(t.s, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    WT_CK(cudaStreamEndCapture(t.s, &graph));
+    const cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    WT_CK(e);
+    g.kernels = t.prof.launches - l0;
+    t.prof.launches = l0;
+  }
+  WT_CK(cudaGraphLaunch(g.exec, t.s));
+  t.prof.launches += g.kernels;
+}
+
+// Right-preconditioned flexible GMRES(m) on the finest level of precision T:
+// x is the initial guess and the result; returns the last true relative
+// residual ||b - A x|| / bnorm computed in precision T.  With pre32 the
+// preconditioner is the FP32 V-cycle: every Arnoldi step then refines the
+// FP64 iterate with an FP32 correction (flexible Krylov iterative refinement).
 template <typename T>
 double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit, int* its_out,
               bool pre32) {
@@ -309,7 +416,8 @@ double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit,
     apply_op<T>(t, 0, x, V, b, false);                       // r = b - A x -> V_0
     WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n, 2.0 * n,
               launch_dots<T>(V, nullptr, 0, 0, n, t.partial, t.nblk, 1, t.s));
-    WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk, 0.0, launch_gmres_init(t.st, t.partial, t.nblk, m, bnorm, t.s));
+    WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk, 0.0,
+              launch_gmres_init(t.st, t.partial, t.nblk, m, bnorm, tol, t.s));
     WT_CK(cudaMemcpyAsync(t.hst, t.st, sizeof(double) * 6, cudaMemcpyDeviceToHost, t.s));
     WT_CK(cudaStreamSynchronize(t.s));
     rel = bnorm > 0 ? t.hst[0] / bnorm : 0.0;
@@ -317,21 +425,7 @@ double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit,
     WT_LAUNCH(t, K_KRYLOV, 2.0 * sizeof(T) * n, (double)n, launch_scale_copy<T>(V, V, n, t.st + 2, 0, t.s));
     int k = 0;
     for (int j = 0; j < m; ++j) {
-      T* vj = V + (long)j * n;
-      T* zj = Z + (long)j * n;
-      T* w = V + (long)(j + 1) * n;
-      precondition<T>(t, vj, zj, pre32);                     // z_j = M^{-1} v_j
-      apply_op<T>(t, 0, zj, w, nullptr, false);              // w = A z_j
-      WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (j + 2), 2.0 * n * (j + 1),
-                launch_dots<T>(w, V, n, j + 1, n, t.partial, t.nblk, 0, t.s));
-      WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk * (j + 1), 0.0,
-                launch_reduce_partials(t.partial, t.nblk, j + 1, t.st + 8, t.s));
-      WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (j + 3), 4.0 * n * (j + 2),
-                launch_update_dots<T>(w, V, n, j + 1, n, t.st + 8, t.partial, t.nblk, t.s));
-      WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk * (j + 2), 0.0,
-                launch_gmres_arnoldi(t.st, nullptr, t.partial, t.nblk, j, m, bnorm, tol, t.s));
-      WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (j + 3), 2.0 * n * (j + 2),
-                launch_update_normalize<T>(w, V, n, j + 1, n, t.st + 72, t.st + 2, w, t.s));
+      arnoldi_step_graph<T>(t, j, pre32);
       WT_CK(cudaMemcpyAsync(t.hst, t.st, sizeof(double) * 6, cudaMemcpyDeviceToHost, t.s));
       WT_CK(cudaStreamSynchronize(t.s));
       ++its;

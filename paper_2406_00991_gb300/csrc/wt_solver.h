@@ -81,6 +81,9 @@ template <typename T>
 double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit, int* its_out,
               bool pre32);
 
+// Release the captured Arnoldi-step graphs (after option / hierarchy changes).
+void destroy_graphs(wt_tank& t);
+
 // Solve A p = b on the finest level (device pointers, FP64) with the tank's
 // options; x holds the initial guess.  Geometry must be set up already.
 int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_solve_info* info);

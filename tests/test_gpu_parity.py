@@ -73,17 +73,20 @@ def test_levels_match_oracle_hierarchy(wt):
         assert T.levels() == pmg.hierarchy(Nx, Ny, Nz, coarsest_max=64)
 
 
-@pytest.mark.parametrize("Nx,Ny,Nz", [(64, 1, 16), (256, 1, 24), (16, 16, 8)])
-def test_vcycle_parity(wt, Nx, Ny, Nz):
+@pytest.mark.parametrize("tail_max", [0, 8192, 100000])
+@pytest.mark.parametrize("Nx,Ny,Nz", [(64, 1, 16), (256, 1, 24), (1024, 1, 24), (16, 16, 8),
+                                      (32, 32, 12)])
+def test_vcycle_parity(wt, Nx, Ny, Nz, tail_max):
     # same algorithm on both sides (block Jacobi with Nyquist split, omega 0.4,
     # nu1 = nu2 = 2, injected boundary rows, coarsest <= 64 unknowns): the
-    # preconditioned vectors agree to rounding.
+    # preconditioned vectors agree to rounding.  tail_max selects how many
+    # levels run in the single-CTA V-cycle kernel (0: none, 100000: all).
     L = 2 * math.pi
     g, h, ea, eb = curved(Nx, Ny, Nz, L)
     r = np.random.default_rng(3).standard_normal(g.shape)
     levels = pmg.build_levels(Nx, Ny, Nz, L, h, ea, eb, coarsest_max=64)
     ref = pmg.vcycle(levels, 0, np.zeros(g.shape), r, 2, 2, "jacobi", 0.4, "inject")
-    T = wt.Tank(Nx, Ny, Nz, L, h)
+    T = wt.Tank(Nx, Ny, Nz, L, h, tail_max=tail_max)
     got = T.precondition(ea, eb, r, wt.WT_FP64)
     scale = np.abs(ref).max()
     assert np.abs(got - ref).max() <= 1e-9 * scale
