@@ -206,6 +206,30 @@ int wt_profile_read(wt_tank* t, int kernel_class, double* ms, long* launches, do
                     double* flops);
 int wt_get_launches(const wt_tank* t, long* launches);
 
+/*
+ * Allocation-free operator apply (the paper has no counterpart; this is a
+ * deployment variant of wt_apply_operator).  For callers that cannot call
+ * cudaMalloc - code living inside another framework's memory pool, an
+ * embedded solver that only ever receives buffers, a process whose device
+ * footprint is fixed after start-up - this entry point needs no tank and
+ * allocates nothing: all temporaries live in one file-scope __device__ array
+ * of 2.5 MiB that every GPU loading the library holds until exit.
+ * Computes Ap = A_{a,b} p of a 2D tank (Ny = 1) in FP64, the same result as
+ * wt_apply_operator(..., WT_FP64), with the same kernels.
+ *   Nx: power of two in [4, 2048]; Nz in [2, 32] (limit of the static array;
+ *   larger sizes return WT_EINVAL).  L: domain length.
+ *   h, eta_a, eta_b: device arrays [Nx]; p, Ap: device arrays [Nz+1][Nx]
+ *   (host pointers return WT_EINVAL).  stream: cudaStream_t or NULL.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it: make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents, so calls that overlap on the GPU (different streams or threads)
+ * race; serialise them.  Returns after Ap is complete; WT_EBREAK when
+ * h + eta <= 0 or a value is not finite.
+ */
+int wt_apply_operator_static(int Nx, int Nz, double L, const double* h, const double* eta_a,
+                             const double* eta_b, const double* p, double* Ap, void* stream);
+
 /* Release every resource of the tank.  t may be NULL. */
 int wt_destroy(wt_tank* t);
 

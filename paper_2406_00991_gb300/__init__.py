@@ -68,6 +68,7 @@ def _load():
         "wt_profile_read": [P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long),
                             ctypes.POINTER(D), ctypes.POINTER(D)],
         "wt_get_launches": [P, ctypes.POINTER(ctypes.c_long)],
+        "wt_apply_operator_static": [I, I, D, P, P, P, P, P, P],
         "wt_last_error": [ctypes.c_char_p, ctypes.c_size_t],
     }
     for name, args in sig.items():
@@ -223,6 +224,12 @@ def wt_profile_read(t, kernel_class):
     st = _lib.wt_profile_read(t, int(kernel_class), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b),
                               ctypes.byref(f))
     return st, ms.value, n.value, b.value, f.value
+
+
+def wt_apply_operator_static(Nx, Nz, L, h, eta_a, eta_b, p, Ap, stream_handle=0):
+    """Allocation-free 2D FP64 operator apply; every array must be a CUDA tensor."""
+    return _lib.wt_apply_operator_static(int(Nx), int(Nz), float(L), _ptr(h), _ptr(eta_a), _ptr(eta_b),
+                                         _ptr(p), _ptr(Ap), ctypes.c_void_p(int(stream_handle)))
 
 
 def wt_get_launches(t):

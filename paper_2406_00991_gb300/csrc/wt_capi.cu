@@ -438,6 +438,8 @@ int rk_stage(wt_tank& t, int k, double dt) {
 
 }  // namespace
 
+int wt::set_error(int code, const char* msg) { return fail(code, msg); }
+
 // ====================================================================== C ABI
 extern "C" {
 

@@ -54,6 +54,9 @@ struct LevelView {
 // {00, N0, 0N, NN} (x-Nyquist, y-Nyquist, both).
 constexpr int kMaxClasses = 4;
 
+// Record the calling thread's last error for wt_last_error (wt_capi.cu).
+int set_error(int code, const char* msg);
+
 // ------------------------------------------------------------------ launchers
 // All launchers enqueue on `s` and return cudaGetLastError().
 
