@@ -179,6 +179,33 @@ int wt_step(wt_tank* t, double dt, int nsteps);
 int wt_get_stats(const wt_tank* t, long* solves, long* iterations);
 
 /*
+ * Batches of independent 2D tanks of uneven size, advanced together by one
+ * persistent kernel launch per wt_batch_step: one CTA owns one tank and runs
+ * all of its Runge-Kutta stages (free surface, metric, smoother set-up,
+ * forcing, mixed-stage Poisson solve with FP64 flexible GMRES and the FP32
+ * p-multigrid V-cycle, projection); the largest tanks start first.
+ * wt_create_batch: tank i has Nx[i], Nz[i], L[i] and bathymetry[i] ([Nx[i]],
+ * host or device), Ny = 1; g and nu as in wt_create.  Each tank's coarsest
+ * level must have at most 64 unknowns.  The batch owns its tanks.
+ * wt_batch_set_options applies one option set to every tank (WT_MIXED only).
+ * wt_batch_set_state / get_state: tank i's eta [Nx], u, w [Nz+1][Nx].
+ * wt_batch_step: nsteps full steps, dt[i] for tank i (host array); returns
+ * after all tanks finished; WT_EBREAK / WT_ENOCONV if any tank failed.
+ * wt_batch_stats: solves, Krylov iterations and the last relative residual of
+ * tank i (accumulated over all wt_batch_step calls).
+ */
+typedef struct wt_batch wt_batch;
+int wt_create_batch(int ntanks, const int* Nx, const int* Nz, const double* L, double g, double nu,
+                    const double* const* bathymetry, wt_batch** out);
+int wt_batch_set_options(wt_batch* b, const wt_options* opt);
+int wt_batch_set_state(wt_batch* b, int i, const double* eta, const double* u, const double* w,
+                       double time);
+int wt_batch_get_state(const wt_batch* b, int i, double* eta, double* u, double* w, double* time);
+int wt_batch_step(wt_batch* b, const double* dt, int nsteps);
+int wt_batch_stats(const wt_batch* b, int i, long* solves, long* iterations, double* last_rel);
+int wt_batch_destroy(wt_batch* b);
+
+/*
  * Launch accounting and kernel timing (no counterpart in the paper; used to
  * measure the kernels against the GB300 roofline).  Kernel classes:
  *   WT_K_ROWPASS  spectral x-row / y-line passes (FFT derivative, resampling,

@@ -69,6 +69,14 @@ def _load():
                             ctypes.POINTER(D), ctypes.POINTER(D)],
         "wt_get_launches": [P, ctypes.POINTER(ctypes.c_long)],
         "wt_apply_operator_static": [I, I, D, P, P, P, P, P, P],
+        "wt_create_batch": [I, P, P, P, D, D, P, ctypes.POINTER(P)],
+        "wt_batch_set_options": [P, ctypes.POINTER(wt_options)],
+        "wt_batch_set_state": [P, I, P, P, P, D],
+        "wt_batch_get_state": [P, I, P, P, P, ctypes.POINTER(D)],
+        "wt_batch_step": [P, P, I],
+        "wt_batch_stats": [P, I, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long),
+                           ctypes.POINTER(D)],
+        "wt_batch_destroy": [P],
         "wt_last_error": [ctypes.c_char_p, ctypes.c_size_t],
     }
     for name, args in sig.items():
@@ -232,6 +240,49 @@ def wt_apply_operator_static(Nx, Nz, L, h, eta_a, eta_b, p, Ap, stream_handle=0)
                                          _ptr(p), _ptr(Ap), ctypes.c_void_p(int(stream_handle)))
 
 
+def wt_create_batch(Nx, Nz, L, bathymetry, g=9.81, nu=0.0):
+    """Batch of 2D tanks; bathymetry is a list of float64 arrays (host or device)."""
+    n = len(Nx)
+    nx = np.ascontiguousarray(Nx, dtype=np.int32)
+    nz = np.ascontiguousarray(Nz, dtype=np.int32)
+    ll = np.ascontiguousarray(L, dtype=np.float64)
+    hp = (ctypes.c_void_p * n)(*[_ptr(h).value for h in bathymetry])
+    b = ctypes.c_void_p()
+    st = _lib.wt_create_batch(n, nx.ctypes.data_as(ctypes.c_void_p), nz.ctypes.data_as(ctypes.c_void_p),
+                              ll.ctypes.data_as(ctypes.c_void_p), g, nu, ctypes.cast(hp, ctypes.c_void_p),
+                              ctypes.byref(b))
+    return st, b
+
+
+def wt_batch_set_options(b, o):
+    return _lib.wt_batch_set_options(b, ctypes.byref(o))
+
+
+def wt_batch_set_state(b, i, eta, u, w, time=0.0):
+    return _lib.wt_batch_set_state(b, int(i), _ptr(eta), _ptr(u), _ptr(w), float(time))
+
+
+def wt_batch_get_state(b, i, eta, u, w):
+    tm = ctypes.c_double()
+    st = _lib.wt_batch_get_state(b, int(i), _ptr(eta), _ptr(u), _ptr(w), ctypes.byref(tm))
+    return st, tm.value
+
+
+def wt_batch_step(b, dt, nsteps):
+    d = np.ascontiguousarray(dt, dtype=np.float64)
+    return _lib.wt_batch_step(b, d.ctypes.data_as(ctypes.c_void_p), int(nsteps))
+
+
+def wt_batch_stats(b, i):
+    s, it, r = ctypes.c_long(), ctypes.c_long(), ctypes.c_double()
+    st = _lib.wt_batch_stats(b, int(i), ctypes.byref(s), ctypes.byref(it), ctypes.byref(r))
+    return st, s.value, it.value, r.value
+
+
+def wt_batch_destroy(b):
+    return _lib.wt_batch_destroy(b)
+
+
 def wt_get_launches(t):
     n = ctypes.c_long()
     st = _lib.wt_get_launches(t, ctypes.byref(n))
@@ -355,6 +406,65 @@ class Tank:
     def close(self):
         if getattr(self, "handle", None) is not None:
             wt_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owning wrapper of a wt_batch handle: independent 2D tanks of uneven
+    size advanced together by one persistent kernel launch per ``step``."""
+
+    def __init__(self, Nx, Nz, L, bathymetry, g=9.81, nu=0.0, **options):
+        self.Nx = [int(v) for v in Nx]
+        self.Nz = [int(v) for v in Nz]
+        self.L = [float(v) for v in L]
+        hs = [h if hasattr(h, "data_ptr") else np.ascontiguousarray(h, dtype=np.float64)
+              for h in bathymetry]
+        st, b = wt_create_batch(self.Nx, self.Nz, self.L, hs, g, nu)
+        _check(st)
+        self.handle = b
+        if options:
+            self.set_options(**options)
+
+    def __len__(self):
+        return len(self.Nx)
+
+    def set_options(self, **kw):
+        o = wt_default_options()
+        for k, v in kw.items():
+            if k not in dict(wt_options._fields_):
+                raise KeyError(k)
+            setattr(o, k, v)
+        _check(wt_batch_set_options(self.handle, o))
+
+    def set_state(self, i, eta, u, w, time=0.0):
+        _check(wt_batch_set_state(self.handle, i, eta, u, w, time))
+
+    def get_state(self, i):
+        M1, Nx = self.Nz[i] + 1, self.Nx[i]
+        eta = np.zeros((1, Nx))
+        u, w = np.zeros((M1, 1, Nx)), np.zeros((M1, 1, Nx))
+        st, tm = wt_batch_get_state(self.handle, i, eta, u, w)
+        _check(st)
+        return eta, u, w, tm
+
+    def step(self, dt, nsteps=1):
+        dt = np.broadcast_to(np.asarray(dt, dtype=np.float64), (len(self),))
+        _check(wt_batch_step(self.handle, dt, nsteps))
+
+    def stats(self, i):
+        st, s, it, r = wt_batch_stats(self.handle, i)
+        _check(st)
+        return s, it, r
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            wt_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -250,6 +250,7 @@ void build_hierarchy(wt_tank& t) {
         v[l].Binv = L.Binv;
         v[l].rhoX = L.rhoX; v[l].rhoY = L.rhoY; v[l].rhoXY = L.rhoXY;
         v[l].Rsig = L.Rsig; v[l].Psig = L.Psig;
+        v[l].nclass = L.nclass; v[l].cxx = L.cxx; v[l].cyy = L.cyy;
       }
     };
     fill(d64, t.L64, t.tw64);
@@ -258,6 +259,11 @@ void build_hierarchy(wt_tank& t) {
     t.tl32 = t.har.alloc<TailLevel<float>>(nl);
     WT_CK(cudaMemcpy(t.tl64, d64.data(), sizeof(TailLevel<double>) * nl, cudaMemcpyHostToDevice));
     WT_CK(cudaMemcpy(t.tl32, d32.data(), sizeof(TailLevel<float>) * nl, cudaMemcpyHostToDevice));
+    std::vector<SurfDesc> sd(nl);
+    for (int l = 0; l < nl; ++l)
+      sd[l] = SurfDesc{t.S[l].h, t.S[l].hx, t.S[l].ea, t.S[l].eax, t.S[l].eb, t.S[l].ebx, t.S[l].tmp};
+    t.sd = t.har.alloc<SurfDesc>(nl);
+    WT_CK(cudaMemcpy(t.sd, sd.data(), sizeof(SurfDesc) * nl, cudaMemcpyHostToDevice));
   }
   auto [cx, cy, cz] = t.dims.back();
   t.ncoarse = cx * cy * (cz + 1);
@@ -820,6 +826,188 @@ int wt_profile_read(wt_tank* t, int k, double* ms, long* launches, double* bytes
 int wt_get_launches(const wt_tank* t, long* launches) {
   if (!t || !launches) return fail(WT_EINVAL, "NULL argument");
   *launches = t->prof.launches;
+  return WT_OK;
+}
+
+// ================================================================ batches
+}  // extern "C"
+
+struct wt_batch {
+  std::vector<wt_tank*> tanks;
+  wt::Arena ar;
+  wt::BatchTankDesc* d_desc = nullptr;
+  int* d_order = nullptr;
+  double* d_dt = nullptr;
+  double* d_stats = nullptr;      // 4 doubles per tank
+  cudaStream_t s = nullptr;
+  int smem = 96 * 1024;
+  std::vector<int> order;
+};
+
+namespace {
+void fill_desc(wt_batch& b) {
+  const int nt = (int)b.tanks.size();
+  std::vector<BatchTankDesc> d(nt);
+  for (int i = 0; i < nt; ++i) {
+    wt_tank& t = *b.tanks[i];
+    BatchTankDesc& D = d[i];
+    D.nl = (int)t.L64.size();
+    D.Nx = t.Nx; D.logNx = ilog2(t.Nx); D.Nz = t.Nz; D.M1 = t.M1; D.ncols = t.ncols; D.n = t.n;
+    D.L = t.L; D.g = t.g;
+    D.lv32 = t.tl32; D.lv64 = t.tl64; D.S = t.sd;
+    D.AinvT = t.cLU; D.cDx = t.cDx; D.cDy = t.cDy;
+    D.V64 = t.V64; D.Z64 = t.Z64; D.b32 = t.b32; D.e32 = t.e32;
+    D.eta = t.eta; D.eta_new = t.eta_new; D.Keta = t.Keta; D.f_eta = t.f_eta; D.eta_x = t.eta_x;
+    D.u = t.u; D.w = t.w; D.Ku = t.Ku; D.Kw = t.Kw; D.p = t.p; D.zero_s = t.zero_s;
+    for (int k = 0; k < 18; ++k) D.work[k] = t.work[k];
+    D.filt_x = t.filt_x; D.Fcheb = t.Fcheb;
+    D.flag = t.dflag;
+    D.stats = b.d_stats + 4 * i;
+    D.tol = t.opt.tol; D.omega = t.opt.omega;
+    D.nu1 = t.opt.nu1; D.nu2 = t.opt.nu2; D.restart = t.opt.restart; D.max_it = t.opt.max_it;
+    D.filter = t.opt.filter; D.linear = t.opt.linear;
+  }
+  WT_CK(cudaMemcpy(b.d_desc, d.data(), sizeof(BatchTankDesc) * nt, cudaMemcpyHostToDevice));
+}
+
+// Everything one CTA stages in its dynamic shared memory must fit in smem
+// bytes: an FP64 row pair of the finest level without prefetch (two complex
+// rows plus half a row of twiddles), the coarsest dense inverse, one block of
+// the smoother per warp.
+int check_batch_tank(const wt_tank& t, int smem) {
+  if (t.Ny != 1) return fail(WT_EINVAL, "batched tanks are 2D (Ny = 1)");
+  if (t.opt.mode != WT_MIXED) return fail(WT_ENOTSUP, "batched tanks run the mixed solver only");
+  const size_t row = (2 * (size_t)t.Nx + t.Nx / 2) * 2 * sizeof(double);
+  const size_t coarse = (size_t)t.ncoarse * (t.ncoarse + 1) * sizeof(double) + (t.ncoarse + 1) * sizeof(int);
+  const size_t blk = (size_t)t.M1 * (2 * t.M1 + 1) * sizeof(float);
+  if (row > (size_t)smem) return fail(WT_ENOTSUP, "batched tanks need Nx <= 2048");
+  if (coarse > (size_t)smem) return fail(WT_ENOTSUP, "batched tank's coarsest level is too large (coarsest_max)");
+  if (blk > (size_t)smem) return fail(WT_ENOTSUP, "batched tank's Nz is too large");
+  return WT_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int wt_create_batch(int ntanks, const int* Nx, const int* Nz, const double* L, double g, double nu,
+                    const double* const* bathymetry, wt_batch** out) {
+  if (!out || !Nx || !Nz || !L || !bathymetry) return fail(WT_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (ntanks < 1 || ntanks > 65535) return fail(WT_EINVAL, "ntanks must be in [1, 65535]");
+  std::unique_ptr<wt_batch> b(new wt_batch());
+  for (int i = 0; i < ntanks; ++i) {
+    wt_tank* t = nullptr;
+    const int st = wt_create(Nx[i], 1, Nz[i], L[i], g, nu, bathymetry[i], &t);
+    if (st != WT_OK) {
+      for (wt_tank* q : b->tanks) wt_destroy(q);
+      return st;
+    }
+    b->tanks.push_back(t);
+    const int c = check_batch_tank(*t, b->smem);
+    if (c != WT_OK) {
+      for (wt_tank* q : b->tanks) wt_destroy(q);
+      return c;
+    }
+  }
+  const int rc = guarded([&]() -> int {
+    WT_CK(cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking));
+    b->d_desc = b->ar.alloc<BatchTankDesc>(ntanks);
+    b->d_order = b->ar.alloc<int>(ntanks);
+    b->d_dt = b->ar.alloc<double>(ntanks);
+    b->d_stats = b->ar.alloc<double>(4 * (size_t)ntanks);
+    WT_CK(cudaMemset(b->d_stats, 0, sizeof(double) * 4 * ntanks));
+    // longest-processing-time first: largest tanks take the first CTAs
+    b->order.resize(ntanks);
+    for (int i = 0; i < ntanks; ++i) b->order[i] = i;
+    std::stable_sort(b->order.begin(), b->order.end(),
+                     [&](int x, int y) { return b->tanks[x]->n > b->tanks[y]->n; });
+    WT_CK(cudaMemcpy(b->d_order, b->order.data(), sizeof(int) * ntanks, cudaMemcpyHostToDevice));
+    fill_desc(*b);
+    return WT_OK;
+  });
+  if (rc != WT_OK) {
+    for (wt_tank* q : b->tanks) wt_destroy(q);
+    if (b->s) cudaStreamDestroy(b->s);
+    return rc;
+  }
+  *out = b.release();
+  return WT_OK;
+}
+
+int wt_batch_set_options(wt_batch* b, const wt_options* o) {
+  if (!b || !o) return fail(WT_EINVAL, "NULL argument");
+  if (o->mode != WT_MIXED) return fail(WT_ENOTSUP, "batched tanks run the mixed solver only");
+  for (wt_tank* t : b->tanks) {
+    const int st = wt_set_options(t, o);
+    if (st != WT_OK) return st;
+    const int c = check_batch_tank(*t, b->smem);
+    if (c != WT_OK) return c;
+  }
+  return guarded([&]() -> int {
+    fill_desc(*b);
+    return WT_OK;
+  });
+}
+
+int wt_batch_set_state(wt_batch* b, int i, const double* eta, const double* u, const double* w,
+                       double time) {
+  if (!b || i < 0 || i >= (int)b->tanks.size()) return fail(WT_EINVAL, "tank index out of range");
+  return wt_set_state(b->tanks[i], eta, u, nullptr, w, time);
+}
+
+int wt_batch_get_state(const wt_batch* b, int i, double* eta, double* u, double* w, double* time) {
+  if (!b || i < 0 || i >= (int)b->tanks.size()) return fail(WT_EINVAL, "tank index out of range");
+  return wt_get_state(b->tanks[i], eta, u, nullptr, w, time);
+}
+
+int wt_batch_step(wt_batch* b, const double* dt, int nsteps) {
+  if (!b || !dt) return fail(WT_EINVAL, "NULL argument");
+  if (nsteps < 0) return fail(WT_EINVAL, "nsteps must be >= 0");
+  const int nt = (int)b->tanks.size();
+  for (int i = 0; i < nt; ++i) {
+    if (!(dt[i] > 0) || !std::isfinite(dt[i])) return fail(WT_EINVAL, "dt must be positive");
+    if (!b->tanks[i]->have_state) return fail(WT_EINVAL, "tank without state: call wt_batch_set_state");
+  }
+  if (nsteps == 0) return WT_OK;
+  return guarded([&]() -> int {
+    fill_desc(*b);
+    for (wt_tank* t : b->tanks) WT_CK(cudaStreamSynchronize(t->s));   // pending state uploads
+    WT_CK(cudaMemcpyAsync(b->d_dt, dt, sizeof(double) * nt, cudaMemcpyHostToDevice, b->s));
+    WT_CK(launch_batch_step(b->d_desc, b->d_order, nt, b->d_dt, nsteps, b->smem, b->s));
+    WT_CK(cudaStreamSynchronize(b->s));
+    int bad = 0;
+    for (int i = 0; i < nt; ++i) {
+      wt_tank& t = *b->tanks[i];
+      t.time += nsteps * dt[i];
+      t.prof.launches += 1;
+      const int f = read_flags(t);
+      if (f & 15) bad |= 1;
+      if (f & 16) bad |= 2;
+    }
+    if (bad & 1) return fail(WT_EBREAK, "a batched tank has depth <= 0 or a non-finite state");
+    if (bad & 2) return fail(WT_ENOCONV, "a batched pressure solve stopped above its tolerance");
+    return WT_OK;
+  });
+}
+
+int wt_batch_stats(const wt_batch* b, int i, long* solves, long* iterations, double* last_rel) {
+  if (!b || i < 0 || i >= (int)b->tanks.size()) return fail(WT_EINVAL, "tank index out of range");
+  return guarded([&]() -> int {
+    double s[4];
+    WT_CK(cudaMemcpy(s, b->d_stats + 4 * i, sizeof(s), cudaMemcpyDeviceToHost));
+    if (solves) *solves = (long)s[0];
+    if (iterations) *iterations = (long)s[1];
+    if (last_rel) *last_rel = s[2];
+    return WT_OK;
+  });
+}
+
+int wt_batch_destroy(wt_batch* b) {
+  if (!b) return WT_OK;
+  if (b->s) cudaStreamSynchronize(b->s);
+  for (wt_tank* t : b->tanks) wt_destroy(t);
+  if (b->s) cudaStreamDestroy(b->s);
+  delete b;
   return WT_OK;
 }
 

@@ -44,98 +44,11 @@ __global__ void __launch_bounds__(256) k_col_matrix(const T* __restrict__ M, int
   colmat_body<T>(M, Mo, Mi, in, out, ncols, accumulate, blockIdx.x, gridDim.x, smraw);
 }
 
-// Diagonal column block of A_{a,b} (the same expression the oracle pins
-// against its dense assembly): interior rows
-//   cdiag I + (sx_a AX_b + sy_a AY_b + Z_a Z_b) D^2 - (sx_a BX_b + sy_a BY_b) D diag(sigma) D,
-// surface row e_0, bottom row (h_x sx_b + h_y sy_b + Z_b) D[Nz, :].
 template <typename T>
 __global__ void __launch_bounds__(128) k_block_inverse(LevelView<T> L, T* __restrict__ Binv,
                                                        int nclass, T cxx, T cyy, int* flag) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int M1 = L.M1;
-  const int W = 2 * M1 + 1;                 // padded row of the augmented matrix
-  T* A = reinterpret_cast<T*>(smraw) + (threadIdx.x >> 5) * (M1 * W);
-  const int lane = threadIdx.x & 31;
-  const int warps_total = gridDim.x * (blockDim.x >> 5);
-  const long nc = L.ncols;
-  const long blk = (long)M1 * M1;
-  for (long task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); task < nc * nclass;
-       task += warps_total) {
-    const int c = (int)(task % nc), cls = (int)(task / nc);
-    const int ix = cls & 1, iy = (cls >> 1) & 1;
-    const T cdiag = (ix ? T(0) : cxx) + (iy ? T(0) : cyy);
-    const T* meta = L.meta;
-    const T AXa = meta[M_AXa * nc + c], BXa = meta[M_BXa * nc + c];
-    const T AYa = meta[M_AYa * nc + c], BYa = meta[M_BYa * nc + c];
-    const T AXb = meta[M_AXb * nc + c], BXb = meta[M_BXb * nc + c];
-    const T AYb = meta[M_AYb * nc + c], BYb = meta[M_BYb * nc + c];
-    const T Za = meta[M_Za * nc + c], Zb = meta[M_Zb * nc + c];
-    const T HX = meta[M_HX * nc + c], HY = meta[M_HY * nc + c];
-    const T sbot = L.sigma[M1 - 1];
-    const T cbot = HX * (AXb - sbot * BXb) + HY * (AYb - sbot * BYb) + Zb;
-    for (int i = lane; i < M1 * M1; i += 32) {
-      const int m = i / M1, k = i - m * M1;
-      T v;
-      if (m == 0) {
-        v = (k == 0) ? T(1) : T(0);
-      } else if (m == M1 - 1) {
-        v = cbot * L.D[m * M1 + k];
-      } else {
-        const T s = L.sigma[m];
-        const T sxa = AXa - s * BXa, sya = AYa - s * BYa;
-        v = (sxa * AXb + sya * AYb + Za * Zb) * L.D2[m * M1 + k] -
-            (sxa * BXb + sya * BYb) * L.DSD[m * M1 + k];
-        if (m == k) v += cdiag;
-      }
-      A[m * W + k] = v;
-      A[m * W + M1 + k] = (m == k) ? T(1) : T(0);
-    }
-    __syncwarp();
-    bool bad = false;
-    for (int piv = 0; piv < M1; ++piv) {
-      // pivot search over rows piv..M1-1
-      T best = T(-1);
-      int bi = piv;
-      for (int i = piv + lane; i < M1; i += 32) {
-        const T a = fabs(A[i * W + piv]);
-        if (a > best) { best = a; bi = i; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (!(best > T(0)) || !isfinite(best)) { bad = true; break; }
-      if (bi != piv) {
-        for (int j = lane; j < 2 * M1; j += 32) {
-          const T t0 = A[piv * W + j];
-          A[piv * W + j] = A[bi * W + j];
-          A[bi * W + j] = t0;
-        }
-      }
-      __syncwarp();
-      const T inv = T(1) / A[piv * W + piv];
-      __syncwarp();
-      for (int j = lane; j < 2 * M1; j += 32) A[piv * W + j] *= inv;
-      __syncwarp();
-      for (int i = lane; i < M1; i += 32) {
-        if (i == piv) continue;
-        const T f = A[i * W + piv];
-        if (f != T(0)) {
-          for (int j = 0; j < 2 * M1; ++j) A[i * W + j] -= f * A[piv * W + j];
-        }
-      }
-      __syncwarp();
-    }
-    if (bad) {
-      if (lane == 0) atomicOr(flag, 1);
-    }
-    for (int i = lane; i < M1 * M1; i += 32) {   // i = k * M1 + m: coalesced stores
-      const int k = i / M1, m = i - k * M1;
-      Binv[((long)c * nclass + cls) * blk + i] = bad ? T(0) : A[m * W + M1 + k];
-    }
-    __syncwarp();
-  }
+  blockinv_body<T>(L, Binv, nclass, cxx, cyy, flag, blockIdx.x, gridDim.x, 4, smraw);
 }
 
 // ------------------------------------------------------------------ launchers

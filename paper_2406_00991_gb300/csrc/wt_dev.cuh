@@ -114,7 +114,7 @@ template <typename T>
 __host__ __device__ inline size_t rowpass_smem(const RowPass<T>& a, int ppc) {
   const int Nmax = a.Nin > a.Nout ? a.Nin : a.Nout;
   const int S = Nmax + (a.ylines ? 1 : 0);
-  const int nepi = (a.epi == EPI_ADD || a.epi == EPI_ACC) ? 1 : (a.epi == EPI_RESID ? 2 : 0);
+  const int nepi = !a.prefetch ? 0 : (a.epi == EPI_ADD || a.epi == EPI_ACC) ? 1 : (a.epi == EPI_RESID ? 2 : 0);
   return ((2 + nepi) * (size_t)ppc * S + (size_t)(Nmax / 2)) * sizeof(c2_t<T>);
 }
 
@@ -128,8 +128,8 @@ __device__ void rowpass_body(const RowPass<T>& a, int ppc, int u0, int ustep, un
   const int Nmax = a.Nin > a.Nout ? a.Nin : a.Nout;
   const int logNmax = a.Nin > a.Nout ? a.logNin : a.logNout;
   const int S = Nmax + (a.ylines ? 1 : 0);
-  const bool use_add = a.epi == EPI_ADD || a.epi == EPI_RESID;
-  const bool use_rhs = a.epi == EPI_RESID || a.epi == EPI_ACC;
+  const bool use_add = a.prefetch && (a.epi == EPI_ADD || a.epi == EPI_RESID);
+  const bool use_rhs = a.prefetch && (a.epi == EPI_RESID || a.epi == EPI_ACC);
   c2* buf0 = reinterpret_cast<c2*>(smraw);
   c2* buf1 = buf0 + ppc * S;
   c2* tws = buf1 + ppc * S;
@@ -206,18 +206,29 @@ __device__ void rowpass_body(const RowPass<T>& a, int ppc, int u0, int ustep, un
       const long o0 = row_offset(a, r0, j, a.Nout);
       const long o1 = row_offset(a, r1, j, a.Nout);
       const bool has1 = r1 < a.nrows;
-      if (a.epi == EPI_ADD) {
-        const c2 ad = eA[q * S + j];
-        v0 += ad.x;
-        v1 += ad.y;
+      if (a.prefetch) {
+        if (a.epi == EPI_ADD) {
+          const c2 ad = eA[q * S + j];
+          v0 += ad.x;
+          v1 += ad.y;
+        } else if (a.epi == EPI_RESID) {
+          const c2 ad = eA[q * S + j], rh = eB[q * S + j];
+          v0 = rh.x - (ad.x + v0);
+          v1 = rh.y - (ad.y + v1);
+        } else if (a.epi == EPI_ACC) {
+          const c2 ol = eB[q * S + j];
+          v0 += ol.x;
+          v1 += ol.y;
+        }
+      } else if (a.epi == EPI_ADD) {
+        v0 += a.add[o0];
+        if (has1) v1 += a.add[o1];
       } else if (a.epi == EPI_RESID) {
-        const c2 ad = eA[q * S + j], rh = eB[q * S + j];
-        v0 = rh.x - (ad.x + v0);
-        v1 = rh.y - (ad.y + v1);
+        v0 = a.rhs[o0] - (a.add[o0] + v0);
+        if (has1) v1 = a.rhs[o1] - (a.add[o1] + v1);
       } else if (a.epi == EPI_ACC) {
-        const c2 ol = eB[q * S + j];
-        v0 += ol.x;
-        v1 += ol.y;
+        v0 += a.out[o0];
+        if (has1) v1 += a.out[o1];
       }
       a.out[o0] = v0;
       if (has1) a.out[o1] = v1;
@@ -464,6 +475,408 @@ __device__ void nyquist_body(const T* WT_DEV_RESTRICT r, int nrows, int N, T* WT
     for (int j = lane; j < N; j += 32) s += ((j & 1) ? T(-1) : T(1)) * r[(long)row * N + j];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) rho[row] = s / T(N);
+  }
+}
+
+// Diagonal column block of A_{a,b} (the same expression the oracle pins
+// against its dense assembly): interior rows
+//   cdiag I + (sx_a AX_b + sy_a AY_b + Z_a Z_b) D^2 - (sx_a BX_b + sy_a BY_b) D diag(sigma) D,
+// surface row e_0, bottom row (h_x sx_b + h_y sy_b + Z_b) D[Nz, :].
+// One warp per (column, class) task; `wmax` warps of the CTA take part (each
+// needs M1 x (2 M1 + 1) values of shared memory), CTA u0 of ustep.
+template <typename T>
+__device__ void blockinv_body(const LevelView<T>& L, T* WT_DEV_RESTRICT Binv, int nclass, T cxx,
+                              T cyy, int* flag, int u0, int ustep, int wmax, unsigned char* smraw) {
+  const int M1 = L.M1;
+  const int W = 2 * M1 + 1;                 // padded row of the augmented matrix
+  const int wib = threadIdx.x >> 5;
+  const int nw = min((int)(blockDim.x >> 5), wmax);
+  T* A = reinterpret_cast<T*>(smraw) + wib * (M1 * W);
+  const int lane = threadIdx.x & 31;
+  const long nc = L.ncols;
+  const long blk = (long)M1 * M1;
+  if (wib >= nw) return;
+  for (long task = (long)u0 * nw + wib; task < nc * nclass; task += (long)ustep * nw) {
+    const int c = (int)(task % nc), cls = (int)(task / nc);
+    const int ix = cls & 1, iy = (cls >> 1) & 1;
+    const T cdiag = (ix ? T(0) : cxx) + (iy ? T(0) : cyy);
+    const T* meta = L.meta;
+    const T AXa = meta[M_AXa * nc + c], BXa = meta[M_BXa * nc + c];
+    const T AYa = meta[M_AYa * nc + c], BYa = meta[M_BYa * nc + c];
+    const T AXb = meta[M_AXb * nc + c], BXb = meta[M_BXb * nc + c];
+    const T AYb = meta[M_AYb * nc + c], BYb = meta[M_BYb * nc + c];
+    const T Za = meta[M_Za * nc + c], Zb = meta[M_Zb * nc + c];
+    const T HX = meta[M_HX * nc + c], HY = meta[M_HY * nc + c];
+    const T sbot = L.sigma[M1 - 1];
+    const T cbot = HX * (AXb - sbot * BXb) + HY * (AYb - sbot * BYb) + Zb;
+    for (int i = lane; i < M1 * M1; i += 32) {
+      const int m = i / M1, k = i - m * M1;
+      T v;
+      if (m == 0) {
+        v = (k == 0) ? T(1) : T(0);
+      } else if (m == M1 - 1) {
+        v = cbot * L.D[m * M1 + k];
+      } else {
+        const T s = L.sigma[m];
+        const T sxa = AXa - s * BXa, sya = AYa - s * BYa;
+        v = (sxa * AXb + sya * AYb + Za * Zb) * L.D2[m * M1 + k] -
+            (sxa * BXb + sya * BYb) * L.DSD[m * M1 + k];
+        if (m == k) v += cdiag;
+      }
+      A[m * W + k] = v;
+      A[m * W + M1 + k] = (m == k) ? T(1) : T(0);
+    }
+    __syncwarp();
+    bool bad = false;
+    for (int piv = 0; piv < M1; ++piv) {
+      // pivot search over rows piv..M1-1
+      T best = T(-1);
+      int bi = piv;
+      for (int i = piv + lane; i < M1; i += 32) {
+        const T a = fabs(A[i * W + piv]);
+        if (a > best) { best = a; bi = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (!(best > T(0)) || !isfinite(best)) { bad = true; break; }
+      if (bi != piv) {
+        for (int j = lane; j < 2 * M1; j += 32) {
+          const T t0 = A[piv * W + j];
+          A[piv * W + j] = A[bi * W + j];
+          A[bi * W + j] = t0;
+        }
+      }
+      __syncwarp();
+      const T inv = T(1) / A[piv * W + piv];
+      __syncwarp();
+      for (int j = lane; j < 2 * M1; j += 32) A[piv * W + j] *= inv;
+      __syncwarp();
+      for (int i = lane; i < M1; i += 32) {
+        if (i == piv) continue;
+        const T f = A[i * W + piv];
+        if (f != T(0)) {
+          for (int j = 0; j < 2 * M1; ++j) A[i * W + j] -= f * A[piv * W + j];
+        }
+      }
+      __syncwarp();
+    }
+    if (bad) {
+      if (lane == 0) atomicOr(flag, 1);
+    }
+    for (int i = lane; i < M1 * M1; i += 32) {   // i = k * M1 + m: coalesced stores
+      const int k = i / M1, m = i - k * M1;
+      Binv[((long)c * nclass + cls) * blk + i] = bad ? T(0) : A[m * W + M1 + k];
+    }
+    __syncwarp();
+  }
+}
+
+// Assemble the dense A_{a,b} of the coarsest level and invert it in shared
+// memory (one CTA; n (n + 1) doubles + n + 1 ints of shared memory).
+__device__ inline void coarse_factor_body(const LevelView<double>& L, const double* WT_DEV_RESTRICT Dx,
+                                          const double* WT_DEV_RESTRICT Dy, double* WT_DEV_RESTRICT LUout,
+                                          int* flag, unsigned char* smraw) {
+  const int Nx = L.Nx, Ny = L.Ny, M1 = L.M1;
+  const int n = M1 * Ny * Nx;
+  const int ld = n + 1;
+  double* A = reinterpret_cast<double*>(smraw);
+  int* perm = reinterpret_cast<int*>(A + (size_t)n * ld);
+  int& spiv = perm[n];
+  const double* Dxx = Dx + Nx * Nx;
+  const double* Dyy = Dy + Ny * Ny;
+  const long nc = L.ncols;
+  const double* meta = L.meta;
+  const double* D = L.D;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - i * n;
+    const int m = i / (Ny * Nx), y = (i / Nx) % Ny, x = i % Nx;
+    const int mp = j / (Ny * Nx), yp = (j / Nx) % Ny, xp = j % Nx;
+    const int c = y * Nx + x;
+    const bool sy_ = (y == yp), sx_ = (x == xp), sm_ = (m == mp);
+    double v = 0.0;
+    if (m == 0) {
+      v = (i == j) ? 1.0 : 0.0;
+    } else if (m == M1 - 1) {
+      const double s = L.sigma[m];
+      const double sxb = meta[M_AXb * nc + c] - s * meta[M_BXb * nc + c];
+      const double syb = meta[M_AYb * nc + c] - s * meta[M_BYb * nc + c];
+      const double HX = meta[M_HX * nc + c], HY = meta[M_HY * nc + c];
+      const double Zb = meta[M_Zb * nc + c];
+      const double Dm = D[m * M1 + mp];
+      if (sy_) v += HX * ((mp == m ? Dx[x * Nx + xp] : 0.0) + (sx_ ? sxb * Dm : 0.0));
+      if (sx_) v += HY * ((mp == m ? Dy[y * Ny + yp] : 0.0) + (sy_ ? syb * Dm : 0.0));
+      if (sx_ && sy_) v += Zb * Dm;
+    } else {
+      const double s = L.sigma[m];
+      const double Dm = D[m * M1 + mp];
+      const double AXa = meta[M_AXa * nc + c], BXa = meta[M_BXa * nc + c];
+      const double AYa = meta[M_AYa * nc + c], BYa = meta[M_BYa * nc + c];
+      const double sxa = AXa - s * BXa, sya = AYa - s * BYa;
+      const double D2m = L.D2[m * M1 + mp], DSDm = L.DSD[m * M1 + mp];
+      if (sy_) {
+        const int cp = y * Nx + xp;   // column (y, x')
+        const double sxb_p = meta[M_AXb * nc + cp] - s * meta[M_BXb * nc + cp];
+        v += (sm_ ? Dxx[x * Nx + xp] : 0.0) + Dx[x * Nx + xp] * sxb_p * Dm;
+        v += sxa * Dm * Dx[x * Nx + xp];
+      }
+      if (sx_) {
+        const int cp = yp * Nx + x;   // column (y', x)
+        const double syb_p = meta[M_AYb * nc + cp] - s * meta[M_BYb * nc + cp];
+        v += (sm_ ? Dyy[y * Ny + yp] : 0.0) + Dy[y * Ny + yp] * syb_p * Dm;
+        v += sya * Dm * Dy[y * Ny + yp];
+      }
+      if (sx_ && sy_) {
+        const double AXb = meta[M_AXb * nc + c], BXb = meta[M_BXb * nc + c];
+        const double AYb = meta[M_AYb * nc + c], BYb = meta[M_BYb * nc + c];
+        v += sxa * (AXb * D2m - BXb * DSDm) + sya * (AYb * D2m - BYb * DSDm);
+        v += meta[M_Za * nc + c] * meta[M_Zb * nc + c] * D2m;
+      }
+    }
+    A[i * ld + j] = v;
+  }
+  __syncthreads();
+  // in-place Gauss-Jordan inversion with row pivoting (the pivot column is
+  // overwritten by the inverse's column; row swaps become column swaps at the end)
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x < 32) {
+      double best = -1.0;
+      int bi = k;
+      for (int i = k + threadIdx.x; i < n; i += 32) {
+        const double a = fabs(A[i * ld + k]);
+        if (a > best) { best = a; bi = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (threadIdx.x == 0) {
+        spiv = bi;
+        perm[k] = bi;
+        if (!(best > 0.0) || !isfinite(best)) atomicOr(flag, 2);
+      }
+    }
+    __syncthreads();
+    const int p = spiv;
+    if (p != k) {
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double t0 = A[k * ld + j];
+        A[k * ld + j] = A[p * ld + j];
+        A[p * ld + j] = t0;
+      }
+      __syncthreads();
+    }
+    const double inv = 1.0 / A[k * ld + k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) A[k * ld + j] = (j == k ? 1.0 : A[k * ld + j]) * inv;
+    __syncthreads();
+    // eliminate column k from every other row; column k of those rows becomes -f * inv
+    for (int idx = threadIdx.x; idx < (n - 1) * n; idx += blockDim.x) {
+      int i = idx / n;
+      const int j = idx - i * n;
+      if (i >= k) ++i;
+      const double f = A[i * ld + k];
+      if (j != k) A[i * ld + j] -= f * A[k * ld + j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (i != k) A[i * ld + k] = -A[i * ld + k] * A[k * ld + k];
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double t0 = A[i * ld + k];
+        A[i * ld + k] = A[i * ld + p];
+        A[i * ld + p] = t0;
+      }
+    }
+    __syncthreads();
+  }
+  // store the inverse transposed: LUout[j * n + i] = Ainv[i][j] (coalesced solve)
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - i * n;
+    LUout[j * n + i] = A[i * ld + j];
+  }
+}
+
+// Metric of Eq. 1_Scoef per column for the geometries a (eta_a) and b (eta_b):
+// d = h + eta, d_x = h_x + eta_x;  sigma_x = (h_x - sigma d_x)/d = AX - sigma BX.
+__device__ inline void metric_body(long t0, long ts, int ncols, const double* WT_DEV_RESTRICT h, const double* WT_DEV_RESTRICT hx,
+                              const double* WT_DEV_RESTRICT hy, const double* WT_DEV_RESTRICT ea,
+                              const double* WT_DEV_RESTRICT eax, const double* WT_DEV_RESTRICT eay,
+                              const double* WT_DEV_RESTRICT eb, const double* WT_DEV_RESTRICT ebx,
+                              const double* WT_DEV_RESTRICT eby, double* WT_DEV_RESTRICT meta, int* flag) {
+  for (long c = t0; c < ncols; c += ts) {
+    const double HX = hx[c], HY = hy ? hy[c] : 0.0;
+    const double da = h[c] + ea[c], db = h[c] + eb[c];
+    const double dxa = HX + eax[c], dxb = HX + ebx[c];
+    const double dya = HY + (eay ? eay[c] : 0.0), dyb = HY + (eby ? eby[c] : 0.0);
+    if (!(da > 0.0) || !(db > 0.0) || !isfinite(da) || !isfinite(db) || !isfinite(dxa) ||
+        !isfinite(dxb) || !isfinite(dya) || !isfinite(dyb))
+      atomicOr(flag, 4);
+    const double ia = 1.0 / da, ib = 1.0 / db;
+    meta[M_AXa * (long)ncols + c] = HX * ia;
+    meta[M_BXa * (long)ncols + c] = dxa * ia;
+    meta[M_AYa * (long)ncols + c] = HY * ia;
+    meta[M_BYa * (long)ncols + c] = dya * ia;
+    meta[M_Za * (long)ncols + c] = ia;
+    meta[M_AXb * (long)ncols + c] = HX * ib;
+    meta[M_BXb * (long)ncols + c] = dxb * ib;
+    meta[M_AYb * (long)ncols + c] = HY * ib;
+    meta[M_BYb * (long)ncols + c] = dyb * ib;
+    meta[M_Zb * (long)ncols + c] = ib;
+    meta[M_HX * (long)ncols + c] = HX;
+    meta[M_HY * (long)ncols + c] = HY;
+    meta[M_D_A * (long)ncols + c] = da;
+    meta[M_D_B * (long)ncols + c] = db;
+  }
+}
+
+
+// Kinematic free-surface condition (Eq. kinematicFS) and its 2N register:
+// f_eta = -u~ eta_x - v~ eta_y + w~ (linear model: w~); K = alpha K + dt f;
+// eta^(k) = eta^(k-1) + beta K.  u~ = surface node (sigma index 0).
+__device__ inline void stage_eta_body(long t0, long ts, int ncols, int linear, double alpha, double beta, double dt,
+                            const double* WT_DEV_RESTRICT u, const double* WT_DEV_RESTRICT v,
+                            const double* WT_DEV_RESTRICT w, const double* WT_DEV_RESTRICT ex,
+                            const double* WT_DEV_RESTRICT ey, double* WT_DEV_RESTRICT Keta,
+                            const double* WT_DEV_RESTRICT eta, double* WT_DEV_RESTRICT eta_new,
+                            double* WT_DEV_RESTRICT f_eta, int* flag) {
+  for (long c = t0; c < ncols; c += ts) {
+    const double ut = u[c], vt = v ? v[c] : 0.0, wt = w[c];
+    const double fe = linear ? wt : (-ut * ex[c] - (v ? vt * ey[c] : 0.0) + wt);
+    const double K = alpha * Keta[c] + dt * fe;
+    Keta[c] = K;
+    const double en = eta[c] + beta * K;
+    eta_new[c] = en;
+    f_eta[c] = fe;
+    if (!isfinite(en)) atomicOr(flag, 8);
+  }
+}
+
+// Momentum forcing without p_D (Eq. forc1 with the pressure split of Sec. 2):
+//   F_q = -(u q_x + v q_y + w_sigma q_sigma) - g (eta_x, eta_y, 0)_q,
+//   w_sigma = sigma_t + u sigma_x + v sigma_y + w sigma_z, sigma_t = -sigma f_eta / d,
+// then K_q <- alpha K_q + dt F_q and q* = q + beta K_q (q* overwrites the
+// sigma-derivative inputs Dq).
+__device__ inline void stage_forcing_body(long t0, long ts, StageArgs a, const double* WT_DEV_RESTRICT u, const double* WT_DEV_RESTRICT v,
+                                const double* WT_DEV_RESTRICT w, const double* WT_DEV_RESTRICT ux,
+                                const double* WT_DEV_RESTRICT uy, const double* WT_DEV_RESTRICT vx,
+                                const double* WT_DEV_RESTRICT vy, const double* WT_DEV_RESTRICT wx,
+                                const double* WT_DEV_RESTRICT wy, const double* WT_DEV_RESTRICT ex,
+                                const double* WT_DEV_RESTRICT ey, const double* WT_DEV_RESTRICT f_eta,
+                                double* WT_DEV_RESTRICT Ku, double* WT_DEV_RESTRICT Kv,
+                                double* WT_DEV_RESTRICT Kw, double* WT_DEV_RESTRICT us,
+                                double* WT_DEV_RESTRICT vs, double* WT_DEV_RESTRICT ws) {
+  const long n = (long)a.M1 * a.ncols;
+  const long nc = a.ncols;
+  for (long e = t0; e < n; e += ts) {
+    const int m = (int)(e / nc);
+    const long c = e - m * nc;
+    const double s = a.sigma[m];
+    const double uu = u[e], ww = w[e], vv = v ? v[e] : 0.0;
+    double Fu = -a.g * ex[c], Fv = v ? -a.g * ey[c] : 0.0, Fw = 0.0;
+    if (!a.linear) {
+      const double* meta = a.meta;
+      const double sxb = meta[M_AXb * nc + c] - s * meta[M_BXb * nc + c];
+      const double syb = meta[M_AYb * nc + c] - s * meta[M_BYb * nc + c];
+      const double Zb = meta[M_Zb * nc + c], db = meta[M_D_B * nc + c];
+      const double wsig = -s * f_eta[c] / db + uu * sxb + vv * syb + ww * Zb;
+      Fu -= uu * ux[e] + wsig * us[e];
+      Fw -= uu * wx[e] + wsig * ws[e];
+      if (v) {
+        Fu -= vv * uy[e];
+        Fw -= vv * wy[e];
+        Fv -= uu * vx[e] + vv * vy[e] + wsig * vs[e];
+      }
+    }
+    const double ku = a.alpha * Ku[e] + a.dt * Fu;
+    const double kw = a.alpha * Kw[e] + a.dt * Fw;
+    Ku[e] = ku;
+    Kw[e] = kw;
+    us[e] = uu + a.beta * ku;
+    ws[e] = ww + a.beta * kw;
+    if (v) {
+      const double kv = a.alpha * Kv[e] + a.dt * Fv;
+      Kv[e] = kv;
+      vs[e] = vv + a.beta * kv;
+    }
+  }
+}
+
+// Poisson right-hand side in projection form (Eq. poissonp, bcpd, bcpdneu):
+// interior Div_a u* / (beta dt), surface 0, bottom (h_x u* + h_y v* + w*)/(beta dt).
+// Inputs: u*_x, v*_y and the sigma-derivatives D u*, D v*, D w* (in Dus, Dvs, Dws).
+__device__ inline void stage_rhs_body(long t0, long ts, StageArgs a, const double* WT_DEV_RESTRICT us, const double* WT_DEV_RESTRICT vs,
+                            const double* WT_DEV_RESTRICT ws, const double* WT_DEV_RESTRICT usx,
+                            const double* WT_DEV_RESTRICT vsy, const double* WT_DEV_RESTRICT Dus,
+                            const double* WT_DEV_RESTRICT Dvs, const double* WT_DEV_RESTRICT Dws,
+                            double* WT_DEV_RESTRICT rhs) {
+  const long n = (long)a.M1 * a.ncols;
+  const long nc = a.ncols;
+  const double ib = 1.0 / (a.beta * a.dt);
+  for (long e = t0; e < n; e += ts) {
+    const int m = (int)(e / nc);
+    const long c = e - m * nc;
+    const double* meta = a.meta;
+    double b;
+    if (m == 0) {
+      b = 0.0;
+    } else if (m == a.M1 - 1) {
+      b = (meta[M_HX * nc + c] * us[e] + (vs ? meta[M_HY * nc + c] * vs[e] : 0.0) + ws[e]) * ib;
+    } else {
+      const double s = a.sigma[m];
+      const double sxa = meta[M_AXa * nc + c] - s * meta[M_BXa * nc + c];
+      double d = usx[e] + sxa * Dus[e] + meta[M_Za * nc + c] * Dws[e];
+      if (vs) {
+        const double sya = meta[M_AYa * nc + c] - s * meta[M_BYa * nc + c];
+        d += vsy[e] + sya * Dvs[e];
+      }
+      b = d * ib;
+    }
+    rhs[e] = b;
+  }
+}
+
+// Projection (Eq. rkforc1): K_q <- K_q - dt (Grad_b p)_q, q^(k) = q^(k-1) + beta K_q.
+__device__ inline void stage_project_body(long t0, long ts, StageArgs a, const double* WT_DEV_RESTRICT px, const double* WT_DEV_RESTRICT py,
+                                const double* WT_DEV_RESTRICT Dp, double* WT_DEV_RESTRICT Ku,
+                                double* WT_DEV_RESTRICT Kv, double* WT_DEV_RESTRICT Kw,
+                                double* WT_DEV_RESTRICT u, double* WT_DEV_RESTRICT v, double* WT_DEV_RESTRICT w,
+                                int* flag) {
+  const long n = (long)a.M1 * a.ncols;
+  const long nc = a.ncols;
+  for (long e = t0; e < n; e += ts) {
+    const int m = (int)(e / nc);
+    const long c = e - m * nc;
+    const double s = a.sigma[m];
+    const double* meta = a.meta;
+    const double sxb = meta[M_AXb * nc + c] - s * meta[M_BXb * nc + c];
+    const double Zb = meta[M_Zb * nc + c];
+    const double Gx = px[e] + sxb * Dp[e];
+    const double Gz = Zb * Dp[e];
+    const double ku = Ku[e] - a.dt * Gx, kw = Kw[e] - a.dt * Gz;
+    Ku[e] = ku;
+    Kw[e] = kw;
+    const double un = u[e] + a.beta * ku, wn = w[e] + a.beta * kw;
+    u[e] = un;
+    w[e] = wn;
+    bool bad = !isfinite(un) || !isfinite(wn);
+    if (v) {
+      const double syb = meta[M_AYb * nc + c] - s * meta[M_BYb * nc + c];
+      const double Gy = py[e] + syb * Dp[e];
+      const double kv = Kv[e] - a.dt * Gy;
+      Kv[e] = kv;
+      const double vn = v[e] + a.beta * kv;
+      v[e] = vn;
+      bad = bad || !isfinite(vn);
+    }
+    if (bad) atomicOr(flag, 8);
   }
 }
 

@@ -135,6 +135,7 @@ struct wt_tank {
   int logNtw = 0;
   wt::TailLevel<double>* tl64 = nullptr;   // device descriptors of every level
   wt::TailLevel<float>* tl32 = nullptr;
+  wt::SurfDesc* sd = nullptr;                 // per-level surfaces (device array)
   double *cLU = nullptr, *cDx = nullptr, *cDy = nullptr;
   int* cpiv = nullptr;
   int ncoarse = 0;

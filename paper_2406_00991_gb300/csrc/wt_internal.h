@@ -89,6 +89,7 @@ struct RowPass {
   int logNtw = 0;
   // y-line geometry (ylines = 1): lines along y of a [planes][Ny][Nx] array
   int ylines = 0, Nxl = 0;     // x extent of each plane
+  int prefetch = 1;            // fetch epilogue operands with the inputs (needs smem)
 };
 
 template <typename T> cudaError_t launch_rowpass(const RowPass<T>& a, cudaStream_t s);
@@ -118,7 +119,37 @@ struct TailLevel {
   const T* Binv;
   T *rhoX, *rhoY, *rhoXY;
   const T *Rsig, *Psig;     // to / from the next coarser level
+  int nclass;               // smoother block classes and their x / y diagonals
+  T cxx, cyy;
 };
+
+// FP64 surfaces of one level (bathymetry, both free surfaces, slopes).
+struct SurfDesc {
+  double *h, *hx, *ea, *eax, *eb, *ebx, *tmp;
+};
+
+// Everything the persistent batch kernel needs about one 2D tank (device
+// pointers into the tank's own buffers, options as values).
+struct BatchTankDesc {
+  int nl, Nx, logNx, Nz, M1, ncols;
+  long n;
+  double L, g;
+  const TailLevel<float>* lv32;
+  const TailLevel<double>* lv64;
+  const SurfDesc* S;
+  double *AinvT, *cDx, *cDy;
+  double *V64, *Z64;
+  float *b32, *e32;
+  double *eta, *eta_new, *Keta, *f_eta, *eta_x, *u, *w, *Ku, *Kw, *p, *zero_s;
+  double* work[18];
+  const double *filt_x, *Fcheb;
+  int* flag;
+  double* stats;            // [0] solves, [1] Krylov iterations, [2] last relative residual
+  double tol, omega;
+  int nu1, nu2, restart, max_it, filter, linear;
+};
+cudaError_t launch_batch_step(const BatchTankDesc* descs, const int* order, int ntanks, const double* dt,
+                              int nsteps, int smem, cudaStream_t s);
 template <typename T>
 struct TailArgs {
   const TailLevel<T>* lv;   // device array, all levels of the hierarchy

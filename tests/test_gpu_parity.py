@@ -211,3 +211,27 @@ def test_airy_period_on_gpu(wt):
     eta = T.get_state()[0]
     assert np.abs(eta - eta0).max() / A < 2e-5
     assert abs(eta.mean()) < 1e-12
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_rk_stages_parity_3d(wt, mode):
+    # five stages of a small directional sea in a 3D tank over a gentle bump
+    N, Nz, L = 16, 8, 2 * math.pi
+    g = op.Grid(N, N, Nz, L)
+    X, Y = np.meshgrid(g.x, g.y, indexing="xy")
+    h = 1.0 - 0.1 * np.cos(X) * np.sin(Y)
+    sea = si.jonswap_sea(seed=2, L=L, ncomp=12, kp=2.0, hs_over_lp=0.01)
+    eta0, u0, v0, w0 = si.jonswap_fields(sea, N, g.sigma)
+    tank_o = rk.Tank(N, N, Nz, L, h, tol=1e-13, coarsest_max=64)
+    st = rk.State(g, eta0, u0, v0, w0)
+    dt = 0.01
+    T = wt.Tank(N, N, Nz, L, h, mode=mode, tol=1e-12, max_it=400)
+    T.set_state(*(np.ascontiguousarray(a) for a in (eta0, u0, v0, w0)))
+    for k in range(1, 6):
+        rk.stage(tank_o, st, k, dt)
+        T.rk_stage(k, dt)
+    eta, u, v, w, tm = T.get_state()
+    for got, ref in ((eta, st.eta), (u, st.u), (v, st.v), (w, st.w)):
+        assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
+    dv, bot = rk.divergence_residual(tank_o, rk.State(g, eta, u, v, w))
+    assert np.abs(dv).max() < 1e-7 and np.abs(bot).max() < 1e-9
