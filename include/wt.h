@@ -58,7 +58,7 @@ enum wt_status {
   WT_ENOTSUP = 7    /* valid request that this build does not support        */
 };
 
-enum wt_precision { WT_FP64 = 0, WT_MIXED = 1, WT_FP32 = 2 };
+enum wt_precision { WT_FP64 = 0, WT_MIXED = 1, WT_FP32 = 2, WT_REFINE = 3 };
 
 typedef struct wt_tank wt_tank;
 
@@ -68,7 +68,12 @@ typedef struct wt_options {
                         WT_MIXED: FP64 flexible GMRES (FP64 residuals and
                         Krylov basis) whose preconditioner is the FP32
                         V-cycle, so every iteration refines the FP64 iterate
-                        with an FP32 correction (default WT_MIXED)           */
+                        with an FP32 correction (default WT_MIXED).
+                        WT_REFINE: FP64 iterative refinement - the FP64
+                        residual r = b - A p, an FP32 flexible GMRES with
+                        the FP32 V-cycle solving A e = r to inner_tol,
+                        p += e, until tol (the FP64 operator runs once per
+                        refinement step only)                               */
   double tol;        /* relative residual ||b - A p||_2 / ||b||_2 (1e-10)   */
   int restart;       /* GMRES restart length m (30)                          */
   int nu1, nu2;      /* pre- / post-smoothing sweeps (2, 2)                  */
@@ -85,12 +90,16 @@ typedef struct wt_options {
                         single-CTA V-cycle launch (0: never, the
                         default; graph replay of the multi-CTA levels is
                         faster at the sizes measured so far)          */
+  double inner_tol;  /* WT_REFINE: relative residual of each FP32 inner
+                        solve (1e-5)                                         */
+  int max_ir;        /* WT_REFINE: refinement steps per solve (30)           */
 } wt_options;
 
 typedef struct wt_solve_info {
   int iterations;        /* Krylov iterations (= preconditioner applications) */
   double rel_residual;   /* final ||b - A p||_2 / ||b||_2, FP64 operator     */
   int status;            /* same code as the call's return value             */
+  int refinements;       /* WT_REFINE: FP64 refinement steps (0 otherwise)   */
 } wt_solve_info;
 
 /* Fill *opt with the defaults listed above.  Never fails for opt != NULL. */
@@ -177,6 +186,23 @@ int wt_step(wt_tank* t, double dt, int nsteps);
 /* Statistics of the last wt_rk_stage / wt_step: total Krylov iterations and
  * solves since the last wt_set_state. */
 int wt_get_stats(const wt_tank* t, long* solves, long* iterations);
+
+/*
+ * Solver autotuner.  Times wt_poisson_solve on this tank's problem
+ * A_{a,b} p = rhs (eta_a, eta_b [Ny][Nx], rhs [Nz+1][Ny][Nx]; host or device)
+ * from a zero initial guess under a grid of settings - omega in {0.3, 0.4,
+ * 0.5, 0.6}, (nu1, nu2) in {(1,1), (2,2), (3,3)}, coarsest_max in {32, 64,
+ * 128}, and mode in {WT_MIXED, WT_REFINE} unless the tank is in WT_FP64 - one
+ * warm-up solve plus the median of reps (1..100) timed solves each, and keeps
+ * the fastest setting that reaches the tolerance.  The paper leaves these
+ * choices open (Sec. 4.1).  On success the tank uses the winner, *best holds
+ * it, *best_ms its median time and *entry_ms that of the options on entry
+ * (best_ms <= entry_ms: the entry options are one of the candidates).  Any
+ * output pointer may be NULL.  WT_ENOCONV (tank options unchanged) if no
+ * candidate converged.  Allocates and frees temporary device buffers.
+ */
+int wt_autotune(wt_tank* t, const double* eta_a, const double* eta_b, const double* rhs, int reps,
+                wt_options* best, double* best_ms, double* entry_ms);
 
 /*
  * Batches of independent 2D tanks of uneven size, advanced together by one

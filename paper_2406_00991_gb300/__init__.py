@@ -20,7 +20,7 @@ import numpy as np
 from .build import LIB as _LIB_PATH
 
 WT_OK, WT_EINVAL, WT_ENOMEM, WT_ENOCONV, WT_EBREAK, WT_ECUDA, WT_ETIMEOUT, WT_ENOTSUP = range(8)
-WT_FP64, WT_MIXED, WT_FP32 = 0, 1, 2
+WT_FP64, WT_MIXED, WT_FP32, WT_REFINE = 0, 1, 2, 3
 STATUS_NAMES = {0: "WT_OK", 1: "WT_EINVAL", 2: "WT_ENOMEM", 3: "WT_ENOCONV", 4: "WT_EBREAK",
                 5: "WT_ECUDA", 6: "WT_ETIMEOUT", 7: "WT_ENOTSUP"}
 
@@ -30,12 +30,13 @@ class wt_options(ctypes.Structure):
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("max_it", ctypes.c_int),
                 ("filter", ctypes.c_int), ("linear", ctypes.c_int), ("coarsest_max", ctypes.c_int),
-                ("bc_transfer", ctypes.c_int), ("tail_max", ctypes.c_int)]
+                ("bc_transfer", ctypes.c_int), ("tail_max", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("max_ir", ctypes.c_int)]
 
 
 class wt_solve_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
-                ("status", ctypes.c_int)]
+                ("status", ctypes.c_int), ("refinements", ctypes.c_int)]
 
 
 def _load():
@@ -69,6 +70,7 @@ def _load():
                             ctypes.POINTER(D), ctypes.POINTER(D)],
         "wt_get_launches": [P, ctypes.POINTER(ctypes.c_long)],
         "wt_apply_operator_static": [I, I, D, P, P, P, P, P, P],
+        "wt_autotune": [P, P, P, P, I, ctypes.POINTER(wt_options), ctypes.POINTER(D), ctypes.POINTER(D)],
         "wt_create_batch": [I, P, P, P, D, D, P, ctypes.POINTER(P)],
         "wt_batch_set_options": [P, ctypes.POINTER(wt_options)],
         "wt_batch_set_state": [P, I, P, P, P, D],
@@ -240,6 +242,14 @@ def wt_apply_operator_static(Nx, Nz, L, h, eta_a, eta_b, p, Ap, stream_handle=0)
                                          _ptr(p), _ptr(Ap), ctypes.c_void_p(int(stream_handle)))
 
 
+def wt_autotune(t, eta_a, eta_b, rhs, reps=3):
+    o = wt_options()
+    b, e = ctypes.c_double(), ctypes.c_double()
+    st = _lib.wt_autotune(t, _ptr(eta_a), _ptr(eta_b), _ptr(rhs), int(reps), ctypes.byref(o),
+                          ctypes.byref(b), ctypes.byref(e))
+    return st, o, b.value, e.value
+
+
 def wt_create_batch(Nx, Nz, L, bathymetry, g=9.81, nu=0.0):
     """Batch of 2D tanks; bathymetry is a list of float64 arrays (host or device)."""
     n = len(Nx)
@@ -381,6 +391,13 @@ class Tank:
 
     def rk_stage(self, k, dt):
         _check(wt_rk_stage(self.handle, k, dt))
+
+    def autotune(self, eta_a, eta_b, rhs, reps=3):
+        """Pick the fastest converging solver settings for this problem; returns
+        (options dict, best ms, ms of the options on entry)."""
+        st, o, best, entry = wt_autotune(self.handle, eta_a, eta_b, rhs, reps)
+        _check(st)
+        return {k: getattr(o, k) for k, _ in wt_options._fields_}, best, entry
 
     def step(self, dt, nsteps=1):
         _check(wt_step(self.handle, dt, nsteps))

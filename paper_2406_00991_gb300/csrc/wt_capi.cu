@@ -290,7 +290,10 @@ void out_copy(wt_tank& t, double* user, const double* dev, size_t count) {
 }
 
 int check_options(const wt_options& o) {
-  if (o.mode != WT_FP64 && o.mode != WT_MIXED) return fail(WT_EINVAL, "mode must be WT_FP64 or WT_MIXED");
+  if (o.mode != WT_FP64 && o.mode != WT_MIXED && o.mode != WT_REFINE)
+    return fail(WT_EINVAL, "mode must be WT_FP64, WT_MIXED or WT_REFINE");
+  if (!(o.inner_tol > 0) || !(o.inner_tol < 1)) return fail(WT_EINVAL, "inner_tol must be in (0, 1)");
+  if (o.max_ir < 1) return fail(WT_EINVAL, "max_ir must be >= 1");
   if (!(o.tol > 0) || !(o.tol < 1)) return fail(WT_EINVAL, "tol must be in (0, 1)");
   if (o.restart < 1 || o.restart > 31) return fail(WT_EINVAL, "restart must be in [1, 31]");
   if (o.nu1 < 0 || o.nu1 > 8 || o.nu2 < 0 || o.nu2 > 8 || o.nu1 + o.nu2 == 0)
@@ -463,6 +466,8 @@ int wt_default_options(wt_options* o) {
   o->coarsest_max = 64;
   o->bc_transfer = 0;
   o->tail_max = 0;
+  o->inner_tol = 1e-5;
+  o->max_ir = 30;
   return WT_OK;
 }
 

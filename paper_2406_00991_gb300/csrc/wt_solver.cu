@@ -444,7 +444,7 @@ double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit,
 int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_solve_info* info) {
   const long n = t.n;
   const double bn = norm2<double>(t, b, n);
-  int its_total = 0;
+  int its_total = 0, refinements = 0;
   double rel = 0.0;
   int status = WT_OK;
   if (bn == 0.0) {
@@ -453,9 +453,30 @@ int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_
   } else {
     // WT_FP64: FP64 V-cycle.  WT_MIXED: FP32 V-cycle inside the FP64 flexible
     // GMRES, i.e. FP64 residuals and Krylov basis, FP32 preconditioner.
-    int its = 0;
-    rel = fgmres<double>(t, b, x, bn, tol, t.opt.max_it, &its, t.opt.mode == WT_MIXED);
-    its_total = its;
+    if (t.opt.mode == WT_REFINE) {
+      // FP64 iterative refinement: r = b - A x (FP64); A e = r / |r| solved by
+      // FP32 flexible GMRES with the FP32 V-cycle to inner_tol; x += |r| e.
+      for (;;) {
+        apply_op<double>(t, 0, x, t.r64, b, false);
+        const double rn = norm2<double>(t, t.r64, n);      // |r| also left in stN[0]
+        rel = rn / bn;
+        if (rel <= tol || refinements >= t.opt.max_ir || its_total >= t.opt.max_it || !std::isfinite(rel))
+          break;
+        WT_LAUNCH(t, K_KRYLOV, 12.0 * n, (double)n,
+                  (launch_convert<double, float>(t.r64, t.b32, n, t.stN, 1, t.s)));
+        WT_CK(cudaMemsetAsync(t.e32, 0, sizeof(float) * n, t.s));
+        int its = 0;
+        fgmres<float>(t, t.b32, t.e32, 1.0, t.opt.inner_tol,
+                      std::min(t.opt.restart, t.opt.max_it - its_total), &its, false);
+        its_total += its;
+        WT_LAUNCH(t, K_KRYLOV, 20.0 * n, 2.0 * n, launch_axpy_from<float>(x, t.e32, n, t.stN, t.s));
+        ++refinements;
+      }
+    } else {
+      int its = 0;
+      rel = fgmres<double>(t, b, x, bn, tol, t.opt.max_it, &its, t.opt.mode == WT_MIXED);
+      its_total = its;
+    }
     if (!(rel <= tol)) status = WT_ENOCONV;
   }
   WT_CK(cudaMemcpyAsync(t.hflag, t.dflag, sizeof(int), cudaMemcpyDeviceToHost, t.s));
@@ -468,6 +489,7 @@ int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_
     info->iterations = its_total;
     info->rel_residual = rel;
     info->status = status;
+    info->refinements = refinements;
   }
   return status;
 }

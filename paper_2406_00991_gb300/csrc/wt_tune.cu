@@ -1,0 +1,120 @@
+// Solver autotuner: times the tank's own pressure problem A_{a,b} p = rhs
+// under a grid of solver settings and keeps the fastest one that reaches the
+// tolerance.  The paper fixes neither the damping, the number of smoothing
+// sweeps nor the size of the coarsest level (Sec. 4.1 leaves them open), and
+// their best values depend on the tank's resolution and depth profile.
+//
+// Everything here goes through the public C ABI: wt_set_options and
+// wt_poisson_solve on device copies of the inputs, timed on the host clock
+// (each solve returns only after its result is on the device).
+#include "../../include/wt.h"
+#include "wt_internal.h"
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+namespace {
+
+struct DevBuf {
+  double* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+};
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+extern "C" int wt_autotune(wt_tank* t, const double* eta_a, const double* eta_b, const double* rhs, int reps,
+                           wt_options* best, double* best_ms, double* entry_ms) {
+  if (!t || !eta_a || !eta_b || !rhs) return wt::set_error(WT_EINVAL, "wt_autotune: NULL argument");
+  if (reps < 1 || reps > 100) return wt::set_error(WT_EINVAL, "wt_autotune: reps must be in [1, 100]");
+  wt_options entry{};
+  wt_get_options(t, &entry);
+  int nl = 0;
+  int dims[3 * 16];
+  if (wt_get_levels(t, &nl, dims) != WT_OK) return WT_EINVAL;
+  const int Nx = dims[0], Ny = dims[1], Nz = dims[2];        // finest level
+  const size_t ncols = (size_t)Nx * Ny, n = ncols * (Nz + 1);
+  DevBuf ea, eb, b, p;
+  cudaError_t e;
+  if ((e = cudaMalloc(&ea.p, sizeof(double) * ncols)) != cudaSuccess ||
+      (e = cudaMalloc(&eb.p, sizeof(double) * ncols)) != cudaSuccess ||
+      (e = cudaMalloc(&b.p, sizeof(double) * n)) != cudaSuccess ||
+      (e = cudaMalloc(&p.p, sizeof(double) * n)) != cudaSuccess) {
+    cudaGetLastError();
+    return wt::set_error(WT_ENOMEM, "wt_autotune: device buffers");
+  }
+  if ((e = cudaMemcpy(ea.p, eta_a, sizeof(double) * ncols, cudaMemcpyDefault)) != cudaSuccess ||
+      (e = cudaMemcpy(eb.p, eta_b, sizeof(double) * ncols, cudaMemcpyDefault)) != cudaSuccess ||
+      (e = cudaMemcpy(b.p, rhs, sizeof(double) * n, cudaMemcpyDefault)) != cudaSuccess)
+    return wt::set_error(WT_ECUDA, cudaGetErrorString(e));
+
+  // one candidate: a warm-up solve (captures its graphs), then the median of
+  // reps solves from a zero initial guess; < 0 if it does not converge
+  auto measure = [&](const wt_options& o, double prune_ms) -> double {
+    if (wt_set_options(t, &o) != WT_OK) return -1.0;
+    std::vector<double> ms;
+    for (int r = 0; r <= reps; ++r) {
+      if (cudaMemset(p.p, 0, sizeof(double) * n) != cudaSuccess) return -1.0;
+      wt_solve_info info{};
+      const double t0 = now_ms();
+      const int st = wt_poisson_solve(t, ea.p, eb.p, b.p, p.p, 0.0, &info);
+      const double dt = now_ms() - t0;
+      if (st != WT_OK) return -1.0;
+      if (r == 0) {
+        if (prune_ms > 0 && dt > 3.0 * prune_ms) return -1.0;   // far slower than the best so far
+        continue;
+      }
+      ms.push_back(dt);
+    }
+    std::sort(ms.begin(), ms.end());
+    return ms[ms.size() / 2];
+  };
+
+  const double e_ms = measure(entry, 0.0);
+  wt_options bo = entry;
+  double bms = e_ms > 0 ? e_ms : 1e300;
+  std::vector<int> modes;
+  if (entry.mode == WT_FP64)
+    modes = {WT_FP64};
+  else
+    modes = {WT_MIXED, WT_REFINE};
+  const double omegas[] = {0.3, 0.4, 0.5, 0.6};
+  const int nus[][2] = {{1, 1}, {2, 2}, {3, 3}};
+  const int coarsest[] = {32, 64, 128};
+  for (int mode : modes)
+    for (double om : omegas)
+      for (const auto& nu : nus)
+        for (int cm : coarsest) {
+          wt_options o = entry;
+          o.mode = mode;
+          o.omega = om;
+          o.nu1 = nu[0];
+          o.nu2 = nu[1];
+          o.coarsest_max = cm;
+          if (o.mode == entry.mode && o.omega == entry.omega && o.nu1 == entry.nu1 && o.nu2 == entry.nu2 &&
+              o.coarsest_max == entry.coarsest_max)
+            continue;                                  // measured above
+          const double ms = measure(o, bms < 1e300 ? bms : 0.0);
+          if (ms > 0 && ms < bms) {
+            bms = ms;
+            bo = o;
+          }
+        }
+  if (bms >= 1e300) {
+    wt_set_options(t, &entry);
+    return wt::set_error(WT_ENOCONV, "wt_autotune: no candidate reached the tolerance");
+  }
+  const int st = wt_set_options(t, &bo);
+  if (st != WT_OK) return st;
+  if (best) *best = bo;
+  if (best_ms) *best_ms = bms;
+  if (entry_ms) *entry_ms = e_ms;
+  return WT_OK;
+}

@@ -107,20 +107,21 @@ def manufactured_rhs():
     return g, np.ascontiguousarray(b), ms.p(X, z)
 
 
-@pytest.mark.parametrize("mode,tol,bound", [(0, 1e-12, 1e-10), (1, 1e-12, 1e-9)])
+@pytest.mark.parametrize("mode,tol,bound", [(0, 1e-12, 1e-10), (1, 1e-12, 1e-9), (3, 1e-12, 1e-9)])
 def test_manufactured_solve(wt, mode, tol, bound):
     g, b, pe = manufactured_rhs()
     T = wt.Tank(64, 1, 16, 2 * math.pi, np.ones((1, 64)), mode=mode, tol=tol)
     z = np.zeros((1, 64))
     p, info = T.poisson_solve(z, z, b)
     assert info.rel_residual <= tol
+    assert (info.refinements >= 1) == (mode == 3)
     assert np.abs(p - pe).max() <= bound * np.abs(pe).max()
     geo = op.Geometry(g, np.ones(64), np.zeros(64))
     r = b - op.apply_A(g, geo, geo, p)
     assert np.linalg.norm(r) <= max(tol, 1e-13) * 10 * np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 3])
 @pytest.mark.parametrize("Nx,Ny,Nz,L", [(1024, 1, 24, 32.0), (128, 1, 12, 8.0), (32, 32, 8, 2 * math.pi)])
 def test_curved_solve_residual_in_oracle_operator(wt, mode, Nx, Ny, Nz, L):
     g, h, ea, eb = curved(Nx, Ny, Nz, L)
@@ -139,7 +140,7 @@ def test_solve_matches_oracle_dense_lu(wt):
     b = np.random.default_rng(5).standard_normal(g.shape)
     lev = pmg.Level(Nx, 1, Nz, L, h, ea, eb)
     ref = krylov.solve_dense(lev, b)
-    for mode, bound in ((0, 1e-9), (1, 1e-8)):
+    for mode, bound in ((0, 1e-9), (1, 1e-8), (3, 1e-8)):
         T = wt.Tank(Nx, 1, Nz, L, h, mode=mode, tol=1e-12)
         p, info = T.poisson_solve(ea, eb, b)
         assert np.abs(p - ref).max() <= bound * np.abs(ref).max()
@@ -165,7 +166,7 @@ def _oracle_state(g, tank_o, eta, u, w):
     return st
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 3])
 def test_rk_stages_parity(wt, mode):
     # five stages of a nonlinear wave over a bump: GPU vs oracle, both solving
     # each Poisson problem to 1e-12
