@@ -22,8 +22,11 @@ Incompressible Navier-Stokes Model For Nonlinear Water Waves"):
 * ``rk``        - low-storage explicit Runge-Kutta (Eq. LSERK) with the
                   pressure projection at every stage (Sec. 3.2-3.3) and the
                   kinematic free-surface update (Eq. kinematicFS).
-* ``adjoint``   - transposed operator (the paper has no adjoint; pinned by the
-                  dot-product identity and by finite differences).
+* ``adjoint``   - exact derivative of the 2D time step and of a gauge loss
+                  (the paper has no adjoint): the step restated in plain
+                  PyTorch CPU float64 with a dense operator and LU solve,
+                  differentiated by torch.autograd; pinned against the numpy
+                  step and by central finite differences.
 
 Parity status of each function is stated in its docstring; every function is
 pinned by a ``-m "not gpu"`` test unless it says "parity unpinned".
