@@ -188,6 +188,39 @@ int wt_step(wt_tank* t, double dt, int nsteps);
 int wt_get_stats(const wt_tank* t, long* solves, long* iterations);
 
 /*
+ * Adjoint (reverse-mode derivative) of the 2D time step.  The paper has no
+ * adjoint; these calls differentiate the discrete forward map of wt_step
+ * (Sec. 3.1-3.3, Eq. kinematicFS, forc1, poissonp, bcpdneu, rkforc1, the
+ * Sec. 3.6 filter when enabled) exactly, up to the solve tolerance.  2D
+ * tanks only (WT_ENOTSUP for Ny > 1).  Arrays: host or device, FP64,
+ * layouts as in wt_set_state.
+ *
+ * wt_set_bathymetry: replace h(x) ([Ny][Nx], > 0) of an existing tank (every
+ *   level's truncated copy is rebuilt).
+ * wt_apply_operator_transposed: out = A_{a,b}^T lam (test hook; precision
+ *   WT_FP64 or WT_FP32).  A^T lam = e_surface lam_surface + Grad_b^T mu with
+ *   mu = Div_a^T lam_interior plus the bottom-row terms; D_x^T = -D_x.
+ * wt_adjoint_solve: A_{a,b}^T lam = rhs by the tank's solver (mode, tol,
+ *   smoother, V-cycle) applied to A^T: transposed column blocks, transposed
+ *   coarsest inverse, the same transfers.  lam: initial guess in, result out.
+ * wt_adjoint_step: reverse one step.  (eta, u, w) is the state at the start
+ *   of the step; the step is recomputed from it (the tank's state becomes
+ *   the state after the step) with every stage's values kept, then the
+ *   stages are reversed: on entry (lam_eta, lam_u, lam_w) hold dJ/d(state
+ *   after the step), on return dJ/d(state at the start); dJ_dh (may be NULL)
+ *   is incremented by this step's dJ/dh.  Every pressure solve of the
+ *   recomputation and the transposed solves use the tank's options.
+ *   WT_ENOCONV if any solve stopped above its tolerance (results written).
+ */
+int wt_set_bathymetry(wt_tank* t, const double* h);
+int wt_apply_operator_transposed(wt_tank* t, const double* eta_a, const double* eta_b, const double* lam,
+                                 double* out, int precision);
+int wt_adjoint_solve(wt_tank* t, const double* eta_a, const double* eta_b, const double* rhs, double* lam,
+                     double tol, wt_solve_info* info);
+int wt_adjoint_step(wt_tank* t, double dt, const double* eta, const double* u, const double* w,
+                    double* lam_eta, double* lam_u, double* lam_w, double* dJ_dh);
+
+/*
  * Solver autotuner.  Times wt_poisson_solve on this tank's problem
  * A_{a,b} p = rhs (eta_a, eta_b [Ny][Nx], rhs [Nz+1][Ny][Nx]; host or device)
  * from a zero initial guess under a grid of settings - omega in {0.3, 0.4,

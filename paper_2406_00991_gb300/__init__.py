@@ -71,6 +71,10 @@ def _load():
         "wt_get_launches": [P, ctypes.POINTER(ctypes.c_long)],
         "wt_apply_operator_static": [I, I, D, P, P, P, P, P, P],
         "wt_autotune": [P, P, P, P, I, ctypes.POINTER(wt_options), ctypes.POINTER(D), ctypes.POINTER(D)],
+        "wt_set_bathymetry": [P, P],
+        "wt_apply_operator_transposed": [P, P, P, P, P, I],
+        "wt_adjoint_solve": [P, P, P, P, P, D, ctypes.POINTER(wt_solve_info)],
+        "wt_adjoint_step": [P, D, P, P, P, P, P, P, P],
         "wt_create_batch": [I, P, P, P, D, D, P, ctypes.POINTER(P)],
         "wt_batch_set_options": [P, ctypes.POINTER(wt_options)],
         "wt_batch_set_state": [P, I, P, P, P, D],
@@ -242,6 +246,26 @@ def wt_apply_operator_static(Nx, Nz, L, h, eta_a, eta_b, p, Ap, stream_handle=0)
                                          _ptr(p), _ptr(Ap), ctypes.c_void_p(int(stream_handle)))
 
 
+def wt_set_bathymetry(t, h):
+    return _lib.wt_set_bathymetry(t, _ptr(h))
+
+
+def wt_apply_operator_transposed(t, eta_a, eta_b, lam, out, precision=WT_FP64):
+    return _lib.wt_apply_operator_transposed(t, _ptr(eta_a), _ptr(eta_b), _ptr(lam), _ptr(out), int(precision))
+
+
+def wt_adjoint_solve(t, eta_a, eta_b, rhs, lam, tol=0.0):
+    info = wt_solve_info()
+    st = _lib.wt_adjoint_solve(t, _ptr(eta_a), _ptr(eta_b), _ptr(rhs), _ptr(lam), float(tol),
+                               ctypes.byref(info))
+    return st, info
+
+
+def wt_adjoint_step(t, dt, eta, u, w, lam_eta, lam_u, lam_w, dJ_dh=None):
+    return _lib.wt_adjoint_step(t, float(dt), _ptr(eta), _ptr(u), _ptr(w), _ptr(lam_eta), _ptr(lam_u),
+                                _ptr(lam_w), _ptr(dJ_dh))
+
+
 def wt_autotune(t, eta_a, eta_b, rhs, reps=3):
     o = wt_options()
     b, e = ctypes.c_double(), ctypes.c_double()
@@ -391,6 +415,24 @@ class Tank:
 
     def rk_stage(self, k, dt):
         _check(wt_rk_stage(self.handle, k, dt))
+
+    def set_bathymetry(self, h):
+        _check(wt_set_bathymetry(self.handle, h))
+
+    def apply_operator_transposed(self, eta_a, eta_b, lam, precision=WT_FP64, out=None):
+        out = np.zeros(self.shape) if out is None else out
+        _check(wt_apply_operator_transposed(self.handle, eta_a, eta_b, lam, out, precision))
+        return out
+
+    def adjoint_solve(self, eta_a, eta_b, rhs, lam=None, tol=0.0):
+        lam = np.zeros(self.shape) if lam is None else lam
+        st, info = wt_adjoint_solve(self.handle, eta_a, eta_b, rhs, lam, tol)
+        _check(st)
+        return lam, info
+
+    def adjoint_step(self, dt, eta, u, w, lam_eta, lam_u, lam_w, dJ_dh=None):
+        """Reverse one step from state (eta, u, w); lam_* and dJ_dh are updated in place."""
+        _check(wt_adjoint_step(self.handle, dt, eta, u, w, lam_eta, lam_u, lam_w, dJ_dh))
 
     def autotune(self, eta_a, eta_b, rhs, reps=3):
         """Pick the fastest converging solver settings for this problem; returns

@@ -380,7 +380,7 @@ void filter_field(wt_tank& t, double* q, int planes, bool cheb) {
   if (cheb) run_col_matrix<double>(t, t.Fcheb, t.M1, t.M1, q, q, t.ncols, 0);
 }
 
-int rk_stage(wt_tank& t, int k, double dt) {
+int rk_stage(wt_tank& t, int k, double dt, AdjStage* rec = nullptr) {
   enter(t);
   const double a = kAlpha[k - 1], b = kBeta[k - 1];
   const bool y = t.Ny > 1;
@@ -392,11 +392,23 @@ int rk_stage(wt_tank& t, int k, double dt) {
     if (y) filter_field(t, t.v, M1, true);
     filter_field(t, t.w, M1, true);
   }
+  auto keep = [&](double* dst, const double* src, long count) {
+    WT_CK(cudaMemcpyAsync(dst, src, sizeof(double) * count, cudaMemcpyDeviceToDevice, t.s));
+  };
+  if (rec) {
+    keep(rec->eta_f, t.eta, t.ncols);
+    keep(rec->u_f, t.u, t.n);
+    keep(rec->w_f, t.w, t.n);
+  }
   // free-surface update (Eq. kinematicFS), independent of p_D
   ddx(t, t.eta, t.eta_x, 1);
   if (y) ddy(t, t.eta, t.eta_y, 1);
   WT_LAUNCH(t, K_STAGE, 8.0 * t.ncols * 9, 8.0 * t.ncols, launch_stage_eta(t.ncols, M1, t.opt.linear, a, b, dt, t.u, y ? t.v : nullptr, t.w, t.eta_x,
                          y ? t.eta_y : t.zero_s, t.Keta, t.eta, t.eta_new, t.f_eta, t.dflag, t.s));
+  if (rec) {
+    keep(rec->eta_n, t.eta_new, t.ncols);
+    keep(rec->f_eta, t.f_eta, t.ncols);
+  }
   // geometry a = eta^(k), b = eta^(k-1) (still water for the linear model)
   const int prec = t.opt.mode == WT_FP64 ? WT_FP64 : WT_FP32;
   setup_geometry(t, t.opt.linear ? t.zero_s : t.eta_new, t.opt.linear ? t.zero_s : t.eta, prec, true, true);
@@ -421,6 +433,10 @@ int rk_stage(wt_tank& t, int k, double dt) {
   if (y) dds(t, t.v, vs);
   WT_LAUNCH(t, K_STAGE, 8.0 * t.n * (y ? 24 : 14), 30.0 * t.n, launch_stage_forcing(sa, t.u, y ? t.v : nullptr, t.w, ux, uy, vx, vy, wx, wy, t.eta_x,
                              y ? t.eta_y : t.zero_s, t.f_eta, t.Ku, t.Kv, t.Kw, us, vs, ws, t.s));
+  if (rec) {
+    keep(rec->us, us, t.n);
+    keep(rec->ws, ws, t.n);
+  }
   // right-hand side of the mixed-stage Poisson problem (Eq. poissonp, bcpdneu)
   ddx(t, us, usx, M1);
   if (y) ddy(t, vs, vsy, M1);
@@ -432,6 +448,7 @@ int rk_stage(wt_tank& t, int k, double dt) {
   wt_solve_info info{};
   int st = poisson_solve_device(t, rhs, t.p, t.opt.tol, &info);
   if (st != WT_OK && st != WT_ENOCONV) return fail(st, "pressure solve failed (depth <= 0 or non-finite)");
+  if (rec) keep(rec->p, t.p, t.n);
   // projection (Eq. rkforc1)
   ddx(t, t.p, px, M1);
   if (y) ddy(t, t.p, py, M1);
@@ -443,6 +460,40 @@ int rk_stage(wt_tank& t, int k, double dt) {
   if (fl) return fail(WT_EBREAK, "water depth d <= 0 or non-finite state after stage " + std::to_string(k));
   if (st == WT_ENOCONV) return fail(WT_ENOCONV, "pressure solve did not reach its tolerance");
   return WT_OK;
+}
+
+// Buffers of the adjoint step, allocated at its first use.
+void alloc_adj(wt_tank& t) {
+  if (t.adj) return;
+  auto B = std::make_unique<AdjBufs>();
+  const long n = t.n, nc = t.ncols;
+  const int M1 = t.M1;
+  auto& A = B->ar;
+  B->ncols = nc;
+  for (auto& S : B->st) {
+    S.eta_f = A.alloc<double>(nc);
+    S.u_f = A.alloc<double>(n);
+    S.w_f = A.alloc<double>(n);
+    S.eta_n = A.alloc<double>(nc);
+    S.f_eta = A.alloc<double>(nc);
+    S.us = A.alloc<double>(n);
+    S.ws = A.alloc<double>(n);
+    S.p = A.alloc<double>(n);
+  }
+  B->Le = A.alloc<double>(nc);
+  B->LKe = A.alloc<double>(nc);
+  B->lh = A.alloc<double>(nc);
+  double** fields[] = {&B->Lu, &B->Lw, &B->LKu, &B->LKw, &B->LKu1, &B->LKw1, &B->LGx, &B->q, &B->lp,
+                       &B->lrhs, &B->t1, &B->px, &B->ux, &B->wx, &B->lux, &B->lwx, &B->lut, &B->lwt,
+                       &B->lFu, &B->lFw};
+  for (double** f : fields) *f = A.alloc<double>(n);
+  B->cols = A.alloc<double>((size_t)kAdjCols * nc);
+  std::vector<double> F(M1 * M1), FT(M1 * M1);
+  WT_CK(cudaMemcpy(F.data(), t.Fcheb, sizeof(double) * M1 * M1, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < M1; ++i)
+    for (int j = 0; j < M1; ++j) FT[i * M1 + j] = F[j * M1 + i];
+  B->FchebT = upload<double>(A, FT);
+  t.adj = std::move(B);
 }
 
 }  // namespace
@@ -832,6 +883,132 @@ int wt_get_launches(const wt_tank* t, long* launches) {
   if (!t || !launches) return fail(WT_EINVAL, "NULL argument");
   *launches = t->prof.launches;
   return WT_OK;
+}
+
+// ================================================================ adjoint
+int wt_set_bathymetry(wt_tank* t, const double* h) {
+  if (!t || !h) return fail(WT_EINVAL, "NULL argument");
+  return guarded([&]() -> int {
+    enter(*t);
+    const double* hd = in_dev(*t, h, t->io_s1, t->ncols);
+    setup_bathymetry(*t, hd);
+    WT_CK(cudaStreamSynchronize(t->s));
+    return WT_OK;
+  });
+}
+
+int wt_apply_operator_transposed(wt_tank* t, const double* eta_a, const double* eta_b, const double* lam,
+                                 double* out, int precision) {
+  if (!t || !eta_a || !eta_b || !lam || !out) return fail(WT_EINVAL, "NULL argument");
+  if (precision != WT_FP64 && precision != WT_FP32) return fail(WT_EINVAL, "precision must be WT_FP64 or WT_FP32");
+  if (t->Ny != 1) return fail(WT_ENOTSUP, "the transposed operator is 2D only");
+  return guarded([&]() -> int {
+    enter(*t);
+    const long n = t->n;
+    const double* ea = in_dev(*t, eta_a, t->io_s1, t->ncols);
+    const double* eb = in_dev(*t, eta_b, t->io_s2, t->ncols);
+    setup_geometry(*t, ea, eb, precision, false, false);
+    const double* ld = in_dev(*t, lam, t->io_f1, n);
+    if (precision == WT_FP64) {
+      apply_op<double>(*t, 0, ld, t->io_f2, nullptr, false, true);
+    } else {
+      auto& L = t->L32[0];
+      WT_LAUNCH(*t, K_KRYLOV, 12.0 * n, 0.0, (launch_convert<double, float>(ld, L.x, n, nullptr, 0, t->s)));
+      apply_op<float>(*t, 0, L.x, L.f, nullptr, false, true);
+      WT_LAUNCH(*t, K_KRYLOV, 12.0 * n, 0.0, (launch_convert<float, double>(L.f, t->io_f2, n, nullptr, 0, t->s)));
+    }
+    out_copy(*t, out, t->io_f2, n);
+    const int fl = read_flags(*t);
+    if (fl) return fail(WT_EBREAK, "water depth d <= 0 or non-finite surface");
+    return WT_OK;
+  });
+}
+
+int wt_adjoint_solve(wt_tank* t, const double* eta_a, const double* eta_b, const double* rhs, double* lam,
+                     double tol, wt_solve_info* info) {
+  if (!t || !eta_a || !eta_b || !rhs || !lam) return fail(WT_EINVAL, "NULL argument");
+  if (t->Ny != 1) return fail(WT_ENOTSUP, "the transposed problem is 2D only");
+  if (tol <= 0) tol = t->opt.tol;
+  return guarded([&]() -> int {
+    enter(*t);
+    const long n = t->n;
+    const double* ea = in_dev(*t, eta_a, t->io_s1, t->ncols);
+    const double* eb = in_dev(*t, eta_b, t->io_s2, t->ncols);
+    const int prec = t->opt.mode == WT_FP64 ? WT_FP64 : WT_FP32;
+    setup_geometry(*t, ea, eb, prec, true, true);
+    const double* bd = in_dev(*t, rhs, t->io_f1, n);
+    WT_CK(cudaMemcpyAsync(t->b64, bd, sizeof(double) * n, cudaMemcpyDeviceToDevice, t->s));
+    const double* l0 = in_dev(*t, lam, t->io_f2, n);
+    WT_CK(cudaMemcpyAsync(t->x64, l0, sizeof(double) * n, cudaMemcpyDeviceToDevice, t->s));
+    wt_solve_info inf{};
+    int st = poisson_solve_device(*t, t->b64, t->x64, tol, &inf, true);
+    out_copy(*t, lam, t->x64, n);
+    WT_CK(cudaStreamSynchronize(t->s));
+    if (info) *info = inf;
+    if (st == WT_ENOCONV) return fail(st, "transposed solve stopped above its tolerance");
+    if (st != WT_OK) return fail(st, "depth <= 0, singular block or non-finite value in the solve");
+    return WT_OK;
+  });
+}
+
+int wt_adjoint_step(wt_tank* t, double dt, const double* eta, const double* u, const double* w,
+                    double* lam_eta, double* lam_u, double* lam_w, double* dJ_dh) {
+  if (!t || !eta || !u || !w || !lam_eta || !lam_u || !lam_w) return fail(WT_EINVAL, "NULL argument");
+  if (t->Ny != 1) return fail(WT_ENOTSUP, "the adjoint step is 2D only");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(WT_EINVAL, "dt must be positive");
+  return guarded([&]() -> int {
+    enter(*t);
+    alloc_adj(*t);
+    AdjBufs& B = *t->adj;
+    const long n = t->n, nc = t->ncols;
+    cudaStream_t s = t->s;
+    auto load = [&](double* dst, const double* user, double* staging, long count) {
+      const double* d = in_dev(*t, user, staging, count);
+      WT_CK(cudaMemcpyAsync(dst, d, sizeof(double) * count, cudaMemcpyDeviceToDevice, s));
+    };
+    // recompute the step from its start, keeping every stage's values
+    load(t->eta, eta, t->io_s1, nc);
+    load(t->u, u, t->io_f1, n);
+    load(t->w, w, t->io_f2, n);
+    WT_CK(cudaMemsetAsync(t->v, 0, sizeof(double) * n, s));
+    WT_CK(cudaMemsetAsync(t->Keta, 0, sizeof(double) * nc, s));
+    WT_CK(cudaMemsetAsync(t->Ku, 0, sizeof(double) * n, s));
+    WT_CK(cudaMemsetAsync(t->Kw, 0, sizeof(double) * n, s));
+    WT_CK(cudaMemsetAsync(t->p, 0, sizeof(double) * n, s));
+    t->have_state = true;
+    bool noconv = false;
+    for (int k = 1; k <= 5; ++k) {
+      const int st = rk_stage(*t, k, dt, &B.st[k - 1]);
+      if (st == WT_ENOCONV) noconv = true;
+      else if (st != WT_OK) return st;
+    }
+    t->time += dt;
+    // reverse the stages
+    load(B.Le, lam_eta, t->io_s1, nc);
+    load(B.Lu, lam_u, t->io_f1, n);
+    load(B.Lw, lam_w, t->io_f2, n);
+    WT_CK(cudaMemsetAsync(B.LKe, 0, sizeof(double) * nc, s));
+    WT_CK(cudaMemsetAsync(B.LKu, 0, sizeof(double) * n, s));
+    WT_CK(cudaMemsetAsync(B.LKw, 0, sizeof(double) * n, s));
+    WT_CK(cudaMemsetAsync(B.lh, 0, sizeof(double) * nc, s));
+    for (int k = 5; k >= 1; --k) {
+      const int st = adjoint_stage(*t, k, dt, kAlpha, kBeta);
+      if (st == WT_ENOCONV) noconv = true;
+      else if (st != WT_OK) return fail(st, "transposed solve failed (depth <= 0 or non-finite)");
+    }
+    out_copy(*t, lam_eta, B.Le, nc);
+    out_copy(*t, lam_u, B.Lu, n);
+    out_copy(*t, lam_w, B.Lw, n);
+    if (dJ_dh) {
+      const double* hd = in_dev(*t, dJ_dh, t->io_s2, nc);
+      WT_CK(launch_add(const_cast<double*>(hd), B.lh, nc, s));
+      if (hd != dJ_dh) out_copy(*t, dJ_dh, hd, nc);
+    }
+    const int fl = read_flags(*t);
+    if (fl) return fail(WT_EBREAK, "water depth d <= 0 or non-finite state in the adjoint step");
+    if (noconv) return fail(WT_ENOCONV, "a forward or transposed solve stopped above its tolerance");
+    return WT_OK;
+  });
 }
 
 // ================================================================ batches

@@ -29,10 +29,11 @@ __global__ void __launch_bounds__(256) k_coarse_factor(LevelView<double> L, cons
   (void)piv;
 }
 
-// x = A^{-1} f with the stored (transposed) inverse: one thread per row.
+// x = A^{-1} f (tr = 0) or x = A^{-T} f (tr = 1) with the stored (transposed)
+// inverse: one thread per row.
 template <typename T>
 __global__ void __launch_bounds__(128) k_coarse_solve(int n, const double* __restrict__ AinvT,
-                                                     const int* __restrict__ piv,
+                                                     const int* __restrict__ piv, int tr,
                                                      const T* __restrict__ f, T* __restrict__ x) {
   __shared__ double b[128];
   for (int i = threadIdx.x; i < n; i += blockDim.x) b[i] = (double)f[i];
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(128) k_coarse_solve(int n, const double* __res
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double acc = 0.0;
 #pragma unroll 8
-    for (int j = 0; j < n; ++j) acc += AinvT[j * n + i] * b[j];
+    for (int j = 0; j < n; ++j) acc += AinvT[tr ? i * n + j : j * n + i] * b[j];
     x[i] = (T)acc;
   }
   (void)piv;
@@ -63,15 +64,15 @@ cudaError_t launch_coarse_factor(const LevelView<double>& L, const double* Dx, c
 }
 
 template <typename T>
-cudaError_t launch_coarse_solve(int n, const double* LU, const int* piv, const T* f, T* x,
+cudaError_t launch_coarse_solve(int n, const double* LU, const int* piv, int tr, const T* f, T* x,
                                 cudaStream_t s) {
-  k_coarse_solve<T><<<1, 128, 0, s>>>(n, LU, piv, f, x);
+  k_coarse_solve<T><<<1, 128, 0, s>>>(n, LU, piv, tr, f, x);
   return cudaGetLastError();
 }
 
-template cudaError_t launch_coarse_solve<float>(int, const double*, const int*, const float*, float*,
-                                                cudaStream_t);
-template cudaError_t launch_coarse_solve<double>(int, const double*, const int*, const double*,
+template cudaError_t launch_coarse_solve<float>(int, const double*, const int*, int, const float*,
+                                                float*, cudaStream_t);
+template cudaError_t launch_coarse_solve<double>(int, const double*, const int*, int, const double*,
                                                  double*, cudaStream_t);
 
 }  // namespace wt

@@ -25,7 +25,15 @@ __global__ void __launch_bounds__(256) k_op_cols(LevelView<T> L, const T* __rest
   opcols_body<T, DIM>(L, p, Px, Py, Gx, Gy, part, blockIdx.x, gridDim.x, smraw);
 }
 
-template <typename T, int DIM>
+template <typename T>
+__global__ void __launch_bounds__(256) k_op_cols_T(LevelView<T> L, const T* __restrict__ lam,
+                                                   const T* __restrict__ Dlam, T* __restrict__ Mx,
+                                                   T* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  opcolsT_body<T>(L, lam, Dlam, Mx, part, blockIdx.x, gridDim.x, smraw);
+}
+
+template <typename T, int DIM, bool TR>
 __global__ void __launch_bounds__(256) k_smooth_cols(LevelView<T> L, const T* __restrict__ r,
                                                      const T* __restrict__ rhoX,
                                                      const T* __restrict__ rhoY,
@@ -33,7 +41,7 @@ __global__ void __launch_bounds__(256) k_smooth_cols(LevelView<T> L, const T* __
                                                      const T* __restrict__ Binv,
                                                      T* __restrict__ x, T omega, int first) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  smooth_any<T, DIM>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first, blockIdx.x, gridDim.x, smraw);
+  smooth_any<T, DIM, TR>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first, blockIdx.x, gridDim.x, smraw);
 }
 
 template <typename T>
@@ -78,15 +86,31 @@ cudaError_t launch_op_cols(const LevelView<T>& L, const T* p, const T* Px, const
 }
 
 template <typename T>
+cudaError_t launch_op_cols_T(const LevelView<T>& L, const T* lam, const T* Dlam, T* Mx, T* part,
+                             cudaStream_t s) {
+  if (L.Ny != 1) return cudaErrorInvalidValue;
+  const int g = grid_cols(L.ncols, 256);
+  k_op_cols_T<T><<<g, 256, opcols_smem<T>(L.M1), s>>>(L, lam, Dlam, Mx, part);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_smooth_cols(const LevelView<T>& L, const T* r, const T* rhoX, const T* rhoY,
                                const T* rhoXY, const T* Binv, int nclass, T* x, T omega, int first,
-                               cudaStream_t s) {
+                               int tr, cudaStream_t s) {
   (void)nclass;
   const int g = grid_cols(L.ncols, 256);
-  if (L.Ny == 1)
-    k_smooth_cols<T, 2><<<g, 256, 0, s>>>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
-  else
-    k_smooth_cols<T, 3><<<g, 256, 0, s>>>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
+  if (L.Ny == 1) {
+    if (tr)
+      k_smooth_cols<T, 2, true><<<g, 256, 0, s>>>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
+    else
+      k_smooth_cols<T, 2, false><<<g, 256, 0, s>>>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
+  } else {
+    if (tr)
+      k_smooth_cols<T, 3, true><<<g, 256, 0, s>>>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
+    else
+      k_smooth_cols<T, 3, false><<<g, 256, 0, s>>>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
+  }
   return cudaGetLastError();
 }
 
@@ -121,7 +145,10 @@ cudaError_t launch_block_inverse(const LevelView<T>& L, T* Binv, int nclass, T c
   template cudaError_t launch_op_cols<T>(const LevelView<T>&, const T*, const T*, const T*, T*,  \
                                          T*, T*, cudaStream_t);                                 \
   template cudaError_t launch_smooth_cols<T>(const LevelView<T>&, const T*, const T*, const T*,  \
-                                             const T*, const T*, int, T*, T, int, cudaStream_t); \
+                                             const T*, const T*, int, T*, T, int, int,          \
+                                             cudaStream_t);                                      \
+  template cudaError_t launch_op_cols_T<T>(const LevelView<T>&, const T*, const T*, T*, T*,      \
+                                           cudaStream_t);                                        \
   template cudaError_t launch_col_matrix<T>(const T*, int, int, const T*, T*, int, int,         \
                                             cudaStream_t);                                      \
   template cudaError_t launch_block_inverse<T>(const LevelView<T>&, T*, int, T, T, int*,        \

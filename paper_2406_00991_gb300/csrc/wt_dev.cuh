@@ -353,10 +353,69 @@ __device__ void opcols_body(const LevelView<T>& L, const T* WT_DEV_RESTRICT p,
   __syncthreads();
 }
 
+// Column part of the transposed operator A_{a,b}^T (2D).  With lam_int =
+// lam without its surface and bottom rows and Dlam = D_x lam (all rows):
+//   mu_x = -Dlam_int + D^T (sx_a lam_int) + h_x lam_bottom e_bottom
+//   mu_z = D^T (Z_a lam_int) + lam_bottom e_bottom
+//   part = D^T (sx_b mu_x + Z_b mu_z) + lam_surface e_surface,
+// so that A^T lam = part + D_x^T mu_x = part - D_x mu_x (the x-derivative
+// matrix is antisymmetric).  mu_x goes to Mx, part to part.
+template <typename T>
+__device__ void opcolsT_body(const LevelView<T>& L, const T* WT_DEV_RESTRICT lam,
+                             const T* WT_DEV_RESTRICT Dlam, T* WT_DEV_RESTRICT Mx,
+                             T* WT_DEV_RESTRICT part, int u0, int ustep, unsigned char* smraw) {
+  const int M1 = L.M1;
+  T* sDt = reinterpret_cast<T*>(smraw);           // D^T, M1*M1
+  T* sS = sDt + M1 * M1;                          // sigma
+  for (int i = threadIdx.x; i < M1 * M1; i += blockDim.x) {
+    const int m = i / M1, k = i - m * M1;
+    sDt[i] = L.D[k * M1 + m];
+  }
+  for (int i = threadIdx.x; i < M1; i += blockDim.x) sS[i] = L.sigma[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const long nc = L.ncols;
+  const int m0 = lane, m1 = lane + 32;
+  const bool r0 = m0 < M1, r1 = m1 < M1;
+  const bool i0 = r0 && m0 > 0 && m0 < M1 - 1, i1 = r1 && m1 < M1 - 1;
+  const T* meta = L.meta;
+  for (long c = (long)u0 * nw + wib; c < nc; c += (long)ustep * nw) {
+    const T l0 = r0 ? lam[m0 * nc + c] : T(0), l1 = r1 ? lam[m1 * nc + c] : T(0);
+    const T lsurf = bcast(l0, l1, 0), lbot = bcast(l0, l1, M1 - 1);
+    const T li0 = i0 ? l0 : T(0), li1 = i1 ? l1 : T(0);
+    const T AXa = meta[M_AXa * nc + c], BXa = meta[M_BXa * nc + c];
+    const T AXb = meta[M_AXb * nc + c], BXb = meta[M_BXb * nc + c];
+    const T Za = meta[M_Za * nc + c], Zb = meta[M_Zb * nc + c];
+    const T HX = meta[M_HX * nc + c];
+    const T s0 = r0 ? sS[m0] : T(0), s1 = r1 ? sS[m1] : T(0);
+    T da0, da1, dz0, dz1;
+    contract(sDt, M1, M1, m0, m1, r0, r1, (AXa - s0 * BXa) * li0, (AXa - s1 * BXa) * li1, da0, da1);
+    contract(sDt, M1, M1, m0, m1, r0, r1, Za * li0, Za * li1, dz0, dz1);
+    const T dl0 = i0 ? Dlam[m0 * nc + c] : T(0), dl1 = i1 ? Dlam[m1 * nc + c] : T(0);
+    const bool b0 = m0 == M1 - 1, b1 = m1 == M1 - 1;
+    const T mx0 = -dl0 + da0 + (b0 ? HX * lbot : T(0));
+    const T mx1 = -dl1 + da1 + (b1 ? HX * lbot : T(0));
+    const T mz0 = dz0 + (b0 ? lbot : T(0)), mz1 = dz1 + (b1 ? lbot : T(0));
+    const T q0 = r0 ? (AXb - s0 * BXb) * mx0 + Zb * mz0 : T(0);
+    const T q1 = r1 ? (AXb - s1 * BXb) * mx1 + Zb * mz1 : T(0);
+    T o0, o1;
+    contract(sDt, M1, M1, m0, m1, r0, r1, q0, q1, o0, o1);
+    if (r0) {
+      Mx[m0 * nc + c] = mx0;
+      part[m0 * nc + c] = o0 + (m0 == 0 ? lsurf : T(0));
+    }
+    if (r1) {
+      Mx[m1 * nc + c] = mx1;
+      part[m1 * nc + c] = o1;
+    }
+  }
+  __syncthreads();
+}
+
 // Block inverses are stored per column, contiguous and transposed:
 // Binv[((c * nclass + cls) * M1 + k) * M1 + m] = (A_rr^{-1})[m][k], so lane m
 // of a warp reads consecutive words for every k.
-template <typename T, int DIM, int MAXM>
+template <typename T, int DIM, int MAXM, bool TR = false>
 __device__ void smooth_body(const LevelView<T>& L, const T* WT_DEV_RESTRICT r,
                             const T* WT_DEV_RESTRICT rhoX, const T* WT_DEV_RESTRICT rhoY,
                             const T* WT_DEV_RESTRICT rhoXY, const T* WT_DEV_RESTRICT Binv,
@@ -408,10 +467,10 @@ __device__ void smooth_body(const LevelView<T>& L, const T* WT_DEV_RESTRICT r,
       T b0[MAXM];
       T b1[MAXM > 32 ? MAXM : 1];
 #pragma unroll
-      for (int k = 0; k < MAXM; ++k) b0[k] = (k < M1 && r0) ? B[k * M1 + m0] : T(0);
+      for (int k = 0; k < MAXM; ++k) b0[k] = (k < M1 && r0) ? B[TR ? m0 * M1 + k : k * M1 + m0] : T(0);
       if constexpr (MAXM > 32) {
 #pragma unroll
-        for (int k = 0; k < MAXM; ++k) b1[k] = (k < M1 && r1) ? B[k * M1 + m1] : T(0);
+        for (int k = 0; k < MAXM; ++k) b1[k] = (k < M1 && r1) ? B[TR ? m1 * M1 + k : k * M1 + m1] : T(0);
       }
 #pragma unroll
       for (int k = 0; k < MAXM; ++k) {
@@ -428,19 +487,20 @@ __device__ void smooth_body(const LevelView<T>& L, const T* WT_DEV_RESTRICT r,
   __syncthreads();
 }
 
-// M1 bucket dispatch of smooth_body (MAXM >= M1).
-template <typename T, int DIM>
+// M1 bucket dispatch of smooth_body (MAXM >= M1).  TR: the transposed
+// blocks (A_rr^{-1})^T = (A^T)_rr^{-1}, the smoother of A^T.
+template <typename T, int DIM, bool TR = false>
 __device__ void smooth_any(const LevelView<T>& L, const T* r, const T* rhoX, const T* rhoY,
                            const T* rhoXY, const T* Binv, T* x, T omega, int first, int u0,
                            int ustep, unsigned char* sm) {
   if (L.M1 <= 9)
-    smooth_body<T, DIM, 9>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first, u0, ustep, sm);
+    smooth_body<T, DIM, 9, TR>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first, u0, ustep, sm);
   else if (L.M1 <= 17)
-    smooth_body<T, DIM, 17>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first, u0, ustep, sm);
+    smooth_body<T, DIM, 17, TR>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first, u0, ustep, sm);
   else if (L.M1 <= 25)
-    smooth_body<T, DIM, 25>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first, u0, ustep, sm);
+    smooth_body<T, DIM, 25, TR>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first, u0, ustep, sm);
   else
-    smooth_body<T, DIM, 33>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first, u0, ustep, sm);
+    smooth_body<T, DIM, 33, TR>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first, u0, ustep, sm);
 }
 
 template <typename T>

@@ -7,6 +7,7 @@
 #include <array>
 #include <stdexcept>
 #include <string>
+#include <memory>
 #include <vector>
 
 namespace wt {
@@ -108,11 +109,39 @@ struct IterGraph {
 
 }  // namespace wt
 
+namespace wt {
+// Forward values of one stage kept for its adjoint (FP64, fine level).
+struct AdjStage {
+  double *eta_f = nullptr, *u_f = nullptr, *w_f = nullptr;   // filtered stage input
+  double *eta_n = nullptr, *f_eta = nullptr;                 // eta^(k), kinematic f
+  double *us = nullptr, *ws = nullptr, *p = nullptr;         // u*, w*, p
+};
+constexpr int kAdjCols = 22;     // per-column accumulators of the reverse stage
+// Buffers of the adjoint step (allocated at the first adjoint call).
+struct AdjBufs {
+  Arena ar;
+  AdjStage st[5];
+  double *Le = nullptr, *Lu = nullptr, *Lw = nullptr;        // adjoints of the stage outputs
+  double *LKe = nullptr, *LKu = nullptr, *LKw = nullptr;
+  double *LKu1 = nullptr, *LKw1 = nullptr, *LGx = nullptr, *q = nullptr, *lp = nullptr;
+  double *lrhs = nullptr, *t1 = nullptr, *px = nullptr, *ux = nullptr, *wx = nullptr;
+  double *lux = nullptr, *lwx = nullptr, *lut = nullptr, *lwt = nullptr, *lFu = nullptr, *lFw = nullptr;
+  double *lh = nullptr;                                      // dJ/dh of this step
+  double* cols = nullptr;                                    // kAdjCols x ncols
+  double* FchebT = nullptr;                                  // transposed sigma filter
+  long ncols = 0;
+  int last_its = 0;
+  double last_rel = 0.0;
+  double* col(int i) { return cols + (long)i * ncols; }
+};
+}  // namespace wt
+
 struct wt_tank {
   wt::Prof prof;
   // graphs[key][j], key = 0: FP64 V-cycle, 1: FP32 V-cycle in FP64 FGMRES,
-  // 2: FP32 FGMRES; rebuilt after any option or hierarchy change
-  std::vector<wt::IterGraph> graphs[3];
+  // 2: FP32 FGMRES; key + 3: the same for A^T; rebuilt after any option or
+  // hierarchy change
+  std::vector<wt::IterGraph> graphs[6];
   bool use_graphs = true;
   cudaStream_t own_stream = nullptr;
   cudaEvent_t order_ev = nullptr;
@@ -159,6 +188,7 @@ struct wt_tank {
   double *io_s1 = nullptr, *io_s2 = nullptr, *io_f1 = nullptr, *io_f2 = nullptr;
   double time = 0;
   bool have_state = false;
+  std::unique_ptr<wt::AdjBufs> adj;   // adjoint step buffers (first adjoint call)
   int* dflag = nullptr;
   int* hflag = nullptr;            // pinned
   double* hst = nullptr;           // pinned

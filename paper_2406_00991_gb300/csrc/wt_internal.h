@@ -98,10 +98,15 @@ template <typename T> cudaError_t launch_rowpass(const RowPass<T>& a, cudaStream
 template <typename T>
 cudaError_t launch_op_cols(const LevelView<T>& L, const T* p, const T* Px, const T* Py,
                            T* Gx, T* Gy, T* part, cudaStream_t s);
+// Column part of A^T (2D only): Mx = mu_x, part as in opcolsT_body.
+template <typename T>
+cudaError_t launch_op_cols_T(const LevelView<T>& L, const T* lam, const T* Dlam, T* Mx, T* part,
+                             cudaStream_t s);
+// tr != 0: the transposed blocks (smoother of A^T).
 template <typename T>
 cudaError_t launch_smooth_cols(const LevelView<T>& L, const T* r, const T* rhoX, const T* rhoY,
                                const T* rhoXY, const T* Binv, int nclass, T* x, T omega,
-                               int first, cudaStream_t s);
+                               int first, int tr, cudaStream_t s);
 // out[mo][c] = sum_mi M[mo][mi] in[mi][c] for c < ncols (sigma transfers, filter)
 template <typename T>
 cudaError_t launch_col_matrix(const T* M, int Mo, int Mi, const T* in, T* out, int ncols,
@@ -168,7 +173,7 @@ template <typename T> cudaError_t launch_vcycle_tail(const TailArgs<T>& a, int d
 cudaError_t launch_coarse_factor(const LevelView<double>& L, const double* Dx, const double* Dy,
                                  double* LU, int* piv, int* flag, cudaStream_t s);
 template <typename T>
-cudaError_t launch_coarse_solve(int n, const double* LU, const int* piv, const T* f, T* x,
+cudaError_t launch_coarse_solve(int n, const double* LU, const int* piv, int tr, const T* f, T* x,
                                 cudaStream_t s);
 
 // Vector / Krylov kernels (wt_krylov.cu).

@@ -111,10 +111,25 @@ void setup_geometry(wt_tank& t, const double* ea, const double* eb, int precisio
 // ------------------------------------------------------------------ operator
 // out = A x (f == nullptr) or out = f - A x; nyq: Nyquist coefficients of out.
 template <typename T>
-void apply_op(wt_tank& t, int l, const T* x, T* out, const T* f, bool nyq) {
+void apply_op(wt_tank& t, int l, const T* x, T* out, const T* f, bool nyq, bool tr) {
   auto& L = levels<T>(t)[l];
   cudaStream_t s = t.s;
   const auto V = L.view(twiddles<T>(t), t.logNtw, t.L);
+  if (tr) {
+    // A^T lam = part - D_x mu_x (2D): D_x lam, the column kernel, then the
+    // x-derivative of mu_x subtracted in the epilogue of the last row pass
+    if (L.Ny != 1) throw WtError{WT_ENOTSUP, "the transposed operator is 2D only"};
+    run_rowpass(t, xpass<T>(t, x, L.t1, L.M1, L.Nx, L.Nx, XOP_DERIV));
+    WT_LAUNCH(t, K_OPCOLS, sizeof(T) * (4.0 * L.n + 7.0 * L.ncols), 6.0 * L.M1 * L.M1 * L.ncols, launch_op_cols_T<T>(V, x, L.t1, L.t2, L.t3, s));
+    RowPass<T> a = xpass<T>(t, L.t2, out, L.M1, L.Nx, L.Nx, XOP_DERIV);
+    a.scale = T(-1);
+    a.add = L.t3;
+    a.rhs = f;
+    a.epi = f ? EPI_RESID : EPI_ADD;
+    a.nyq = nyq ? L.rhoX : nullptr;
+    run_rowpass(t, a);
+    return;
+  }
   if (L.Ny == 1) {
     run_rowpass(t, xpass<T>(t, x, L.t1, L.M1, L.Nx, L.Nx, XOP_DERIV));
     WT_LAUNCH(t, K_OPCOLS, sizeof(T) * (4.0 * L.n + 7.0 * L.ncols), 6.0 * L.M1 * L.M1 * L.ncols, launch_op_cols<T>(V, x, L.t1, nullptr, L.t2, nullptr, L.t3, s));
@@ -171,7 +186,7 @@ static void nyquist_of(wt_tank& t, Level<T>& L, const T* f) {
 
 // ------------------------------------------------------------------ V-cycle
 template <typename T>
-static void smooth(wt_tank& t, int l, T* x, const T* f, bool first, bool f_has_nyq) {
+static void smooth(wt_tank& t, int l, T* x, const T* f, bool first, bool f_has_nyq, bool tr) {
   auto& L = levels<T>(t)[l];
   const auto V = L.view(twiddles<T>(t), t.logNtw, t.L);
   const T om = (T)t.opt.omega;
@@ -179,11 +194,11 @@ static void smooth(wt_tank& t, int l, T* x, const T* f, bool first, bool f_has_n
     const bool y = L.Ny > 1;
     if (f_has_nyq) nyquist_of<T>(t, L, f);
     WT_LAUNCH(t, K_SMOOTH, sizeof(T) * (2.0 * L.n + (double)L.nclass * L.M1 * L.M1 * L.ncols), 2.0 * L.nclass * L.M1 * L.M1 * L.ncols, launch_smooth_cols<T>(V, f, f_has_nyq ? L.rhoX : nullptr, (f_has_nyq && y) ? L.rhoY : nullptr,
-                                (f_has_nyq && y) ? L.rhoXY : nullptr, L.Binv, L.nclass, x, om, 1, t.s));
+                                (f_has_nyq && y) ? L.rhoXY : nullptr, L.Binv, L.nclass, x, om, 1, tr, t.s));
   } else {
-    apply_op<T>(t, l, x, L.r, f, true);
+    apply_op<T>(t, l, x, L.r, f, true, tr);
     WT_LAUNCH(t, K_SMOOTH, sizeof(T) * (3.0 * L.n + (double)L.nclass * L.M1 * L.M1 * L.ncols), 2.0 * L.nclass * L.M1 * L.M1 * L.ncols, launch_smooth_cols<T>(V, L.r, L.rhoX, L.Ny > 1 ? L.rhoY : nullptr, L.Ny > 1 ? L.rhoXY : nullptr,
-                                L.Binv, L.nclass, x, om, 0, t.s));
+                                L.Binv, L.nclass, x, om, 0, tr, t.s));
   }
 }
 
@@ -230,8 +245,8 @@ template <> TailLevel<float>* tail_desc<float>(wt_tank& t) { return t.tl32; }
 
 // First level handled by the single-CTA V-cycle kernel (-1: none).
 template <typename T>
-static int tail_level(wt_tank& t) {
-  if (t.opt.tail_max <= 0) return -1;
+static int tail_level(wt_tank& t, bool tr) {
+  if (t.opt.tail_max <= 0 || tr) return -1;
   auto& lev = levels<T>(t);
   for (size_t l = 0; l < lev.size(); ++l)
     if (lev[l].n <= t.opt.tail_max) return (int)l;
@@ -239,11 +254,11 @@ static int tail_level(wt_tank& t) {
 }
 
 template <typename T>
-void vcycle(wt_tank& t, int l, const T* f, T* x) {
+void vcycle(wt_tank& t, int l, const T* f, T* x, bool tr) {
   auto& lev = levels<T>(t);
   const int nl = (int)lev.size();
   auto& L = lev[l];
-  if (l == tail_level<T>(t)) {
+  if (l == tail_level<T>(t, tr)) {
     TailArgs<T> a;
     a.lv = tail_desc<T>(t);
     a.l0 = l;
@@ -265,7 +280,7 @@ void vcycle(wt_tank& t, int l, const T* f, T* x) {
     return;
   }
   if (l == nl - 1) {
-    WT_LAUNCH(t, K_COARSE, 8.0 * L.n * L.n + 2.0 * sizeof(T) * L.n, 2.0 * L.n * L.n, launch_coarse_solve<T>((int)L.n, t.cLU, t.cpiv, f, x, t.s));
+    WT_LAUNCH(t, K_COARSE, 8.0 * L.n * L.n + 2.0 * sizeof(T) * L.n, 2.0 * L.n * L.n, launch_coarse_solve<T>((int)L.n, t.cLU, t.cpiv, tr ? 1 : 0, f, x, t.s));
     return;
   }
   // pre-smoothing (nu1 sweeps from a zero initial state).  A right-hand side
@@ -273,17 +288,17 @@ void vcycle(wt_tank& t, int l, const T* f, T* x) {
   // the finest level and levels reached by sigma-only coarsening may have some.
   const bool f_nyq = (l == 0) || (lev[l - 1].Nx == L.Nx);
   if (t.opt.nu1 > 0) {
-    smooth<T>(t, l, x, f, true, f_nyq);
-    for (int i = 1; i < t.opt.nu1; ++i) smooth<T>(t, l, x, f, false, false);
-    apply_op<T>(t, l, x, L.r, f, false);      // r = f - A u
+    smooth<T>(t, l, x, f, true, f_nyq, tr);
+    for (int i = 1; i < t.opt.nu1; ++i) smooth<T>(t, l, x, f, false, false, tr);
+    apply_op<T>(t, l, x, L.r, f, false, tr);  // r = f - A u
     restrict_to<T>(t, l, L.r);
   } else {
     WT_CK(cudaMemsetAsync(x, 0, sizeof(T) * L.n, t.s));
     restrict_to<T>(t, l, f);
   }
-  vcycle<T>(t, l + 1, lev[l + 1].f, lev[l + 1].x);
+  vcycle<T>(t, l + 1, lev[l + 1].f, lev[l + 1].x, tr);
   prolong_add<T>(t, l, x);                     // u = u + P e_c
-  for (int i = 0; i < t.opt.nu2; ++i) smooth<T>(t, l, x, f, false, false);
+  for (int i = 0; i < t.opt.nu2; ++i) smooth<T>(t, l, x, f, false, false, tr);
 }
 
 // ------------------------------------------------------------------ norms
@@ -308,20 +323,20 @@ template <> float* Zbuf<float>(wt_tank& t) { return t.Z32; }
 // vectors, or (pre32 with T = double) an FP32 V-cycle on the rounded vector
 // with the correction widened back to FP64.
 template <typename T>
-static void precondition(wt_tank& t, const T* v, T* z, bool pre32);
+static void precondition(wt_tank& t, const T* v, T* z, bool pre32, bool tr);
 template <>
-void precondition<float>(wt_tank& t, const float* v, float* z, bool) {
-  vcycle<float>(t, 0, v, z);
+void precondition<float>(wt_tank& t, const float* v, float* z, bool, bool tr) {
+  vcycle<float>(t, 0, v, z, tr);
 }
 template <>
-void precondition<double>(wt_tank& t, const double* v, double* z, bool pre32) {
+void precondition<double>(wt_tank& t, const double* v, double* z, bool pre32, bool tr) {
   if (!pre32) {
-    vcycle<double>(t, 0, v, z);
+    vcycle<double>(t, 0, v, z, tr);
     return;
   }
   const long n = t.n;
   WT_LAUNCH(t, K_KRYLOV, 12.0 * n, 0.0, (launch_convert<double, float>(v, t.b32, n, nullptr, 0, t.s)));
-  vcycle<float>(t, 0, t.b32, t.e32);
+  vcycle<float>(t, 0, t.b32, t.e32, tr);
   WT_LAUNCH(t, K_KRYLOV, 12.0 * n, 0.0, (launch_convert<float, double>(t.e32, z, n, nullptr, 0, t.s)));
 }
 
@@ -341,7 +356,7 @@ void destroy_graphs(wt_tank& t) {
 // Arnoldi step j: z_j = M^{-1} v_j, w = A z_j, CGS2 against v_0..v_j,
 // Givens update, v_{j+1} = w / h_{j+1,j}.  Device-only: capturable.
 template <typename T>
-static void arnoldi_step(wt_tank& t, int j, bool pre32) {
+static void arnoldi_step(wt_tank& t, int j, bool pre32, bool tr) {
   const long n = levels<T>(t)[0].n;
   const int m = t.opt.restart;
   T* V = Vbuf<T>(t);
@@ -349,8 +364,8 @@ static void arnoldi_step(wt_tank& t, int j, bool pre32) {
   T* vj = V + (long)j * n;
   T* zj = Z + (long)j * n;
   T* w = V + (long)(j + 1) * n;
-  precondition<T>(t, vj, zj, pre32);                     // z_j = M^{-1} v_j
-  apply_op<T>(t, 0, zj, w, nullptr, false);              // w = A z_j
+  precondition<T>(t, vj, zj, pre32, tr);                 // z_j = M^{-1} v_j
+  apply_op<T>(t, 0, zj, w, nullptr, false, tr);          // w = A z_j
   WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (j + 2), 2.0 * n * (j + 1),
             launch_dots<T>(w, V, n, j + 1, n, t.partial, t.nblk, 0, t.s));
   WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk * (j + 1), 0.0,
@@ -366,10 +381,10 @@ static void arnoldi_step(wt_tank& t, int j, bool pre32) {
 // Run Arnoldi step j, replaying its CUDA graph (captured at first use) unless
 // per-launch timing is on.
 template <typename T>
-static void arnoldi_step_graph(wt_tank& t, int j, bool pre32) {
-  const int key = sizeof(T) == 4 ? 2 : (pre32 ? 1 : 0);
+static void arnoldi_step_graph(wt_tank& t, int j, bool pre32, bool tr) {
+  const int key = (sizeof(T) == 4 ? 2 : (pre32 ? 1 : 0)) + (tr ? 3 : 0);
   if (!t.use_graphs || t.prof.mask != 0) {
-    arnoldi_step<T>(t, j, pre32);
+    arnoldi_step<T>(t, j, pre32, tr);
     return;
   }
   auto& gv = t.graphs[key];
@@ -380,7 +395,7 @@ static void arnoldi_step_graph(wt_tank& t, int j, bool pre32) {
     cudaGraph_t graph = nullptr;
     WT_CK(cudaStreamBeginCapture(t.s, cudaStreamCaptureModeThreadLocal));
     try {
-      arnoldi_step<T>(t, j, pre32);
+      arnoldi_step<T>(t, j, pre32, tr);
     } catch (...) {
       cudaStreamEndCapture(t.s, &graph);
       if (graph) cudaGraphDestroy(graph);
@@ -404,7 +419,7 @@ static void arnoldi_step_graph(wt_tank& t, int j, bool pre32) {
 // FP64 iterate with an FP32 correction (flexible Krylov iterative refinement).
 template <typename T>
 double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit, int* its_out,
-              bool pre32) {
+              bool pre32, bool tr) {
   auto& L0 = levels<T>(t)[0];
   const long n = L0.n;
   const int m = t.opt.restart;
@@ -413,7 +428,7 @@ double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit,
   int its = 0;
   double rel = 1.0;
   for (;;) {
-    apply_op<T>(t, 0, x, V, b, false);                       // r = b - A x -> V_0
+    apply_op<T>(t, 0, x, V, b, false, tr);                   // r = b - A x -> V_0
     WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n, 2.0 * n,
               launch_dots<T>(V, nullptr, 0, 0, n, t.partial, t.nblk, 1, t.s));
     WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk, 0.0,
@@ -425,7 +440,7 @@ double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit,
     WT_LAUNCH(t, K_KRYLOV, 2.0 * sizeof(T) * n, (double)n, launch_scale_copy<T>(V, V, n, t.st + 2, 0, t.s));
     int k = 0;
     for (int j = 0; j < m; ++j) {
-      arnoldi_step_graph<T>(t, j, pre32);
+      arnoldi_step_graph<T>(t, j, pre32, tr);
       WT_CK(cudaMemcpyAsync(t.hst, t.st, sizeof(double) * 6, cudaMemcpyDeviceToHost, t.s));
       WT_CK(cudaStreamSynchronize(t.s));
       ++its;
@@ -441,7 +456,8 @@ double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit,
 }
 
 // ------------------------------------------------------------------ solves
-int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_solve_info* info) {
+int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_solve_info* info,
+                         bool tr) {
   const long n = t.n;
   const double bn = norm2<double>(t, b, n);
   int its_total = 0, refinements = 0;
@@ -457,7 +473,7 @@ int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_
       // FP64 iterative refinement: r = b - A x (FP64); A e = r / |r| solved by
       // FP32 flexible GMRES with the FP32 V-cycle to inner_tol; x += |r| e.
       for (;;) {
-        apply_op<double>(t, 0, x, t.r64, b, false);
+        apply_op<double>(t, 0, x, t.r64, b, false, tr);
         const double rn = norm2<double>(t, t.r64, n);      // |r| also left in stN[0]
         rel = rn / bn;
         if (rel <= tol || refinements >= t.opt.max_ir || its_total >= t.opt.max_it || !std::isfinite(rel))
@@ -467,14 +483,14 @@ int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_
         WT_CK(cudaMemsetAsync(t.e32, 0, sizeof(float) * n, t.s));
         int its = 0;
         fgmres<float>(t, t.b32, t.e32, 1.0, t.opt.inner_tol,
-                      std::min(t.opt.restart, t.opt.max_it - its_total), &its, false);
+                      std::min(t.opt.restart, t.opt.max_it - its_total), &its, false, tr);
         its_total += its;
         WT_LAUNCH(t, K_KRYLOV, 20.0 * n, 2.0 * n, launch_axpy_from<float>(x, t.e32, n, t.stN, t.s));
         ++refinements;
       }
     } else {
       int its = 0;
-      rel = fgmres<double>(t, b, x, bn, tol, t.opt.max_it, &its, t.opt.mode == WT_MIXED);
+      rel = fgmres<double>(t, b, x, bn, tol, t.opt.max_it, &its, t.opt.mode == WT_MIXED, tr);
       its_total = its;
     }
     if (!(rel <= tol)) status = WT_ENOCONV;
@@ -494,9 +510,9 @@ int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_
   return status;
 }
 
-template void apply_op<double>(wt_tank&, int, const double*, double*, const double*, bool);
-template void apply_op<float>(wt_tank&, int, const float*, float*, const float*, bool);
-template void vcycle<double>(wt_tank&, int, const double*, double*);
-template void vcycle<float>(wt_tank&, int, const float*, float*);
+template void apply_op<double>(wt_tank&, int, const double*, double*, const double*, bool, bool);
+template void apply_op<float>(wt_tank&, int, const float*, float*, const float*, bool, bool);
+template void vcycle<double>(wt_tank&, int, const double*, double*, bool);
+template void vcycle<float>(wt_tank&, int, const float*, float*, bool);
 
 }  // namespace wt

@@ -75,17 +75,28 @@ void setup_bathymetry(wt_tank& t, const double* h_fine);
 void setup_geometry(wt_tank& t, const double* ea, const double* eb, int precision, bool blocks,
                     bool coarse);
 
-template <typename T> void apply_op(wt_tank& t, int l, const T* x, T* out, const T* f, bool nyq);
-template <typename T> void vcycle(wt_tank& t, int l, const T* f, T* x);
+// tr: the transposed operator A^T (2D) and the V-cycle of A^T (transposed
+// smoother blocks and coarsest inverse, the same transfers).
+template <typename T> void apply_op(wt_tank& t, int l, const T* x, T* out, const T* f, bool nyq,
+                                    bool tr = false);
+template <typename T> void vcycle(wt_tank& t, int l, const T* f, T* x, bool tr = false);
 template <typename T>
 double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit, int* its_out,
-              bool pre32);
+              bool pre32, bool tr = false);
 
 // Release the captured Arnoldi-step graphs (after option / hierarchy changes).
 void destroy_graphs(wt_tank& t);
 
 // Solve A p = b on the finest level (device pointers, FP64) with the tank's
 // options; x holds the initial guess.  Geometry must be set up already.
-int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_solve_info* info);
+int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_solve_info* info,
+                         bool tr = false);
+
+// Reverse one recorded Runge-Kutta stage k of a 2D tank (wt_adjoint.cu):
+// adjoints in t.adj (Le, Lu, Lw, LKe, LKu, LKw) go from the stage output to
+// its input; t.adj->lh accumulates dJ/dh.  alpha, beta: the 2N coefficients.
+int adjoint_stage(wt_tank& t, int k, double dt, const double* alpha, const double* beta);
+// y += x (n values, device pointers).
+cudaError_t launch_add(double* y, const double* x, long n, cudaStream_t s);
 
 }  // namespace wt
