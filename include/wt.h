@@ -93,6 +93,10 @@ typedef struct wt_options {
   double inner_tol;  /* WT_REFINE: relative residual of each FP32 inner
                         solve (1e-5)                                         */
   int max_ir;        /* WT_REFINE: refinement steps per solve (30)           */
+  int vcycle_grid;   /* 1: the whole V-cycle of the finest-level
+                        preconditioner as one cooperative launch with grid
+                        barriers (bounded waits; WT_ETIMEOUT if one gives
+                        up); 0: one launch per phase (default 0)            */
 } wt_options;
 
 typedef struct wt_solve_info {
@@ -236,6 +240,10 @@ int wt_adjoint_step(wt_tank* t, double dt, const double* eta, const double* u, c
  */
 int wt_autotune(wt_tank* t, const double* eta_a, const double* eta_b, const double* rhs, int reps,
                 wt_options* best, double* best_ms, double* entry_ms);
+/* The same search with one wt_step(dt) from the tank's current state as the
+ * timed unit (the state, time included, is restored after every trial and on
+ * return; solver statistics restart).  Needs a state (wt_set_state). */
+int wt_autotune_step(wt_tank* t, double dt, int reps, wt_options* best, double* best_ms, double* entry_ms);
 
 /*
  * Batches of independent 2D tanks of uneven size, advanced together by one

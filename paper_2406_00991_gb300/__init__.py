@@ -31,7 +31,7 @@ class wt_options(ctypes.Structure):
                 ("max_it", ctypes.c_int),
                 ("filter", ctypes.c_int), ("linear", ctypes.c_int), ("coarsest_max", ctypes.c_int),
                 ("bc_transfer", ctypes.c_int), ("tail_max", ctypes.c_int),
-                ("inner_tol", ctypes.c_double), ("max_ir", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("max_ir", ctypes.c_int), ("vcycle_grid", ctypes.c_int)]
 
 
 class wt_solve_info(ctypes.Structure):
@@ -71,6 +71,7 @@ def _load():
         "wt_get_launches": [P, ctypes.POINTER(ctypes.c_long)],
         "wt_apply_operator_static": [I, I, D, P, P, P, P, P, P],
         "wt_autotune": [P, P, P, P, I, ctypes.POINTER(wt_options), ctypes.POINTER(D), ctypes.POINTER(D)],
+        "wt_autotune_step": [P, D, I, ctypes.POINTER(wt_options), ctypes.POINTER(D), ctypes.POINTER(D)],
         "wt_set_bathymetry": [P, P],
         "wt_apply_operator_transposed": [P, P, P, P, P, I],
         "wt_adjoint_solve": [P, P, P, P, P, D, ctypes.POINTER(wt_solve_info)],
@@ -274,6 +275,13 @@ def wt_autotune(t, eta_a, eta_b, rhs, reps=3):
     return st, o, b.value, e.value
 
 
+def wt_autotune_step(t, dt, reps=3):
+    o = wt_options()
+    b, e = ctypes.c_double(), ctypes.c_double()
+    st = _lib.wt_autotune_step(t, float(dt), int(reps), ctypes.byref(o), ctypes.byref(b), ctypes.byref(e))
+    return st, o, b.value, e.value
+
+
 def wt_create_batch(Nx, Nz, L, bathymetry, g=9.81, nu=0.0):
     """Batch of 2D tanks; bathymetry is a list of float64 arrays (host or device)."""
     n = len(Nx)
@@ -415,6 +423,12 @@ class Tank:
 
     def rk_stage(self, k, dt):
         _check(wt_rk_stage(self.handle, k, dt))
+
+    def autotune_step(self, dt, reps=3):
+        """Pick the fastest settings for one step from the current state (restored)."""
+        st, o, best, entry = wt_autotune_step(self.handle, dt, reps)
+        _check(st)
+        return {k: getattr(o, k) for k, _ in wt_options._fields_}, best, entry
 
     def set_bathymetry(self, h):
         _check(wt_set_bathymetry(self.handle, h))

@@ -294,6 +294,7 @@ int check_options(const wt_options& o) {
     return fail(WT_EINVAL, "mode must be WT_FP64, WT_MIXED or WT_REFINE");
   if (!(o.inner_tol > 0) || !(o.inner_tol < 1)) return fail(WT_EINVAL, "inner_tol must be in (0, 1)");
   if (o.max_ir < 1) return fail(WT_EINVAL, "max_ir must be >= 1");
+  if (o.vcycle_grid != 0 && o.vcycle_grid != 1) return fail(WT_EINVAL, "vcycle_grid must be 0 or 1");
   if (!(o.tol > 0) || !(o.tol < 1)) return fail(WT_EINVAL, "tol must be in (0, 1)");
   if (o.restart < 1 || o.restart > 31) return fail(WT_EINVAL, "restart must be in [1, 31]");
   if (o.nu1 < 0 || o.nu1 > 8 || o.nu2 < 0 || o.nu2 > 8 || o.nu1 + o.nu2 == 0)
@@ -519,6 +520,7 @@ int wt_default_options(wt_options* o) {
   o->tail_max = 0;
   o->inner_tol = 1e-5;
   o->max_ir = 30;
+  o->vcycle_grid = 0;
   return WT_OK;
 }
 
@@ -589,6 +591,7 @@ int wt_create(int Nx, int Ny, int Nz, double L, double g, double nu, const doubl
     t->partial = ar.alloc<double>((size_t)t->nblk * 40);
     t->st = ar.alloc<double>(4608);
     t->stN = ar.alloc<double>(4608);
+    t->gbar = ar.alloc<GridBar>(1);
     t->x64 = ar.alloc<double>(n); t->r64 = ar.alloc<double>(n); t->b64 = ar.alloc<double>(n);
     t->b32 = ar.alloc<float>(n); t->e32 = ar.alloc<float>(n);
     t->eta = ar.alloc<double>(nc); t->eta_new = ar.alloc<double>(nc); t->Keta = ar.alloc<double>(nc);

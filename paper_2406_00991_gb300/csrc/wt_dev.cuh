@@ -135,8 +135,9 @@ __device__ void rowpass_body(const RowPass<T>& a, int ppc, int u0, int ustep, un
   c2* tws = buf1 + ppc * S;
   c2* eA = tws + Nmax / 2;                     // add operand rows (pair packed)
   c2* eB = eA + (use_add ? ppc * S : 0);       // rhs (RESID) or old out (ACC)
-  for (int t = threadIdx.x; t < Nmax / 2; t += blockDim.x) tws[t] = a.tw[t << (a.logNtw - logNmax)];
   const int npairs = (a.nrows + 1) >> 1;
+  if (u0 * ppc >= npairs) return;              // no unit for this CTA
+  for (int t = threadIdx.x; t < Nmax / 2; t += blockDim.x) tws[t] = a.tw[t << (a.logNtw - logNmax)];
   const T inv_n = T(1) / T(a.Nin);
 
   for (int p0 = u0 * ppc; p0 < npairs; p0 += ustep * ppc) {
@@ -180,6 +181,14 @@ __device__ void rowpass_body(const RowPass<T>& a, int ppc, int u0, int ustep, un
         if (2 * an < nkeep2) {
           const int nin = ns < 0 ? ns + a.Nin : ns;
           v = X[q * S + nin];
+        }
+      } else if (a.op == XOP_RESAMPLE_DERIV) {
+        const int an = ns < 0 ? -ns : ns;
+        if (2 * an < nkeep2) {
+          const int nin = ns < 0 ? ns + a.Nin : ns;
+          const c2 x = X[q * S + nin];
+          const T kap = a.kscale * T(ns);
+          v = mk<T>(-kap * x.y, kap * x.x);
         }
       } else if (a.op == XOP_FILTER) {
         const c2 x = X[q * S + n];

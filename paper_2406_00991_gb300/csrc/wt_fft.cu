@@ -49,4 +49,40 @@ cudaError_t launch_rowpass(const RowPass<T>& a, cudaStream_t s) {
 template cudaError_t launch_rowpass<float>(const RowPass<float>&, cudaStream_t);
 template cudaError_t launch_rowpass<double>(const RowPass<double>&, cudaStream_t);
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_rowpass_multi(const __grid_constant__ MultiPass<T> m) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int i = 0;
+  while (i + 1 < m.n && (int)blockIdx.x >= m.start[i + 1]) ++i;
+  const int u = blockIdx.x - m.start[i];
+  rowpass_body<T>(m.d[i], 1, u, m.start[i + 1] - m.start[i], smraw);
+}
+
+template <typename T>
+cudaError_t launch_rowpass_multi(const MultiPass<T>& m0, cudaStream_t s) {
+  if (m0.n <= 0) return cudaSuccess;
+  if (m0.n > kMaxPasses) return cudaErrorInvalidValue;
+  MultiPass<T> m = m0;
+  size_t smem = 0;
+  m.start[0] = 0;
+  for (int i = 0; i < m.n; ++i) {
+    const int npairs = (m.d[i].nrows + 1) / 2;
+    m.start[i + 1] = m.start[i] + npairs;
+    smem = std::max(smem, rowpass_smem(m.d[i], 1));
+  }
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_rowpass_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  if (m.start[m.n] <= 0) return cudaSuccess;
+  k_rowpass_multi<T><<<m.start[m.n], 256, smem, s>>>(m);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_rowpass_multi<float>(const MultiPass<float>&, cudaStream_t);
+template cudaError_t launch_rowpass_multi<double>(const MultiPass<double>&, cudaStream_t);
+
 }  // namespace wt

@@ -192,5 +192,6 @@ struct wt_tank {
   int* dflag = nullptr;
   int* hflag = nullptr;            // pinned
   double* hst = nullptr;           // pinned
+  wt::GridBar* gbar = nullptr;     // barrier of the cooperative V-cycle
   long solves = 0, iterations = 0;
 };

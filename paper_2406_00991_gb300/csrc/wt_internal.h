@@ -62,7 +62,9 @@ int set_error(int code, const char* msg);
 
 // Spectral x-row / y-line passes (wt_fft.cu).
 enum XEpi { EPI_STORE = 0, EPI_ADD = 1, EPI_RESID = 2, EPI_ACC = 3 };
-enum XOp { XOP_DERIV = 0, XOP_RESAMPLE = 1, XOP_FILTER = 2, XOP_NONE = 3 };
+// XOP_RESAMPLE_DERIV: the derivative of the Fourier-resampled row (truncate or
+// zero-pad to Nout, then multiply by i kappa) in one transform pair.
+enum XOp { XOP_DERIV = 0, XOP_RESAMPLE = 1, XOP_FILTER = 2, XOP_NONE = 3, XOP_RESAMPLE_DERIV = 4 };
 
 template <typename T>
 struct RowPass {
@@ -93,6 +95,32 @@ struct RowPass {
 };
 
 template <typename T> cudaError_t launch_rowpass(const RowPass<T>& a, cudaStream_t s);
+
+// Independent row passes in one launch (one pair of rows per CTA): the
+// passes must not read what another pass of the same launch writes.
+constexpr int kMaxPasses = 32;
+template <typename T>
+struct MultiPass {
+  RowPass<T> d[kMaxPasses];
+  int start[kMaxPasses + 1];   // first CTA of each pass; start[n] = grid size
+  int n = 0;
+};
+template <typename T> cudaError_t launch_rowpass_multi(const MultiPass<T>& m, cudaStream_t s);
+
+// Metric of several levels in one launch (FP64, plus the FP32 copy when m32).
+struct MetricLevel {
+  int ncols;
+  const double *h, *hx, *hy, *ea, *eax, *eay, *eb, *ebx, *eby;   // y slopes NULL in 2D
+  double* meta;
+  float* meta32;               // NULL: no FP32 copy
+};
+constexpr int kMaxMetricLevels = 16;
+struct MetricMulti {
+  MetricLevel lv[kMaxMetricLevels];
+  int n = 0;
+  int* flag = nullptr;
+};
+cudaError_t launch_metric_multi(const MetricMulti& m, cudaStream_t s);
 
 // Column kernels (wt_col.cu).
 template <typename T>
@@ -168,6 +196,20 @@ struct TailArgs {
   int smem;                 // dynamic shared memory of the launch
 };
 template <typename T> cudaError_t launch_vcycle_tail(const TailArgs<T>& a, int dim, cudaStream_t s);
+
+// Grid-wide barrier state of the cooperative V-cycle (device memory, zeroed
+// at creation): a monotonic arrival counter and the abort flag.
+struct GridBar {
+  unsigned long long count;   // arrivals since creation (monotonic)
+  int abort;
+  int pad;
+};
+// The whole V-cycle from level a.l0 in one cooperative launch (every CTA
+// resident); phases separated by a bounded grid barrier.  A barrier that
+// waits longer than about a second sets bit 32 of *flag and bar->abort, and
+// every CTA returns at its next barrier.
+template <typename T>
+cudaError_t launch_vcycle_grid(const TailArgs<T>& a, int dim, GridBar* bar, int* flag, cudaStream_t s);
 
 // Dense coarsest level (wt_coarse.cu), always FP64 arithmetic.
 cudaError_t launch_coarse_factor(const LevelView<double>& L, const double* Dx, const double* Dy,

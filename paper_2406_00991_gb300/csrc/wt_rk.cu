@@ -23,6 +23,18 @@ __global__ void k_metric_fill(int ncols, const double* __restrict__ h, const dou
   metric_body(TLOOP, ncols, h, hx, hy, ea, eax, eay, eb, ebx, eby, meta, flag);
 }
 
+// Every level's metric in one launch: blockIdx.y = level.
+__global__ void k_metric_multi(const __grid_constant__ MetricMulti m) {
+  const MetricLevel& L = m.lv[blockIdx.y];
+  const long t0 = (long)blockIdx.x * blockDim.x + threadIdx.x, ts = (long)gridDim.x * blockDim.x;
+  metric_body(t0, ts, L.ncols, L.h, L.hx, L.hy, L.ea, L.eax, L.eay, L.eb, L.ebx, L.eby, L.meta, m.flag);
+  if (L.meta32) {
+    // each thread converts the columns it wrote
+    for (long c = t0; c < L.ncols; c += ts)
+      for (int f = 0; f < kMeta; ++f) L.meta32[f * (long)L.ncols + c] = (float)L.meta[f * (long)L.ncols + c];
+  }
+}
+
 template <typename Ti, typename To>
 __global__ void k_cast(const Ti* __restrict__ in, To* __restrict__ out, long n) {
   GRID_LOOP(i, n) out[i] = (To)in[i];
@@ -70,6 +82,15 @@ cudaError_t launch_metric_fill(int ncols, const double* h, const double* hx, con
                                const double* eb, const double* ebx, const double* eby, double* meta,
                                int* flag, cudaStream_t s) {
   k_metric_fill<<<blocks_n(ncols), 256, 0, s>>>(ncols, h, hx, hy, ea, eax, eay, eb, ebx, eby, meta, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_metric_multi(const MetricMulti& m, cudaStream_t s) {
+  if (m.n <= 0) return cudaSuccess;
+  if (m.n > kMaxMetricLevels) return cudaErrorInvalidValue;
+  int maxc = 1;
+  for (int i = 0; i < m.n; ++i) maxc = std::max(maxc, m.lv[i].ncols);
+  k_metric_multi<<<dim3(blocks_n(maxc), m.n), 256, 0, s>>>(m);
   return cudaGetLastError();
 }
 

@@ -78,7 +78,51 @@ void setup_bathymetry(wt_tank& t, const double* h_fine) {
 void setup_geometry(wt_tank& t, const double* ea, const double* eb, int precision, bool blocks,
                     bool coarse) {
   const int nl = (int)t.L64.size();
-  for (int l = 0; l < nl; ++l) {
+  if (t.Ny == 1) {
+    // 2D: every level's truncated surfaces and slopes read only the fine
+    // surfaces, so all of them are independent passes of one launch; then
+    // one launch fills every level's metric (and its FP32 copy)
+    MultiPass<double> mp;
+    auto flush = [&]() {
+      WT_LAUNCH(t, K_ROWPASS, 0.0, 0.0, launch_rowpass_multi<double>(mp, t.s));
+      mp.n = 0;
+    };
+    auto add = [&](const double* in, double* out, int Nout, int op) {
+      if (mp.n == kMaxPasses) flush();
+      mp.d[mp.n++] = xpass<double>(t, in, out, 1, t.Nx, Nout, op);
+    };
+    MetricMulti mm;
+    mm.flag = t.dflag;
+    for (int l = 0; l < nl; ++l) {
+      auto& S = t.S[l];
+      auto& L = t.L64[l];
+      if (l == 0) {
+        add(ea, S.eax, t.Nx, XOP_DERIV);
+        add(eb, S.ebx, t.Nx, XOP_DERIV);
+      } else {
+        add(ea, S.ea, L.Nx, XOP_RESAMPLE);
+        add(ea, S.eax, L.Nx, XOP_RESAMPLE_DERIV);
+        add(eb, S.eb, L.Nx, XOP_RESAMPLE);
+        add(eb, S.ebx, L.Nx, XOP_RESAMPLE_DERIV);
+      }
+      MetricLevel& M = mm.lv[mm.n++];
+      M.ncols = L.ncols;
+      M.h = S.h;
+      M.hx = S.hx;
+      M.hy = nullptr;
+      M.ea = l == 0 ? ea : S.ea;
+      M.eax = S.eax;
+      M.eay = nullptr;
+      M.eb = l == 0 ? eb : S.eb;
+      M.ebx = S.ebx;
+      M.eby = nullptr;
+      M.meta = L.meta;
+      M.meta32 = precision == WT_FP32 ? t.L32[l].meta : nullptr;
+    }
+    flush();
+    WT_LAUNCH(t, K_STAGE, 8.0 * t.ncols * 23, 20.0 * t.ncols, launch_metric_multi(mm, t.s));
+  }
+  for (int l = 0; l < nl && t.Ny > 1; ++l) {
     auto& S = t.S[l];
     auto& L = t.L64[l];
     const bool y = L.Ny > 1;
@@ -258,6 +302,30 @@ void vcycle(wt_tank& t, int l, const T* f, T* x, bool tr) {
   auto& lev = levels<T>(t);
   const int nl = (int)lev.size();
   auto& L = lev[l];
+  if (l == 0 && !tr && t.opt.vcycle_grid) {
+    // the whole cycle in one cooperative launch; the dynamic shared memory
+    // holds the largest unprefetched row pair (twice the finest row plus
+    // half a row of twiddles) and the small per-phase tables
+    const int Nmax = std::max(L.Nx, L.Ny);
+    const size_t need = (size_t)(2 * Nmax + Nmax / 2) * sizeof(c2_t<T>);
+    const size_t smem = std::max<size_t>(need, 48 * 1024);
+    if (smem <= 200 * 1024) {
+      TailArgs<T> a;
+      a.lv = tail_desc<T>(t);
+      a.l0 = 0;
+      a.nl = nl;
+      a.f0 = f;
+      a.x0 = x;
+      a.f0_nyq = 1;
+      a.omega = (T)t.opt.omega;
+      a.nu1 = t.opt.nu1;
+      a.nu2 = t.opt.nu2;
+      a.AinvT = t.cLU;
+      a.smem = (int)smem;
+      WT_LAUNCH(t, K_TAIL, 0.0, 0.0, launch_vcycle_grid<T>(a, L.Ny > 1 ? 3 : 2, t.gbar, t.dflag, t.s));
+      return;
+    }
+  }
   if (l == tail_level<T>(t, tr)) {
     TailArgs<T> a;
     a.lv = tail_desc<T>(t);
@@ -498,6 +566,11 @@ int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_
   WT_CK(cudaMemcpyAsync(t.hflag, t.dflag, sizeof(int), cudaMemcpyDeviceToHost, t.s));
   WT_CK(cudaStreamSynchronize(t.s));
   if (*t.hflag & 7) status = WT_EBREAK;
+  if (*t.hflag & 32) {
+    status = WT_ETIMEOUT;                 // a grid barrier gave up: reset it
+    WT_CK(cudaMemsetAsync(t.gbar, 0, sizeof(GridBar), t.s));
+    WT_CK(cudaStreamSynchronize(t.s));
+  }
   if (!std::isfinite(rel)) status = WT_EBREAK;
   t.solves += 1;
   t.iterations += its_total;

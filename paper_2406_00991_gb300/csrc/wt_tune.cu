@@ -118,3 +118,87 @@ extern "C" int wt_autotune(wt_tank* t, const double* eta_a, const double* eta_b,
   if (entry_ms) *entry_ms = e_ms;
   return WT_OK;
 }
+
+// Step-level variant: the tank's own Runge-Kutta step (current state, dt) is
+// the timed unit, so the choice covers every solve of a step and the stage
+// work around it.  The state is restored after every trial.
+extern "C" int wt_autotune_step(wt_tank* t, double dt, int reps, wt_options* best, double* best_ms,
+                                double* entry_ms) {
+  if (!t) return wt::set_error(WT_EINVAL, "wt_autotune_step: NULL tank");
+  if (reps < 1 || reps > 100) return wt::set_error(WT_EINVAL, "wt_autotune_step: reps must be in [1, 100]");
+  if (!(dt > 0)) return wt::set_error(WT_EINVAL, "wt_autotune_step: dt must be positive");
+  wt_options entry{};
+  wt_get_options(t, &entry);
+  int nl = 0;
+  int dims[3 * 16];
+  if (wt_get_levels(t, &nl, dims) != WT_OK) return WT_EINVAL;
+  const int Nx = dims[0], Ny = dims[1], Nz = dims[2];
+  const size_t ncols = (size_t)Nx * Ny, n = ncols * (Nz + 1);
+  DevBuf e0, u0, v0, w0;
+  if (cudaMalloc(&e0.p, sizeof(double) * ncols) != cudaSuccess || cudaMalloc(&u0.p, sizeof(double) * n) != cudaSuccess ||
+      cudaMalloc(&v0.p, sizeof(double) * n) != cudaSuccess || cudaMalloc(&w0.p, sizeof(double) * n) != cudaSuccess) {
+    cudaGetLastError();
+    return wt::set_error(WT_ENOMEM, "wt_autotune_step: device buffers");
+  }
+  double time0 = 0.0;
+  int st = wt_get_state(t, e0.p, u0.p, v0.p, w0.p, &time0);
+  if (st != WT_OK) return st;
+  auto restore = [&]() { return wt_set_state(t, e0.p, u0.p, v0.p, w0.p, time0); };
+  auto measure = [&](const wt_options& o, double prune_ms) -> double {
+    if (wt_set_options(t, &o) != WT_OK) return -1.0;
+    if (restore() != WT_OK) return -1.0;
+    std::vector<double> ms;
+    for (int r = 0; r <= reps; ++r) {
+      const double t0 = now_ms();
+      const int s = wt_step(t, dt, 1);
+      const double d = now_ms() - t0;
+      if (s != WT_OK) return -1.0;
+      if (r == 0) {
+        if (prune_ms > 0 && d > 3.0 * prune_ms) return -1.0;
+        continue;
+      }
+      ms.push_back(d);
+    }
+    std::sort(ms.begin(), ms.end());
+    return ms[ms.size() / 2];
+  };
+  const double e_ms = measure(entry, 0.0);
+  wt_options bo = entry;
+  double bms = e_ms > 0 ? e_ms : 1e300;
+  const std::vector<int> modes = entry.mode == WT_FP64 ? std::vector<int>{WT_FP64}
+                                                       : std::vector<int>{WT_MIXED, WT_REFINE};
+  const double omegas[] = {0.3, 0.4, 0.5, 0.6};
+  const int nus[][2] = {{1, 1}, {2, 2}, {3, 3}};
+  const int coarsest[] = {32, 64, 128};
+  for (int mode : modes)
+    for (double om : omegas)
+      for (const auto& nu : nus)
+        for (int cm : coarsest) {
+          wt_options o = entry;
+          o.mode = mode;
+          o.omega = om;
+          o.nu1 = nu[0];
+          o.nu2 = nu[1];
+          o.coarsest_max = cm;
+          if (o.mode == entry.mode && o.omega == entry.omega && o.nu1 == entry.nu1 && o.nu2 == entry.nu2 &&
+              o.coarsest_max == entry.coarsest_max)
+            continue;
+          const double ms = measure(o, bms < 1e300 ? bms : 0.0);
+          if (ms > 0 && ms < bms) {
+            bms = ms;
+            bo = o;
+          }
+        }
+  if (bms >= 1e300) {
+    wt_set_options(t, &entry);
+    restore();
+    return wt::set_error(WT_ENOCONV, "wt_autotune_step: no candidate completed a step");
+  }
+  st = wt_set_options(t, &bo);
+  if (st == WT_OK) st = restore();
+  if (st != WT_OK) return st;
+  if (best) *best = bo;
+  if (best_ms) *best_ms = bms;
+  if (entry_ms) *entry_ms = e_ms;
+  return WT_OK;
+}

@@ -1,0 +1,61 @@
+// The whole p-multigrid V-cycle (Algorithm 1) in one cooperative launch.
+//
+// Launched as separate kernels, a V-cycle of the 1024 x 24 tank is ~170
+// launches of a few microseconds each, most of it launch and drain latency
+// rather than work.  Here every CTA of a cooperative (co-resident) grid takes
+// its share of each phase - row passes by row pair, column kernels by column
+// - and a grid barrier separates the phases (wt_cta.cuh: grid_sync, bounded
+// by the SM clock).  The phases are the same device bodies as the
+// multi-kernel path.
+#define WT_DEV_RESTRICT
+#include "wt_cta.cuh"
+
+#include <algorithm>
+
+namespace wt {
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(512, 1) k_vcycle_grid(TailArgs<T> A, GridBar* bar, int* flag) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  vcycle_grid<T, DIM>(A, bar, flag, sm);
+}
+
+template <typename T, int DIM>
+static cudaError_t launch_dim(const TailArgs<T>& a, GridBar* bar, int* flag, cudaStream_t s) {
+  static int configured = 0, nblocks = 0;
+  if (a.smem > configured || nblocks == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k_vcycle_grid<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         a.smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0, occ = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vcycle_grid<T, DIM>, 512, a.smem)) !=
+        cudaSuccess)
+      return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    nblocks = nsm;                                   // one CTA per SM
+    configured = a.smem;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nblocks);
+  cfg.blockDim = dim3(512);
+  cfg.dynamicSmemBytes = a.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_vcycle_grid<T, DIM>, a, bar, flag);
+}
+
+template <typename T>
+cudaError_t launch_vcycle_grid(const TailArgs<T>& a, int dim, GridBar* bar, int* flag, cudaStream_t s) {
+  return dim == 3 ? launch_dim<T, 3>(a, bar, flag, s) : launch_dim<T, 2>(a, bar, flag, s);
+}
+
+template cudaError_t launch_vcycle_grid<float>(const TailArgs<float>&, int, GridBar*, int*, cudaStream_t);
+template cudaError_t launch_vcycle_grid<double>(const TailArgs<double>&, int, GridBar*, int*, cudaStream_t);
+
+}  // namespace wt

@@ -73,20 +73,21 @@ def test_levels_match_oracle_hierarchy(wt):
         assert T.levels() == pmg.hierarchy(Nx, Ny, Nz, coarsest_max=64)
 
 
-@pytest.mark.parametrize("tail_max", [0, 8192, 100000])
+@pytest.mark.parametrize("tail_max,grid", [(0, 0), (8192, 0), (100000, 0), (0, 1)])
 @pytest.mark.parametrize("Nx,Ny,Nz", [(64, 1, 16), (256, 1, 24), (1024, 1, 24), (16, 16, 8),
                                       (32, 32, 12)])
-def test_vcycle_parity(wt, Nx, Ny, Nz, tail_max):
+def test_vcycle_parity(wt, Nx, Ny, Nz, tail_max, grid):
     # same algorithm on both sides (block Jacobi with Nyquist split, omega 0.4,
     # nu1 = nu2 = 2, injected boundary rows, coarsest <= 64 unknowns): the
     # preconditioned vectors agree to rounding.  tail_max selects how many
-    # levels run in the single-CTA V-cycle kernel (0: none, 100000: all).
+    # levels run in the single-CTA V-cycle kernel (0: none, 100000: all);
+    # grid = 1 runs the whole cycle as one cooperative launch.
     L = 2 * math.pi
     g, h, ea, eb = curved(Nx, Ny, Nz, L)
     r = np.random.default_rng(3).standard_normal(g.shape)
     levels = pmg.build_levels(Nx, Ny, Nz, L, h, ea, eb, coarsest_max=64)
     ref = pmg.vcycle(levels, 0, np.zeros(g.shape), r, 2, 2, "jacobi", 0.4, "inject")
-    T = wt.Tank(Nx, Ny, Nz, L, h, tail_max=tail_max)
+    T = wt.Tank(Nx, Ny, Nz, L, h, tail_max=tail_max, vcycle_grid=grid)
     got = T.precondition(ea, eb, r, wt.WT_FP64)
     scale = np.abs(ref).max()
     assert np.abs(got - ref).max() <= 1e-9 * scale
@@ -132,6 +133,36 @@ def test_curved_solve_residual_in_oracle_operator(wt, mode, Nx, Ny, Nz, L):
     r = b - op.apply_A(g, op.Geometry(g, h, ea), op.Geometry(g, h, eb), p)
     bound = 1e-10 if mode == 0 else 1e-9
     assert np.linalg.norm(r) <= bound * np.linalg.norm(b) * 1.5
+
+
+@pytest.mark.parametrize("Nx,Ny,Nz,L", [(1024, 1, 24, 32.0), (32, 32, 12, 2 * math.pi)])
+def test_grid_vcycle_matches_launch_per_phase(wt, Nx, Ny, Nz, L):
+    # the cooperative V-cycle runs the same bodies: a mixed solve and (2D) a
+    # nonlinear step agree with the one-launch-per-phase path to rounding
+    g, h, ea, eb = curved(Nx, Ny, Nz, L)
+    b = np.random.default_rng(6).standard_normal(g.shape)
+    out = []
+    for grid in (0, 1):
+        T = wt.Tank(Nx, Ny, Nz, L, h, mode=1, tol=1e-10, max_it=300, vcycle_grid=grid)
+        p, info = T.poisson_solve(ea, eb, b)
+        assert info.rel_residual <= 1e-10
+        out.append((p, info.iterations))
+    assert out[0][1] == out[1][1]
+    assert np.abs(out[0][0] - out[1][0]).max() <= 1e-9 * np.abs(out[0][0]).max()
+    if Ny == 1:
+        x = np.arange(Nx) * L / Nx
+        eta = si.stokes2_eta(x, 0.1, 2 * math.pi * 5 / L, 1.0)[None]
+        geo = op.Geometry(g, h, eta)
+        u, w = si.linear_velocity(x[None, None, :], geo.z_nodes(g), 0.1, 2 * math.pi * 5 / L, 1.0)
+        st = []
+        for grid in (0, 1):
+            T = wt.Tank(Nx, 1, Nz, L, h, tol=1e-10, filter=1, vcycle_grid=grid)
+            T.set_state(np.ascontiguousarray(eta), np.ascontiguousarray(u), np.zeros_like(u),
+                        np.ascontiguousarray(w))
+            T.step(0.005, 2)
+            st.append(T.get_state())
+        for a, c in zip(st[0][:4], st[1][:4]):
+            assert np.abs(a - c).max() <= 1e-9 * max(np.abs(c).max(), 1e-30)
 
 
 def test_solve_matches_oracle_dense_lu(wt):
