@@ -239,9 +239,11 @@ __device__ void rowpass_body(const RowPass<T>& a, int ppc, int u0, int ustep, un
         v0 += a.out[o0];
         if (has1) v1 += a.out[o1];
       }
-      a.out[o0] = v0;
-      if (has1) a.out[o1] = v1;
-      if (a.nyq) Y[q * S + j] = mk<T>(v0, has1 ? v1 : T(0));
+      if (a.write_out) {
+        a.out[o0] = v0;
+        if (has1) a.out[o1] = v1;
+      }
+      if (a.nyq || a.out2) Y[q * S + j] = mk<T>(v0, has1 ? v1 : T(0));
     }
     if (a.nyq) {
       __syncthreads();
@@ -263,6 +265,39 @@ __device__ void rowpass_body(const RowPass<T>& a, int ppc, int u0, int ustep, un
           a.nyq[r0] = s0 / T(a.Nout);
           if (r1 < a.nrows) a.nyq[r1] = s1 / T(a.Nout);
         }
+      }
+    }
+    if (a.out2) {
+      // second transform of the result rows held in Y: forward FFT, spectral
+      // op2, inverse FFT of length Nout2, store with 1 / Nout
+      __syncthreads();
+      c2* Z = (Y == X) ? Yb : X;
+      c2* F = fft_smem<T>(Y, Z, a.logNout, nb, S, tws, logNmax, false);
+      c2* G = (F == Y) ? Z : Y;
+      const int keep = a.Nout < a.Nout2 ? a.Nout : a.Nout2;
+      for (int idx = threadIdx.x; idx < nb * a.Nout2; idx += blockDim.x) {
+        const int q = idx >> a.logNout2, n = idx & (a.Nout2 - 1);
+        const int ns = n < a.Nout2 / 2 ? n : n - a.Nout2;
+        const int an = ns < 0 ? -ns : ns;
+        c2 v = mk<T>(T(0), T(0));
+        if (a.op2 == XOP_DERIV) {
+          const c2 x = F[q * S + n];
+          const T kap = (n == a.Nout2 / 2) ? T(0) : a.kscale * T(ns);
+          v = mk<T>(-kap * x.y, kap * x.x);
+        } else if (2 * an < keep) {
+          v = F[q * S + (ns < 0 ? ns + a.Nout : ns)];
+        }
+        G[q * S + n] = v;
+      }
+      __syncthreads();
+      c2* R = fft_smem<T>(G, F, a.logNout2, nb, S, tws, logNmax, true);
+      const T s2 = T(1) / T(a.Nout);
+      for (int idx = threadIdx.x; idx < nb * a.Nout2; idx += blockDim.x) {
+        const int q = idx >> a.logNout2, j = idx & (a.Nout2 - 1);
+        const int r0 = 2 * (p0 + q), r1 = r0 + 1;
+        const c2 y = R[q * S + j];
+        a.out2[(long)r0 * a.Nout2 + j] = y.x * s2;
+        if (r1 < a.nrows) a.out2[(long)r1 * a.Nout2 + j] = y.y * s2;
       }
     }
     __syncthreads();

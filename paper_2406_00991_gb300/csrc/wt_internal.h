@@ -92,6 +92,13 @@ struct RowPass {
   // y-line geometry (ylines = 1): lines along y of a [planes][Ny][Nx] array
   int ylines = 0, Nxl = 0;     // x extent of each plane
   int prefetch = 1;            // fetch epilogue operands with the inputs (needs smem)
+  // Optional second transform of the epilogue's result (x-rows only): out2
+  // receives it resampled to Nout2 (op2 = XOP_RESAMPLE) or differentiated
+  // (op2 = XOP_DERIV, Nout2 = Nout); write_out = 0 skips storing `out`.
+  T* out2 = nullptr;
+  int Nout2 = 0, logNout2 = 0;
+  int op2 = XOP_RESAMPLE;
+  int write_out = 1;
 };
 
 template <typename T> cudaError_t launch_rowpass(const RowPass<T>& a, cudaStream_t s);

@@ -155,15 +155,23 @@ void setup_geometry(wt_tank& t, const double* ea, const double* eb, int precisio
 // ------------------------------------------------------------------ operator
 // out = A x (f == nullptr) or out = f - A x; nyq: Nyquist coefficients of out.
 template <typename T>
-void apply_op(wt_tank& t, int l, const T* x, T* out, const T* f, bool nyq, bool tr) {
+void apply_op(wt_tank& t, int l, const T* x, T* out, const T* f, bool nyq, bool tr, const OpExtra<T>& ex) {
   auto& L = levels<T>(t)[l];
   cudaStream_t s = t.s;
   const auto V = L.view(twiddles<T>(t), t.logNtw, t.L);
+  auto extra = [&](RowPass<T>& a) {
+    if (!ex.out2) return;
+    a.out2 = ex.out2;
+    a.Nout2 = ex.Nout2;
+    a.logNout2 = ilog2(ex.Nout2);
+    a.op2 = ex.op2;
+    a.write_out = ex.write_out ? 1 : 0;
+  };
   if (tr) {
     // A^T lam = part - D_x mu_x (2D): D_x lam, the column kernel, then the
     // x-derivative of mu_x subtracted in the epilogue of the last row pass
     if (L.Ny != 1) throw WtError{WT_ENOTSUP, "the transposed operator is 2D only"};
-    run_rowpass(t, xpass<T>(t, x, L.t1, L.M1, L.Nx, L.Nx, XOP_DERIV));
+    if (!ex.have_dx) run_rowpass(t, xpass<T>(t, x, L.t1, L.M1, L.Nx, L.Nx, XOP_DERIV));
     WT_LAUNCH(t, K_OPCOLS, sizeof(T) * (4.0 * L.n + 7.0 * L.ncols), 6.0 * L.M1 * L.M1 * L.ncols, launch_op_cols_T<T>(V, x, L.t1, L.t2, L.t3, s));
     RowPass<T> a = xpass<T>(t, L.t2, out, L.M1, L.Nx, L.Nx, XOP_DERIV);
     a.scale = T(-1);
@@ -171,11 +179,12 @@ void apply_op(wt_tank& t, int l, const T* x, T* out, const T* f, bool nyq, bool 
     a.rhs = f;
     a.epi = f ? EPI_RESID : EPI_ADD;
     a.nyq = nyq ? L.rhoX : nullptr;
+    extra(a);
     run_rowpass(t, a);
     return;
   }
   if (L.Ny == 1) {
-    run_rowpass(t, xpass<T>(t, x, L.t1, L.M1, L.Nx, L.Nx, XOP_DERIV));
+    if (!ex.have_dx) run_rowpass(t, xpass<T>(t, x, L.t1, L.M1, L.Nx, L.Nx, XOP_DERIV));
     WT_LAUNCH(t, K_OPCOLS, sizeof(T) * (4.0 * L.n + 7.0 * L.ncols), 6.0 * L.M1 * L.M1 * L.ncols, launch_op_cols<T>(V, x, L.t1, nullptr, L.t2, nullptr, L.t3, s));
     RowPass<T> a = xpass<T>(t, L.t2, out, L.M1, L.Nx, L.Nx, XOP_DERIV);
     a.skip_bc = 1;
@@ -185,6 +194,7 @@ void apply_op(wt_tank& t, int l, const T* x, T* out, const T* f, bool nyq, bool 
     a.rhs = f;
     a.epi = f ? EPI_RESID : EPI_ADD;
     a.nyq = nyq ? L.rhoX : nullptr;
+    extra(a);
     run_rowpass(t, a);
   } else {
     run_rowpass(t, xpass<T>(t, x, L.t1, L.M1 * L.Ny, L.Nx, L.Nx, XOP_DERIV));
@@ -230,7 +240,8 @@ static void nyquist_of(wt_tank& t, Level<T>& L, const T* f) {
 
 // ------------------------------------------------------------------ V-cycle
 template <typename T>
-static void smooth(wt_tank& t, int l, T* x, const T* f, bool first, bool f_has_nyq, bool tr) {
+static void smooth(wt_tank& t, int l, T* x, const T* f, bool first, bool f_has_nyq, bool tr,
+                   bool have_dx = false) {
   auto& L = levels<T>(t)[l];
   const auto V = L.view(twiddles<T>(t), t.logNtw, t.L);
   const T om = (T)t.opt.omega;
@@ -240,7 +251,9 @@ static void smooth(wt_tank& t, int l, T* x, const T* f, bool first, bool f_has_n
     WT_LAUNCH(t, K_SMOOTH, sizeof(T) * (2.0 * L.n + (double)L.nclass * L.M1 * L.M1 * L.ncols), 2.0 * L.nclass * L.M1 * L.M1 * L.ncols, launch_smooth_cols<T>(V, f, f_has_nyq ? L.rhoX : nullptr, (f_has_nyq && y) ? L.rhoY : nullptr,
                                 (f_has_nyq && y) ? L.rhoXY : nullptr, L.Binv, L.nclass, x, om, 1, tr, t.s));
   } else {
-    apply_op<T>(t, l, x, L.r, f, true, tr);
+    OpExtra<T> ex;
+    ex.have_dx = have_dx;
+    apply_op<T>(t, l, x, L.r, f, true, tr, ex);
     WT_LAUNCH(t, K_SMOOTH, sizeof(T) * (3.0 * L.n + (double)L.nclass * L.M1 * L.M1 * L.ncols), 2.0 * L.nclass * L.M1 * L.M1 * L.ncols, launch_smooth_cols<T>(V, L.r, L.rhoX, L.Ny > 1 ? L.rhoY : nullptr, L.Ny > 1 ? L.rhoXY : nullptr,
                                 L.Binv, L.nclass, x, om, 0, tr, t.s));
   }
@@ -263,14 +276,17 @@ static void restrict_to(wt_tank& t, int l, const T* r) {
   run_col_matrix<T>(t, F.Rsig, C.M1, F.M1, cur, C.f, C.ncols, 0);
 }
 
+// x += P e_c.  With dx_out (2D, Fourier-refined levels) the same row pass
+// also writes D_x of the corrected x there (for the next smoothing sweep);
+// returns whether it did.
 template <typename T>
-static void prolong_add(wt_tank& t, int l, T* x) {
+static bool prolong_add(wt_tank& t, int l, T* x, T* dx_out = nullptr) {
   auto& F = levels<T>(t)[l];
   auto& C = levels<T>(t)[l + 1];
   cudaStream_t s = t.s;
   if (C.Nx == F.Nx) {
     run_col_matrix<T>(t, F.Psig, F.M1, C.M1, C.x, x, F.ncols, 1);
-    return;
+    return false;
   }
   run_col_matrix<T>(t, F.Psig, F.M1, C.M1, C.x, F.t4, C.ncols, 0);
   const T* cur = F.t4;
@@ -280,7 +296,15 @@ static void prolong_add(wt_tank& t, int l, T* x) {
   }
   RowPass<T> a = xpass<T>(t, cur, x, F.M1 * F.Ny, C.Nx, F.Nx, XOP_RESAMPLE);
   a.epi = EPI_ACC;
+  const bool fuse = dx_out && F.Ny == 1;
+  if (fuse) {
+    a.out2 = dx_out;
+    a.Nout2 = F.Nx;
+    a.logNout2 = ilog2(F.Nx);
+    a.op2 = XOP_DERIV;
+  }
   run_rowpass(t, a);
+  return fuse;
 }
 
 template <typename T> static TailLevel<T>* tail_desc(wt_tank& t);
@@ -358,15 +382,28 @@ void vcycle(wt_tank& t, int l, const T* f, T* x, bool tr) {
   if (t.opt.nu1 > 0) {
     smooth<T>(t, l, x, f, true, f_nyq, tr);
     for (int i = 1; i < t.opt.nu1; ++i) smooth<T>(t, l, x, f, false, false, tr);
-    apply_op<T>(t, l, x, L.r, f, false, tr);  // r = f - A u
-    restrict_to<T>(t, l, L.r);
+    auto& C = lev[l + 1];
+    if (L.Ny == 1 && C.Nx != L.Nx) {
+      // r = f - A u and its Fourier truncation in the same row pass; only the
+      // truncated rows are stored, then the Chebyshev truncation
+      OpExtra<T> ex;
+      ex.out2 = L.t4;
+      ex.Nout2 = C.Nx;
+      ex.op2 = XOP_RESAMPLE;
+      ex.write_out = false;
+      apply_op<T>(t, l, x, L.r, f, false, tr, ex);
+      run_col_matrix<T>(t, L.Rsig, C.M1, L.M1, L.t4, C.f, C.ncols, 0);
+    } else {
+      apply_op<T>(t, l, x, L.r, f, false, tr);  // r = f - A u
+      restrict_to<T>(t, l, L.r);
+    }
   } else {
     WT_CK(cudaMemsetAsync(x, 0, sizeof(T) * L.n, t.s));
     restrict_to<T>(t, l, f);
   }
   vcycle<T>(t, l + 1, lev[l + 1].f, lev[l + 1].x, tr);
-  prolong_add<T>(t, l, x);                     // u = u + P e_c
-  for (int i = 0; i < t.opt.nu2; ++i) smooth<T>(t, l, x, f, false, false, tr);
+  const bool dx = prolong_add<T>(t, l, x, t.opt.nu2 > 0 ? L.t1 : nullptr);   // u = u + P e_c
+  for (int i = 0; i < t.opt.nu2; ++i) smooth<T>(t, l, x, f, false, false, tr, dx && i == 0);
 }
 
 // ------------------------------------------------------------------ norms
@@ -583,8 +620,10 @@ int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_
   return status;
 }
 
-template void apply_op<double>(wt_tank&, int, const double*, double*, const double*, bool, bool);
-template void apply_op<float>(wt_tank&, int, const float*, float*, const float*, bool, bool);
+template void apply_op<double>(wt_tank&, int, const double*, double*, const double*, bool, bool,
+                               const OpExtra<double>&);
+template void apply_op<float>(wt_tank&, int, const float*, float*, const float*, bool, bool,
+                              const OpExtra<float>&);
 template void vcycle<double>(wt_tank&, int, const double*, double*, bool);
 template void vcycle<float>(wt_tank&, int, const float*, float*, bool);
 

@@ -77,8 +77,19 @@ void setup_geometry(wt_tank& t, const double* ea, const double* eb, int precisio
 
 // tr: the transposed operator A^T (2D) and the V-cycle of A^T (transposed
 // smoother blocks and coarsest inverse, the same transfers).
+// Options of one operator apply: out2 / Nout2 / op2 give a second transform
+// of the last row pass's result (x-rows; write_out = false skips `out`);
+// have_dx: L.t1 already holds D_x x.
+template <typename T>
+struct OpExtra {
+  T* out2 = nullptr;
+  int Nout2 = 0;
+  int op2 = XOP_RESAMPLE;
+  bool write_out = true;
+  bool have_dx = false;
+};
 template <typename T> void apply_op(wt_tank& t, int l, const T* x, T* out, const T* f, bool nyq,
-                                    bool tr = false);
+                                    bool tr = false, const OpExtra<T>& ex = OpExtra<T>());
 template <typename T> void vcycle(wt_tank& t, int l, const T* f, T* x, bool tr = false);
 template <typename T>
 double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit, int* its_out,
