@@ -231,7 +231,8 @@ int wt_adjoint_step(wt_tank* t, double dt, const double* eta, const double* u, c
  * 0.5, 0.6}, (nu1, nu2) in {(1,1), (2,2), (3,3)}, coarsest_max in {32, 64,
  * 128}, and mode in {WT_MIXED, WT_REFINE} unless the tank is in WT_FP64 - one
  * warm-up solve plus the median of reps (1..100) timed solves each, and keeps
- * the fastest setting that reaches the tolerance.  The paper leaves these
+ * the fastest setting that reaches the tolerance; then, on that setting, the
+ * V-cycle's launch schedule (tail_max 2048 or 8192, or vcycle_grid = 1).  The paper leaves these
  * choices open (Sec. 4.1).  On success the tank uses the winner, *best holds
  * it, *best_ms its median time and *entry_ms that of the options on entry
  * (best_ms <= entry_ms: the entry options are one of the candidates).  Any

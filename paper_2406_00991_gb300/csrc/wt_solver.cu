@@ -133,22 +133,27 @@ void setup_geometry(wt_tank& t, const double* ea, const double* eb, int precisio
     if (precision == WT_FP32)
       WT_LAUNCH(t, K_STAGE, 12.0 * kMeta * L.ncols, 0.0, (launch_cast<double, float>(L.meta, t.L32[l].meta, (long)kMeta * L.ncols, t.s)));
   }
+  setup_blocks(t, precision, blocks, coarse, t.s);
+}
+
+void setup_blocks(wt_tank& t, int precision, bool blocks, bool coarse, cudaStream_t s) {
+  const int nl = (int)t.L64.size();
   if (blocks) {
     for (int l = 0; l < nl - 1; ++l) {
       if (precision == WT_FP32) {
         auto& L = t.L32[l];
         WT_LAUNCH(t, K_BLOCKINV, 4.0 * L.ncols * (L.nclass * L.M1 * L.M1 + kMeta), 2.0 * L.nclass * L.ncols * L.M1 * L.M1 * L.M1, launch_block_inverse<float>(L.view(t.tw32, t.logNtw, t.L), L.Binv, L.nclass, L.cxx, L.cyy,
-                                          t.dflag, t.s));
+                                          t.dflag, s));
       } else {
         auto& L = t.L64[l];
         WT_LAUNCH(t, K_BLOCKINV, 8.0 * L.ncols * (L.nclass * L.M1 * L.M1 + kMeta), 2.0 * L.nclass * L.ncols * L.M1 * L.M1 * L.M1, launch_block_inverse<double>(L.view(t.tw64, t.logNtw, t.L), L.Binv, L.nclass, L.cxx, L.cyy,
-                                           t.dflag, t.s));
+                                           t.dflag, s));
       }
     }
   }
   if (coarse) {
     auto& C = t.L64[nl - 1];
-    WT_LAUNCH(t, K_COARSE, 8.0 * t.ncoarse * t.ncoarse, 2.0 / 3.0 * t.ncoarse * t.ncoarse * t.ncoarse, launch_coarse_factor(C.view(t.tw64, t.logNtw, t.L), t.cDx, t.cDy, t.cLU, t.cpiv, t.dflag, t.s));
+    WT_LAUNCH(t, K_COARSE, 8.0 * t.ncoarse * t.ncoarse, 2.0 / 3.0 * t.ncoarse * t.ncoarse * t.ncoarse, launch_coarse_factor(C.view(t.tw64, t.logNtw, t.L), t.cDx, t.cDy, t.cLU, t.cpiv, t.dflag, s));
   }
 }
 

@@ -74,6 +74,9 @@ void setup_bathymetry(wt_tank& t, const double* h_fine);
 // FP64 LU of the coarsest level.
 void setup_geometry(wt_tank& t, const double* ea, const double* eb, int precision, bool blocks,
                     bool coarse);
+// The block inverses of every level but the coarsest and the coarsest FP64
+// inverse, from the current metric, on stream s.
+void setup_blocks(wt_tank& t, int precision, bool blocks, bool coarse, cudaStream_t s);
 
 // tr: the transposed operator A^T (2D) and the V-cycle of A^T (transposed
 // smoother blocks and coarsest inverse, the same transfers).

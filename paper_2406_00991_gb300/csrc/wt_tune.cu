@@ -28,6 +28,33 @@ double now_ms() {
   return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
+// Second stage on the winner: the launch schedule of the V-cycle - the
+// single-CTA kernel for the levels below tail_max unknowns, or the whole
+// cycle as one cooperative launch - kept only where it is faster.
+template <typename F>
+void refine_schedule(wt_options& bo, double& bms, F&& measure) {
+  const wt_options base = bo;
+  const int tails[] = {2048, 8192};
+  for (int tm : tails) {
+    wt_options o = base;
+    o.tail_max = tm;
+    o.vcycle_grid = 0;
+    const double ms = measure(o, bms);
+    if (ms > 0 && ms < bms) {
+      bms = ms;
+      bo = o;
+    }
+  }
+  wt_options o = base;
+  o.vcycle_grid = 1;
+  o.tail_max = 0;
+  const double ms = measure(o, bms);
+  if (ms > 0 && ms < bms) {
+    bms = ms;
+    bo = o;
+  }
+}
+
 }  // namespace
 
 extern "C" int wt_autotune(wt_tank* t, const double* eta_a, const double* eta_b, const double* rhs, int reps,
@@ -107,6 +134,7 @@ extern "C" int wt_autotune(wt_tank* t, const double* eta_a, const double* eta_b,
             bo = o;
           }
         }
+  if (bms < 1e300) refine_schedule(bo, bms, measure);
   if (bms >= 1e300) {
     wt_set_options(t, &entry);
     return wt::set_error(WT_ENOCONV, "wt_autotune: no candidate reached the tolerance");
@@ -189,6 +217,7 @@ extern "C" int wt_autotune_step(wt_tank* t, double dt, int reps, wt_options* bes
             bo = o;
           }
         }
+  if (bms < 1e300) refine_schedule(bo, bms, measure);
   if (bms >= 1e300) {
     wt_set_options(t, &entry);
     restore();
