@@ -36,7 +36,7 @@ def _sources():
 
 
 def _headers_mtime():
-    hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     hs.append(os.path.join(os.path.dirname(HERE), "include", "wt.h"))
     return max(os.path.getmtime(h) for h in hs if os.path.exists(h))
 

@@ -66,8 +66,7 @@ cudaError_t launch_coarse_factor(const LevelView<double>& L, const double* Dx, c
 template <typename T>
 cudaError_t launch_coarse_solve(int n, const double* LU, const int* piv, int tr, const T* f, T* x,
                                 cudaStream_t s) {
-  k_coarse_solve<T><<<1, 128, 0, s>>>(n, LU, piv, tr, f, x);
-  return cudaGetLastError();
+  return launch_k(k_coarse_solve<T>, dim3(1), dim3(128), 0, s, n, LU, piv, tr, f, x);
 }
 
 template cudaError_t launch_coarse_solve<float>(int, const double*, const int*, int, const float*,

@@ -78,11 +78,8 @@ cudaError_t launch_op_cols(const LevelView<T>& L, const T* p, const T* Px, const
                            T* Gy, T* part, cudaStream_t s) {
   const int g = grid_cols(L.ncols, 256);
   const size_t smem = opcols_smem<T>(L.M1);
-  if (L.Ny == 1)
-    k_op_cols<T, 2><<<g, 256, smem, s>>>(L, p, Px, Py, Gx, Gy, part);
-  else
-    k_op_cols<T, 3><<<g, 256, smem, s>>>(L, p, Px, Py, Gx, Gy, part);
-  return cudaGetLastError();
+  if (L.Ny == 1) return launch_k(k_op_cols<T, 2>, dim3(g), dim3(256), smem, s, L, p, Px, Py, Gx, Gy, part);
+  return launch_k(k_op_cols<T, 3>, dim3(g), dim3(256), smem, s, L, p, Px, Py, Gx, Gy, part);
 }
 
 template <typename T>
@@ -90,8 +87,7 @@ cudaError_t launch_op_cols_T(const LevelView<T>& L, const T* lam, const T* Dlam,
                              cudaStream_t s) {
   if (L.Ny != 1) return cudaErrorInvalidValue;
   const int g = grid_cols(L.ncols, 256);
-  k_op_cols_T<T><<<g, 256, opcols_smem<T>(L.M1), s>>>(L, lam, Dlam, Mx, part);
-  return cudaGetLastError();
+  return launch_k(k_op_cols_T<T>, dim3(g), dim3(256), opcols_smem<T>(L.M1), s, L, lam, Dlam, Mx, part);
 }
 
 template <typename T>
@@ -100,18 +96,13 @@ cudaError_t launch_smooth_cols(const LevelView<T>& L, const T* r, const T* rhoX,
                                int tr, cudaStream_t s) {
   (void)nclass;
   const int g = grid_cols(L.ncols, 256);
+  const dim3 G(g), B(256);
   if (L.Ny == 1) {
-    if (tr)
-      k_smooth_cols<T, 2, true><<<g, 256, 0, s>>>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
-    else
-      k_smooth_cols<T, 2, false><<<g, 256, 0, s>>>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
-  } else {
-    if (tr)
-      k_smooth_cols<T, 3, true><<<g, 256, 0, s>>>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
-    else
-      k_smooth_cols<T, 3, false><<<g, 256, 0, s>>>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
+    if (tr) return launch_k(k_smooth_cols<T, 2, true>, G, B, 0, s, L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
+    return launch_k(k_smooth_cols<T, 2, false>, G, B, 0, s, L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
   }
-  return cudaGetLastError();
+  if (tr) return launch_k(k_smooth_cols<T, 3, true>, G, B, 0, s, L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
+  return launch_k(k_smooth_cols<T, 3, false>, G, B, 0, s, L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
 }
 
 template <typename T>
@@ -119,8 +110,7 @@ cudaError_t launch_col_matrix(const T* M, int Mo, int Mi, const T* in, T* out, i
                               int accumulate, cudaStream_t s) {
   const int g = grid_cols(ncols, 256);
   const size_t smem = sizeof(T) * (size_t)Mo * Mi;
-  k_col_matrix<T><<<g, 256, smem, s>>>(M, Mo, Mi, in, out, ncols, accumulate);
-  return cudaGetLastError();
+  return launch_k(k_col_matrix<T>, dim3(g), dim3(256), smem, s, M, Mo, Mi, in, out, ncols, accumulate);
 }
 
 template <typename T>

@@ -41,7 +41,16 @@ __device__ __forceinline__ c2_t<T> cmul(c2_t<T> a, c2_t<T> b) {
 // radix-4 stages; each stage reads a[k + j m + s N/4], takes the 4-point DFT
 // and writes W^{t j m} y_t to b[k + 4 j m + t m].  tws holds
 // exp(-2 pi i t / Nt), t < Nt/2, Nt = 2^logNt >= N.  Returns the result buffer.
-template <typename T>
+// The thread group that runs a row pass (the whole CTA; the FFT and the row
+// pass core are written against this interface).
+struct BlockG {
+  static constexpr bool block = true;
+  static __device__ __forceinline__ int rank() { return threadIdx.x; }
+  static __device__ __forceinline__ int size() { return blockDim.x; }
+  static __device__ __forceinline__ void sync() { __syncthreads(); }
+};
+
+template <typename T, typename G = BlockG>
 __device__ c2_t<T>* fft_smem(c2_t<T>* a, c2_t<T>* b, int logN, int nb, int S, const c2_t<T>* tws,
                              int logNt, bool inverse) {
   using c2 = c2_t<T>;
@@ -51,7 +60,7 @@ __device__ c2_t<T>* fft_smem(c2_t<T>* a, c2_t<T>* b, int logN, int nb, int S, co
   int lm = 0;                                  // log2 m
   if (logN & 1) {
     const int half = N >> 1;
-    for (int idx = threadIdx.x; idx < nb * half; idx += blockDim.x) {
+    for (int idx = G::rank(); idx < nb * half; idx += G::size()) {
       const int q = idx >> (logN - 1);
       const int k = idx & (half - 1);          // m = 1: j = k, k' = 0
       const c2 c0 = a[q * S + k], c1 = a[q * S + k + half];
@@ -59,7 +68,7 @@ __device__ c2_t<T>* fft_smem(c2_t<T>* a, c2_t<T>* b, int logN, int nb, int S, co
       b[q * S + 2 * k] = mk<T>(c0.x + c1.x, c0.y + c1.y);
       b[q * S + 2 * k + 1] = cmul<T>(w, mk<T>(c0.x - c1.x, c0.y - c1.y));
     }
-    __syncthreads();
+    G::sync();
     c2* t = a; a = b; b = t;
     lm = 1;
   }
@@ -67,7 +76,7 @@ __device__ c2_t<T>* fft_smem(c2_t<T>* a, c2_t<T>* b, int logN, int nb, int S, co
   const int lq = logN - 2;
   for (; lm < logN; lm += 2) {
     const int m = 1 << lm;
-    for (int idx = threadIdx.x; idx < (nb << lq); idx += blockDim.x) {
+    for (int idx = G::rank(); idx < (nb << lq); idx += G::size()) {
       const int q = idx >> lq;
       const int bf = idx & (quarter - 1);
       const int j = bf >> lm, k = bf & (m - 1);
@@ -88,7 +97,7 @@ __device__ c2_t<T>* fft_smem(c2_t<T>* a, c2_t<T>* b, int logN, int nb, int S, co
       dst[2 * m] = cmul<T>(twiddle<T>(tws, 2 * u, halfNt, inverse), y2);
       dst[3 * m] = cmul<T>(twiddle<T>(tws, 3 * u, halfNt, inverse), y3);
     }
-    __syncthreads();
+    G::sync();
     c2* t = a; a = b; b = t;
   }
   return a;
@@ -122,28 +131,22 @@ __host__ __device__ inline size_t rowpass_smem(const RowPass<T>& a, int ppc) {
 // ustep, ...  The twiddles of the larger size are staged in shared memory and
 // the epilogue operands (add / rhs / out) are fetched in the same loop as the
 // input rows, so each batch costs one global round trip before the FFT.
-template <typename T>
-__device__ void rowpass_body(const RowPass<T>& a, int ppc, int u0, int ustep, unsigned char* smraw) {
+template <typename T, typename G>
+__device__ void rowpass_core(const RowPass<T>& a, int ppc, int u0, int ustep, c2_t<T>* buf0, c2_t<T>* buf1,
+                             const c2_t<T>* tws, c2_t<T>* eA, c2_t<T>* eB) {
   using c2 = c2_t<T>;
   const int Nmax = a.Nin > a.Nout ? a.Nin : a.Nout;
   const int logNmax = a.Nin > a.Nout ? a.logNin : a.logNout;
   const int S = Nmax + (a.ylines ? 1 : 0);
   const bool use_add = a.prefetch && (a.epi == EPI_ADD || a.epi == EPI_RESID);
   const bool use_rhs = a.prefetch && (a.epi == EPI_RESID || a.epi == EPI_ACC);
-  c2* buf0 = reinterpret_cast<c2*>(smraw);
-  c2* buf1 = buf0 + ppc * S;
-  c2* tws = buf1 + ppc * S;
-  c2* eA = tws + Nmax / 2;                     // add operand rows (pair packed)
-  c2* eB = eA + (use_add ? ppc * S : 0);       // rhs (RESID) or old out (ACC)
   const int npairs = (a.nrows + 1) >> 1;
-  if (u0 * ppc >= npairs) return;              // no unit for this CTA
-  for (int t = threadIdx.x; t < Nmax / 2; t += blockDim.x) tws[t] = a.tw[t << (a.logNtw - logNmax)];
   const T inv_n = T(1) / T(a.Nin);
 
   for (int p0 = u0 * ppc; p0 < npairs; p0 += ustep * ppc) {
     const int nb = min(ppc, npairs - p0);
     // ---- load two real rows per complex sequence (+ epilogue operands)
-    for (int idx = threadIdx.x; idx < nb * a.Nin; idx += blockDim.x) {
+    for (int idx = G::rank(); idx < nb * a.Nin; idx += G::size()) {
       int q, j;
       if (a.ylines) { q = idx % nb; j = idx / nb; } else { q = idx >> a.logNin; j = idx & (a.Nin - 1); }
       const int r0 = 2 * (p0 + q), r1 = r0 + 1;
@@ -153,7 +156,7 @@ __device__ void rowpass_body(const RowPass<T>& a, int ppc, int u0, int ustep, un
     }
     if (use_add || use_rhs) {
       const T* B = a.epi == EPI_ACC ? a.out : a.rhs;
-      for (int idx = threadIdx.x; idx < nb * a.Nout; idx += blockDim.x) {
+      for (int idx = G::rank(); idx < nb * a.Nout; idx += G::size()) {
         int q, j;
         if (a.ylines) { q = idx % nb; j = idx / nb; } else { q = idx >> a.logNout; j = idx & (a.Nout - 1); }
         const int r0 = 2 * (p0 + q), r1 = r0 + 1;
@@ -163,12 +166,12 @@ __device__ void rowpass_body(const RowPass<T>& a, int ppc, int u0, int ustep, un
         if (use_rhs) eB[q * S + j] = mk<T>(B[o0], has1 ? B[o1] : T(0));
       }
     }
-    __syncthreads();
-    c2* X = fft_smem<T>(buf0, buf1, a.logNin, nb, S, tws, logNmax, false);
+    G::sync();
+    c2* X = fft_smem<T, G>(buf0, buf1, a.logNin, nb, S, tws, logNmax, false);
     c2* Yb = (X == buf0) ? buf1 : buf0;
     // ---- spectral operation into Yb (length Nout)
     const int nkeep2 = (a.Nin < a.Nout ? a.Nin : a.Nout);   // keep |n| < nkeep2 / 2
-    for (int idx = threadIdx.x; idx < nb * a.Nout; idx += blockDim.x) {
+    for (int idx = G::rank(); idx < nb * a.Nout; idx += G::size()) {
       const int q = idx >> a.logNout, n = idx & (a.Nout - 1);
       const int ns = n < a.Nout / 2 ? n : n - a.Nout;          // signed wavenumber index
       c2 v = mk<T>(T(0), T(0));
@@ -200,11 +203,11 @@ __device__ void rowpass_body(const RowPass<T>& a, int ppc, int u0, int ustep, un
       }
       Yb[q * S + n] = v;
     }
-    __syncthreads();
-    c2* Y = fft_smem<T>(Yb, X, a.logNout, nb, S, tws, logNmax, true);
+    G::sync();
+    c2* Y = fft_smem<T, G>(Yb, X, a.logNout, nb, S, tws, logNmax, true);
     // ---- epilogue
     const T sc = a.scale * inv_n;
-    for (int idx = threadIdx.x; idx < nb * a.Nout; idx += blockDim.x) {
+    for (int idx = G::rank(); idx < nb * a.Nout; idx += G::size()) {
       int q, j;
       if (a.ylines) { q = idx % nb; j = idx / nb; } else { q = idx >> a.logNout; j = idx & (a.Nout - 1); }
       const int r0 = 2 * (p0 + q), r1 = r0 + 1;
@@ -246,8 +249,9 @@ __device__ void rowpass_body(const RowPass<T>& a, int ppc, int u0, int ustep, un
       if (a.nyq || a.out2) Y[q * S + j] = mk<T>(v0, has1 ? v1 : T(0));
     }
     if (a.nyq) {
-      __syncthreads();
-      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+      G::sync();
+      const int lane = threadIdx.x & 31;
+      const int warp = G::block ? (threadIdx.x >> 5) : 0, nw = G::block ? (blockDim.x >> 5) : 1;
       for (int q = warp; q < nb; q += nw) {
         T s0 = 0, s1 = 0;
         for (int j = lane; j < a.Nout; j += 32) {
@@ -270,29 +274,29 @@ __device__ void rowpass_body(const RowPass<T>& a, int ppc, int u0, int ustep, un
     if (a.out2) {
       // second transform of the result rows held in Y: forward FFT, spectral
       // op2, inverse FFT of length Nout2, store with 1 / Nout
-      __syncthreads();
+      G::sync();
       c2* Z = (Y == X) ? Yb : X;
-      c2* F = fft_smem<T>(Y, Z, a.logNout, nb, S, tws, logNmax, false);
-      c2* G = (F == Y) ? Z : Y;
+      c2* Fq = fft_smem<T, G>(Y, Z, a.logNout, nb, S, tws, logNmax, false);
+      c2* Gq = (Fq == Y) ? Z : Y;
       const int keep = a.Nout < a.Nout2 ? a.Nout : a.Nout2;
-      for (int idx = threadIdx.x; idx < nb * a.Nout2; idx += blockDim.x) {
+      for (int idx = G::rank(); idx < nb * a.Nout2; idx += G::size()) {
         const int q = idx >> a.logNout2, n = idx & (a.Nout2 - 1);
         const int ns = n < a.Nout2 / 2 ? n : n - a.Nout2;
         const int an = ns < 0 ? -ns : ns;
         c2 v = mk<T>(T(0), T(0));
         if (a.op2 == XOP_DERIV) {
-          const c2 x = F[q * S + n];
+          const c2 x = Fq[q * S + n];
           const T kap = (n == a.Nout2 / 2) ? T(0) : a.kscale * T(ns);
           v = mk<T>(-kap * x.y, kap * x.x);
         } else if (2 * an < keep) {
-          v = F[q * S + (ns < 0 ? ns + a.Nout : ns)];
+          v = Fq[q * S + (ns < 0 ? ns + a.Nout : ns)];
         }
-        G[q * S + n] = v;
+        Gq[q * S + n] = v;
       }
-      __syncthreads();
-      c2* R = fft_smem<T>(G, F, a.logNout2, nb, S, tws, logNmax, true);
+      G::sync();
+      c2* R = fft_smem<T, G>(Gq, Fq, a.logNout2, nb, S, tws, logNmax, true);
       const T s2 = T(1) / T(a.Nout);
-      for (int idx = threadIdx.x; idx < nb * a.Nout2; idx += blockDim.x) {
+      for (int idx = G::rank(); idx < nb * a.Nout2; idx += G::size()) {
         const int q = idx >> a.logNout2, j = idx & (a.Nout2 - 1);
         const int r0 = 2 * (p0 + q), r1 = r0 + 1;
         const c2 y = R[q * S + j];
@@ -300,8 +304,28 @@ __device__ void rowpass_body(const RowPass<T>& a, int ppc, int u0, int ustep, un
         if (r1 < a.nrows) a.out2[(long)r1 * a.Nout2 + j] = y.y * s2;
       }
     }
-    __syncthreads();
+    G::sync();
   }
+}
+
+
+// Row pass by the whole CTA: units of ppc pairs, unit u0, u0 + ustep, ...
+template <typename T>
+__device__ void rowpass_body(const RowPass<T>& a, int ppc, int u0, int ustep, unsigned char* smraw) {
+  using c2 = c2_t<T>;
+  const int Nmax = a.Nin > a.Nout ? a.Nin : a.Nout;
+  const int logNmax = a.Nin > a.Nout ? a.logNin : a.logNout;
+  const int S = Nmax + (a.ylines ? 1 : 0);
+  const bool use_add = a.prefetch && (a.epi == EPI_ADD || a.epi == EPI_RESID);
+  c2* buf0 = reinterpret_cast<c2*>(smraw);
+  c2* buf1 = buf0 + ppc * S;
+  c2* tws = buf1 + ppc * S;
+  c2* eA = tws + Nmax / 2;                     // add operand rows (pair packed)
+  c2* eB = eA + (use_add ? ppc * S : 0);       // rhs (RESID) or old out (ACC)
+  const int npairs = (a.nrows + 1) >> 1;
+  if (u0 * ppc >= npairs) return;              // no unit for this CTA
+  for (int t = threadIdx.x; t < Nmax / 2; t += blockDim.x) tws[t] = a.tw[t << (a.logNtw - logNmax)];
+  rowpass_core<T, BlockG>(a, ppc, u0, ustep, buf0, buf1, tws, eA, eB);
 }
 
 // Column kernels: one warp owns one vertical column.  Lane l holds the

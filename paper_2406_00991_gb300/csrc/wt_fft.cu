@@ -42,8 +42,7 @@ cudaError_t launch_rowpass(const RowPass<T>& a, cudaStream_t s) {
   }
   int grid = (npairs + ppc - 1) / ppc;
   grid = std::min(grid, 152 * 16);
-  k_rowpass<T><<<grid, 256, smem, s>>>(a, ppc);
-  return cudaGetLastError();
+  return launch_k(k_rowpass<T>, dim3(grid), dim3(256), smem, s, a, ppc);
 }
 
 template cudaError_t launch_rowpass<float>(const RowPass<float>&, cudaStream_t);

@@ -101,6 +101,19 @@ struct RowPass {
   int write_out = 1;
 };
 
+// Launch through cudaLaunchKernelEx (grid, block, dynamic shared memory,
+// stream); returns the launch status.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <typename T> cudaError_t launch_rowpass(const RowPass<T>& a, cudaStream_t s);
 
 // Independent row passes in one launch (one pair of rows per CTA): the

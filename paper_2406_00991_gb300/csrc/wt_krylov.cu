@@ -256,48 +256,40 @@ static inline int blocks_for(long n) {
 template <typename T>
 cudaError_t launch_dots(const T* w, const T* V, long ldv, int nvec, long n, double* partial, int nblk,
                         int with_norm, cudaStream_t s) {
-  k_dots<T><<<nblk, 256, 0, s>>>(w, V, ldv, nvec, n, partial, with_norm);
-  return cudaGetLastError();
+  return launch_k(k_dots<T>, dim3(nblk), dim3(256), 0, s, w, V, ldv, nvec, n, partial, with_norm);
 }
 cudaError_t launch_reduce_partials(const double* partial, int nblk, int nvals, double* out,
                                    cudaStream_t s) {
-  k_reduce_partials<<<1, 64, 0, s>>>(partial, nblk, nvals, out);
-  return cudaGetLastError();
+  return launch_k(k_reduce_partials, dim3(1), dim3(64), 0, s, partial, nblk, nvals, out);
 }
 template <typename T>
 cudaError_t launch_update_dots(T* w, const T* V, long ldv, int nvec, long n, const double* h,
                                double* partial, int nblk, cudaStream_t s) {
-  k_update_dots<T><<<nblk, 256, 0, s>>>(w, V, ldv, nvec, n, h, partial);
-  return cudaGetLastError();
+  return launch_k(k_update_dots<T>, dim3(nblk), dim3(256), 0, s, w, V, ldv, nvec, n, h, partial);
 }
 template <typename T>
 cudaError_t launch_update_normalize(T* w, const T* V, long ldv, int nvec, long n, const double* h,
                                     const double* inv_norm, T* vout, cudaStream_t s) {
-  k_update_normalize<T><<<blocks_for(n), 256, 0, s>>>(w, V, ldv, nvec, n, h, inv_norm, vout);
-  return cudaGetLastError();
+  return launch_k(k_update_normalize<T>, dim3(blocks_for(n)), dim3(256), 0, s, w, V, ldv, nvec, n, h, inv_norm, vout);
 }
 template <typename T>
 cudaError_t launch_lincomb(T* x, const T* Z, long ldz, int nvec, long n, const double* y,
                            cudaStream_t s) {
-  k_lincomb<T><<<blocks_for(n), 256, 0, s>>>(x, Z, ldz, nvec, n, y);
-  return cudaGetLastError();
+  return launch_k(k_lincomb<T>, dim3(blocks_for(n)), dim3(256), 0, s, x, Z, ldz, nvec, n, y);
 }
 template <typename T>
 cudaError_t launch_scale_copy(const T* in, T* out, long n, const double* scale, int invert,
                               cudaStream_t s) {
-  k_convert<T, T><<<blocks_for(n), 256, 0, s>>>(in, out, n, scale, invert);
-  return cudaGetLastError();
+  return launch_k(k_convert<T, T>, dim3(blocks_for(n)), dim3(256), 0, s, in, out, n, scale, invert);
 }
 template <typename Ti, typename To>
 cudaError_t launch_convert(const Ti* in, To* out, long n, const double* scale, int invert,
                            cudaStream_t s) {
-  k_convert<Ti, To><<<blocks_for(n), 256, 0, s>>>(in, out, n, scale, invert);
-  return cudaGetLastError();
+  return launch_k(k_convert<Ti, To>, dim3(blocks_for(n)), dim3(256), 0, s, in, out, n, scale, invert);
 }
 template <typename T>
 cudaError_t launch_axpy_from(double* x, const T* e, long n, const double* scale, cudaStream_t s) {
-  k_axpy_from<T><<<blocks_for(n), 256, 0, s>>>(x, e, n, scale);
-  return cudaGetLastError();
+  return launch_k(k_axpy_from<T>, dim3(blocks_for(n)), dim3(256), 0, s, x, e, n, scale);
 }
 cudaError_t launch_nyquist_coef(const void* r, int is_double, int nrows, int Nx, int logNx, void* rho,
                                 cudaStream_t s) {
@@ -305,27 +297,22 @@ cudaError_t launch_nyquist_coef(const void* r, int is_double, int nrows, int Nx,
   const int threads = 256;
   const int blocks = (nrows * 32 + threads - 1) / threads;
   if (is_double)
-    k_nyquist_coef_d<<<blocks, threads, 0, s>>>((const double*)r, nrows, Nx, (double*)rho);
-  else
-    k_nyquist_coef_f<<<blocks, threads, 0, s>>>((const float*)r, nrows, Nx, (float*)rho);
-  return cudaGetLastError();
+    return launch_k(k_nyquist_coef_d, dim3(blocks), dim3(threads), 0, s, (const double*)r, nrows, Nx, (double*)rho);
+  return launch_k(k_nyquist_coef_f, dim3(blocks), dim3(threads), 0, s, (const float*)r, nrows, Nx, (float*)rho);
 }
 cudaError_t launch_gmres_init(double* st, const double* partial, int nblk, int m, double bnorm,
                               double tol, cudaStream_t s) {
-  k_gmres_init<<<1, 32, 0, s>>>(st, partial, nblk, m, bnorm, tol);
-  return cudaGetLastError();
+  return launch_k(k_gmres_init, dim3(1), dim3(32), 0, s, st, partial, nblk, m, bnorm, tol);
 }
 cudaError_t launch_gmres_arnoldi(double* st, const double* partial1, const double* partial2, int nblk,
                                  int j, int m, double bnorm, double tol, cudaStream_t s) {
   (void)partial1;
   (void)bnorm;
   (void)tol;
-  k_gmres_arnoldi<<<1, 64, 0, s>>>(st, partial2, nblk, j, m);
-  return cudaGetLastError();
+  return launch_k(k_gmres_arnoldi, dim3(1), dim3(64), 0, s, st, partial2, nblk, j, m);
 }
 cudaError_t launch_gmres_solve_y(double* st, int k, int m, cudaStream_t s) {
-  k_gmres_solve_y<<<1, 32, 0, s>>>(st, k, m);
-  return cudaGetLastError();
+  return launch_k(k_gmres_solve_y, dim3(1), dim3(32), 0, s, st, k, m);
 }
 
 #define WT_KINST(T)                                                                                  \
