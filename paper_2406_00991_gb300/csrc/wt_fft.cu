@@ -24,9 +24,84 @@ __global__ void __launch_bounds__(256) k_rowpass(RowPass<T> a, int ppc) {
   rowpass_body<T>(a, ppc, blockIdx.x, gridDim.x, smraw);
 }
 
+// x-derivative of single real rows through a half-length complex FFT, one
+// row per CTA (used for FP64, whose per-SM arithmetic rate makes the row
+// pair transform of k_rowpass the long pole): with H = N/2,
+//   z_k = x_2k + i x_2k+1,  Z = DFT_H(z),
+//   X_m = E_m + W^m O_m, E_m = (Z_m + conj Z_{H-m}) / 2, O_m = (Z_m - conj Z_{H-m}) / 2i,
+//   Y_m = i kappa_m X_m (m < H; the Nyquist coefficient Y_H = 0),
+//   C_m = (Y_m + conj Y_{H-m}) + i W^-m (Y_m - conj Y_{H-m}),  W = exp(-2 pi i / N),
+//   IDFT_H(C)_k / N = y_2k + i y_2k+1,
+// then the store / add / residual epilogue of the general pass.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rowpass_real(RowPass<T> a) {
+  using c2 = c2_t<T>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int N = a.Nin, logN = a.logNin, H = N >> 1;
+  c2* z = reinterpret_cast<c2*>(smraw);
+  c2* w = z + H;
+  c2* tws = w + H;                                  // exp(-2 pi i t / N), t < N/2
+  for (int t = threadIdx.x; t < H; t += blockDim.x) tws[t] = a.tw[t << (a.logNtw - logN)];
+  const int r = blockIdx.x;
+  const T* in = a.in + (long)r * N;
+  for (int k = threadIdx.x; k < H; k += blockDim.x) z[k] = mk<T>(in[2 * k], in[2 * k + 1]);
+  __syncthreads();
+  c2* Z = fft_smem<T>(z, w, logN - 1, 1, H, tws, logN, false);
+  c2* Yb = (Z == z) ? w : z;
+  for (int m = threadIdx.x; m < H; m += blockDim.x) {
+    const c2 zm = Z[m], zc0 = Z[(H - m) & (H - 1)];
+    const c2 zc = mk<T>(zc0.x, -zc0.y);
+    const c2 E = mk<T>(T(0.5) * (zm.x + zc.x), T(0.5) * (zm.y + zc.y));
+    const c2 Om = mk<T>(T(0.5) * (zm.y - zc.y), -T(0.5) * (zm.x - zc.x));   // (zm - zc) / 2i
+    const c2 X = mk<T>(E.x, E.y);
+    const c2 WO = cmul<T>(tws[m], Om);
+    const T kap = a.kscale * T(m);
+    // Y_m = i kappa (E + W^m O)
+    Yb[m] = mk<T>(-kap * (X.y + WO.y), kap * (X.x + WO.x));
+  }
+  __syncthreads();
+  for (int m = threadIdx.x; m < H; m += blockDim.x) {
+    const c2 ym = Yb[m];
+    const c2 yh = m == 0 ? mk<T>(T(0), T(0)) : Yb[H - m];          // Y_H = 0
+    const c2 yc = mk<T>(yh.x, -yh.y);
+    const c2 sum = mk<T>(ym.x + yc.x, ym.y + yc.y);
+    const c2 dif = mk<T>(ym.x - yc.x, ym.y - yc.y);
+    const c2 wm = mk<T>(tws[m].x, -tws[m].y);                        // W^-m
+    const c2 t = cmul<T>(wm, dif);
+    Z[m] = mk<T>(sum.x - t.y, sum.y + t.x);                          // sum + i t
+  }
+  __syncthreads();
+  c2* R = fft_smem<T>(Z, Yb, logN - 1, 1, H, tws, logN, true);
+  const T sc = a.scale / T(N);
+  for (int k = threadIdx.x; k < H; k += blockDim.x) {
+    const c2 y = R[k];
+    for (int h = 0; h < 2; ++h) {
+      const long o = (long)r * N + 2 * k + h;
+      T v = (h ? y.y : y.x) * sc;
+      if (bc_row(a, r)) v = T(0);
+      if (a.epi == EPI_ADD) v += a.add[o];
+      else if (a.epi == EPI_RESID) v = a.rhs[o] - (a.add[o] + v);
+      else if (a.epi == EPI_ACC) v += a.out[o];
+      a.out[o] = v;
+    }
+  }
+}
+
 template <typename T>
 cudaError_t launch_rowpass(const RowPass<T>& a, cudaStream_t s) {
   if (a.nrows <= 0) return cudaSuccess;
+  if (sizeof(T) == 8 && a.op == XOP_DERIV && a.Nin == a.Nout && a.Nin >= 8 && !a.ylines && !a.nyq &&
+      !a.out2) {
+    const size_t smem = (size_t)(3 * (a.Nin / 2)) * sizeof(c2_t<T>);
+    static size_t configured = 0;
+    if (smem > 48 * 1024 && smem > configured) {
+      cudaError_t e = cudaFuncSetAttribute(k_rowpass_real<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+      if (e != cudaSuccess) return e;
+      configured = smem;
+    }
+    return launch_k(k_rowpass_real<T>, dim3(a.nrows), dim3(256), smem, s, a);
+  }
   const int Nmax = std::max(a.Nin, a.Nout);
   const int npairs = (a.nrows + 1) / 2;
   int ppc = std::max(1, 1024 / Nmax);
