@@ -25,14 +25,16 @@ __global__ void __launch_bounds__(256) k_rowpass(RowPass<T> a, int ppc) {
 }
 
 // x-derivative of single real rows through a half-length complex FFT, one
-// row per CTA (used for FP64, whose per-SM arithmetic rate makes the row
-// pair transform of k_rowpass the long pole): with H = N/2,
+// row per CTA: half the transform length and twice the CTAs of the row-pair
+// pass (measured faster in FP32 and FP64; FP64 gains most, its per-SM rate
+// makes the row-pair transform the long pole): with H = N/2,
 //   z_k = x_2k + i x_2k+1,  Z = DFT_H(z),
 //   X_m = E_m + W^m O_m, E_m = (Z_m + conj Z_{H-m}) / 2, O_m = (Z_m - conj Z_{H-m}) / 2i,
 //   Y_m = i kappa_m X_m (m < H; the Nyquist coefficient Y_H = 0),
 //   C_m = (Y_m + conj Y_{H-m}) + i W^-m (Y_m - conj Y_{H-m}),  W = exp(-2 pi i / N),
 //   IDFT_H(C)_k / N = y_2k + i y_2k+1,
-// then the store / add / residual epilogue of the general pass.
+// then the store / add / residual / accumulate epilogue of the general pass
+// and, when asked, the output row's Nyquist coefficient.
 template <typename T>
 __global__ void __launch_bounds__(256) k_rowpass_real(RowPass<T> a) {
   using c2 = c2_t<T>;
@@ -73,6 +75,7 @@ __global__ void __launch_bounds__(256) k_rowpass_real(RowPass<T> a) {
   __syncthreads();
   c2* R = fft_smem<T>(Z, Yb, logN - 1, 1, H, tws, logN, true);
   const T sc = a.scale / T(N);
+  T alt = T(0);                                  // sum of (-1)^n out_n for the Nyquist coefficient
   for (int k = threadIdx.x; k < H; k += blockDim.x) {
     const c2 y = R[k];
     for (int h = 0; h < 2; ++h) {
@@ -83,6 +86,18 @@ __global__ void __launch_bounds__(256) k_rowpass_real(RowPass<T> a) {
       else if (a.epi == EPI_RESID) v = a.rhs[o] - (a.add[o] + v);
       else if (a.epi == EPI_ACC) v += a.out[o];
       a.out[o] = v;
+      alt += h ? -v : v;
+    }
+  }
+  if (a.nyq) {
+    __shared__ T red[32];
+    for (int o = 16; o > 0; o >>= 1) alt += __shfl_xor_sync(0xffffffffu, alt, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = alt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T s = T(0);
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+      a.nyq[r] = s / T(N);
     }
   }
 }
@@ -90,8 +105,7 @@ __global__ void __launch_bounds__(256) k_rowpass_real(RowPass<T> a) {
 template <typename T>
 cudaError_t launch_rowpass(const RowPass<T>& a, cudaStream_t s) {
   if (a.nrows <= 0) return cudaSuccess;
-  if (sizeof(T) == 8 && a.op == XOP_DERIV && a.Nin == a.Nout && a.Nin >= 8 && !a.ylines && !a.nyq &&
-      !a.out2) {
+  if (a.op == XOP_DERIV && a.Nin == a.Nout && a.Nin >= 8 && !a.ylines && !a.out2) {
     const size_t smem = (size_t)(3 * (a.Nin / 2)) * sizeof(c2_t<T>);
     static size_t configured = 0;
     if (smem > 48 * 1024 && smem > configured) {
