@@ -25,6 +25,15 @@ __global__ void __launch_bounds__(256) k_op_cols(LevelView<T> L, const T* __rest
   opcols_body<T, DIM>(L, p, Px, Py, Gx, Gy, part, blockIdx.x, gridDim.x, smraw);
 }
 
+template <typename T, int DIM, int MAXM>
+__global__ void __launch_bounds__(128) k_op_cols_tpc(LevelView<T> L, const T* __restrict__ p,
+                                                     const T* __restrict__ Px, const T* __restrict__ Py,
+                                                     T* __restrict__ Gx, T* __restrict__ Gy,
+                                                     T* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  opcols_tpc_body<T, DIM, MAXM>(L, p, Px, Py, Gx, Gy, part, smraw);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_op_cols_T(LevelView<T> L, const T* __restrict__ lam,
                                                    const T* __restrict__ Dlam, T* __restrict__ Mx,
@@ -68,6 +77,10 @@ static cudaError_t set_smem(const void* fn, size_t smem) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+// Levels with at least this many columns use the thread-per-column sigma
+// operator (k_op_cols_tpc) when M1 <= 17.
+constexpr long kTpcMinCols = 8192;
+
 static inline int grid_cols(long ncols, int threads) {
   const long w = threads / 32;
   return (int)std::min<long>(std::max<long>(1, (ncols + w - 1) / w), 152L * 64);
@@ -76,8 +89,18 @@ static inline int grid_cols(long ncols, int threads) {
 template <typename T>
 cudaError_t launch_op_cols(const LevelView<T>& L, const T* p, const T* Px, const T* Py, T* Gx,
                            T* Gy, T* part, cudaStream_t s) {
-  const int g = grid_cols(L.ncols, 256);
   const size_t smem = opcols_smem<T>(L.M1);
+  if (L.ncols >= kTpcMinCols && L.M1 <= 17) {
+    // many columns: one thread per column, coalesced sigma rows
+    const dim3 G((unsigned)((L.ncols + 127) / 128)), B(128);
+    if (L.Ny == 1) {
+      if (L.M1 <= 9) return launch_k(k_op_cols_tpc<T, 2, 9>, G, B, smem, s, L, p, Px, Py, Gx, Gy, part);
+      return launch_k(k_op_cols_tpc<T, 2, 17>, G, B, smem, s, L, p, Px, Py, Gx, Gy, part);
+    }
+    if (L.M1 <= 9) return launch_k(k_op_cols_tpc<T, 3, 9>, G, B, smem, s, L, p, Px, Py, Gx, Gy, part);
+    return launch_k(k_op_cols_tpc<T, 3, 17>, G, B, smem, s, L, p, Px, Py, Gx, Gy, part);
+  }
+  const int g = grid_cols(L.ncols, 256);
   if (L.Ny == 1) return launch_k(k_op_cols<T, 2>, dim3(g), dim3(256), smem, s, L, p, Px, Py, Gx, Gy, part);
   return launch_k(k_op_cols<T, 3>, dim3(g), dim3(256), smem, s, L, p, Px, Py, Gx, Gy, part);
 }

@@ -480,6 +480,99 @@ __device__ void opcolsT_body(const LevelView<T>& L, const T* WT_DEV_RESTRICT lam
   __syncthreads();
 }
 
+// The same sigma part with one thread per column, for levels with many
+// columns (3D): adjacent threads take adjacent columns, so every load and
+// store of a sigma row is coalesced across the warp (the warp-per-column
+// layout reads one sector per element there).  MAXM >= M1.
+template <typename T, int DIM, int MAXM>
+__device__ void opcols_tpc_body(const LevelView<T>& L, const T* WT_DEV_RESTRICT p,
+                                const T* WT_DEV_RESTRICT Px, const T* WT_DEV_RESTRICT Py,
+                                T* WT_DEV_RESTRICT Gx, T* WT_DEV_RESTRICT Gy, T* WT_DEV_RESTRICT part,
+                                unsigned char* smraw) {
+  const int M1 = L.M1;
+  T* sD = reinterpret_cast<T*>(smraw);
+  T* sS = sD + M1 * M1;
+  for (int i = threadIdx.x; i < M1 * M1; i += blockDim.x) sD[i] = L.D[i];
+  for (int i = threadIdx.x; i < M1; i += blockDim.x) sS[i] = L.sigma[i];
+  __syncthreads();
+  const long nc = L.ncols;
+  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const T* meta = L.meta;
+  T pv[MAXM], ps[MAXM], gx[MAXM], gy[DIM == 3 ? MAXM : 1];
+#pragma unroll
+  for (int m = 0; m < MAXM; ++m) pv[m] = m < M1 ? p[m * nc + c] : T(0);
+#pragma unroll
+  for (int m = 0; m < MAXM; ++m) {
+    T a = 0;
+#pragma unroll
+    for (int k = 0; k < MAXM; ++k)
+      if (m < M1 && k < M1) a += sD[m * M1 + k] * pv[k];
+    ps[m] = a;
+  }
+  const T AXb = meta[M_AXb * nc + c], BXb = meta[M_BXb * nc + c];
+  const T AXa = meta[M_AXa * nc + c], BXa = meta[M_BXa * nc + c];
+  const T Za = meta[M_Za * nc + c], Zb = meta[M_Zb * nc + c];
+  const T HX = meta[M_HX * nc + c];
+  T AYa = 0, BYa = 0, HY = 0;
+#pragma unroll
+  for (int m = 0; m < MAXM; ++m) {
+    if (m < M1) {
+      gx[m] = Px[m * nc + c] + (AXb - sS[m] * BXb) * ps[m];
+      Gx[m * nc + c] = gx[m];
+    } else {
+      gx[m] = T(0);
+    }
+  }
+  if constexpr (DIM == 3) {
+    const T AYb = meta[M_AYb * nc + c], BYb = meta[M_BYb * nc + c];
+    AYa = meta[M_AYa * nc + c];
+    BYa = meta[M_BYa * nc + c];
+    HY = meta[M_HY * nc + c];
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) {
+      if (m < M1) {
+        gy[m] = Py[m * nc + c] + (AYb - sS[m] * BYb) * ps[m];
+        Gy[m * nc + c] = gy[m];
+      } else {
+        gy[m] = T(0);
+      }
+    }
+  }
+  const T ZZ = Za * Zb;
+  part[c] = pv[0];                                                   // surface row: p
+#pragma unroll
+  for (int m = 1; m < MAXM; ++m) {
+    if (m >= M1 - 1) continue;
+    T q = 0, z = 0, y = 0;
+#pragma unroll
+    for (int k = 0; k < MAXM; ++k) {
+      if (k < M1) {
+        const T d = sD[m * M1 + k];
+        q += d * gx[k];
+        z += d * ps[k];
+        if constexpr (DIM == 3) y += d * gy[k];
+      }
+    }
+    const T s = sS[m];
+    T o = (AXa - s * BXa) * q + ZZ * z;
+    if constexpr (DIM == 3) o += (AYa - s * BYa) * y;
+    part[m * nc + c] = o;
+  }
+  const int N = M1 - 1;                                              // bottom row: n . Grad_b p
+  T bsum = 0, gxN = 0, gyN = 0, psN = 0;
+#pragma unroll
+  for (int m = 0; m < MAXM; ++m)
+    if (m == N) {
+      gxN = gx[m];
+      psN = ps[m];
+      if constexpr (DIM == 3) gyN = gy[m];
+    }
+  bsum = HX * gxN + Zb * psN;
+  if constexpr (DIM == 3) bsum += HY * gyN;
+  part[N * nc + c] = bsum;
+}
+
 // Block inverses are stored per column, contiguous and transposed:
 // Binv[((c * nclass + cls) * M1 + k) * M1 + m] = (A_rr^{-1})[m][k], so lane m
 // of a warp reads consecutive words for every k.

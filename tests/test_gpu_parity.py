@@ -53,7 +53,9 @@ def test_operator_parity_2d(wt, Nx, Nz, L):
     assert np.abs(got32 - ref).max() <= 2e-4 * scale
 
 
-@pytest.mark.parametrize("Nx,Ny,Nz", [(8, 8, 4), (32, 32, 8), (64, 64, 16)])
+# (128, 128, 8) and (128, 128, 16) have >= 8192 columns: the thread-per-column
+# sigma kernel; the smaller ones the warp-per-column kernel
+@pytest.mark.parametrize("Nx,Ny,Nz", [(8, 8, 4), (32, 32, 8), (64, 64, 16), (128, 128, 8), (128, 128, 16)])
 def test_operator_parity_3d(wt, Nx, Ny, Nz):
     L = 2 * math.pi
     g, h, ea, eb = curved(Nx, Ny, Nz, L)
