@@ -298,6 +298,7 @@ def run_ours(args):
     if not args.no_extras:
         line["batch"] = bench_batch(w, args)
         line["adjoint"] = bench_adjoint(w, torch, args)
+        line["sea3d"] = bench_sea3d(w, torch, args)
     print(json.dumps(line), flush=True)
 
 
@@ -330,6 +331,45 @@ def bench_batch(w, args):
             "solves_per_s": STAGES * len(tanks) / (ms / 1e3), "steps": K, "tanks_redrawn": redrawn,
             "krylov_iterations_per_solve": float(np.mean([a[1] / max(1, a[0]) for a in its])),
             "timing": "host clock around one wt_batch_step call of K steps (it returns when all tanks are done)"}
+
+
+def bench_sea3d(w, torch, args):
+    """The 3D directional sea: 256 x 256 x 16, 4096 JONSWAP components, mixed solver."""
+    N, Nz, L = 256, 16, 64.0
+    T = w.Tank(N, N, Nz, L, np.ones((N, N)), mode=w.WT_MIXED, tol=1e-10, filter=1, omega=0.6, max_it=400)
+    _, _, sigma = T.grid()
+    sea = si.jonswap_sea(seed=3, L=L, ncomp=4096, kp=1.5, hs_over_lp=0.02)
+    eta0, u0, v0, w0 = si.jonswap_fields(sea, N, sigma)
+    T.set_state(*(np.ascontiguousarray(a) for a in (eta0, u0, v0, w0)))
+    dt = 0.5 * (L / N) / math.sqrt(9.81)
+    T.step(dt, 1)                                    # warm-up (graph capture)
+    K = 2
+    s0, i0 = T.stats()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    T.step(dt, K)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / K
+    s1, i1 = T.stats()
+    # one more step with CUDA events around every launch, per kernel class
+    T.profile((1 << len(w.KERNEL_CLASSES)) - 1)
+    T.step(dt, 1)
+    cls = [T.profile_read(c) for c in range(len(w.KERNEL_CLASSES))]
+    T.profile(0)
+    T.close()
+    dom = int(np.argmax([c["ms"] for c in cls]))
+    hbm, _ = peaks()
+    ach = cls[dom]["bytes"] / (cls[dom]["ms"] / 1e3) / 1e9 if cls[dom]["ms"] > 0 else 0.0
+    dof = STAGES * N * N * (Nz + 1)
+    return {"workload": "3D directional JONSWAP sea, 256 x 256 x 16, L = 64, 4096 components, filter on, "
+                        "mixed solver at 1e-10, omega 0.6",
+            "metric": "RK4 DOF-updates/s", "value": dof / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "krylov_iterations_per_solve": (i1 - i0) / max(1, s1 - s0), "steps": K,
+            "roofline": {"bound": "hbm", "kernel": w.KERNEL_CLASSES[dom], "achieved": ach, "peak": hbm,
+                         "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+                         "timing": "CUDA events around each launch of the class in one profiled step"},
+            "kernel_classes_ms": {w.KERNEL_CLASSES[c]: round(cls[c]["ms"], 2) for c in range(len(cls))},
+            "timing": "host clock around wt_step of K steps (returns after the step)"}
 
 
 def bench_adjoint(w, torch, args):
