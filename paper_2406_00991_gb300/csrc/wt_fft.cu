@@ -108,7 +108,9 @@ cudaError_t launch_rowpass(const RowPass<T>& a, cudaStream_t s) {
   if (a.op == XOP_DERIV && a.Nin == a.Nout && a.Nin >= 8 && !a.ylines && !a.out2) {
     const size_t smem = (size_t)(3 * (a.Nin / 2)) * sizeof(c2_t<T>);
     static size_t configured = 0;
-    if (smem > 48 * 1024 && smem > configured) {
+    // the kernel's 32-word static reduction buffer counts against the
+    // default 48 KB as well
+    if (smem + 32 * sizeof(T) > 48 * 1024 && smem > configured) {
       cudaError_t e = cudaFuncSetAttribute(k_rowpass_real<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
       if (e != cudaSuccess) return e;

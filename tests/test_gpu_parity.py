@@ -37,7 +37,7 @@ def curved(Nx, Ny, Nz, L, seed=0, amp=0.05, bump=0.3):
     return g, np.ascontiguousarray(h), np.ascontiguousarray(ea), np.ascontiguousarray(eb)
 
 
-CASES_2D = [(8, 4, 2 * math.pi), (64, 16, 2 * math.pi), (256, 24, 32.0), (1024, 24, 32.0)]
+CASES_2D = [(8, 4, 2 * math.pi), (64, 16, 2 * math.pi), (256, 24, 32.0), (1024, 24, 32.0), (2048, 16, 64.0)]
 
 
 @pytest.mark.parametrize("Nx,Nz,L", CASES_2D)
