@@ -302,12 +302,8 @@ __global__ void __launch_bounds__(512) k_batch_step(const BatchTankDesc* descs, 
 
 cudaError_t launch_batch_step(const BatchTankDesc* descs, const int* order, int ntanks, const double* dt,
                               int nsteps, int smem, cudaStream_t s) {
-  static int configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_batch_step, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
+  cudaError_t e = ensure_dyn_smem((const void*)k_batch_step, (size_t)smem);
+  if (e != cudaSuccess) return e;
   k_batch_step<<<ntanks, 512, smem, s>>>(descs, order, dt, nsteps, smem);
   return cudaGetLastError();
 }

@@ -52,12 +52,9 @@ cudaError_t launch_coarse_factor(const LevelView<double>& L, const double* Dx, c
   const int n = L.M1 * L.Ny * L.Nx;
   if (n > 128) return cudaErrorInvalidValue;
   const size_t smem = (size_t)n * (n + 1) * sizeof(double) + sizeof(int) * (n + 1);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_coarse_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+  if (smem > 32 * 1024) {
+    cudaError_t e = ensure_dyn_smem((const void*)k_coarse_factor, smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   k_coarse_factor<<<1, 256, smem, s>>>(L, Dx, Dy, LU, piv, flag);
   return cudaGetLastError();

@@ -141,12 +141,9 @@ cudaError_t launch_block_inverse(const LevelView<T>& L, T* Binv, int nclass, T c
                                  int* flag, cudaStream_t s) {
   const int W = 2 * L.M1 + 1;
   const size_t smem = 4 * (size_t)L.M1 * W * sizeof(T);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_block_inverse<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 32 * 1024) {
+    cudaError_t e = ensure_dyn_smem((const void*)k_block_inverse<T>, smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   const long tasks = (long)L.ncols * nclass;
   const int g = (int)std::min<long>(std::max<long>(1, (tasks + 3) / 4), 152 * 8);

@@ -107,14 +107,11 @@ cudaError_t launch_rowpass(const RowPass<T>& a, cudaStream_t s) {
   if (a.nrows <= 0) return cudaSuccess;
   if (a.op == XOP_DERIV && a.Nin == a.Nout && a.Nin >= 8 && !a.ylines && !a.out2) {
     const size_t smem = (size_t)(3 * (a.Nin / 2)) * sizeof(c2_t<T>);
-    static size_t configured = 0;
-    // the kernel's 32-word static reduction buffer counts against the
-    // default 48 KB as well
-    if (smem + 32 * sizeof(T) > 48 * 1024 && smem > configured) {
-      cudaError_t e = cudaFuncSetAttribute(k_rowpass_real<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
+    // (the kernel's 32-word static reduction buffer counts against the
+    // default 48 KB as well)
+    if (smem > 32 * 1024) {
+      cudaError_t e = ensure_dyn_smem((const void*)k_rowpass_real<T>, smem);
       if (e != cudaSuccess) return e;
-      configured = smem;
     }
     return launch_k(k_rowpass_real<T>, dim3(a.nrows), dim3(256), smem, s, a);
   }
@@ -124,12 +121,9 @@ cudaError_t launch_rowpass(const RowPass<T>& a, cudaStream_t s) {
   const int want = (npairs + 303) / 304;     // spread small passes over the SMs
   ppc = std::max(1, std::min(ppc, want));
   const size_t smem = rowpass_smem(a, ppc);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_rowpass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+  if (smem > 32 * 1024) {
+    cudaError_t e = ensure_dyn_smem((const void*)k_rowpass<T>, smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   int grid = (npairs + ppc - 1) / ppc;
   grid = std::min(grid, 152 * 16);
@@ -160,12 +154,9 @@ cudaError_t launch_rowpass_multi(const MultiPass<T>& m0, cudaStream_t s) {
     m.start[i + 1] = m.start[i] + npairs;
     smem = std::max(smem, rowpass_smem(m.d[i], 1));
   }
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_rowpass_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+  if (smem > 32 * 1024) {
+    cudaError_t e = ensure_dyn_smem((const void*)k_rowpass_multi<T>, smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   if (m.start[m.n] <= 0) return cudaSuccess;
   k_rowpass_multi<T><<<m.start[m.n], 256, smem, s>>>(m);

@@ -101,6 +101,11 @@ struct RowPass {
   int write_out = 1;
 };
 
+// Raise kernel `fn`'s dynamic shared-memory limit to at least `bytes` on the
+// current device.  The attribute belongs to (kernel, device), so the cache of
+// what has been set is kept per pair (wt_launch.cu); thread-safe.
+cudaError_t ensure_dyn_smem(const void* fn, size_t bytes);
+
 // Launch through cudaLaunchKernelEx (grid, block, dynamic shared memory,
 // stream); returns the launch status.
 template <typename... KArgs, typename... Args>

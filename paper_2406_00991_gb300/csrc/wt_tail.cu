@@ -23,16 +23,9 @@ __global__ void __launch_bounds__(512) k_vcycle_tail(TailArgs<T> A) {
 
 template <typename T>
 cudaError_t launch_vcycle_tail(const TailArgs<T>& a, int dim, cudaStream_t s) {
-  static int configured[2] = {0, 0};
-  const int k = dim == 3 ? 1 : 0;
-  if (a.smem > configured[k]) {
-    cudaError_t e = dim == 3 ? cudaFuncSetAttribute(k_vcycle_tail<T, 3>,
-                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem)
-                             : cudaFuncSetAttribute(k_vcycle_tail<T, 2>,
-                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem);
-    if (e != cudaSuccess) return e;
-    configured[k] = a.smem;
-  }
+  cudaError_t e = dim == 3 ? ensure_dyn_smem((const void*)k_vcycle_tail<T, 3>, (size_t)a.smem)
+                           : ensure_dyn_smem((const void*)k_vcycle_tail<T, 2>, (size_t)a.smem);
+  if (e != cudaSuccess) return e;
   if (dim == 3)
     k_vcycle_tail<T, 3><<<1, 512, a.smem, s>>>(a);
   else

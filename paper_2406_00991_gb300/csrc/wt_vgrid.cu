@@ -22,21 +22,16 @@ __global__ void __launch_bounds__(512, 1) k_vcycle_grid(TailArgs<T> A, GridBar* 
 
 template <typename T, int DIM>
 static cudaError_t launch_dim(const TailArgs<T>& a, GridBar* bar, int* flag, cudaStream_t s) {
-  static int configured = 0, nblocks = 0;
-  if (a.smem > configured || nblocks == 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_vcycle_grid<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         a.smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, nsm = 0, occ = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vcycle_grid<T, DIM>, 512, a.smem)) !=
-        cudaSuccess)
-      return e;
-    if (occ < 1) return cudaErrorInvalidConfiguration;
-    nblocks = nsm;                                   // one CTA per SM
-    configured = a.smem;
-  }
+  cudaError_t e = ensure_dyn_smem((const void*)k_vcycle_grid<T, DIM>, (size_t)a.smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, occ = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vcycle_grid<T, DIM>, 512, a.smem)) !=
+      cudaSuccess)
+    return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;  // one CTA per SM must fit for co-residency
+  const int nblocks = nsm;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nblocks);
   cfg.blockDim = dim3(512);
