@@ -508,6 +508,9 @@ class Batch:
         return len(self.Nx)
 
     def set_options(self, **kw):
+        """Apply one option set to every tank of the batch: the keys given here
+        on top of the library defaults (unlike Tank.set_options, which changes
+        only the given keys of the tank's current options)."""
         o = wt_default_options()
         for k, v in kw.items():
             if k not in dict(wt_options._fields_):
