@@ -129,6 +129,26 @@ def peaks():
 
 
 # ------------------------------------------------------------------- our arm
+def over_ranks(dist, v, op, device):
+    """v reduced ("max" or "sum") over the ranks of the process group `dist`
+    (the torch.distributed module, or None for a single process)."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_throughput(dist, device, units, ms):
+    """Whole-job throughput of independent replicas (one per rank): the units
+    every rank processed divided by the slowest rank's time.  Returns
+    (units per second, slowest ms)."""
+    ms_max = over_ranks(dist, ms, "max", device)
+    total = over_ranks(dist, units, "sum", device)
+    return total / (ms_max / 1e3), ms_max
+
+
 def run_ours(args):
     import torch
     import paper_2406_00991_gb300 as w
@@ -154,18 +174,10 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return over_ranks(dist, v, "max", dev)
 
     def sum_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return over_ranks(dist, v, "sum", dev)
 
     p, x, h = workload()
     T = w.Tank(p["Nx"], 1, p["Nz"], p["L"], h, mode=w.WT_MIXED, tol=1e-10, filter=1)
@@ -215,8 +227,7 @@ def run_ours(args):
     clocks.start()
     ms, wall, launches, (solves, iters) = timed_steps(args.steps)          # graphs, no events
     ck = clocks.stop()
-    step_ms = max_over_ranks(float(np.mean(ms)))
-    value = sum_over_ranks(dof_step) / (step_ms / 1e3)
+    value, step_ms = replica_throughput(dist, dev, dof_step, float(np.mean(ms)))
     solves_s = sum_over_ranks(STAGES) / (step_ms / 1e3)
     # second pass of the same number of steps with CUDA events around every
     # launch of the dominant kernel class (events force eager launches)
