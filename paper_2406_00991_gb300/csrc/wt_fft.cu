@@ -24,70 +24,108 @@ __global__ void __launch_bounds__(256) k_rowpass(RowPass<T> a, int ppc) {
   rowpass_body<T>(a, ppc, blockIdx.x, gridDim.x, smraw);
 }
 
-// x-derivative of single real rows through a half-length complex FFT, one
-// row per CTA: half the transform length and twice the CTAs of the row-pair
-// pass (measured faster in FP32 and FP64; FP64 gains most, its per-SM rate
-// makes the row-pair transform the long pole): with H = N/2,
+// Single real rows through a half-length complex FFT, one row per CTA: half
+// the transform length and twice the CTAs of the row-pair pass (measured
+// faster in FP32 and FP64; FP64 gains most, its per-SM rate makes the
+// row-pair transform the long pole).  For a real row x of length N, H = N/2:
 //   z_k = x_2k + i x_2k+1,  Z = DFT_H(z),
 //   X_m = E_m + W^m O_m, E_m = (Z_m + conj Z_{H-m}) / 2, O_m = (Z_m - conj Z_{H-m}) / 2i,
-//   Y_m = i kappa_m X_m (m < H; the Nyquist coefficient Y_H = 0),
-//   C_m = (Y_m + conj Y_{H-m}) + i W^-m (Y_m - conj Y_{H-m}),  W = exp(-2 pi i / N),
-//   IDFT_H(C)_k / N = y_2k + i y_2k+1,
-// then the store / add / residual / accumulate epilogue of the general pass
-// and, when asked, the output row's Nyquist coefficient.
+//   X_H = E_0 - O_0,  W = exp(-2 pi i / N)      (m = 0..H: the Hermitian half);
+// the spectral operation maps X (length Nin) to Y (length Nout, m = 0..Hout);
+// then with H = Hout, W = exp(-2 pi i / Nout)
+//   C_m = (Y_m + conj Y_{H-m}) + i W^-m (Y_m - conj Y_{H-m})   (Y_{H-0} = Y_H),
+//   IDFT_H(C)_k = y_2k + i y_2k+1  (times Nin, removed by the epilogue scale).
+template <typename T>
+__device__ c2_t<T>* real_spectral(c2_t<T>* A, c2_t<T>* B, int logNin, int logNout, int op, T kscale,
+                                  const T* filt, const c2_t<T>* tws, int logNt) {
+  using c2 = c2_t<T>;
+  const int Hin = 1 << (logNin - 1), Hout = 1 << (logNout - 1);
+  const int keep = (Hin < Hout ? Hin : Hout) * 2;          // resample: keep |m| < keep / 2
+  const int sin = logNt - logNin, sout = logNt - logNout;
+  c2* Z = fft_smem<T>(A, B, logNin - 1, 1, 0, tws, logNt, false);
+  c2* Y = (Z == A) ? B : A;
+  for (int m = threadIdx.x; m <= Hout; m += blockDim.x) {
+    c2 X = mk<T>(T(0), T(0));
+    if (m < Hin) {
+      const c2 zm = Z[m], zc0 = Z[(Hin - m) & (Hin - 1)];
+      const c2 E = mk<T>(T(0.5) * (zm.x + zc0.x), T(0.5) * (zm.y - zc0.y));
+      const c2 Om = mk<T>(T(0.5) * (zm.y + zc0.y), -T(0.5) * (zm.x - zc0.x));   // (zm - conj zc) / 2i
+      const c2 WO = cmul<T>(tws[m << sin], Om);
+      X = mk<T>(E.x + WO.x, E.y + WO.y);
+    } else if (m == Hin) {
+      const c2 z0 = Z[0];
+      X = mk<T>(z0.x - z0.y, T(0));                         // E_0 - O_0 (real)
+    }
+    c2 v = mk<T>(T(0), T(0));
+    if (op == XOP_DERIV || op == XOP_RESAMPLE_DERIV) {
+      if (m < Hout && 2 * m < keep) {
+        const T kap = kscale * T(m);
+        v = mk<T>(-kap * X.y, kap * X.x);
+      }
+    } else if (op == XOP_RESAMPLE) {
+      if (2 * m < keep) v = X;
+    } else if (op == XOP_FILTER) {
+      const T f = filt[m];
+      v = mk<T>(f * X.x, f * X.y);
+    } else {
+      v = X;                                                // XOP_NONE
+    }
+    Y[m] = v;
+  }
+  __syncthreads();
+  for (int m = threadIdx.x; m < Hout; m += blockDim.x) {
+    const c2 ym = Y[m];
+    const c2 yh = Y[Hout - m];                              // m = 0: the Nyquist term
+    const c2 yc = mk<T>(yh.x, -yh.y);
+    const c2 sum = mk<T>(ym.x + yc.x, ym.y + yc.y);
+    const c2 dif = mk<T>(ym.x - yc.x, ym.y - yc.y);
+    const c2 w = tws[m << sout];
+    const c2 t = cmul<T>(mk<T>(w.x, -w.y), dif);              // W^-m (Y_m - conj Y_{H-m})
+    Z[m] = mk<T>(sum.x - t.y, sum.y + t.x);
+  }
+  __syncthreads();
+  return fft_smem<T>(Z, Y, logNout - 1, 1, 0, tws, logNt, true);
+}
+
+// One real x-row per CTA: the spectral operation of the pass, its epilogue
+// (store / add / residual / accumulate, boundary rows, Nyquist coefficient)
+// and the optional second transform of the result into out2.
 template <typename T>
 __global__ void __launch_bounds__(256) k_rowpass_real(RowPass<T> a) {
   using c2 = c2_t<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = a.Nin, logN = a.logNin, H = N >> 1;
-  c2* z = reinterpret_cast<c2*>(smraw);
-  c2* w = z + H;
-  c2* tws = w + H;                                  // exp(-2 pi i t / N), t < N/2
-  for (int t = threadIdx.x; t < H; t += blockDim.x) tws[t] = a.tw[t << (a.logNtw - logN)];
+  const int Nin = a.Nin, Nout = a.Nout;
+  const int logNt = a.Nin > a.Nout ? a.logNin : a.logNout;
+  const int Nt = 1 << logNt;
+  const int Hb = Nt / 2 + 1;
+  c2* P = reinterpret_cast<c2*>(smraw);
+  c2* Q = P + Hb;
+  c2* tws = Q + Hb;                                         // exp(-2 pi i t / Nt), t < Nt/2
+  for (int t = threadIdx.x; t < Nt / 2; t += blockDim.x) tws[t] = a.tw[t << (a.logNtw - logNt)];
   const int r = blockIdx.x;
-  const T* in = a.in + (long)r * N;
-  for (int k = threadIdx.x; k < H; k += blockDim.x) z[k] = mk<T>(in[2 * k], in[2 * k + 1]);
+  const int Hin = Nin >> 1, Hout = Nout >> 1;
+  const T* in = a.in + (long)r * Nin;
+  for (int k = threadIdx.x; k < Hin; k += blockDim.x) P[k] = mk<T>(in[2 * k], in[2 * k + 1]);
   __syncthreads();
-  c2* Z = fft_smem<T>(z, w, logN - 1, 1, H, tws, logN, false);
-  c2* Yb = (Z == z) ? w : z;
-  for (int m = threadIdx.x; m < H; m += blockDim.x) {
-    const c2 zm = Z[m], zc0 = Z[(H - m) & (H - 1)];
-    const c2 zc = mk<T>(zc0.x, -zc0.y);
-    const c2 E = mk<T>(T(0.5) * (zm.x + zc.x), T(0.5) * (zm.y + zc.y));
-    const c2 Om = mk<T>(T(0.5) * (zm.y - zc.y), -T(0.5) * (zm.x - zc.x));   // (zm - zc) / 2i
-    const c2 X = mk<T>(E.x, E.y);
-    const c2 WO = cmul<T>(tws[m], Om);
-    const T kap = a.kscale * T(m);
-    // Y_m = i kappa (E + W^m O)
-    Yb[m] = mk<T>(-kap * (X.y + WO.y), kap * (X.x + WO.x));
-  }
-  __syncthreads();
-  for (int m = threadIdx.x; m < H; m += blockDim.x) {
-    const c2 ym = Yb[m];
-    const c2 yh = m == 0 ? mk<T>(T(0), T(0)) : Yb[H - m];          // Y_H = 0
-    const c2 yc = mk<T>(yh.x, -yh.y);
-    const c2 sum = mk<T>(ym.x + yc.x, ym.y + yc.y);
-    const c2 dif = mk<T>(ym.x - yc.x, ym.y - yc.y);
-    const c2 wm = mk<T>(tws[m].x, -tws[m].y);                        // W^-m
-    const c2 t = cmul<T>(wm, dif);
-    Z[m] = mk<T>(sum.x - t.y, sum.y + t.x);                          // sum + i t
-  }
-  __syncthreads();
-  c2* R = fft_smem<T>(Z, Yb, logN - 1, 1, H, tws, logN, true);
-  const T sc = a.scale / T(N);
+  c2* R = real_spectral<T>(P, Q, a.logNin, a.logNout, a.op, a.kscale, a.filt, tws, logNt);
+  const T sc = a.scale / T(Nin);
+  const bool bc = bc_row(a, r);
   T alt = T(0);                                  // sum of (-1)^n out_n for the Nyquist coefficient
-  for (int k = threadIdx.x; k < H; k += blockDim.x) {
+  for (int k = threadIdx.x; k < Hout; k += blockDim.x) {
     const c2 y = R[k];
+    T vv[2];
     for (int h = 0; h < 2; ++h) {
-      const long o = (long)r * N + 2 * k + h;
+      const long o = (long)r * Nout + 2 * k + h;
       T v = (h ? y.y : y.x) * sc;
-      if (bc_row(a, r)) v = T(0);
+      if (bc) v = T(0);
       if (a.epi == EPI_ADD) v += a.add[o];
       else if (a.epi == EPI_RESID) v = a.rhs[o] - (a.add[o] + v);
       else if (a.epi == EPI_ACC) v += a.out[o];
-      a.out[o] = v;
+      if (a.write_out) a.out[o] = v;
       alt += h ? -v : v;
+      vv[h] = v;
     }
+    if (a.out2) R[k] = mk<T>(vv[0], vv[1]);       // input of the second transform
   }
   if (a.nyq) {
     __shared__ T red[32];
@@ -97,7 +135,18 @@ __global__ void __launch_bounds__(256) k_rowpass_real(RowPass<T> a) {
     if (threadIdx.x == 0) {
       T s = T(0);
       for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-      a.nyq[r] = s / T(N);
+      a.nyq[r] = s / T(Nout);
+    }
+  }
+  if (a.out2) {
+    __syncthreads();
+    c2* O = (R == P) ? Q : P;
+    c2* R2 = real_spectral<T>(R, O, a.logNout, a.logNout2, a.op2, a.kscale, nullptr, tws, logNt);
+    const T s2 = T(1) / T(Nout);
+    for (int k = threadIdx.x; k < (a.Nout2 >> 1); k += blockDim.x) {
+      const c2 y = R2[k];
+      a.out2[(long)r * a.Nout2 + 2 * k] = y.x * s2;
+      a.out2[(long)r * a.Nout2 + 2 * k + 1] = y.y * s2;
     }
   }
 }
@@ -105,8 +154,9 @@ __global__ void __launch_bounds__(256) k_rowpass_real(RowPass<T> a) {
 template <typename T>
 cudaError_t launch_rowpass(const RowPass<T>& a, cudaStream_t s) {
   if (a.nrows <= 0) return cudaSuccess;
-  if (a.op == XOP_DERIV && a.Nin == a.Nout && a.Nin >= 8 && !a.ylines && !a.out2) {
-    const size_t smem = (size_t)(3 * (a.Nin / 2)) * sizeof(c2_t<T>);
+  if (!a.ylines && a.Nin >= 8 && a.Nout >= 8 && (!a.out2 || (a.Nout2 >= 8 && a.Nout2 <= a.Nout))) {
+    const int Nt = std::max(a.Nin, a.Nout);
+    const size_t smem = (size_t)(2 * (Nt / 2 + 1) + Nt / 2) * sizeof(c2_t<T>);
     // (the kernel's 32-word static reduction buffer counts against the
     // default 48 KB as well)
     if (smem > 32 * 1024) {
