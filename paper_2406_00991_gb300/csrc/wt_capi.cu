@@ -607,6 +607,7 @@ int wt_create(int Nx, int Ny, int Nz, double L, double g, double nu, const doubl
     t->st = ar.alloc<double>(4608);
     t->stN = ar.alloc<double>(4608);
     t->gbar = ar.alloc<GridBar>(1);
+    t->tickets = ar.alloc<unsigned>(4);
     t->x64 = ar.alloc<double>(n); t->r64 = ar.alloc<double>(n); t->b64 = ar.alloc<double>(n);
     t->b32 = ar.alloc<float>(n); t->e32 = ar.alloc<float>(n);
     t->eta = ar.alloc<double>(nc); t->eta_new = ar.alloc<double>(nc); t->Keta = ar.alloc<double>(nc);

@@ -195,5 +195,6 @@ struct wt_tank {
   int* hflag = nullptr;            // pinned
   double* hst = nullptr;           // pinned
   wt::GridBar* gbar = nullptr;     // barrier of the cooperative V-cycle
+  unsigned* tickets = nullptr;     // last-CTA counters of the one-launch Krylov reductions
   long solves = 0, iterations = 0;
 };

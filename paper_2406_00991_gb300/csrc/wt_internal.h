@@ -247,14 +247,24 @@ cudaError_t launch_coarse_solve(int n, const double* LU, const int* piv, int tr,
 template <typename T>
 cudaError_t launch_dots(const T* w, const T* V, long ldv, int nvec, long n, double* partial,
                         int nblk, int with_norm, cudaStream_t s);
+// One-launch forms: the last CTA sums the partials (dots -> out), or sums
+// them and performs the Arnoldi / Givens update of column j (update_dots);
+// `ticket` is a zero-initialised device counter per call site.
+template <typename T>
+cudaError_t launch_dots_sum(const T* w, const T* V, long ldv, int nvec, long n, double* partial, int nblk,
+                            int with_norm, double* out, unsigned* ticket, cudaStream_t s);
+template <typename T>
+cudaError_t launch_update_dots_arnoldi(T* w, const T* V, long ldv, int nvec, long n, double* st,
+                                       double* partial, int nblk, int j, int m, unsigned* ticket,
+                                       cudaStream_t s);
 cudaError_t launch_reduce_partials(const double* partial, int nblk, int nvals, double* out,
                                    cudaStream_t s);
 template <typename T>
 cudaError_t launch_update_dots(T* w, const T* V, long ldv, int nvec, long n, const double* h,
                                double* partial, int nblk, cudaStream_t s);
 template <typename T>
-cudaError_t launch_update_normalize(T* w, const T* V, long ldv, int nvec, long n,
-                                    const double* h, const double* inv_norm, T* vout,
+cudaError_t launch_update_normalize(const T* w, const T* V, long ldv, int nvec, long n,
+                                    const double* h, const double* inv_norm, T* vout, float* v32,
                                     cudaStream_t s);
 template <typename T>
 cudaError_t launch_lincomb(T* x, const T* Z, long ldz, int nvec, long n, const double* y,

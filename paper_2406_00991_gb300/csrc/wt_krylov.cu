@@ -104,13 +104,15 @@ __global__ void __launch_bounds__(256) k_update_dots(T* __restrict__ w, const T*
   }
 }
 
-// vout = (w - V h) * inv_norm, h = st[OFF_H2..], inv_norm = st[2]
+// vout = (w - V h) * inv_norm, h = st[OFF_H2..], inv_norm = st[2]; vout may
+// be w itself (each element is read and written by one thread), and v32, if
+// given, receives the FP32 rounding of vout (the FP32 V-cycle's input).
 template <typename T>
-__global__ void __launch_bounds__(256) k_update_normalize(T* __restrict__ w, const T* __restrict__ V,
+__global__ void __launch_bounds__(256) k_update_normalize(const T* w, const T* __restrict__ V,
                                                          long ldv, int nvec, long n,
                                                          const double* __restrict__ h,
                                                          const double* __restrict__ inv_norm,
-                                                         T* __restrict__ vout) {
+                                                         T* vout, float* __restrict__ v32) {
   __shared__ T sh[32];
   for (int i = threadIdx.x; i < 32; i += blockDim.x) sh[i] = i < nvec ? (T)h[i] : T(0);
   __syncthreads();
@@ -120,7 +122,9 @@ __global__ void __launch_bounds__(256) k_update_normalize(T* __restrict__ w, con
 #pragma unroll
     for (int i = 0; i < 32; ++i)
       if (i < nvec) wv -= sh[i] * V[i * ldv + e];
-    vout[e] = wv * s;
+    wv *= s;
+    vout[e] = wv;
+    if (v32) v32[e] = (float)wv;
   }
 }
 
@@ -196,18 +200,11 @@ __global__ void k_gmres_init(double* st, const double* __restrict__ partial, int
   st[OFF_G] = beta;
 }
 
-__global__ void k_gmres_arnoldi(double* st, const double* __restrict__ partial2, int nblk, int j,
-                                int m) {
+// Column j of the Hessenberg matrix from the two Gram-Schmidt passes (h1 in
+// st, h2 and ||w||^2 given), the Givens rotations, the residual estimate and
+// the done flag (one thread).
+__device__ void arnoldi_update(double* st, const double* h2, double ww, int j, int m) {
   const double tol = st[6];
-  __shared__ double h2[64];
-  __shared__ double ww;
-  const int nvals = j + 2;    // j+1 dots and ||w||^2
-  for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
-    const double s = block_sum_partial(partial2, nblk, nvals, i);
-    if (i < j + 1) h2[i] = s; else ww = s;
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
   double* H = st + OFF_H + (long)j * (m + 1);
   double hh = ww;
   for (int i = 0; i <= j; ++i) {
@@ -239,6 +236,19 @@ __global__ void k_gmres_arnoldi(double* st, const double* __restrict__ partial2,
   st[3] = (res <= tol * st[4] || breakdown) ? 1.0 : 0.0;
 }
 
+__global__ void k_gmres_arnoldi(double* st, const double* __restrict__ partial2, int nblk, int j,
+                                int m) {
+  __shared__ double h2[64];
+  __shared__ double ww;
+  const int nvals = j + 2;    // j+1 dots and ||w||^2
+  for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
+    const double s = block_sum_partial(partial2, nblk, nvals, i);
+    if (i < j + 1) h2[i] = s; else ww = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) arnoldi_update(st, h2, ww, j, m);
+}
+
 __global__ void k_gmres_solve_y(double* st, int k, int m) {
   if (threadIdx.x != 0) return;
   for (int i = k - 1; i >= 0; --i) {
@@ -246,6 +256,118 @@ __global__ void k_gmres_solve_y(double* st, int k, int m) {
     for (int l = i + 1; l < k; ++l) s -= st[OFF_H + (long)l * (m + 1) + i] * st[OFF_Y + l];
     st[OFF_Y + i] = s / st[OFF_H + (long)i * (m + 1) + i];
   }
+}
+
+// ---- single-launch reductions: every CTA writes its partial sums, and the
+// last CTA to finish (an atomic ticket; no CTA waits for another) adds them
+// up.  The ticket counter returns to zero for the next launch.
+__device__ inline bool last_block(unsigned* ticket) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    if (threadIdx.x == 0) *ticket = 0u;
+  }
+  return s_last != 0;
+}
+
+// k_dots followed (in the last CTA) by the sum of the partials into out.
+template <typename T>
+__global__ void __launch_bounds__(256) k_dots_sum(const T* __restrict__ w, const T* __restrict__ V, long ldv,
+                                                 int nvec, long n, double* __restrict__ partial, int with_norm,
+                                                 double* __restrict__ out, unsigned* ticket) {
+  __shared__ double red[8][33];
+  T acc[33];
+#pragma unroll
+  for (int i = 0; i < 33; ++i) acc[i] = T(0);
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    const T wv = w[e];
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < nvec) acc[i] += wv * V[i * ldv + e];
+    acc[32] += wv * wv;
+  }
+  const int nvals = nvec + with_norm;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 33; ++i) {
+    const bool used = (i < nvec) || (i == 32 && with_norm);
+    if (!used) continue;
+    double v = (double)acc[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][i] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
+    const int src = (i < nvec) ? i : 32;
+    double s = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k][src];
+    partial[(long)blockIdx.x * nvals + i] = s;
+  }
+  if (!last_block(ticket)) return;
+  for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
+    double s = 0;
+    for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partial + (long)b * nvals + i);
+    out[i] = s;
+  }
+}
+
+// k_update_dots followed (in the last CTA) by the Arnoldi / Givens update of
+// k_gmres_arnoldi for column j.
+template <typename T>
+__global__ void __launch_bounds__(256) k_update_dots_arnoldi(T* __restrict__ w, const T* __restrict__ V,
+                                                            long ldv, int nvec, long n, double* st,
+                                                            double* __restrict__ partial, int j, int m,
+                                                            unsigned* ticket) {
+  __shared__ double red[8][33];
+  __shared__ T sh[32];
+  const double* h = st + OFF_H1;
+  for (int i = threadIdx.x; i < 32; i += blockDim.x) sh[i] = i < nvec ? (T)h[i] : T(0);
+  __syncthreads();
+  T acc[33];
+#pragma unroll
+  for (int i = 0; i < 33; ++i) acc[i] = T(0);
+  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+    T v[32];
+    T wv = w[e];
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < nvec) { v[i] = V[i * ldv + e]; wv -= sh[i] * v[i]; }
+    w[e] = wv;
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < nvec) acc[i] += wv * v[i];
+    acc[32] += wv * wv;
+  }
+  const int nvals = nvec + 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 33; ++i) {
+    if (!(i < nvec || i == 32)) continue;
+    double v = (double)acc[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][i] = v;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
+    const int src = (i < nvec) ? i : 32;
+    double s = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k][src];
+    partial[(long)blockIdx.x * nvals + i] = s;
+  }
+  if (!last_block(ticket)) return;
+  __shared__ double h2[64];
+  __shared__ double ww;
+  for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
+    double s = 0;
+    for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partial + (long)b * nvals + i);
+    if (i < j + 1) h2[i] = s; else ww = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) arnoldi_update(st, h2, ww, j, m);
 }
 
 // ------------------------------------------------------------------ launchers
@@ -268,9 +390,10 @@ cudaError_t launch_update_dots(T* w, const T* V, long ldv, int nvec, long n, con
   return launch_k(k_update_dots<T>, dim3(nblk), dim3(256), 0, s, w, V, ldv, nvec, n, h, partial);
 }
 template <typename T>
-cudaError_t launch_update_normalize(T* w, const T* V, long ldv, int nvec, long n, const double* h,
-                                    const double* inv_norm, T* vout, cudaStream_t s) {
-  return launch_k(k_update_normalize<T>, dim3(blocks_for(n)), dim3(256), 0, s, w, V, ldv, nvec, n, h, inv_norm, vout);
+cudaError_t launch_update_normalize(const T* w, const T* V, long ldv, int nvec, long n, const double* h,
+                                    const double* inv_norm, T* vout, float* v32, cudaStream_t s) {
+  return launch_k(k_update_normalize<T>, dim3(blocks_for(n)), dim3(256), 0, s, w, V, ldv, nvec, n, h, inv_norm, vout,
+                  v32);
 }
 template <typename T>
 cudaError_t launch_lincomb(T* x, const T* Z, long ldz, int nvec, long n, const double* y,
@@ -315,16 +438,34 @@ cudaError_t launch_gmres_solve_y(double* st, int k, int m, cudaStream_t s) {
   return launch_k(k_gmres_solve_y, dim3(1), dim3(32), 0, s, st, k, m);
 }
 
+template <typename T>
+cudaError_t launch_dots_sum(const T* w, const T* V, long ldv, int nvec, long n, double* partial, int nblk,
+                            int with_norm, double* out, unsigned* ticket, cudaStream_t s) {
+  return launch_k(k_dots_sum<T>, dim3(nblk), dim3(256), 0, s, w, V, ldv, nvec, n, partial, with_norm, out,
+                  ticket);
+}
+template <typename T>
+cudaError_t launch_update_dots_arnoldi(T* w, const T* V, long ldv, int nvec, long n, double* st,
+                                       double* partial, int nblk, int j, int m, unsigned* ticket,
+                                       cudaStream_t s) {
+  return launch_k(k_update_dots_arnoldi<T>, dim3(nblk), dim3(256), 0, s, w, V, ldv, nvec, n, st, partial, j, m,
+                  ticket);
+}
+
 #define WT_KINST(T)                                                                                  \
   template cudaError_t launch_dots<T>(const T*, const T*, long, int, long, double*, int, int,         \
                                       cudaStream_t);                                                 \
   template cudaError_t launch_update_dots<T>(T*, const T*, long, int, long, const double*, double*,   \
                                              int, cudaStream_t);                                     \
-  template cudaError_t launch_update_normalize<T>(T*, const T*, long, int, long, const double*,       \
-                                                  const double*, T*, cudaStream_t);                  \
+  template cudaError_t launch_update_normalize<T>(const T*, const T*, long, int, long, const double*, \
+                                                  const double*, T*, float*, cudaStream_t);          \
   template cudaError_t launch_lincomb<T>(T*, const T*, long, int, long, const double*, cudaStream_t); \
   template cudaError_t launch_scale_copy<T>(const T*, T*, long, const double*, int, cudaStream_t);    \
-  template cudaError_t launch_axpy_from<T>(double*, const T*, long, const double*, cudaStream_t);
+  template cudaError_t launch_axpy_from<T>(double*, const T*, long, const double*, cudaStream_t);     \
+  template cudaError_t launch_dots_sum<T>(const T*, const T*, long, int, long, double*, int, int,      \
+                                          double*, unsigned*, cudaStream_t);                          \
+  template cudaError_t launch_update_dots_arnoldi<T>(T*, const T*, long, int, long, double*, double*, \
+                                                     int, int, int, unsigned*, cudaStream_t);
 WT_KINST(float)
 WT_KINST(double)
 template cudaError_t launch_convert<double, float>(const double*, float*, long, const double*, int,

@@ -431,6 +431,7 @@ template <> float* Zbuf<float>(wt_tank& t) { return t.Z32; }
 
 // Preconditioner z = M^{-1} v: one V-cycle in the precision of the Krylov
 // vectors, or (pre32 with T = double) an FP32 V-cycle on the rounded vector
+// t.b32 = (float)v, which the kernel that produced v has already written,
 // with the correction widened back to FP64.
 template <typename T>
 static void precondition(wt_tank& t, const T* v, T* z, bool pre32, bool tr);
@@ -445,7 +446,6 @@ void precondition<double>(wt_tank& t, const double* v, double* z, bool pre32, bo
     return;
   }
   const long n = t.n;
-  WT_LAUNCH(t, K_KRYLOV, 12.0 * n, 0.0, (launch_convert<double, float>(v, t.b32, n, nullptr, 0, t.s)));
   vcycle<float>(t, 0, t.b32, t.e32, tr);
   WT_LAUNCH(t, K_KRYLOV, 12.0 * n, 0.0, (launch_convert<float, double>(t.e32, z, n, nullptr, 0, t.s)));
 }
@@ -476,16 +476,14 @@ static void arnoldi_step(wt_tank& t, int j, bool pre32, bool tr) {
   T* w = V + (long)(j + 1) * n;
   precondition<T>(t, vj, zj, pre32, tr);                 // z_j = M^{-1} v_j
   apply_op<T>(t, 0, zj, w, nullptr, false, tr);          // w = A z_j
+  // CGS2: h1 = V^T w (one launch, summed by its last CTA), then w -= V h1,
+  // h2 = V^T w, ||w|| and the Givens update of column j (one launch)
   WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (j + 2), 2.0 * n * (j + 1),
-            launch_dots<T>(w, V, n, j + 1, n, t.partial, t.nblk, 0, t.s));
-  WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk * (j + 1), 0.0,
-            launch_reduce_partials(t.partial, t.nblk, j + 1, t.st + 8, t.s));
+            launch_dots_sum<T>(w, V, n, j + 1, n, t.partial, t.nblk, 0, t.st + 8, t.tickets, t.s));
   WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (j + 3), 4.0 * n * (j + 2),
-            launch_update_dots<T>(w, V, n, j + 1, n, t.st + 8, t.partial, t.nblk, t.s));
-  WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk * (j + 2), 0.0,
-            launch_gmres_arnoldi(t.st, nullptr, t.partial, t.nblk, j, m, 0.0, 0.0, t.s));
-  WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (j + 3), 2.0 * n * (j + 2),
-            launch_update_normalize<T>(w, V, n, j + 1, n, t.st + 72, t.st + 2, w, t.s));
+            launch_update_dots_arnoldi<T>(w, V, n, j + 1, n, t.st, t.partial, t.nblk, j, m, t.tickets + 1, t.s));
+  WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n * (j + 3) + (pre32 ? 4.0 * n : 0.0), 2.0 * n * (j + 2),
+            launch_update_normalize<T>(w, V, n, j + 1, n, t.st + 72, t.st + 2, w, pre32 ? t.b32 : nullptr, t.s));
 }
 
 // Run Arnoldi step j, replaying its CUDA graph (captured at first use) unless
@@ -547,7 +545,9 @@ double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit,
     WT_CK(cudaStreamSynchronize(t.s));
     rel = bnorm > 0 ? t.hst[0] / bnorm : 0.0;
     if (rel <= tol || its >= maxit || t.hst[0] == 0.0) break;
-    WT_LAUNCH(t, K_KRYLOV, 2.0 * sizeof(T) * n, (double)n, launch_scale_copy<T>(V, V, n, t.st + 2, 0, t.s));
+    // v_0 = r / beta (and its FP32 rounding for the FP32 V-cycle)
+    WT_LAUNCH(t, K_KRYLOV, 2.0 * sizeof(T) * n + (pre32 ? 4.0 * n : 0.0), (double)n,
+              launch_update_normalize<T>(V, V, n, 0, n, t.st + 72, t.st + 2, V, pre32 ? t.b32 : nullptr, t.s));
     int k = 0;
     for (int j = 0; j < m; ++j) {
       arnoldi_step_graph<T>(t, j, pre32, tr);
