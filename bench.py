@@ -277,7 +277,8 @@ def run_ours(args):
                                         "refine: FP64 iterative refinement around FP32 FGMRES + FP32 V-cycle"),
                              "autotuned": {"omega": tuned["omega"], "nu1": tuned["nu1"], "nu2": tuned["nu2"],
                                            "coarsest_max": tuned["coarsest_max"], "mode": tuned["mode"],
-                                           "tail_max": tuned["tail_max"], "vcycle_grid": tuned["vcycle_grid"],
+                                           "tail_max": tuned["tail_max"], "tail_cluster": tuned["tail_cluster"],
+                                           "vcycle_grid": tuned["vcycle_grid"],
                                            "tuned_ms_per_step": tuned_ms, "default_ms_per_step": entry_ms}}),
         "solves_per_s": solves_s,
         "krylov_iterations_per_solve": iters / max(1, solves),

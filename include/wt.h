@@ -87,9 +87,10 @@ typedef struct wt_options {
                         coarse boundary rows (default); 1: whole column
                         through the Chebyshev truncation as printed          */
   int tail_max;      /* levels with at most this many unknowns run in one
-                        single-CTA V-cycle launch (0: never, the
-                        default; graph replay of the multi-CTA levels is
-                        faster at the sizes measured so far)          */
+                        V-cycle launch of one CTA (or of the cluster that
+                        tail_cluster sets); 0: never, the default - graph
+                        replay of the multi-CTA levels is faster at the
+                        sizes measured so far                               */
   double inner_tol;  /* WT_REFINE: relative residual of each FP32 inner
                         solve (1e-5)                                         */
   int max_ir;        /* WT_REFINE: refinement steps per solve (30)           */
@@ -97,6 +98,10 @@ typedef struct wt_options {
                         preconditioner as one cooperative launch with grid
                         barriers (bounded waits; WT_ETIMEOUT if one gives
                         up); 0: one launch per phase (default 0)            */
+  int tail_cluster;  /* CTAs (2..16) of the thread-block cluster that runs
+                        the levels at or below tail_max in one launch, the
+                        phases separated by the cluster's hardware barrier;
+                        0 or 1: one CTA (default 0)                          */
 } wt_options;
 
 typedef struct wt_solve_info {
@@ -232,7 +237,8 @@ int wt_adjoint_step(wt_tank* t, double dt, const double* eta, const double* u, c
  * 128}, and mode in {WT_MIXED, WT_REFINE} unless the tank is in WT_FP64 - one
  * warm-up solve plus the median of reps (1..100) timed solves each, and keeps
  * the fastest setting that reaches the tolerance; then, on that setting, the
- * V-cycle's launch schedule (tail_max 2048 or 8192, or vcycle_grid = 1).  The paper leaves these
+ * V-cycle's launch schedule (tail_max 2048 or 8192 with tail_cluster 0 or
+ * 16, or vcycle_grid = 1).  The paper leaves these
  * choices open (Sec. 4.1).  On success the tank uses the winner, *best holds
  * it, *best_ms its median time and *entry_ms that of the options on entry
  * (best_ms <= entry_ms: the entry options are one of the candidates).  Any

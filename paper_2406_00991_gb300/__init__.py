@@ -31,7 +31,8 @@ class wt_options(ctypes.Structure):
                 ("max_it", ctypes.c_int),
                 ("filter", ctypes.c_int), ("linear", ctypes.c_int), ("coarsest_max", ctypes.c_int),
                 ("bc_transfer", ctypes.c_int), ("tail_max", ctypes.c_int),
-                ("inner_tol", ctypes.c_double), ("max_ir", ctypes.c_int), ("vcycle_grid", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("max_ir", ctypes.c_int), ("vcycle_grid", ctypes.c_int),
+                ("tail_cluster", ctypes.c_int)]
 
 
 class wt_solve_info(ctypes.Structure):

@@ -295,6 +295,7 @@ int check_options(const wt_options& o) {
   if (!(o.inner_tol > 0) || !(o.inner_tol < 1)) return fail(WT_EINVAL, "inner_tol must be in (0, 1)");
   if (o.max_ir < 1) return fail(WT_EINVAL, "max_ir must be >= 1");
   if (o.vcycle_grid != 0 && o.vcycle_grid != 1) return fail(WT_EINVAL, "vcycle_grid must be 0 or 1");
+  if (o.tail_cluster < 0 || o.tail_cluster > 16) return fail(WT_EINVAL, "tail_cluster must be in [0, 16]");
   if (!(o.tol > 0) || !(o.tol < 1)) return fail(WT_EINVAL, "tol must be in (0, 1)");
   if (o.restart < 1 || o.restart > 31) return fail(WT_EINVAL, "restart must be in [1, 31]");
   if (o.nu1 < 0 || o.nu1 > 8 || o.nu2 < 0 || o.nu2 > 8 || o.nu1 + o.nu2 == 0)
@@ -533,6 +534,7 @@ int wt_default_options(wt_options* o) {
   o->inner_tol = 1e-5;
   o->max_ir = 30;
   o->vcycle_grid = 0;
+  o->tail_cluster = 0;
   return WT_OK;
 }
 

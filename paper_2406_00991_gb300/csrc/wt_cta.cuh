@@ -204,9 +204,9 @@ __device__ void vcycle_cta(const TailArgs<T>& A, unsigned char* sm) {
 }  // namespace wt
 
 // ---------------------------------------------------------------------------
-// Grid-wide versions: every CTA of a cooperative launch takes its share of a
-// phase (unit blockIdx.x of gridDim.x), and the phases are separated by a
-// grid barrier.  The barrier is release/acquire at GPU scope: arrivals
+// Grid-wide versions: every CTA of a cooperative launch (or of a launch that
+// is one thread-block cluster) takes its share of a phase (unit blockIdx.x of
+// gridDim.x), and the phases are separated by a grid (or cluster) barrier.  The barrier is release/acquire at GPU scope: arrivals
 // publish the CTA's writes, the spin reads the generation with ld.acquire so
 // that later loads see the other CTAs' writes.  Every wait is bounded by the
 // SM clock; a barrier that gives up sets the shared abort flag, and any CTA
@@ -268,25 +268,38 @@ __device__ inline bool grid_sync(GridBar* b, int* flag) {
   return s_ok != 0;
 }
 
-template <typename T>
+// Phase separators: the bounded grid barrier of a cooperative launch, or
+// the hardware barrier of a thread-block cluster when the grid is a single
+// cluster (release / acquire at cluster scope; no spin in this code).
+struct GridSync {
+  __device__ static bool sync(GridBar* b, int* flag) { return grid_sync(b, flag); }
+};
+struct ClusterSync {
+  __device__ static bool sync(GridBar*, int*) {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+    return true;
+  }
+};
+
+template <typename T, typename S>
 __device__ inline bool g_rowpass(const RowPass<T>& a0, int smem, unsigned char* sm, GridBar* b, int* flag) {
   RowPass<T> a = a0;
   if (rowpass_smem(a, 1) > (size_t)smem) a.prefetch = 0;
   rowpass_body<T>(a, 1, blockIdx.x, gridDim.x, sm);
-  return grid_sync(b, flag);
+  return S::sync(b, flag);
 }
 
-template <typename T, int DIM>
+template <typename T, int DIM, typename S>
 __device__ bool g_apply_op(const TailLevel<T>& L, const T* x, T* out, const T* f, bool nyq, int smem,
                            unsigned char* sm, GridBar* b, int* flag) {
   const LevelView<T>& V = L.V;
   const int nw = blockDim.x >> 5;
   const int gw = blockIdx.x * nw + (threadIdx.x >> 5), gws = gridDim.x * nw;
   if (DIM == 2) {
-    if (!g_rowpass(tpass(V, x, L.t1, V.M1, V.Nx, V.logNx, V.Nx, V.logNx, XOP_DERIV), smem, sm, b, flag))
+    if (!g_rowpass<T, S>(tpass(V, x, L.t1, V.M1, V.Nx, V.logNx, V.Nx, V.logNx, XOP_DERIV), smem, sm, b, flag))
       return false;
     opcols_body<T, 2>(V, x, L.t1, nullptr, L.t2, nullptr, L.t3, blockIdx.x, gridDim.x, sm);
-    if (!grid_sync(b, flag)) return false;
+    if (!S::sync(b, flag)) return false;
     RowPass<T> a = tpass(V, L.t2, out, V.M1, V.Nx, V.logNx, V.Nx, V.logNx, XOP_DERIV);
     a.skip_bc = 1;
     a.Ny = 1;
@@ -295,23 +308,23 @@ __device__ bool g_apply_op(const TailLevel<T>& L, const T* x, T* out, const T* f
     a.rhs = f;
     a.epi = f ? EPI_RESID : EPI_ADD;
     a.nyq = nyq ? L.rhoX : nullptr;
-    return g_rowpass(a, smem, sm, b, flag);
+    return g_rowpass<T, S>(a, smem, sm, b, flag);
   }
-  if (!g_rowpass(tpass(V, x, L.t1, V.M1 * V.Ny, V.Nx, V.logNx, V.Nx, V.logNx, XOP_DERIV), smem, sm, b, flag))
+  if (!g_rowpass<T, S>(tpass(V, x, L.t1, V.M1 * V.Ny, V.Nx, V.logNx, V.Nx, V.logNx, XOP_DERIV), smem, sm, b, flag))
     return false;
   RowPass<T> y1 = tpass(V, x, L.t4, V.M1 * V.Nx, V.Ny, V.logNy, V.Ny, V.logNy, XOP_DERIV);
   y1.ylines = 1;
   y1.Nxl = V.Nx;
-  if (!g_rowpass(y1, smem, sm, b, flag)) return false;
+  if (!g_rowpass<T, S>(y1, smem, sm, b, flag)) return false;
   opcols_body<T, 3>(V, x, L.t1, L.t4, L.t2, L.t5, L.t3, blockIdx.x, gridDim.x, sm);
-  if (!grid_sync(b, flag)) return false;
+  if (!S::sync(b, flag)) return false;
   RowPass<T> a = tpass(V, L.t2, L.t6, V.M1 * V.Ny, V.Nx, V.logNx, V.Nx, V.logNx, XOP_DERIV);
   a.skip_bc = 1;
   a.Ny = V.Ny;
   a.M1 = V.M1;
   a.add = L.t3;
   a.epi = EPI_ADD;
-  if (!g_rowpass(a, smem, sm, b, flag)) return false;
+  if (!g_rowpass<T, S>(a, smem, sm, b, flag)) return false;
   RowPass<T> c = tpass(V, L.t5, out, V.M1 * V.Nx, V.Ny, V.logNy, V.Ny, V.logNy, XOP_DERIV);
   c.ylines = 1;
   c.Nxl = V.Nx;
@@ -321,17 +334,17 @@ __device__ bool g_apply_op(const TailLevel<T>& L, const T* x, T* out, const T* f
   c.rhs = f;
   c.epi = f ? EPI_RESID : EPI_ADD;
   c.nyq = nyq ? L.rhoY : nullptr;
-  if (!g_rowpass(c, smem, sm, b, flag)) return false;
+  if (!g_rowpass<T, S>(c, smem, sm, b, flag)) return false;
   if (nyq) {
     nyquist_body<T>(out, V.M1 * V.Ny, V.Nx, L.rhoX, gw, gws);
-    if (!grid_sync(b, flag)) return false;
+    if (!S::sync(b, flag)) return false;
     nyquist_body<T>(L.rhoX, V.M1, V.Ny, L.rhoXY, gw, gws);
-    if (!grid_sync(b, flag)) return false;
+    if (!S::sync(b, flag)) return false;
   }
   return true;
 }
 
-template <typename T, int DIM>
+template <typename T, int DIM, typename S>
 __device__ bool g_nyquist_of(const TailLevel<T>& L, const T* f, int smem, unsigned char* sm, GridBar* b,
                              int* flag) {
   const LevelView<T>& V = L.V;
@@ -339,30 +352,30 @@ __device__ bool g_nyquist_of(const TailLevel<T>& L, const T* f, int smem, unsign
   const int gw = blockIdx.x * nw + (threadIdx.x >> 5), gws = gridDim.x * nw;
   if (DIM == 2) {
     nyquist_body<T>(f, V.M1, V.Nx, L.rhoX, gw, gws);
-    return grid_sync(b, flag);
+    return S::sync(b, flag);
   }
   RowPass<T> c = tpass(V, f, L.t6, V.M1 * V.Nx, V.Ny, V.logNy, V.Ny, V.logNy, XOP_NONE);
   c.ylines = 1;
   c.Nxl = V.Nx;
   c.nyq = L.rhoY;
-  if (!g_rowpass(c, smem, sm, b, flag)) return false;
+  if (!g_rowpass<T, S>(c, smem, sm, b, flag)) return false;
   nyquist_body<T>(f, V.M1 * V.Ny, V.Nx, L.rhoX, gw, gws);
-  if (!grid_sync(b, flag)) return false;
+  if (!S::sync(b, flag)) return false;
   nyquist_body<T>(L.rhoX, V.M1, V.Ny, L.rhoXY, gw, gws);
-  return grid_sync(b, flag);
+  return S::sync(b, flag);
 }
 
-template <typename T, int DIM>
+template <typename T, int DIM, typename S>
 __device__ bool g_sweep(const TailArgs<T>& A, const TailLevel<T>& L, T* x, const T* f, int smem,
                         unsigned char* sm, GridBar* b, int* flag) {
-  if (!g_apply_op<T, DIM>(L, x, L.r, f, true, smem, sm, b, flag)) return false;
+  if (!g_apply_op<T, DIM, S>(L, x, L.r, f, true, smem, sm, b, flag)) return false;
   smooth_any<T, DIM>(L.V, L.r, L.rhoX, DIM == 3 ? L.rhoY : nullptr, DIM == 3 ? L.rhoXY : nullptr, L.Binv, x,
                       A.omega, 0, blockIdx.x, gridDim.x, sm);
-  return grid_sync(b, flag);
+  return S::sync(b, flag);
 }
 
 // The V-cycle of vcycle_cta with every phase spread over the grid.
-template <typename T, int DIM>
+template <typename T, int DIM, typename S>
 __device__ void vcycle_grid(const TailArgs<T>& A, GridBar* b, int* flag, unsigned char* sm) {
   const int smem = A.smem;
   const int nl = A.nl, l0 = A.l0;
@@ -376,21 +389,21 @@ __device__ void vcycle_grid(const TailArgs<T>& A, GridBar* b, int* flag, unsigne
     const bool fnyq = (l == l0) ? (A.f0_nyq != 0) : (A.lv[l - 1].V.Nx == V.Nx);
     const T* resid = f;
     if (A.nu1 > 0) {
-      if (fnyq && !g_nyquist_of<T, DIM>(L, f, smem, sm, b, flag)) return;
+      if (fnyq && !g_nyquist_of<T, DIM, S>(L, f, smem, sm, b, flag)) return;
       smooth_any<T, DIM>(V, f, fnyq ? L.rhoX : nullptr, (fnyq && DIM == 3) ? L.rhoY : nullptr,
                           (fnyq && DIM == 3) ? L.rhoXY : nullptr, L.Binv, x, A.omega, 1, blockIdx.x, gridDim.x, sm);
-      if (!grid_sync(b, flag)) return;
+      if (!S::sync(b, flag)) return;
       for (int i = 1; i < A.nu1; ++i)
-        if (!g_sweep<T, DIM>(A, L, x, f, smem, sm, b, flag)) return;
-      if (!g_apply_op<T, DIM>(L, x, L.r, f, false, smem, sm, b, flag)) return;
+        if (!g_sweep<T, DIM, S>(A, L, x, f, smem, sm, b, flag)) return;
+      if (!g_apply_op<T, DIM, S>(L, x, L.r, f, false, smem, sm, b, flag)) return;
       resid = L.r;
     } else {
       for (long i = gt; i < V.n; i += gts) x[i] = T(0);
-      if (!grid_sync(b, flag)) return;
+      if (!S::sync(b, flag)) return;
     }
     const T* cur = resid;
     if (C.V.Nx != V.Nx) {
-      if (!g_rowpass(tpass(V, cur, L.t4, V.M1 * V.Ny, V.Nx, V.logNx, C.V.Nx, C.V.logNx, XOP_RESAMPLE), smem, sm, b,
+      if (!g_rowpass<T, S>(tpass(V, cur, L.t4, V.M1 * V.Ny, V.Nx, V.logNx, C.V.Nx, C.V.logNx, XOP_RESAMPLE), smem, sm, b,
                      flag))
         return;
       cur = L.t4;
@@ -398,12 +411,12 @@ __device__ void vcycle_grid(const TailArgs<T>& A, GridBar* b, int* flag, unsigne
         RowPass<T> a = tpass(V, cur, L.t5, V.M1 * C.V.Nx, V.Ny, V.logNy, C.V.Ny, C.V.logNy, XOP_RESAMPLE);
         a.ylines = 1;
         a.Nxl = C.V.Nx;
-        if (!g_rowpass(a, smem, sm, b, flag)) return;
+        if (!g_rowpass<T, S>(a, smem, sm, b, flag)) return;
         cur = L.t5;
       }
     }
     colmat_body<T>(L.Rsig, C.V.M1, V.M1, cur, C.f, C.V.ncols, 0, blockIdx.x, gridDim.x, sm);
-    if (!grid_sync(b, flag)) return;
+    if (!S::sync(b, flag)) return;
   }
   {
     // coarsest level: x = A^{-1} f with the FP64 inverse, one CTA
@@ -421,7 +434,7 @@ __device__ void vcycle_grid(const TailArgs<T>& A, GridBar* b, int* flag, unsigne
         x[i] = (T)acc;
       }
     }
-    if (!grid_sync(b, flag)) return;
+    if (!S::sync(b, flag)) return;
   }
   for (int l = nl - 2; l >= l0; --l) {
     const TailLevel<T>& L = A.lv[l];
@@ -431,24 +444,24 @@ __device__ void vcycle_grid(const TailArgs<T>& A, GridBar* b, int* flag, unsigne
     T* x = (l == l0) ? A.x0 : L.x;
     if (C.V.Nx == V.Nx) {
       colmat_body<T>(L.Psig, V.M1, C.V.M1, C.x, x, V.ncols, 1, blockIdx.x, gridDim.x, sm);
-      if (!grid_sync(b, flag)) return;
+      if (!S::sync(b, flag)) return;
     } else {
       colmat_body<T>(L.Psig, V.M1, C.V.M1, C.x, L.t4, C.V.ncols, 0, blockIdx.x, gridDim.x, sm);
-      if (!grid_sync(b, flag)) return;
+      if (!S::sync(b, flag)) return;
       const T* cur = L.t4;
       if (DIM == 3) {
         RowPass<T> a = tpass(V, cur, L.t5, V.M1 * C.V.Nx, C.V.Ny, C.V.logNy, V.Ny, V.logNy, XOP_RESAMPLE);
         a.ylines = 1;
         a.Nxl = C.V.Nx;
-        if (!g_rowpass(a, smem, sm, b, flag)) return;
+        if (!g_rowpass<T, S>(a, smem, sm, b, flag)) return;
         cur = L.t5;
       }
       RowPass<T> a = tpass(V, cur, x, V.M1 * V.Ny, C.V.Nx, C.V.logNx, V.Nx, V.logNx, XOP_RESAMPLE);
       a.epi = EPI_ACC;
-      if (!g_rowpass(a, smem, sm, b, flag)) return;
+      if (!g_rowpass<T, S>(a, smem, sm, b, flag)) return;
     }
     for (int i = 0; i < A.nu2; ++i)
-      if (!g_sweep<T, DIM>(A, L, x, f, smem, sm, b, flag)) return;
+      if (!g_sweep<T, DIM, S>(A, L, x, f, smem, sm, b, flag)) return;
   }
 }
 

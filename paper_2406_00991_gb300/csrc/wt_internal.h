@@ -105,6 +105,9 @@ struct RowPass {
 // current device.  The attribute belongs to (kernel, device), so the cache of
 // what has been set is kept per pair (wt_launch.cu); thread-safe.
 cudaError_t ensure_dyn_smem(const void* fn, size_t bytes);
+// Allow cluster sizes above the portable 8 for kernel `fn` on the current
+// device (cached per (kernel, device) likewise).
+cudaError_t ensure_nonportable_cluster(const void* fn);
 
 // Launch through cudaLaunchKernelEx (grid, block, dynamic shared memory,
 // stream); returns the launch status.
@@ -235,6 +238,12 @@ struct GridBar {
 // every CTA returns at its next barrier.
 template <typename T>
 cudaError_t launch_vcycle_grid(const TailArgs<T>& a, int dim, GridBar* bar, int* flag, cudaStream_t s);
+// The levels from a.l0 down and back up in one launch of a single
+// thread-block cluster of csize CTAs (2..16), phases separated by the
+// cluster's hardware barrier.  cudaErrorInvalidConfiguration if a cluster of
+// that size with a.smem bytes per CTA cannot be resident on this device.
+template <typename T>
+cudaError_t launch_vcycle_cluster(const TailArgs<T>& a, int dim, int csize, cudaStream_t s);
 
 // Dense coarsest level (wt_coarse.cu), always FP64 arithmetic.
 cudaError_t launch_coarse_factor(const LevelView<double>& L, const double* Dx, const double* Dy,

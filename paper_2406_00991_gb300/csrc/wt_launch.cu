@@ -21,4 +21,18 @@ cudaError_t ensure_dyn_smem(const void* fn, size_t bytes) {
   return e;
 }
 
+cudaError_t ensure_nonportable_cluster(const void* fn) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, bool> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  bool& have = done[{fn, dev}];
+  if (have) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess) have = true;
+  return e;
+}
+
 }  // namespace wt

@@ -316,7 +316,8 @@ template <typename T> static TailLevel<T>* tail_desc(wt_tank& t);
 template <> TailLevel<double>* tail_desc<double>(wt_tank& t) { return t.tl64; }
 template <> TailLevel<float>* tail_desc<float>(wt_tank& t) { return t.tl32; }
 
-// First level handled by the single-CTA V-cycle kernel (-1: none).
+// First level handled by the single-launch tail of the V-cycle (one CTA, or
+// one thread-block cluster with tail_cluster >= 2); -1: none.
 template <typename T>
 static int tail_level(wt_tank& t, bool tr) {
   if (t.opt.tail_max <= 0 || tr) return -1;
@@ -373,7 +374,10 @@ void vcycle(wt_tank& t, int l, const T* f, T* x, bool tr) {
       bytes += sizeof(T) * (double)lev[k].n * (14.0 * (t.opt.nu1 + t.opt.nu2) + 16.0) +
                sizeof(T) * (double)lev[k].nclass * lev[k].M1 * lev[k].M1 * lev[k].ncols *
                    (t.opt.nu1 + t.opt.nu2);
-    WT_LAUNCH(t, K_TAIL, bytes, 0.0, launch_vcycle_tail<T>(a, L.Ny > 1 ? 3 : 2, t.s));
+    if (t.opt.tail_cluster >= 2)
+      WT_LAUNCH(t, K_TAIL, bytes, 0.0, launch_vcycle_cluster<T>(a, L.Ny > 1 ? 3 : 2, t.opt.tail_cluster, t.s));
+    else
+      WT_LAUNCH(t, K_TAIL, bytes, 0.0, launch_vcycle_tail<T>(a, L.Ny > 1 ? 3 : 2, t.s));
     return;
   }
   if (l == nl - 1) {

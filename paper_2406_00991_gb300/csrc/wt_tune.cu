@@ -29,25 +29,30 @@ double now_ms() {
 }
 
 // Second stage on the winner: the launch schedule of the V-cycle - the
-// single-CTA kernel for the levels below tail_max unknowns, or the whole
-// cycle as one cooperative launch - kept only where it is faster.
+// levels below tail_max unknowns in one launch (one CTA, or a cluster of 16
+// CTAs), or the whole cycle as one cooperative launch - kept only where it
+// is faster.
 template <typename F>
 void refine_schedule(wt_options& bo, double& bms, F&& measure) {
   const wt_options base = bo;
   const int tails[] = {2048, 8192};
-  for (int tm : tails) {
-    wt_options o = base;
-    o.tail_max = tm;
-    o.vcycle_grid = 0;
-    const double ms = measure(o, bms);
-    if (ms > 0 && ms < bms) {
-      bms = ms;
-      bo = o;
+  const int clusters[] = {0, 16};
+  for (int tm : tails)
+    for (int cl : clusters) {
+      wt_options o = base;
+      o.tail_max = tm;
+      o.tail_cluster = cl;
+      o.vcycle_grid = 0;
+      const double ms = measure(o, bms);
+      if (ms > 0 && ms < bms) {
+        bms = ms;
+        bo = o;
+      }
     }
-  }
   wt_options o = base;
   o.vcycle_grid = 1;
   o.tail_max = 0;
+  o.tail_cluster = 0;
   const double ms = measure(o, bms);
   if (ms > 0 && ms < bms) {
     bms = ms;

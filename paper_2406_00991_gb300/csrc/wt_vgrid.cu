@@ -17,8 +17,50 @@ namespace wt {
 template <typename T, int DIM>
 __global__ void __launch_bounds__(512, 1) k_vcycle_grid(TailArgs<T> A, GridBar* bar, int* flag) {
   extern __shared__ __align__(16) unsigned char sm[];
-  vcycle_grid<T, DIM>(A, bar, flag, sm);
+  vcycle_grid<T, DIM, GridSync>(A, bar, flag, sm);
 }
+
+// The levels from A.l0 down and back up in one thread-block cluster: the
+// grid is the cluster, and the phases are separated by the cluster's
+// hardware barrier (every CTA runs every phase, so all of them arrive).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(512, 1) k_vcycle_cluster(TailArgs<T> A) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  vcycle_grid<T, DIM, ClusterSync>(A, nullptr, nullptr, sm);
+}
+
+template <typename T, int DIM>
+static cudaError_t launch_cluster_dim(const TailArgs<T>& a, int csize, cudaStream_t s) {
+  const void* fn = (const void*)k_vcycle_cluster<T, DIM>;
+  cudaError_t e = ensure_dyn_smem(fn, (size_t)a.smem);
+  if (e != cudaSuccess) return e;
+  if (csize > 8 && (e = ensure_nonportable_cluster(fn)) != cudaSuccess) return e;   // above the portable 8
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(csize);
+  cfg.blockDim = dim3(512);
+  cfg.dynamicSmemBytes = a.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if ((e = cudaOccupancyMaxActiveClusters(&nclusters, k_vcycle_cluster<T, DIM>, &cfg)) != cudaSuccess) return e;
+  if (nclusters < 1) return cudaErrorInvalidConfiguration;   // this cluster size cannot be resident
+  return cudaLaunchKernelEx(&cfg, k_vcycle_cluster<T, DIM>, a);
+}
+
+template <typename T>
+cudaError_t launch_vcycle_cluster(const TailArgs<T>& a, int dim, int csize, cudaStream_t s) {
+  if (csize < 1 || csize > 16) return cudaErrorInvalidValue;
+  return dim == 3 ? launch_cluster_dim<T, 3>(a, csize, s) : launch_cluster_dim<T, 2>(a, csize, s);
+}
+
+template cudaError_t launch_vcycle_cluster<float>(const TailArgs<float>&, int, int, cudaStream_t);
+template cudaError_t launch_vcycle_cluster<double>(const TailArgs<double>&, int, int, cudaStream_t);
 
 template <typename T, int DIM>
 static cudaError_t launch_dim(const TailArgs<T>& a, GridBar* bar, int* flag, cudaStream_t s) {

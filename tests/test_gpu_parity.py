@@ -75,21 +75,23 @@ def test_levels_match_oracle_hierarchy(wt):
         assert T.levels() == pmg.hierarchy(Nx, Ny, Nz, coarsest_max=64)
 
 
-@pytest.mark.parametrize("tail_max,grid", [(0, 0), (8192, 0), (100000, 0), (0, 1)])
+@pytest.mark.parametrize("tail_max,grid,cluster", [(0, 0, 0), (8192, 0, 0), (100000, 0, 0), (0, 1, 0),
+                                                   (8192, 0, 16), (100000, 0, 8), (2048, 0, 2)])
 @pytest.mark.parametrize("Nx,Ny,Nz", [(64, 1, 16), (256, 1, 24), (1024, 1, 24), (16, 16, 8),
                                       (32, 32, 12)])
-def test_vcycle_parity(wt, Nx, Ny, Nz, tail_max, grid):
+def test_vcycle_parity(wt, Nx, Ny, Nz, tail_max, grid, cluster):
     # same algorithm on both sides (block Jacobi with Nyquist split, omega 0.4,
     # nu1 = nu2 = 2, injected boundary rows, coarsest <= 64 unknowns): the
     # preconditioned vectors agree to rounding.  tail_max selects how many
-    # levels run in the single-CTA V-cycle kernel (0: none, 100000: all);
-    # grid = 1 runs the whole cycle as one cooperative launch.
+    # levels run in the single-launch tail of the V-cycle (0: none, 100000:
+    # all), cluster the CTAs of the thread-block cluster that runs it (0: one
+    # CTA); grid = 1 runs the whole cycle as one cooperative launch.
     L = 2 * math.pi
     g, h, ea, eb = curved(Nx, Ny, Nz, L)
     r = np.random.default_rng(3).standard_normal(g.shape)
     levels = pmg.build_levels(Nx, Ny, Nz, L, h, ea, eb, coarsest_max=64)
     ref = pmg.vcycle(levels, 0, np.zeros(g.shape), r, 2, 2, "jacobi", 0.4, "inject")
-    T = wt.Tank(Nx, Ny, Nz, L, h, tail_max=tail_max, vcycle_grid=grid)
+    T = wt.Tank(Nx, Ny, Nz, L, h, tail_max=tail_max, vcycle_grid=grid, tail_cluster=cluster)
     got = T.precondition(ea, eb, r, wt.WT_FP64)
     scale = np.abs(ref).max()
     assert np.abs(got - ref).max() <= 1e-9 * scale
@@ -137,15 +139,21 @@ def test_curved_solve_residual_in_oracle_operator(wt, mode, Nx, Ny, Nz, L):
     assert np.linalg.norm(r) <= bound * np.linalg.norm(b) * 1.5
 
 
+SCHEDULES = [dict(vcycle_grid=1), dict(tail_max=8192, tail_cluster=16), dict(tail_max=2048, tail_cluster=8)]
+
+
+@pytest.mark.parametrize("sched", range(len(SCHEDULES)))
 @pytest.mark.parametrize("Nx,Ny,Nz,L", [(1024, 1, 24, 32.0), (32, 32, 12, 2 * math.pi)])
-def test_grid_vcycle_matches_launch_per_phase(wt, Nx, Ny, Nz, L):
-    # the cooperative V-cycle runs the same bodies: a mixed solve and (2D) a
-    # nonlinear step agree with the one-launch-per-phase path to rounding
+def test_grid_vcycle_matches_launch_per_phase(wt, Nx, Ny, Nz, L, sched):
+    # the cooperative V-cycle and the cluster tail run the same bodies: a
+    # mixed solve and (2D) a nonlinear step agree with the
+    # one-launch-per-phase path to rounding
     g, h, ea, eb = curved(Nx, Ny, Nz, L)
     b = np.random.default_rng(6).standard_normal(g.shape)
     out = []
-    for grid in (0, 1):
-        T = wt.Tank(Nx, Ny, Nz, L, h, mode=1, tol=1e-10, max_it=300, vcycle_grid=grid)
+    opts = [dict(), SCHEDULES[sched]]
+    for o in opts:
+        T = wt.Tank(Nx, Ny, Nz, L, h, mode=1, tol=1e-10, max_it=300, **o)
         p, info = T.poisson_solve(ea, eb, b)
         assert info.rel_residual <= 1e-10
         out.append((p, info.iterations))
@@ -157,8 +165,8 @@ def test_grid_vcycle_matches_launch_per_phase(wt, Nx, Ny, Nz, L):
         geo = op.Geometry(g, h, eta)
         u, w = si.linear_velocity(x[None, None, :], geo.z_nodes(g), 0.1, 2 * math.pi * 5 / L, 1.0)
         st = []
-        for grid in (0, 1):
-            T = wt.Tank(Nx, 1, Nz, L, h, tol=1e-10, filter=1, vcycle_grid=grid)
+        for o in opts:
+            T = wt.Tank(Nx, 1, Nz, L, h, tol=1e-10, filter=1, **o)
             T.set_state(np.ascontiguousarray(eta), np.ascontiguousarray(u), np.zeros_like(u),
                         np.ascontiguousarray(w))
             T.step(0.005, 2)
