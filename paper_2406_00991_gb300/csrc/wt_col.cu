@@ -42,7 +42,10 @@ __global__ void __launch_bounds__(256) k_op_cols_T(LevelView<T> L, const T* __re
   opcolsT_body<T>(L, lam, Dlam, Mx, part, blockIdx.x, gridDim.x, smraw);
 }
 
-template <typename T, int DIM, bool TR>
+// One instantiation per column-length bucket (MAXM >= M1, chosen on the
+// host): a kernel holding every bucket would be register-allocated for the
+// largest one.
+template <typename T, int DIM, bool TR, int MAXM, bool EXACT>
 __global__ void __launch_bounds__(256) k_smooth_cols(LevelView<T> L, const T* __restrict__ r,
                                                      const T* __restrict__ rhoX,
                                                      const T* __restrict__ rhoY,
@@ -50,7 +53,7 @@ __global__ void __launch_bounds__(256) k_smooth_cols(LevelView<T> L, const T* __
                                                      const T* __restrict__ Binv,
                                                      T* __restrict__ x, T omega, int first) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  smooth_any<T, DIM, TR>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first, blockIdx.x, gridDim.x, smraw);
+  smooth_body<T, DIM, MAXM, TR, EXACT>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first, blockIdx.x, gridDim.x, smraw);
 }
 
 template <typename T>
@@ -113,6 +116,25 @@ cudaError_t launch_op_cols_T(const LevelView<T>& L, const T* lam, const T* Dlam,
   return launch_k(k_op_cols_T<T>, dim3(g), dim3(256), opcols_smem<T>(L.M1), s, L, lam, Dlam, Mx, part);
 }
 
+template <typename T, int DIM, bool TR>
+static cudaError_t launch_smooth_m(const LevelView<T>& L, dim3 G, dim3 B, cudaStream_t s, const T* r, const T* rhoX,
+                                   const T* rhoY, const T* rhoXY, const T* Binv, T* x, T omega, int first) {
+#define WT_SMOOTH(MM, EX) \
+  launch_k(k_smooth_cols<T, DIM, TR, MM, EX>, G, B, 0, s, L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first)
+  switch (L.M1) {                           // the finest levels: exact column lengths
+    case 9: return WT_SMOOTH(9, true);
+    case 17: return WT_SMOOTH(17, true);
+    case 25: return WT_SMOOTH(25, true);
+    case 33: return WT_SMOOTH(33, true);
+    default: break;
+  }
+  if (L.M1 <= 9) return WT_SMOOTH(9, false);
+  if (L.M1 <= 17) return WT_SMOOTH(17, false);
+  if (L.M1 <= 25) return WT_SMOOTH(25, false);
+  return WT_SMOOTH(33, false);
+#undef WT_SMOOTH
+}
+
 template <typename T>
 cudaError_t launch_smooth_cols(const LevelView<T>& L, const T* r, const T* rhoX, const T* rhoY,
                                const T* rhoXY, const T* Binv, int nclass, T* x, T omega, int first,
@@ -121,11 +143,11 @@ cudaError_t launch_smooth_cols(const LevelView<T>& L, const T* r, const T* rhoX,
   const int g = grid_cols(L.ncols, 256);
   const dim3 G(g), B(256);
   if (L.Ny == 1) {
-    if (tr) return launch_k(k_smooth_cols<T, 2, true>, G, B, 0, s, L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
-    return launch_k(k_smooth_cols<T, 2, false>, G, B, 0, s, L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
+    if (tr) return launch_smooth_m<T, 2, true>(L, G, B, s, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
+    return launch_smooth_m<T, 2, false>(L, G, B, s, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
   }
-  if (tr) return launch_k(k_smooth_cols<T, 3, true>, G, B, 0, s, L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
-  return launch_k(k_smooth_cols<T, 3, false>, G, B, 0, s, L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
+  if (tr) return launch_smooth_m<T, 3, true>(L, G, B, s, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
+  return launch_smooth_m<T, 3, false>(L, G, B, s, r, rhoX, rhoY, rhoXY, Binv, x, omega, first);
 }
 
 template <typename T>

@@ -575,15 +575,17 @@ __device__ void opcols_tpc_body(const LevelView<T>& L, const T* WT_DEV_RESTRICT 
 
 // Block inverses are stored per column, contiguous and transposed:
 // Binv[((c * nclass + cls) * M1 + k) * M1 + m] = (A_rr^{-1})[m][k], so lane m
-// of a warp reads consecutive words for every k.
-template <typename T, int DIM, int MAXM, bool TR = false>
+// of a warp reads consecutive words for every k.  EXACT: M1 == MAXM, so the
+// block stride is a compile-time constant (immediate load offsets from one
+// base instead of one address register pair per hoisted load).
+template <typename T, int DIM, int MAXM, bool TR = false, bool EXACT = false>
 __device__ void smooth_body(const LevelView<T>& L, const T* WT_DEV_RESTRICT r,
                             const T* WT_DEV_RESTRICT rhoX, const T* WT_DEV_RESTRICT rhoY,
                             const T* WT_DEV_RESTRICT rhoXY, const T* WT_DEV_RESTRICT Binv,
                             T* WT_DEV_RESTRICT x, T omega, int first, int u0, int ustep,
                             unsigned char* smraw) {
   constexpr int NC = DIM == 2 ? 2 : 4;
-  const int M1 = L.M1;
+  const int M1 = EXACT ? MAXM : L.M1;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const long nc = L.ncols;
   const int m0 = lane, m1 = lane + 32;
