@@ -127,7 +127,8 @@ def test_manufactured_solve(wt, mode, tol, bound):
 
 
 @pytest.mark.parametrize("mode", [0, 1, 3])
-@pytest.mark.parametrize("Nx,Ny,Nz,L", [(1024, 1, 24, 32.0), (128, 1, 12, 8.0), (32, 32, 8, 2 * math.pi)])
+@pytest.mark.parametrize("Nx,Ny,Nz,L", [(1024, 1, 24, 32.0), (128, 1, 12, 8.0), (32, 32, 8, 2 * math.pi),
+                                        (128, 128, 16, 8.0)])
 def test_curved_solve_residual_in_oracle_operator(wt, mode, Nx, Ny, Nz, L):
     g, h, ea, eb = curved(Nx, Ny, Nz, L)
     b = np.random.default_rng(4).standard_normal(g.shape)
