@@ -414,16 +414,20 @@ int rk_stage(wt_tank& t, int k, double dt, AdjStage* rec = nullptr) {
   // geometry a = eta^(k), b = eta^(k-1) (still water for the linear model)
   const int prec = t.opt.mode == WT_FP64 ? WT_FP64 : WT_FP32;
   // the smoother's block inverses and the coarsest inverse depend only on the
-  // metric: they run on a side stream while the forcing and the right-hand
-  // side run here (not while per-launch timing is on)
-  const bool overlap = t.side && t.prof.mask == 0;
+  // metric: they run on two side streams, concurrently with each other and
+  // with the forcing and the right-hand side here (not while per-launch
+  // timing is on)
+  const bool overlap = t.side && t.side2 && t.prof.mask == 0;
   setup_geometry(t, t.opt.linear ? t.zero_s : t.eta_new, t.opt.linear ? t.zero_s : t.eta, prec, !overlap,
                  !overlap);
   if (overlap) {
     WT_CK(cudaEventRecord(t.ev_fork, t.s));
     WT_CK(cudaStreamWaitEvent(t.side, t.ev_fork, 0));
-    setup_blocks(t, prec, true, true, t.side);
+    WT_CK(cudaStreamWaitEvent(t.side2, t.ev_fork, 0));
+    setup_blocks(t, prec, true, false, t.side);
+    setup_blocks(t, prec, false, true, t.side2);
     WT_CK(cudaEventRecord(t.ev_join, t.side));
+    WT_CK(cudaEventRecord(t.ev_join2, t.side2));
   }
   StageArgs sa;
   sa.Nx = t.Nx; sa.Ny = t.Ny; sa.M1 = M1; sa.ncols = t.ncols;
@@ -457,7 +461,10 @@ int rk_stage(wt_tank& t, int k, double dt, AdjStage* rec = nullptr) {
   dds(t, ws, Dws);
   if (y) dds(t, vs, Dvs);
   WT_LAUNCH(t, K_STAGE, 8.0 * t.n * (y ? 9 : 6), 10.0 * t.n, launch_stage_rhs(sa, us, y ? vs : nullptr, ws, usx, vsy, Dus, Dvs, Dws, rhs, t.s));
-  if (overlap) WT_CK(cudaStreamWaitEvent(t.s, t.ev_join, 0));
+  if (overlap) {
+    WT_CK(cudaStreamWaitEvent(t.s, t.ev_join, 0));
+    WT_CK(cudaStreamWaitEvent(t.s, t.ev_join2, 0));
+  }
   // solve with the previous stage's p_D as the initial guess
   wt_solve_info info{};
   int st = poisson_solve_device(t, rhs, t.p, t.opt.tol, &info);
@@ -558,8 +565,10 @@ int wt_create(int Nx, int Ny, int Nz, double L, double g, double nu, const doubl
     WT_CK(cudaStreamCreateWithFlags(&t->own_stream, cudaStreamNonBlocking));
     WT_CK(cudaEventCreateWithFlags(&t->order_ev, cudaEventDisableTiming));
     WT_CK(cudaStreamCreateWithFlags(&t->side, cudaStreamNonBlocking));
+    WT_CK(cudaStreamCreateWithFlags(&t->side2, cudaStreamNonBlocking));
     WT_CK(cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming));
     WT_CK(cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming));
+    WT_CK(cudaEventCreateWithFlags(&t->ev_join2, cudaEventDisableTiming));
     t->s = t->own_stream;
     t->Nx = Nx; t->Ny = Ny; t->Nz = Nz; t->M1 = Nz + 1; t->ncols = Nx * Ny; t->n = (long)t->M1 * t->ncols;
     t->L = L; t->g = g; t->nu = nu;
@@ -1219,9 +1228,12 @@ int wt_destroy(wt_tank* t) {
   cudaStreamSynchronize(t->s);
   destroy_graphs(*t);
   if (t->side) cudaStreamSynchronize(t->side);
+  if (t->side2) cudaStreamSynchronize(t->side2);
   if (t->ev_fork) cudaEventDestroy(t->ev_fork);
   if (t->ev_join) cudaEventDestroy(t->ev_join);
+  if (t->ev_join2) cudaEventDestroy(t->ev_join2);
   if (t->side) cudaStreamDestroy(t->side);
+  if (t->side2) cudaStreamDestroy(t->side2);
   if (t->order_ev) cudaEventDestroy(t->order_ev);
   if (t->own_stream) cudaStreamDestroy(t->own_stream);
   if (t->hflag) cudaFreeHost(t->hflag);

@@ -71,6 +71,21 @@ __global__ void __launch_bounds__(128) k_block_inverse(LevelView<T> L, T* __rest
   blockinv_body<T>(L, Binv, nclass, cxx, cyy, flag, blockIdx.x, gridDim.x, 4, smraw);
 }
 
+// Every level's (column, class) tasks in one launch: the levels' inverses
+// cost one level's latency (a warp's Gauss-Jordan) instead of the sum.
+template <typename T>
+__global__ void __launch_bounds__(128) k_block_inverse_multi(const __grid_constant__ BlockInvMulti<T> m, int* flag) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T* A = reinterpret_cast<T*>(smraw) + wib * (m.maxM1 * (2 * m.maxM1 + 1));
+  const long total = m.start[m.nlev];
+  for (long g = (long)blockIdx.x * nw + wib; g < total; g += (long)gridDim.x * nw) {
+    int l = 0;
+    while (g >= m.start[l + 1]) ++l;
+    blockinv_task<T>(m.L[l], m.Binv[l], m.nclass[l], m.cxx[l], m.cyy[l], flag, g - m.start[l], A);
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 static inline int grid_for(long n, int bs) { return (int)std::max<long>(1, (n + bs - 1) / bs); }
 
@@ -173,6 +188,20 @@ cudaError_t launch_block_inverse(const LevelView<T>& L, T* Binv, int nclass, T c
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_block_inverse_multi(const BlockInvMulti<T>& m, int* flag, cudaStream_t s) {
+  if (m.nlev <= 0) return cudaSuccess;
+  const int W = 2 * m.maxM1 + 1;
+  const size_t smem = 4 * (size_t)m.maxM1 * W * sizeof(T);
+  if (smem > 32 * 1024) {
+    cudaError_t e = ensure_dyn_smem((const void*)k_block_inverse_multi<T>, smem);
+    if (e != cudaSuccess) return e;
+  }
+  const long total = m.start[m.nlev];
+  const int g = (int)std::min<long>(std::max<long>(1, (total + 3) / 4), 152 * 8);
+  return launch_k(k_block_inverse_multi<T>, dim3(g), dim3(128), smem, s, m, flag);
+}
+
 #define WT_INST(T)                                                                              \
   template cudaError_t launch_op_cols<T>(const LevelView<T>&, const T*, const T*, const T*, T*,  \
                                          T*, T*, cudaStream_t);                                 \
@@ -184,7 +213,8 @@ cudaError_t launch_block_inverse(const LevelView<T>& L, T* Binv, int nclass, T c
   template cudaError_t launch_col_matrix<T>(const T*, int, int, const T*, T*, int, int,         \
                                             cudaStream_t);                                      \
   template cudaError_t launch_block_inverse<T>(const LevelView<T>&, T*, int, T, T, int*,        \
-                                               cudaStream_t);
+                                               cudaStream_t);                                    \
+  template cudaError_t launch_block_inverse_multi<T>(const BlockInvMulti<T>&, int*, cudaStream_t);
 WT_INST(float)
 WT_INST(double)
 

@@ -705,21 +705,17 @@ __device__ void nyquist_body(const T* WT_DEV_RESTRICT r, int nrows, int N, T* WT
 // against its dense assembly): interior rows
 //   cdiag I + (sx_a AX_b + sy_a AY_b + Z_a Z_b) D^2 - (sx_a BX_b + sy_a BY_b) D diag(sigma) D,
 // surface row e_0, bottom row (h_x sx_b + h_y sy_b + Z_b) D[Nz, :].
-// One warp per (column, class) task; `wmax` warps of the CTA take part (each
-// needs M1 x (2 M1 + 1) values of shared memory), CTA u0 of ustep.
+// One (column, class) task of the calling warp, in A (M1 x (2 M1 + 1)
+// values of shared memory).
 template <typename T>
-__device__ void blockinv_body(const LevelView<T>& L, T* WT_DEV_RESTRICT Binv, int nclass, T cxx,
-                              T cyy, int* flag, int u0, int ustep, int wmax, unsigned char* smraw) {
+__device__ void blockinv_task(const LevelView<T>& L, T* WT_DEV_RESTRICT Binv, int nclass, T cxx, T cyy,
+                              int* flag, long task, T* A) {
   const int M1 = L.M1;
   const int W = 2 * M1 + 1;                 // padded row of the augmented matrix
-  const int wib = threadIdx.x >> 5;
-  const int nw = min((int)(blockDim.x >> 5), wmax);
-  T* A = reinterpret_cast<T*>(smraw) + wib * (M1 * W);
   const int lane = threadIdx.x & 31;
   const long nc = L.ncols;
   const long blk = (long)M1 * M1;
-  if (wib >= nw) return;
-  for (long task = (long)u0 * nw + wib; task < nc * nclass; task += (long)ustep * nw) {
+  {
     const int c = (int)(task % nc), cls = (int)(task / nc);
     const int ix = cls & 1, iy = (cls >> 1) & 1;
     const T cdiag = (ix ? T(0) : cxx) + (iy ? T(0) : cyy);
@@ -795,6 +791,20 @@ __device__ void blockinv_body(const LevelView<T>& L, T* WT_DEV_RESTRICT Binv, in
     }
     __syncwarp();
   }
+}
+
+// One warp per (column, class) task; `wmax` warps of the CTA take part (each
+// needs M1 x (2 M1 + 1) values of shared memory), CTA u0 of ustep.
+template <typename T>
+__device__ void blockinv_body(const LevelView<T>& L, T* WT_DEV_RESTRICT Binv, int nclass, T cxx,
+                              T cyy, int* flag, int u0, int ustep, int wmax, unsigned char* smraw) {
+  const int M1 = L.M1;
+  const int wib = threadIdx.x >> 5;
+  const int nw = min((int)(blockDim.x >> 5), wmax);
+  T* A = reinterpret_cast<T*>(smraw) + wib * (M1 * (2 * M1 + 1));
+  if (wib >= nw) return;
+  for (long task = (long)u0 * nw + wib; task < (long)L.ncols * nclass; task += (long)ustep * nw)
+    blockinv_task<T>(L, Binv, nclass, cxx, cyy, flag, task, A);
 }
 
 // Assemble the dense A_{a,b} of the coarsest level and invert it in shared

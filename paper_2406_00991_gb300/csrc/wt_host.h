@@ -145,8 +145,9 @@ struct wt_tank {
   bool use_graphs = true;
   cudaStream_t own_stream = nullptr;
   cudaEvent_t order_ev = nullptr;
-  cudaStream_t side = nullptr;                 // stage set-up overlapped with the forcing
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t side = nullptr;                 // stage set-up overlapped with the forcing:
+  cudaStream_t side2 = nullptr;                //   block inverses on side, coarsest LU on side2
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
   int Nx = 0, Ny = 0, Nz = 0, M1 = 0, ncols = 0;
   long n = 0;
   double L = 0, g = 9.81, nu = 0;

@@ -170,6 +170,20 @@ cudaError_t launch_col_matrix(const T* M, int Mo, int Mi, const T* in, T* out, i
 template <typename T>
 cudaError_t launch_block_inverse(const LevelView<T>& L, T* Binv, int nclass, T cxx, T cyy,
                                  int* flag, cudaStream_t s);
+// The block inverses of several levels in one launch: the (column, class)
+// tasks of level l are start[l] .. start[l+1]-1, one warp each.
+template <typename T>
+struct BlockInvMulti {
+  int nlev = 0;
+  int maxM1 = 0;
+  LevelView<T> L[kMaxLevels];
+  T* Binv[kMaxLevels];
+  int nclass[kMaxLevels];
+  T cxx[kMaxLevels], cyy[kMaxLevels];
+  long start[kMaxLevels + 1];
+};
+template <typename T>
+cudaError_t launch_block_inverse_multi(const BlockInvMulti<T>& m, int* flag, cudaStream_t s);
 
 // Single-CTA V-cycle over the levels l0..nl-1 (wt_tail.cu): all small levels
 // run in one launch with __syncthreads between the phases.

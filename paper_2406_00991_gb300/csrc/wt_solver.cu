@@ -8,6 +8,7 @@
 #include "wt_solver.h"
 
 #include <algorithm>
+#include <utility>
 #include <cmath>
 #include <cstring>
 
@@ -138,17 +139,34 @@ void setup_geometry(wt_tank& t, const double* ea, const double* eb, int precisio
 
 void setup_blocks(wt_tank& t, int precision, bool blocks, bool coarse, cudaStream_t s) {
   const int nl = (int)t.L64.size();
-  if (blocks) {
-    for (int l = 0; l < nl - 1; ++l) {
-      if (precision == WT_FP32) {
-        auto& L = t.L32[l];
-        WT_LAUNCH(t, K_BLOCKINV, 4.0 * L.ncols * (L.nclass * L.M1 * L.M1 + kMeta), 2.0 * L.nclass * L.ncols * L.M1 * L.M1 * L.M1, launch_block_inverse<float>(L.view(t.tw32, t.logNtw, t.L), L.Binv, L.nclass, L.cxx, L.cyy,
-                                          t.dflag, s));
-      } else {
-        auto& L = t.L64[l];
-        WT_LAUNCH(t, K_BLOCKINV, 8.0 * L.ncols * (L.nclass * L.M1 * L.M1 + kMeta), 2.0 * L.nclass * L.ncols * L.M1 * L.M1 * L.M1, launch_block_inverse<double>(L.view(t.tw64, t.logNtw, t.L), L.Binv, L.nclass, L.cxx, L.cyy,
-                                           t.dflag, s));
+  if (blocks && nl > 1) {
+    // every level's column blocks in one launch
+    auto fill = [&](auto& lev, auto tw, auto& m, double wbytes) {
+      double bytes = 0.0, flops = 0.0;
+      m.nlev = nl - 1;
+      m.start[0] = 0;
+      for (int l = 0; l < nl - 1; ++l) {
+        auto& L = lev[l];
+        m.L[l] = L.view(tw, t.logNtw, t.L);
+        m.Binv[l] = L.Binv;
+        m.nclass[l] = L.nclass;
+        m.cxx[l] = L.cxx;
+        m.cyy[l] = L.cyy;
+        m.start[l + 1] = m.start[l] + (long)L.ncols * L.nclass;
+        m.maxM1 = std::max(m.maxM1, L.M1);
+        bytes += wbytes * L.ncols * (L.nclass * L.M1 * L.M1 + kMeta);
+        flops += 2.0 * L.nclass * L.ncols * L.M1 * L.M1 * L.M1;
       }
+      return std::make_pair(bytes, flops);
+    };
+    if (precision == WT_FP32) {
+      BlockInvMulti<float> m;
+      const auto bf = fill(t.L32, t.tw32, m, 4.0);
+      WT_LAUNCH(t, K_BLOCKINV, bf.first, bf.second, launch_block_inverse_multi<float>(m, t.dflag, s));
+    } else {
+      BlockInvMulti<double> m;
+      const auto bf = fill(t.L64, t.tw64, m, 8.0);
+      WT_LAUNCH(t, K_BLOCKINV, bf.first, bf.second, launch_block_inverse_multi<double>(m, t.dflag, s));
     }
   }
   if (coarse) {
