@@ -236,6 +236,19 @@ void build_hierarchy(wt_tank& t) {
     t.L64[l].Psig = upload<double>(t.har, P);
     t.L32[l].Rsig = upload<float>(t.har, R);
     t.L32[l].Psig = upload<float>(t.har, P);
+    // a step that coarsens in x only keeps the sigma nodes: both transfers
+    // are then the identity (checked on the assembled matrices), and the
+    // V-cycle skips their column passes
+    bool id = Nzf == Nzc;
+    for (int i = 0; id && i <= Nzf; ++i)
+      for (int k = 0; k <= Nzf; ++k) {
+        const double e = (i == k) ? 1.0 : 0.0;
+        if (std::fabs(R[i * (Nzf + 1) + k] - e) > 1e-12 || std::fabs(P[i * (Nzf + 1) + k] - e) > 1e-12) {
+          id = false;
+          break;
+        }
+      }
+    t.L64[l].sig_id = t.L32[l].sig_id = id;
   }
   // level descriptors for the single-CTA V-cycle kernel
   {

@@ -16,13 +16,13 @@
 
 namespace wt {
 
-template <typename T, int DIM>
+template <typename T, int DIM, int KM>
 __global__ void __launch_bounds__(256) k_op_cols(LevelView<T> L, const T* __restrict__ p,
                                                  const T* __restrict__ Px, const T* __restrict__ Py,
                                                  T* __restrict__ Gx, T* __restrict__ Gy,
                                                  T* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  opcols_body<T, DIM>(L, p, Px, Py, Gx, Gy, part, blockIdx.x, gridDim.x, smraw);
+  opcols_body<T, DIM, KM>(L, p, Px, Py, Gx, Gy, part, blockIdx.x, gridDim.x, smraw);
 }
 
 template <typename T, int DIM, int MAXM>
@@ -104,6 +104,22 @@ static inline int grid_cols(long ncols, int threads) {
   return (int)std::min<long>(std::max<long>(1, (ncols + w - 1) / w), 152L * 64);
 }
 
+// Warp-per-column operator with the column length fixed at compile time where
+// it is one of the finest levels' lengths, else read from the level.
+template <typename T, int DIM>
+static cudaError_t launch_op_cols_m(const LevelView<T>& L, int g, size_t smem, cudaStream_t s, const T* p,
+                                    const T* Px, const T* Py, T* Gx, T* Gy, T* part) {
+#define WT_OPC(KM) launch_k(k_op_cols<T, DIM, KM>, dim3(g), dim3(256), smem, s, L, p, Px, Py, Gx, Gy, part)
+  switch (L.M1) {
+    case 9: return WT_OPC(9);
+    case 17: return WT_OPC(17);
+    case 25: return WT_OPC(25);
+    case 33: return WT_OPC(33);
+    default: return WT_OPC(0);
+  }
+#undef WT_OPC
+}
+
 template <typename T>
 cudaError_t launch_op_cols(const LevelView<T>& L, const T* p, const T* Px, const T* Py, T* Gx,
                            T* Gy, T* part, cudaStream_t s) {
@@ -119,8 +135,8 @@ cudaError_t launch_op_cols(const LevelView<T>& L, const T* p, const T* Px, const
     return launch_k(k_op_cols_tpc<T, 3, 17>, G, B, smem, s, L, p, Px, Py, Gx, Gy, part);
   }
   const int g = grid_cols(L.ncols, 256);
-  if (L.Ny == 1) return launch_k(k_op_cols<T, 2>, dim3(g), dim3(256), smem, s, L, p, Px, Py, Gx, Gy, part);
-  return launch_k(k_op_cols<T, 3>, dim3(g), dim3(256), smem, s, L, p, Px, Py, Gx, Gy, part);
+  if (L.Ny == 1) return launch_op_cols_m<T, 2>(L, g, smem, s, p, Px, Py, Gx, Gy, part);
+  return launch_op_cols_m<T, 3>(L, g, smem, s, p, Px, Py, Gx, Gy, part);
 }
 
 template <typename T>

@@ -340,15 +340,26 @@ __device__ __forceinline__ T bcast(T v0, T v1, int k) {
   return k < 32 ? __shfl_sync(kFull, v0, k) : __shfl_sync(kFull, v1, k - 32);
 }
 
-// sum_k M[m][k] v[k] for the lane's two rows (row-major M, leading dimension ld)
-template <typename T>
+// sum_k M[m][k] v[k] for the lane's two rows (row-major M, leading dimension
+// ld).  KM > 0: Mi == ld == KM at compile time, so the loop unrolls and the
+// broadcasts issue back to back.
+template <typename T, int KM = 0>
 __device__ __forceinline__ void contract(const T* sM, int ld, int Mi, int m0, int m1, bool r0, bool r1,
                                          T v0, T v1, T& o0, T& o1) {
   T a0 = 0, a1 = 0;
-  for (int k = 0; k < Mi; ++k) {
-    const T vk = bcast(v0, v1, k);
-    if (r0) a0 += sM[m0 * ld + k] * vk;
-    if (r1) a1 += sM[m1 * ld + k] * vk;
+  if constexpr (KM > 0) {
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      const T vk = bcast(v0, v1, k);
+      if (r0) a0 += sM[m0 * KM + k] * vk;
+      if (KM > 32 && r1) a1 += sM[m1 * KM + k] * vk;
+    }
+  } else {
+    for (int k = 0; k < Mi; ++k) {
+      const T vk = bcast(v0, v1, k);
+      if (r0) a0 += sM[m0 * ld + k] * vk;
+      if (r1) a1 += sM[m1 * ld + k] * vk;
+    }
   }
   o0 = a0;
   o1 = a1;
@@ -359,12 +370,13 @@ __host__ __device__ inline size_t opcols_smem(int M1) {
   return sizeof(T) * ((size_t)M1 * M1 + 64);
 }
 
-template <typename T, int DIM>
+// KM > 0: the level's M1 equals KM (compile-time column length).
+template <typename T, int DIM, int KM = 0>
 __device__ void opcols_body(const LevelView<T>& L, const T* WT_DEV_RESTRICT p,
                             const T* WT_DEV_RESTRICT Px, const T* WT_DEV_RESTRICT Py,
                             T* WT_DEV_RESTRICT Gx, T* WT_DEV_RESTRICT Gy, T* WT_DEV_RESTRICT part,
                             int u0, int ustep, unsigned char* smraw) {
-  const int M1 = L.M1;
+  const int M1 = KM > 0 ? KM : L.M1;
   T* sD = reinterpret_cast<T*>(smraw);            // M1*M1
   T* sS = sD + M1 * M1;                           // sigma
   for (int i = threadIdx.x; i < M1 * M1; i += blockDim.x) sD[i] = L.D[i];
@@ -378,7 +390,7 @@ __device__ void opcols_body(const LevelView<T>& L, const T* WT_DEV_RESTRICT p,
   for (long c = (long)u0 * nw + wib; c < nc; c += (long)ustep * nw) {
     const T p0 = r0 ? p[m0 * nc + c] : T(0), p1 = r1 ? p[m1 * nc + c] : T(0);
     T ps0, ps1;
-    contract(sD, M1, M1, m0, m1, r0, r1, p0, p1, ps0, ps1);            // P_s = D p
+    contract<T, KM>(sD, M1, M1, m0, m1, r0, r1, p0, p1, ps0, ps1);            // P_s = D p
     const T AXb = meta[M_AXb * nc + c], BXb = meta[M_BXb * nc + c];
     const T AXa = meta[M_AXa * nc + c], BXa = meta[M_BXa * nc + c];
     const T Za = meta[M_Za * nc + c], Zb = meta[M_Zb * nc + c];
@@ -400,9 +412,9 @@ __device__ void opcols_body(const LevelView<T>& L, const T* WT_DEV_RESTRICT p,
       if (r1) Gy[m1 * nc + c] = gy1;
     }
     T q0, q1, z0, z1, y0 = 0, y1 = 0;
-    contract(sD, M1, M1, m0, m1, r0, r1, gx0, gx1, q0, q1);            // D G_x
-    contract(sD, M1, M1, m0, m1, r0, r1, ps0, ps1, z0, z1);            // D P_s
-    if constexpr (DIM == 3) contract(sD, M1, M1, m0, m1, r0, r1, gy0, gy1, y0, y1);
+    contract<T, KM>(sD, M1, M1, m0, m1, r0, r1, gx0, gx1, q0, q1);            // D G_x
+    contract<T, KM>(sD, M1, M1, m0, m1, r0, r1, ps0, ps1, z0, z1);            // D P_s
+    if constexpr (DIM == 3) contract<T, KM>(sD, M1, M1, m0, m1, r0, r1, gy0, gy1, y0, y1);
     const T ZZ = Za * Zb;
     auto row = [&](int m, T pv, T ps, T gx, T gy, T q, T z, T y, T s) -> T {
       if (m == 0) return pv;                                        // surface row: p

@@ -62,6 +62,7 @@ struct Level {
   T cxx = 0, cyy = 0;
   T *rhoX = nullptr, *rhoY = nullptr, *rhoXY = nullptr;
   T *Rsig = nullptr, *Psig = nullptr;   // to / from the next coarser level
+  bool sig_id = false;                   // both are the identity (same sigma nodes)
   LevelView<T> view(const c2_t<T>* tw, int logNtw, double Ld) const {
     LevelView<T> v;
     v.Nx = Nx; v.Ny = Ny; v.Nz = Nz; v.M1 = M1; v.logNx = logNx; v.logNy = logNy;

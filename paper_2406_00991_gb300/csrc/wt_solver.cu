@@ -289,12 +289,17 @@ static void restrict_to(wt_tank& t, int l, const T* r) {
   cudaStream_t s = t.s;
   const T* cur = r;
   if (C.Nx != F.Nx) {
-    run_rowpass(t, xpass<T>(t, cur, F.t4, F.M1 * F.Ny, F.Nx, C.Nx, XOP_RESAMPLE));
-    cur = F.t4;
+    // with identity sigma transfers the last Fourier truncation writes C.f
+    const bool direct = F.sig_id;
+    T* dx = (direct && F.Ny == 1) ? C.f : F.t4;
+    run_rowpass(t, xpass<T>(t, cur, dx, F.M1 * F.Ny, F.Nx, C.Nx, XOP_RESAMPLE));
+    cur = dx;
     if (F.Ny > 1) {
-      run_rowpass(t, ypass<T>(t, cur, F.t5, F.M1, C.Nx, F.Ny, C.Ny, XOP_RESAMPLE));
-      cur = F.t5;
+      T* dy = direct ? C.f : F.t5;
+      run_rowpass(t, ypass<T>(t, cur, dy, F.M1, C.Nx, F.Ny, C.Ny, XOP_RESAMPLE));
+      cur = dy;
     }
+    if (direct) return;
   }
   run_col_matrix<T>(t, F.Rsig, C.M1, F.M1, cur, C.f, C.ncols, 0);
 }
@@ -311,8 +316,11 @@ static bool prolong_add(wt_tank& t, int l, T* x, T* dx_out = nullptr) {
     run_col_matrix<T>(t, F.Psig, F.M1, C.M1, C.x, x, F.ncols, 1);
     return false;
   }
-  run_col_matrix<T>(t, F.Psig, F.M1, C.M1, C.x, F.t4, C.ncols, 0);
-  const T* cur = F.t4;
+  const T* cur = C.x;                       // identity sigma transfer: read e_c itself
+  if (!F.sig_id) {
+    run_col_matrix<T>(t, F.Psig, F.M1, C.M1, C.x, F.t4, C.ncols, 0);
+    cur = F.t4;
+  }
   if (F.Ny > 1) {
     run_rowpass(t, ypass<T>(t, cur, F.t5, F.M1, C.Nx, C.Ny, F.Ny, XOP_RESAMPLE));
     cur = F.t5;
@@ -414,12 +422,12 @@ void vcycle(wt_tank& t, int l, const T* f, T* x, bool tr) {
       // r = f - A u and its Fourier truncation in the same row pass; only the
       // truncated rows are stored, then the Chebyshev truncation
       OpExtra<T> ex;
-      ex.out2 = L.t4;
+      ex.out2 = L.sig_id ? C.f : L.t4;          // identity sigma transfer: straight to C.f
       ex.Nout2 = C.Nx;
       ex.op2 = XOP_RESAMPLE;
       ex.write_out = false;
       apply_op<T>(t, l, x, L.r, f, false, tr, ex);
-      run_col_matrix<T>(t, L.Rsig, C.M1, L.M1, L.t4, C.f, C.ncols, 0);
+      if (!L.sig_id) run_col_matrix<T>(t, L.Rsig, C.M1, L.M1, L.t4, C.f, C.ncols, 0);
     } else {
       apply_op<T>(t, l, x, L.r, f, false, tr);  // r = f - A u
       restrict_to<T>(t, l, L.r);
