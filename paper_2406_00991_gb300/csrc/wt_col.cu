@@ -105,13 +105,17 @@ static inline int grid_cols(long ncols, int threads) {
 }
 
 // Warp-per-column operator with the column length fixed at compile time where
-// it is one of the finest levels' lengths, else read from the level.
+// it is one of the common lengths (Nz = 4, 6, 8, 12, 16, 24, 32), else read
+// from the level.
 template <typename T, int DIM>
 static cudaError_t launch_op_cols_m(const LevelView<T>& L, int g, size_t smem, cudaStream_t s, const T* p,
                                     const T* Px, const T* Py, T* Gx, T* Gy, T* part) {
 #define WT_OPC(KM) launch_k(k_op_cols<T, DIM, KM>, dim3(g), dim3(256), smem, s, L, p, Px, Py, Gx, Gy, part)
   switch (L.M1) {
+    case 5: return WT_OPC(5);
+    case 7: return WT_OPC(7);
     case 9: return WT_OPC(9);
+    case 13: return WT_OPC(13);
     case 17: return WT_OPC(17);
     case 25: return WT_OPC(25);
     case 33: return WT_OPC(33);
@@ -152,8 +156,11 @@ static cudaError_t launch_smooth_m(const LevelView<T>& L, dim3 G, dim3 B, cudaSt
                                    const T* rhoY, const T* rhoXY, const T* Binv, T* x, T omega, int first) {
 #define WT_SMOOTH(MM, EX) \
   launch_k(k_smooth_cols<T, DIM, TR, MM, EX>, G, B, 0, s, L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first)
-  switch (L.M1) {                           // the finest levels: exact column lengths
+  switch (L.M1) {                           // the common column lengths: exact
+    case 5: return WT_SMOOTH(5, true);
+    case 7: return WT_SMOOTH(7, true);
     case 9: return WT_SMOOTH(9, true);
+    case 13: return WT_SMOOTH(13, true);
     case 17: return WT_SMOOTH(17, true);
     case 25: return WT_SMOOTH(25, true);
     case 33: return WT_SMOOTH(33, true);
