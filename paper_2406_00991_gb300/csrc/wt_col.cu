@@ -8,8 +8,9 @@
 //  k_smooth_cols  damped block-Jacobi update x += omega sum_class B_class^{-1} r_class
 //                 (Sec. 4.3, Nyquist-split column blocks).
 //  k_col_matrix   out = M in along sigma (Chebyshev transfers of Sec. 4.2, filter).
-//  k_block_inverse  builds and inverts the (Nz+1)^2 diagonal block of every
-//                 column by Gauss-Jordan with partial pivoting, one warp per column.
+//  k_block_inverse_multi  builds and inverts the (Nz+1)^2 diagonal block of
+//                 every column of every level by Gauss-Jordan with partial
+//                 pivoting, one warp per (column, class), all levels in one launch.
 #include "wt_dev.cuh"
 
 #include <algorithm>
@@ -62,13 +63,6 @@ __global__ void __launch_bounds__(256) k_col_matrix(const T* __restrict__ M, int
                                                     int ncols, int accumulate) {
   extern __shared__ __align__(16) unsigned char smraw[];
   colmat_body<T>(M, Mo, Mi, in, out, ncols, accumulate, blockIdx.x, gridDim.x, smraw);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(128) k_block_inverse(LevelView<T> L, T* __restrict__ Binv,
-                                                       int nclass, T cxx, T cyy, int* flag) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  blockinv_body<T>(L, Binv, nclass, cxx, cyy, flag, blockIdx.x, gridDim.x, 4, smraw);
 }
 
 // Every level's (column, class) tasks in one launch: the levels' inverses
@@ -197,21 +191,6 @@ cudaError_t launch_col_matrix(const T* M, int Mo, int Mi, const T* in, T* out, i
 }
 
 template <typename T>
-cudaError_t launch_block_inverse(const LevelView<T>& L, T* Binv, int nclass, T cxx, T cyy,
-                                 int* flag, cudaStream_t s) {
-  const int W = 2 * L.M1 + 1;
-  const size_t smem = 4 * (size_t)L.M1 * W * sizeof(T);
-  if (smem > 32 * 1024) {
-    cudaError_t e = ensure_dyn_smem((const void*)k_block_inverse<T>, smem);
-    if (e != cudaSuccess) return e;
-  }
-  const long tasks = (long)L.ncols * nclass;
-  const int g = (int)std::min<long>(std::max<long>(1, (tasks + 3) / 4), 152 * 8);
-  k_block_inverse<T><<<g, 128, smem, s>>>(L, Binv, nclass, cxx, cyy, flag);
-  return cudaGetLastError();
-}
-
-template <typename T>
 cudaError_t launch_block_inverse_multi(const BlockInvMulti<T>& m, int* flag, cudaStream_t s) {
   if (m.nlev <= 0) return cudaSuccess;
   const int W = 2 * m.maxM1 + 1;
@@ -235,8 +214,6 @@ cudaError_t launch_block_inverse_multi(const BlockInvMulti<T>& m, int* flag, cud
                                            cudaStream_t);                                        \
   template cudaError_t launch_col_matrix<T>(const T*, int, int, const T*, T*, int, int,         \
                                             cudaStream_t);                                      \
-  template cudaError_t launch_block_inverse<T>(const LevelView<T>&, T*, int, T, T, int*,        \
-                                               cudaStream_t);                                    \
   template cudaError_t launch_block_inverse_multi<T>(const BlockInvMulti<T>&, int*, cudaStream_t);
 WT_INST(float)
 WT_INST(double)

@@ -167,9 +167,6 @@ cudaError_t launch_smooth_cols(const LevelView<T>& L, const T* r, const T* rhoX,
 template <typename T>
 cudaError_t launch_col_matrix(const T* M, int Mo, int Mi, const T* in, T* out, int ncols,
                               int accumulate, cudaStream_t s);
-template <typename T>
-cudaError_t launch_block_inverse(const LevelView<T>& L, T* Binv, int nclass, T cxx, T cyy,
-                                 int* flag, cudaStream_t s);
 // The block inverses of several levels in one launch: the (column, class)
 // tasks of level l are start[l] .. start[l+1]-1, one warp each.
 template <typename T>
@@ -271,7 +268,7 @@ template <typename T>
 cudaError_t launch_dots(const T* w, const T* V, long ldv, int nvec, long n, double* partial,
                         int nblk, int with_norm, cudaStream_t s);
 // One-launch forms: the last CTA sums the partials (dots -> out), or sums
-// them and performs the Arnoldi / Givens update of column j (update_dots);
+// them and performs the Arnoldi / Givens update of column j (update_dots_arnoldi);
 // `ticket` is a zero-initialised device counter per call site.
 template <typename T>
 cudaError_t launch_dots_sum(const T* w, const T* V, long ldv, int nvec, long n, double* partial, int nblk,
@@ -280,11 +277,6 @@ template <typename T>
 cudaError_t launch_update_dots_arnoldi(T* w, const T* V, long ldv, int nvec, long n, double* st,
                                        double* partial, int nblk, int j, int m, unsigned* ticket,
                                        cudaStream_t s);
-cudaError_t launch_reduce_partials(const double* partial, int nblk, int nvals, double* out,
-                                   cudaStream_t s);
-template <typename T>
-cudaError_t launch_update_dots(T* w, const T* V, long ldv, int nvec, long n, const double* h,
-                               double* partial, int nblk, cudaStream_t s);
 template <typename T>
 cudaError_t launch_update_normalize(const T* w, const T* V, long ldv, int nvec, long n,
                                     const double* h, const double* inv_norm, T* vout, float* v32,
@@ -292,9 +284,6 @@ cudaError_t launch_update_normalize(const T* w, const T* V, long ldv, int nvec, 
 template <typename T>
 cudaError_t launch_lincomb(T* x, const T* Z, long ldz, int nvec, long n, const double* y,
                            cudaStream_t s);
-template <typename T>
-cudaError_t launch_scale_copy(const T* in, T* out, long n, const double* scale, int invert,
-                              cudaStream_t s);
 template <typename Ti, typename To>
 cudaError_t launch_convert(const Ti* in, To* out, long n, const double* scale, int invert,
                            cudaStream_t s);
@@ -305,9 +294,6 @@ cudaError_t launch_nyquist_coef(const void* r, int is_double, int nrows, int Nx,
 // GMRES small dense part on one thread: see wt_krylov.cu for the state layout.
 cudaError_t launch_gmres_init(double* st, const double* partial, int nblk, int m, double bnorm,
                               double tol, cudaStream_t s);
-cudaError_t launch_gmres_arnoldi(double* st, const double* partial1, const double* partial2,
-                                 int nblk, int j, int m, double bnorm, double tol,
-                                 cudaStream_t s);
 cudaError_t launch_gmres_solve_y(double* st, int k, int m, cudaStream_t s);
 
 // Surface metric (wt_metric.cu).

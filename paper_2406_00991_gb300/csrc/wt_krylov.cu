@@ -52,58 +52,6 @@ __global__ void __launch_bounds__(256) k_dots(const T* __restrict__ w, const T* 
   }
 }
 
-__global__ void k_reduce_partials(const double* __restrict__ partial, int nblk, int nvals,
-                                  double* __restrict__ out) {
-  for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
-    double s = 0;
-    for (int b = 0; b < nblk; ++b) s += partial[(long)b * nvals + i];
-    out[i] = s;
-  }
-}
-
-// w -= V h (h = st[OFF_H1..]); then partial2 = (V^T w, ||w||^2).
-template <typename T>
-__global__ void __launch_bounds__(256) k_update_dots(T* __restrict__ w, const T* __restrict__ V,
-                                                    long ldv, int nvec, long n,
-                                                    const double* __restrict__ h,
-                                                    double* __restrict__ partial) {
-  __shared__ double red[8][33];
-  __shared__ T sh[32];
-  for (int i = threadIdx.x; i < 32; i += blockDim.x) sh[i] = i < nvec ? (T)h[i] : T(0);
-  __syncthreads();
-  T acc[33];
-#pragma unroll
-  for (int i = 0; i < 33; ++i) acc[i] = T(0);
-  for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
-    T v[32];
-    T wv = w[e];
-#pragma unroll
-    for (int i = 0; i < 32; ++i)
-      if (i < nvec) { v[i] = V[i * ldv + e]; wv -= sh[i] * v[i]; }
-    w[e] = wv;
-#pragma unroll
-    for (int i = 0; i < 32; ++i)
-      if (i < nvec) acc[i] += wv * v[i];
-    acc[32] += wv * wv;
-  }
-  const int nvals = nvec + 1;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int i = 0; i < 33; ++i) {
-    if (!(i < nvec || i == 32)) continue;
-    double v = (double)acc[i];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[warp][i] = v;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
-    const int src = (i < nvec) ? i : 32;
-    double s = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k][src];
-    partial[(long)blockIdx.x * nvals + i] = s;
-  }
-}
-
 // vout = (w - V h) * inv_norm, h = st[OFF_H2..], inv_norm = st[2]; vout may
 // be w itself (each element is read and written by one thread), and v32, if
 // given, receives the FP32 rounding of vout (the FP32 V-cycle's input).
@@ -236,19 +184,6 @@ __device__ void arnoldi_update(double* st, const double* h2, double ww, int j, i
   st[3] = (res <= tol * st[4] || breakdown) ? 1.0 : 0.0;
 }
 
-__global__ void k_gmres_arnoldi(double* st, const double* __restrict__ partial2, int nblk, int j,
-                                int m) {
-  __shared__ double h2[64];
-  __shared__ double ww;
-  const int nvals = j + 2;    // j+1 dots and ||w||^2
-  for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
-    const double s = block_sum_partial(partial2, nblk, nvals, i);
-    if (i < j + 1) h2[i] = s; else ww = s;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) arnoldi_update(st, h2, ww, j, m);
-}
-
 __global__ void k_gmres_solve_y(double* st, int k, int m) {
   if (threadIdx.x != 0) return;
   for (int i = k - 1; i >= 0; --i) {
@@ -315,8 +250,9 @@ __global__ void __launch_bounds__(256) k_dots_sum(const T* __restrict__ w, const
   }
 }
 
-// k_update_dots followed (in the last CTA) by the Arnoldi / Givens update of
-// k_gmres_arnoldi for column j.
+// w -= V h1 (h1 = st[OFF_H1..]) and the per-CTA sums of (V^T w, ||w||^2);
+// the last CTA adds them up and performs the Arnoldi / Givens update of
+// column j (arnoldi_update).
 template <typename T>
 __global__ void __launch_bounds__(256) k_update_dots_arnoldi(T* __restrict__ w, const T* __restrict__ V,
                                                             long ldv, int nvec, long n, double* st,
@@ -380,15 +316,6 @@ cudaError_t launch_dots(const T* w, const T* V, long ldv, int nvec, long n, doub
                         int with_norm, cudaStream_t s) {
   return launch_k(k_dots<T>, dim3(nblk), dim3(256), 0, s, w, V, ldv, nvec, n, partial, with_norm);
 }
-cudaError_t launch_reduce_partials(const double* partial, int nblk, int nvals, double* out,
-                                   cudaStream_t s) {
-  return launch_k(k_reduce_partials, dim3(1), dim3(64), 0, s, partial, nblk, nvals, out);
-}
-template <typename T>
-cudaError_t launch_update_dots(T* w, const T* V, long ldv, int nvec, long n, const double* h,
-                               double* partial, int nblk, cudaStream_t s) {
-  return launch_k(k_update_dots<T>, dim3(nblk), dim3(256), 0, s, w, V, ldv, nvec, n, h, partial);
-}
 template <typename T>
 cudaError_t launch_update_normalize(const T* w, const T* V, long ldv, int nvec, long n, const double* h,
                                     const double* inv_norm, T* vout, float* v32, cudaStream_t s) {
@@ -399,11 +326,6 @@ template <typename T>
 cudaError_t launch_lincomb(T* x, const T* Z, long ldz, int nvec, long n, const double* y,
                            cudaStream_t s) {
   return launch_k(k_lincomb<T>, dim3(blocks_for(n)), dim3(256), 0, s, x, Z, ldz, nvec, n, y);
-}
-template <typename T>
-cudaError_t launch_scale_copy(const T* in, T* out, long n, const double* scale, int invert,
-                              cudaStream_t s) {
-  return launch_k(k_convert<T, T>, dim3(blocks_for(n)), dim3(256), 0, s, in, out, n, scale, invert);
 }
 template <typename Ti, typename To>
 cudaError_t launch_convert(const Ti* in, To* out, long n, const double* scale, int invert,
@@ -427,13 +349,6 @@ cudaError_t launch_gmres_init(double* st, const double* partial, int nblk, int m
                               double tol, cudaStream_t s) {
   return launch_k(k_gmres_init, dim3(1), dim3(32), 0, s, st, partial, nblk, m, bnorm, tol);
 }
-cudaError_t launch_gmres_arnoldi(double* st, const double* partial1, const double* partial2, int nblk,
-                                 int j, int m, double bnorm, double tol, cudaStream_t s) {
-  (void)partial1;
-  (void)bnorm;
-  (void)tol;
-  return launch_k(k_gmres_arnoldi, dim3(1), dim3(64), 0, s, st, partial2, nblk, j, m);
-}
 cudaError_t launch_gmres_solve_y(double* st, int k, int m, cudaStream_t s) {
   return launch_k(k_gmres_solve_y, dim3(1), dim3(32), 0, s, st, k, m);
 }
@@ -455,12 +370,9 @@ cudaError_t launch_update_dots_arnoldi(T* w, const T* V, long ldv, int nvec, lon
 #define WT_KINST(T)                                                                                  \
   template cudaError_t launch_dots<T>(const T*, const T*, long, int, long, double*, int, int,         \
                                       cudaStream_t);                                                 \
-  template cudaError_t launch_update_dots<T>(T*, const T*, long, int, long, const double*, double*,   \
-                                             int, cudaStream_t);                                     \
   template cudaError_t launch_update_normalize<T>(const T*, const T*, long, int, long, const double*, \
                                                   const double*, T*, float*, cudaStream_t);          \
   template cudaError_t launch_lincomb<T>(T*, const T*, long, int, long, const double*, cudaStream_t); \
-  template cudaError_t launch_scale_copy<T>(const T*, T*, long, const double*, int, cudaStream_t);    \
   template cudaError_t launch_axpy_from<T>(double*, const T*, long, const double*, cudaStream_t);     \
   template cudaError_t launch_dots_sum<T>(const T*, const T*, long, int, long, double*, int, int,      \
                                           double*, unsigned*, cudaStream_t);                          \
