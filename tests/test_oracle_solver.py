@@ -72,3 +72,36 @@ def test_vcycle_is_a_contraction():
     for _ in range(6):
         x = x + pmg.vcycle(levels, 0, np.zeros(g.shape), b - levels[0].apply(x))
     assert np.linalg.norm(b - levels[0].apply(x)) < 0.5 * r0
+
+
+def test_sigma_transfers_between_equal_degrees_are_the_identity():
+    # Truncating the degree-Nz Chebyshev interpolant of a column to degree Nz
+    # and evaluating it at the same Gauss-Lobatto nodes returns the column,
+    # and so does interpolating it there (Sec. 4.2 transfers): a coarsening
+    # step in x only moves the residual and the correction through the
+    # Fourier resampling alone.
+    from oracle import spectral as sp
+    for Nz in (4, 6, 8, 12, 16, 24, 32):
+        for bc in ("inject", "paper"):
+            R = pmg.restrict_sigma_matrix(Nz, Nz, bc)
+            assert np.abs(R - np.eye(Nz + 1)).max() < 1e-12, (Nz, bc)
+        P = sp.cheb_prolong_matrix(Nz, Nz)
+        assert np.abs(P - np.eye(Nz + 1)).max() < 1e-12, Nz
+    # between different degrees, restriction after interpolation is exact on
+    # the coarse polynomials (R P = I) while P R is a projection, not I
+    for Nf, Nc in ((24, 12), (16, 8), (12, 6)):
+        P = sp.cheb_prolong_matrix(Nc, Nf)
+        for bc in ("inject", "paper"):
+            R = pmg.restrict_sigma_matrix(Nf, Nc, bc)
+            assert np.abs(R @ P - np.eye(Nc + 1)).max() < 1e-12, (Nf, Nc, bc)
+        PR = P @ pmg.restrict_sigma_matrix(Nf, Nc, "paper")
+        assert np.abs(PR @ PR - PR).max() < 1e-10 and np.abs(PR - np.eye(Nf + 1)).max() > 0.1
+    # the whole restriction of an x-only coarsening step is the Fourier truncation
+    g, h, ea, eb, b = problem(32, 1, 8)
+    lev = pmg.build_levels(32, 1, 8, 2 * math.pi, h, ea, eb, coarsest_max=64)
+    fine, coarse = lev[0].grid, lev[1].grid
+    assert (coarse.Nx, coarse.Nz) == (16, 8)
+    r = pmg.restrict(fine, coarse, b)
+    assert np.abs(r - sp.fourier_resample(b, 16, axis=2)).max() < 1e-12 * np.abs(b).max()
+    e = np.random.default_rng(2).standard_normal(coarse.shape)
+    assert np.abs(pmg.prolong(coarse, fine, e) - sp.fourier_resample(e, 32, axis=2)).max() < 1e-12 * np.abs(e).max()
