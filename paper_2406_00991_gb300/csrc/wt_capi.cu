@@ -250,7 +250,8 @@ void build_hierarchy(wt_tank& t) {
       }
     t.L64[l].sig_id = t.L32[l].sig_id = id;
   }
-  // level descriptors for the single-CTA V-cycle kernel
+  // level descriptors for the one-launch V-cycle kernels (one CTA, one
+  // cluster, the cooperative grid)
   {
     std::vector<TailLevel<double>> d64(nl);
     std::vector<TailLevel<float>> d32(nl);

@@ -9,8 +9,9 @@
 
 #include "wt_internal.h"
 
-// Pointer qualifier of the body parameters: the single-CTA V-cycle kernel
-// reads buffers it wrote earlier in the same launch and therefore compiles
+// Pointer qualifier of the body parameters: the one-launch V-cycle kernels
+// (one CTA, one cluster, the cooperative grid) and the batched tank kernel
+// read buffers they wrote earlier in the same launch and therefore compile
 // the bodies without WT_DEV_RESTRICT (no read-only-cache loads).
 #ifndef WT_DEV_RESTRICT
 #define WT_DEV_RESTRICT __restrict__
