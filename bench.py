@@ -74,12 +74,17 @@ def initial_state(p, x, h, sigma):
 
 # --------------------------------------------------------------------- clocks
 class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every `interval_ms` while the
+    timed region runs (start() returns once the first sample is written, so
+    the samples cover the region that follows)."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, interval_ms=50, wait_s=3.0):
         self.idx = gpu_index
+        self.interval_ms = interval_ms
+        self.wait_s = wait_s
         self.proc = None
         self.path = None
 
@@ -89,10 +94,19 @@ class ClockSampler:
             os.close(fd)
             self.out = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.interval_ms)],
                                          stdout=self.out, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        deadline = time.time() + self.wait_s
+        while time.time() < deadline:
+            try:
+                if self.proc.poll() is not None or os.path.getsize(self.path) > 0:
+                    break
+            except OSError:
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -116,7 +130,8 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "interval_ms": self.interval_ms}
 
 
 def peaks():
