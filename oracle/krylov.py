@@ -2,7 +2,7 @@
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
-Reading: the paper names GMRES with one p-multigrid cycle as the
+Reading of the paper: it names GMRES with one p-multigrid cycle as the
 preconditioner but gives neither restart length nor orthogonalisation nor
 side.  Used here: GMRES(m) with right preconditioning (so the monitored
 residual is the true residual of the original system), modified

@@ -21,7 +21,7 @@ Definitions followed:
   (Eq. bcpd) and the sigma = 0 rows the Neumann condition
   n . Grad_b p (Eq. bcpdneu) with n = (h_x, h_y, 1).
 
-Reading: the operator is the composite Div_a o Grad_b of the
+Reading of the paper: the operator is the composite Div_a o Grad_b of the
 discrete first derivatives, not the expanded transformed Laplacian; mixed
 derivatives are derivatives applied one after the other (Sec. 3.5).  The
 outward normal's sign and length cancel because the same n multiplies the

@@ -4,7 +4,7 @@ coarsest-level solve.
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
-Readings of the paper (listed in the design doc):
+Readings of the paper:
 
 * Coarsening (Sec. 4.1): the printed case condition is contradictory.  Going
   from fine to coarse: if Nx > Nz halve Nx (and Ny); if Nz > Nx set

@@ -3,7 +3,7 @@ at every stage (paper Sec. 3.1-3.3) and the kinematic free-surface update.
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
-Readings of the paper (listed in the design doc):
+Readings of the paper:
 
 * Eq. (LSERK) gives the 2N-storage form but no coefficients; the "4th order"
   low-storage method is read as Carpenter & Kennedy's five-stage,

@@ -2,7 +2,7 @@
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
-Readings of the paper used here (each is listed in the design doc):
+Readings of the paper used here:
 
 * Fourier grid (Sec. 3.4): the printed nodes 2*pi*n/(N+1), n=0..N are read as
   the even-count periodic grid x_j = j*L/Nx, j=0..Nx-1, with wavenumbers
