@@ -102,6 +102,11 @@ typedef struct wt_options {
                         the levels at or below tail_max in one launch, the
                         phases separated by the cluster's hardware barrier;
                         0 or 1: one CTA (default 0)                          */
+  long long barrier_cycles; /* vcycle_grid = 1: SM clock cycles a CTA waits
+                        at a grid barrier before it gives up, sets the
+                        abort word and the call returns WT_ETIMEOUT (the
+                        barrier is then reset and the tank stays usable);
+                        0: the default 2e9 (about one second)               */
 } wt_options;
 
 typedef struct wt_solve_info {

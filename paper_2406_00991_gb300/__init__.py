@@ -32,7 +32,7 @@ class wt_options(ctypes.Structure):
                 ("filter", ctypes.c_int), ("linear", ctypes.c_int), ("coarsest_max", ctypes.c_int),
                 ("bc_transfer", ctypes.c_int), ("tail_max", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_ir", ctypes.c_int), ("vcycle_grid", ctypes.c_int),
-                ("tail_cluster", ctypes.c_int)]
+                ("tail_cluster", ctypes.c_int), ("barrier_cycles", ctypes.c_longlong)]
 
 
 class wt_solve_info(ctypes.Structure):

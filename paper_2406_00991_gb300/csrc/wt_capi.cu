@@ -294,8 +294,11 @@ const double* in_dev(wt_tank& t, const double* user, double* staging, size_t cou
   cudaPointerAttributes at{};
   cudaError_t e = cudaPointerGetAttributes(&at, user);
   if (e != cudaSuccess) cudaGetLastError();
-  if (e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged))
+  if (e == cudaSuccess && (at.type == cudaMemoryTypeManaged ||
+                           (at.type == cudaMemoryTypeDevice && at.device == t.device)))
     return user;
+  if (e == cudaSuccess && at.type == cudaMemoryTypeDevice)
+    throw WtError{WT_EINVAL, "an array lives on another GPU than the tank's"};
   WT_CK(cudaMemcpyAsync(staging, user, sizeof(double) * count, cudaMemcpyHostToDevice, t.s));
   return staging;
 }
@@ -318,6 +321,7 @@ int check_options(const wt_options& o) {
   if (o.max_it < 1) return fail(WT_EINVAL, "max_it must be >= 1");
   if (o.coarsest_max < 1 || o.coarsest_max > 128) return fail(WT_EINVAL, "coarsest_max must be in [1, 128]");
   if (o.tail_max < 0) return fail(WT_EINVAL, "tail_max must be >= 0");
+  if (o.barrier_cycles < 0) return fail(WT_EINVAL, "barrier_cycles must be >= 0");
   if ((o.filter != 0 && o.filter != 1) || (o.linear != 0 && o.linear != 1) ||
       (o.bc_transfer != 0 && o.bc_transfer != 1))
     return fail(WT_EINVAL, "filter, linear, bc_transfer are 0 or 1");
@@ -556,6 +560,7 @@ int wt_default_options(wt_options* o) {
   o->max_ir = 30;
   o->vcycle_grid = 0;
   o->tail_cluster = 0;
+  o->barrier_cycles = 0;
   return WT_OK;
 }
 
@@ -673,6 +678,7 @@ int wt_set_options(wt_tank* t, const wt_options* o) {
     WT_CK(cudaStreamSynchronize(t->s));
     destroy_graphs(*t);
     t->opt = *o;
+    write_barrier_limit(*t);
     if (rebuild) {
       WT_CK(cudaStreamSynchronize(t->s));
       // keep the fine-level bathymetry across the rebuild
@@ -857,6 +863,7 @@ int wt_poisson_solve(wt_tank* t, const double* eta_a, const double* eta_b, const
     WT_CK(cudaStreamSynchronize(t->s));
     if (info) *info = inf;
     if (st == WT_ENOCONV) return fail(st, "solve stopped above its tolerance");
+    if (st == WT_ETIMEOUT) return fail(st, "a grid barrier of the one-launch V-cycle gave up waiting");
     if (st != WT_OK) return fail(st, "depth <= 0, singular block or non-finite value in the solve");
     return WT_OK;
   });

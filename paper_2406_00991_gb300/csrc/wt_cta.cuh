@@ -243,6 +243,7 @@ __device__ inline bool grid_sync(GridBar* b, int* flag) {
     const unsigned long long old = atom_add_acq_rel_u64(&b->count, 1ull);
     const unsigned long long target = (old / nb + 1ull) * nb;
     if (old + 1ull != target) {
+      const long long lim = b->limit > 0 ? b->limit : kBarrierCycles;
       const long long t0 = clock64();
       unsigned polls = 0;
       while (ld_acquire_u64(&b->count) < target) {
@@ -251,7 +252,7 @@ __device__ inline bool grid_sync(GridBar* b, int* flag) {
             ok = 0;
             break;
           }
-          if (clock64() - t0 > kBarrierCycles) {
+          if (clock64() - t0 > lim) {
             atomicExch(&b->abort, 1);
             atomicOr(flag, 32);
             ok = 0;

@@ -242,6 +242,7 @@ struct GridBar {
   unsigned long long count;   // arrivals since creation (monotonic)
   int abort;
   int pad;
+  long long limit;            // SM cycles a CTA waits before giving up (0: kBarrierCycles)
 };
 // The whole V-cycle from level a.l0 in one cooperative launch (every CTA
 // resident); phases separated by a bounded grid barrier.  A barrier that

@@ -574,7 +574,7 @@ double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit,
     WT_CK(cudaMemcpyAsync(t.hst, t.st, sizeof(double) * 6, cudaMemcpyDeviceToHost, t.s));
     WT_CK(cudaStreamSynchronize(t.s));
     rel = bnorm > 0 ? t.hst[0] / bnorm : 0.0;
-    if (rel <= tol || its >= maxit || t.hst[0] == 0.0) break;
+    if (rel <= tol || its >= maxit || t.hst[0] == 0.0 || !std::isfinite(rel)) break;
     // v_0 = r / beta (and its FP32 rounding for the FP32 V-cycle)
     WT_LAUNCH(t, K_KRYLOV, 2.0 * sizeof(T) * n + (pre32 ? 4.0 * n : 0.0), (double)n,
               launch_update_normalize<T>(V, V, n, 0, n, t.st + 72, t.st + 2, V, pre32 ? t.b32 : nullptr, t.s));
@@ -595,6 +595,13 @@ double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit,
   return rel;
 }
 
+// The grid barrier's wait bound from the options (0: the compiled default).
+void write_barrier_limit(wt_tank& t) {
+  const long long lim = t.opt.barrier_cycles;
+  WT_CK(cudaMemcpyAsync(&t.gbar->limit, &lim, sizeof(lim), cudaMemcpyHostToDevice, t.s));
+  WT_CK(cudaStreamSynchronize(t.s));
+}
+
 // ------------------------------------------------------------------ solves
 int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_solve_info* info,
                          bool tr) {
@@ -603,7 +610,11 @@ int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_
   int its_total = 0, refinements = 0;
   double rel = 0.0;
   int status = WT_OK;
-  if (bn == 0.0) {
+  if (!std::isfinite(bn)) {
+    // a non-finite right-hand side (state or input): nothing to iterate on
+    status = WT_EBREAK;
+    rel = bn;
+  } else if (bn == 0.0) {
     WT_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, t.s));
     rel = 0.0;
   } else {
@@ -634,16 +645,22 @@ int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_
       its_total = its;
     }
     if (!(rel <= tol)) status = WT_ENOCONV;
+    // a non-finite residual cannot improve: both loops stop on it
+    if (!std::isfinite(rel)) status = WT_EBREAK;
   }
   WT_CK(cudaMemcpyAsync(t.hflag, t.dflag, sizeof(int), cudaMemcpyDeviceToHost, t.s));
   WT_CK(cudaStreamSynchronize(t.s));
-  if (*t.hflag & 7) status = WT_EBREAK;
-  if (*t.hflag & 32) {
+  const int fl = *t.hflag;
+  if (fl & 7) status = WT_EBREAK;
+  if (fl & 32) {
     status = WT_ETIMEOUT;                 // a grid barrier gave up: reset it
     WT_CK(cudaMemsetAsync(t.gbar, 0, sizeof(GridBar), t.s));
+    write_barrier_limit(t);
+  }
+  if (fl) {                               // reported once; the next call starts clean
+    WT_CK(cudaMemsetAsync(t.dflag, 0, sizeof(int), t.s));
     WT_CK(cudaStreamSynchronize(t.s));
   }
-  if (!std::isfinite(rel)) status = WT_EBREAK;
   t.solves += 1;
   t.iterations += its_total;
   if (info) {

@@ -100,6 +100,8 @@ double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit,
 
 // Release the captured Arnoldi-step graphs (after option / hierarchy changes).
 void destroy_graphs(wt_tank& t);
+// Copy the options' grid-barrier wait bound into the tank's barrier state.
+void write_barrier_limit(wt_tank& t);
 
 // Solve A p = b on the finest level (device pointers, FP64) with the tank's
 // options; x holds the initial guess.  Geometry must be set up already.

@@ -37,13 +37,16 @@ int fail(int code, const char* msg) { return wt::set_error(code, msg); }
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-bool is_device_ptr(const void* p) {
+// Device memory of the current device (or managed memory): memory of another
+// GPU would be read without peer access, so it is refused like host memory.
+bool is_device_ptr(const void* p, int dev) {
   cudaPointerAttributes a{};
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 // Host-side address of the scratch array on the current device (the array's
@@ -75,9 +78,14 @@ extern "C" int wt_apply_operator_static(int Nx, int Nz, double L, const double* 
   if (Nz < 2 || Nz > kMaxNz) return fail(WT_EINVAL, "wt_apply_operator_static: Nz must be in [2, 32]");
   if (!(L > 0) || !std::isfinite(L)) return fail(WT_EINVAL, "wt_apply_operator_static: L must be positive");
   if (!h || !eta_a || !eta_b || !p || !Ap) return fail(WT_EINVAL, "wt_apply_operator_static: NULL pointer");
-  if (!is_device_ptr(h) || !is_device_ptr(eta_a) || !is_device_ptr(eta_b) || !is_device_ptr(p) ||
-      !is_device_ptr(Ap))
-    return fail(WT_EINVAL, "wt_apply_operator_static: all arrays must be device memory");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(WT_ECUDA, "wt_apply_operator_static: no current CUDA device");
+  }
+  if (!is_device_ptr(h, dev) || !is_device_ptr(eta_a, dev) || !is_device_ptr(eta_b, dev) ||
+      !is_device_ptr(p, dev) || !is_device_ptr(Ap, dev))
+    return fail(WT_EINVAL, "wt_apply_operator_static: all arrays must be device memory of the current device");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   void* base = nullptr;
   cudaError_t e = scratch_address(&base);

@@ -186,10 +186,15 @@ def test_solve_matches_oracle_dense_lu(wt):
     b = np.random.default_rng(5).standard_normal(g.shape)
     lev = pmg.Level(Nx, 1, Nz, L, h, ea, eb)
     ref = krylov.solve_dense(lev, b)
-    for mode, bound in ((0, 1e-9), (1, 1e-8), (3, 1e-8)):
+    # the oracle's own GMRES + p-multigrid at 1e-12 lands 3e-13 from the LU
+    # solution (cond(A) ~ 2e4 here), so the solve bounds of the method apply
+    # directly: 1e-10 for the FP64 path, 1e-9 for the mixed paths
+    for mode, bound in ((0, 1e-10), (1, 1e-9), (3, 1e-9)):
         T = wt.Tank(Nx, 1, Nz, L, h, mode=mode, tol=1e-12)
         p, info = T.poisson_solve(ea, eb, b)
-        assert np.abs(p - ref).max() <= bound * np.abs(ref).max()
+        err = np.abs(p - ref).max() / np.abs(ref).max()
+        print("dense LU parity, mode %d: %.2e (%d iterations)" % (mode, err, info.iterations))
+        assert err <= bound
 
 
 def test_zero_rhs_and_invalid_geometry(wt):
