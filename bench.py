@@ -40,6 +40,11 @@ if ROOT not in sys.path:
 import seeded_inputs as si  # noqa: E402
 
 METRIC = "RK4 DOF-updates/s (mixed FP32/FP64 p-MG Poisson solves at 1e-10 residual)"
+# DRAM bytes (read + write) of one FP32 operator apply, summed over its
+# kernels, from one ncu capture of the same build and size (see profiles/);
+# None until measured
+OP_TRAFFIC_2D = None
+OP_TRAFFIC_3D = None
 UNIT = "DOF-updates/s"
 STAGES = 5
 
@@ -244,11 +249,13 @@ def run_ours(args):
     ck = clocks.stop()
     value, step_ms = replica_throughput(dist, dev, dof_step, float(np.mean(ms)))
     solves_s = sum_over_ranks(STAGES) / (step_ms / 1e3)
-    # second pass of the same number of steps with CUDA events around every
-    # launch of the dominant kernel class (events force eager launches)
-    ms_prof, _, _, _ = timed_steps(args.steps, prof_mask=1 << dom)
-    kern = T.profile_read(dom)
-    T.profile(0)
+    # the unit whose algorithmic traffic the roofline counts: one FP32 operator
+    # apply A_{a,b} p (read p, write Ap: 8 B per DOF) on this tank's geometry,
+    # and the FP32 V-cycle, each timed as one CUDA graph of many units between
+    # two events (no per-launch events to inflate them)
+    eta0 = np.ascontiguousarray(st0[0])
+    op_ms, op_launches = T.time_kernel(eta0, eta0, w.WT_TIME_OPERATOR, w.WT_FP32, reps=400)
+    vc_ms, vc_launches = T.time_kernel(eta0, eta0, w.WT_TIME_VCYCLE, w.WT_FP32, reps=50)
 
     # ---------------- end to end through the C ABI with pinned host buffers
     host = [torch.from_numpy(a.copy()).pin_memory().numpy() for a in st0]
@@ -280,8 +287,9 @@ def run_ours(args):
     if rank != 0:
         return
     hbm, peak_src = peaks()
-    achieved = kern["bytes"] / (kern["ms"] / 1e3) / 1e9 if kern["ms"] > 0 else 0.0
-    per_launch = kern["bytes"] / max(1, kern["launches"])
+    dof = p["Nx"] * (p["Nz"] + 1)
+    op_bytes = 8.0 * dof
+    achieved = op_bytes / (op_ms / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
@@ -305,32 +313,42 @@ def run_ours(args):
                 "ms_per_step": e2e_step, "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io,
                 "note": "wt_set_state(host) + wt_step + wt_get_state(host), pinned buffers"},
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "kernel": w.KERNEL_CLASSES[dom], "achieved": achieved,
-                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                     "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
-                     "algorithmic_bytes_per_launch": per_launch,
-                     "avg_launch_us": kern["ms"] * 1e3 / max(1, kern["launches"]),
-                     "launches": kern["launches"],
-                     "timing": "CUDA events around each launch of this class on the tank's stream, "
-                               "in a second pass of the same %d steps (%.2f ms/step with the events)"
-                               % (args.steps, float(np.mean(ms_prof)))},
+        "roofline": {"bound": "hbm", "kernel": "FP32 operator apply A_{a,b} p (x-row pass, sigma columns, "
+                                                "x-row pass: %d launches)" % op_launches,
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": OP_TRAFFIC_2D,
+                     "peak_source": ("measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if peak_src == "measured"
+                                     else peak_src),
+                     "algorithmic_bytes_per_apply": op_bytes, "apply_us": op_ms * 1e3,
+                     "timing": "one CUDA-event pair around a graph of 400 applies on the tank's stream",
+                     "note": "the 1024 x 25 FP32 field (100 KB) is L2-resident; the apply is bound by "
+                             "launch and per-phase latency, not by HBM"},
+        "vcycle": {"ms": vc_ms, "launches": vc_launches, "precision": "fp32",
+                   "timing": "one CUDA-event pair around a graph of 50 V-cycles"},
         "kernel_classes_first_warmup_step": {
             w.KERNEL_CLASSES[c]: {"ms": round(cls_ms[c]["ms"], 3), "launches": cls_ms[c]["launches"],
                                   "avg_us": round(cls_ms[c]["ms"] * 1e3 / max(1, cls_ms[c]["launches"]), 2)}
             for c in range(len(cls_ms))},
+        "kernel_classes_note": "CUDA events around every launch of one warm-up step: per-launch event "
+                               "overhead inflates these times; shares only (the ncu launch list in "
+                               "profiles/ is the reference)",
         "clocks": ck,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, x, h, budget_s=args.cpu_budget)
+        line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.cpu_budget)
     if not args.no_extras:
-        line["batch"] = bench_batch(w, args)
+        line["batch"] = bench_batch(w, torch, args)
+        line["table1_cycles"] = bench_cycles(w, torch, p, h, st0)
         line["adjoint"] = bench_adjoint(w, torch, args)
         line["sea3d"] = bench_sea3d(w, torch, args)
     print(json.dumps(line), flush=True)
 
 
-def bench_batch(w, args):
-    """The batched workload: 256 uneven 2D tanks, one persistent launch per step."""
+def bench_batch(w, torch, args):
+    """The batched workload: 256 uneven 2D tanks, one persistent launch per
+    call, in the mixed form (FP32 V-cycle) and the plain FP64 form on the same
+    GPU, each timed with CUDA events on the batch's stream."""
     tanks, redrawn = si.batch_tanks()
     st, hs = [], []
     for q in tanks:
@@ -340,30 +358,48 @@ def bench_batch(w, args):
         e, u, _, ww = initial_state(q, xq, hq[None], sig)
         st.append((e, u, ww))
         hs.append(hq[None])
-    B = w.Batch([q["Nx"] for q in tanks], [q["Nz"] for q in tanks], [q["L"] for q in tanks], hs, tol=1e-10)
-    for i, s in enumerate(st):
-        B.set_state(i, *s)
     dts = [q["dt"] for q in tanks]
-    B.step(dts, 1)                                   # warm-up
-    K = max(1, min(args.steps, 3))
-    t0 = time.perf_counter()
-    B.step(dts, K)                                   # one launch for all K steps of all tanks
-    ms = (time.perf_counter() - t0) * 1e3 / K
     dof = sum(STAGES * q["Nx"] * (q["Nz"] + 1) for q in tanks)
-    its = [B.stats(i) for i in range(len(tanks))]
-    B.close()
-    return {"workload": "256 uneven 2D tanks (Nx 128-2048, Nz 8-32, Battjes-limited Stokes-2 waves "
-                        "over Gaussian bars), one persistent launch (one CTA per tank, largest first)",
-            "metric": "RK4 DOF-updates/s", "value": dof / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
-            "solves_per_s": STAGES * len(tanks) / (ms / 1e3), "steps": K, "tanks_redrawn": redrawn,
-            "krylov_iterations_per_solve": float(np.mean([a[1] / max(1, a[0]) for a in its])),
-            "timing": "host clock around one wt_batch_step call of K steps (it returns when all tanks are done)"}
+    stream = torch.cuda.current_stream()
+    K = max(1, min(args.steps, 2))
+    out = {"workload": "256 uneven 2D tanks (Nx 128-2048, Nz 8-32, Battjes-limited Stokes-2 waves "
+                       "over Gaussian bars), one persistent launch (one CTA per tank, largest first)",
+           "metric": "RK4 DOF-updates/s", "unit": UNIT, "steps": K, "tanks_redrawn": redrawn,
+           "timing": "CUDA events on the batch's stream around one wt_batch_step call of K steps"}
+    for name, mode in (("mixed", w.WT_MIXED), ("fp64", w.WT_FP64)):
+        B = w.Batch([q["Nx"] for q in tanks], [q["Nz"] for q in tanks], [q["L"] for q in tanks], hs,
+                    tol=1e-10, mode=mode)
+        B.set_stream(stream.cuda_stream)
+        for i, s_ in enumerate(st):
+            B.set_state(i, *s_)
+        B.step(dts, 1)                               # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        B.step(dts, K)                               # one launch for all K steps of all tanks
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / K
+        its = [B.stats(i) for i in range(len(tanks))]
+        B.close()
+        out[name] = {"value": dof / (ms / 1e3), "ms_per_step": ms,
+                     "solves_per_s": STAGES * len(tanks) / (ms / 1e3),
+                     "krylov_iterations_per_solve": float(np.sum([a[1] for a in its]) /
+                                                          max(1, np.sum([a[0] for a in its]))),
+                     "max_last_rel_residual": float(max(a[2] for a in its))}
+    out["value"] = out["mixed"]["value"]
+    out["ms_per_step"] = out["mixed"]["ms_per_step"]
+    out["solves_per_s"] = out["mixed"]["solves_per_s"]
+    out["mixed_over_fp64_solves"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    return out
 
 
 def bench_sea3d(w, torch, args):
     """The 3D directional sea: 256 x 256 x 16, 4096 JONSWAP components, mixed solver."""
     N, Nz, L = 256, 16, 64.0
     T = w.Tank(N, N, Nz, L, np.ones((N, N)), mode=w.WT_MIXED, tol=1e-10, filter=1, omega=0.6, max_it=400)
+    stream = torch.cuda.current_stream()
+    T.set_stream(stream.cuda_stream)
     _, _, sigma = T.grid()
     sea = si.jonswap_sea(seed=3, L=L, ncomp=4096, kp=1.5, hs_over_lp=0.02)
     eta0, u0, v0, w0 = si.jonswap_fields(sea, N, sigma)
@@ -372,31 +408,70 @@ def bench_sea3d(w, torch, args):
     T.step(dt, 1)                                    # warm-up (graph capture)
     K = 2
     s0, i0 = T.stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    e0.record(stream)
     T.step(dt, K)
+    e1.record(stream)
     torch.cuda.synchronize()
-    ms = (time.perf_counter() - t0) * 1e3 / K
+    ms = e0.elapsed_time(e1) / K
     s1, i1 = T.stats()
-    # one more step with CUDA events around every launch, per kernel class
-    T.profile((1 << len(w.KERNEL_CLASSES)) - 1)
-    T.step(dt, 1)
-    cls = [T.profile_read(c) for c in range(len(w.KERNEL_CLASSES))]
-    T.profile(0)
+    eta_now = np.ascontiguousarray(T.get_state()[0])
+    op_ms, op_launches = T.time_kernel(eta_now, eta_now, w.WT_TIME_OPERATOR, w.WT_FP32, reps=100)
+    vc_ms, vc_launches = T.time_kernel(eta_now, eta_now, w.WT_TIME_VCYCLE, w.WT_FP32, reps=10)
     T.close()
-    dom = int(np.argmax([c["ms"] for c in cls]))
     hbm, _ = peaks()
-    ach = cls[dom]["bytes"] / (cls[dom]["ms"] / 1e3) / 1e9 if cls[dom]["ms"] > 0 else 0.0
-    dof = STAGES * N * N * (Nz + 1)
+    dof1 = N * N * (Nz + 1)
+    ach = 8.0 * dof1 / (op_ms / 1e3) / 1e9
     return {"workload": "3D directional JONSWAP sea, 256 x 256 x 16, L = 64, 4096 components, filter on, "
                         "mixed solver at 1e-10, omega 0.6",
-            "metric": "RK4 DOF-updates/s", "value": dof / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "metric": "RK4 DOF-updates/s", "value": STAGES * dof1 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "solves_per_s": STAGES / (ms / 1e3),
             "krylov_iterations_per_solve": (i1 - i0) / max(1, s1 - s0), "steps": K,
-            "roofline": {"bound": "hbm", "kernel": w.KERNEL_CLASSES[dom], "achieved": ach, "peak": hbm,
-                         "unit": "GB/s", "frac": ach / hbm, "traffic": None,
-                         "timing": "CUDA events around each launch of the class in one profiled step"},
-            "kernel_classes_ms": {w.KERNEL_CLASSES[c]: round(cls[c]["ms"], 2) for c in range(len(cls))},
-            "timing": "host clock around wt_step of K steps (returns after the step)"}
+            "roofline": {"bound": "hbm", "kernel": "FP32 operator apply A_{a,b} p (%d launches)" % op_launches,
+                         "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                         "traffic": OP_TRAFFIC_3D, "algorithmic_bytes_per_apply": 8.0 * dof1,
+                         "apply_us": op_ms * 1e3,
+                         "timing": "one CUDA-event pair around a graph of 100 applies"},
+            "vcycle": {"ms": vc_ms, "launches": vc_launches, "precision": "fp32"},
+            "timing": "CUDA events on the tank's stream around wt_step of K steps"}
+
+
+def bench_cycles(w, torch, p, h, st0):
+    """Table 1's comparison on the benchmark tank's geometry: iterations and
+    device time per solve for V-cycle + GMRES and FMG + GMRES (Algorithms 1
+    and 2 as the preconditioner) at relative residuals 1e-4, 1e-8, 1e-12, in
+    the mixed and the FP64 form, on a seeded right-hand side."""
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    eta = torch.from_numpy(np.ascontiguousarray(st0[0])).to(dev)
+    shape = (p["Nz"] + 1, 1, p["Nx"])
+    b = torch.from_numpy(si.rng(5).standard_normal(shape)).to(dev)
+    out = {"workload": "one mixed-stage Poisson problem on the 1024 x 24 bar geometry (seeded N(0,1) "
+                       "right-hand side, zero initial guess)",
+           "timing": "CUDA events on the tank's stream, median of 3 solves"}
+    for mname, mode in (("mixed", w.WT_MIXED), ("fp64", w.WT_FP64)):
+        for cname, cyc in (("vcycle", 0), ("fmg", 1)):
+            T = w.Tank(p["Nx"], 1, p["Nz"], p["L"], h, mode=mode, cycle=cyc, max_it=400)
+            T.set_stream(stream.cuda_stream)
+            row = {}
+            for tol in (1e-4, 1e-8, 1e-12):
+                x = torch.zeros(shape, dtype=torch.float64, device=dev)
+                _, info = T.poisson_solve(eta, eta, b, x, tol=tol, raise_noconv=False)   # warm-up
+                ms = []
+                for _ in range(3):
+                    x.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    _, info = T.poisson_solve(eta, eta, b, x, tol=tol, raise_noconv=False)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                row["%.0e" % tol] = {"iterations": info.iterations, "ms": float(np.median(ms)),
+                                     "rel_residual": info.rel_residual}
+            T.close()
+            out["%s_%s" % (mname, cname)] = row
+    return out
 
 
 def bench_adjoint(w, torch, args):
@@ -466,9 +541,30 @@ def cpu_baseline(p, x, h, budget_s=15.0):
             break
     el = time.perf_counter() - t0
     dof = p["Nx"] * (p["Nz"] + 1)
-    return {"value": n * dof / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d Runge-Kutta stage(s) of the first step (%.1f s, numpy float64, one thread)"
-                      % (n, el)}
+    threads = int(os.environ.get("OPENBLAS_NUM_THREADS", "1"))
+    return {"value": n * dof / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d Runge-Kutta stage(s) of the first step (%.1f s, numpy float64, %d BLAS thread(s))"
+                      % (n, el, threads)}
+
+
+def cpu_baseline_all_cores(budget_s):
+    """The same oracle sample with numpy's BLAS on every host core (a fresh
+    interpreter started with the thread counts set, since they are fixed at
+    import)."""
+    nproc = os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS=str(nproc), OPENBLAS_NUM_THREADS=str(nproc),
+               MKL_NUM_THREADS=str(nproc))
+    code = ("import json, bench; p, x, h = bench.workload(); "
+            "print(json.dumps(bench.cpu_baseline(p, x, h, budget_s=%r)))" % budget_s)
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=600)
+        out = json.loads(r.stdout.strip().splitlines()[-1])
+        out["cores"] = nproc
+        out["nproc"] = nproc
+        return out
+    except Exception as e:          # report, do not fail the benchmark line
+        return {"error": "all-cores oracle run failed: %s" % e, "nproc": nproc}
 
 
 def run_reference(args):

@@ -107,6 +107,11 @@ typedef struct wt_options {
                         abort word and the call returns WT_ETIMEOUT (the
                         barrier is then reset and the tank stays usable);
                         0: the default 2e9 (about one second)               */
+  int cycle;         /* preconditioner of the Krylov solver: 0 = one V-cycle
+                        (Algorithm 1, default); 1 = one full-multigrid cycle
+                        (Algorithm 2: the right-hand side restricted to every
+                        level, the coarsest solved, and on each finer level a
+                        V-cycle from the prolongated coarse result)         */
 } wt_options;
 
 typedef struct wt_solve_info {
@@ -169,7 +174,9 @@ int wt_apply_operator(wt_tank* t, const double* eta_a, const double* eta_b,
 
 /*
  * z = M^{-1} r: one p-multigrid V-cycle (Algorithm 1) from a zero initial
- * state, damped block-Jacobi smoothing, spectral transfers (Sec. 4.2-4.3).
+ * state - or one full-multigrid cycle (Algorithm 2) when the option cycle is
+ * 1 - with damped block-Jacobi smoothing and spectral transfers
+ * (Sec. 4.2-4.3).
  * precision: WT_FP64 or WT_FP32.  Test hook for the preconditioner.
  */
 int wt_precondition(wt_tank* t, const double* eta_a, const double* eta_b,
@@ -242,7 +249,7 @@ int wt_adjoint_step(wt_tank* t, double dt, const double* eta, const double* u, c
  * 128}, and mode in {WT_MIXED, WT_REFINE} unless the tank is in WT_FP64 - one
  * warm-up solve plus the median of reps (1..100) timed solves each, and keeps
  * the fastest setting that reaches the tolerance; then, on that setting, the
- * V-cycle's launch schedule (tail_max 2048 or 8192 with tail_cluster 0 or
+ * full-multigrid cycle (cycle = 1) and the V-cycle's launch schedule (tail_max 2048 or 8192 with tail_cluster 0 or
  * 16, or vcycle_grid = 1).  The paper leaves these
  * choices open (Sec. 4.1).  On success the tank uses the winner, *best holds
  * it, *best_ms its median time and *entry_ms that of the options on entry
@@ -262,11 +269,13 @@ int wt_autotune_step(wt_tank* t, double dt, int reps, wt_options* best, double* 
  * persistent kernel launch per wt_batch_step: one CTA owns one tank and runs
  * all of its Runge-Kutta stages (free surface, metric, smoother set-up,
  * forcing, mixed-stage Poisson solve with FP64 flexible GMRES and the FP32
- * p-multigrid V-cycle, projection); the largest tanks start first.
+ * or FP64 p-multigrid V-cycle, projection); the largest tanks start first.
  * wt_create_batch: tank i has Nx[i], Nz[i], L[i] and bathymetry[i] ([Nx[i]],
  * host or device), Ny = 1; g and nu as in wt_create.  Each tank's coarsest
  * level must have at most 64 unknowns.  The batch owns its tanks.
- * wt_batch_set_options applies one option set to every tank (WT_MIXED only).
+ * wt_batch_set_options applies one option set to every tank: WT_MIXED (FP64
+ * GMRES, FP32 V-cycle; the default) or WT_FP64 (FP64 GMRES, FP64 V-cycle, the
+ * plain method); WT_REFINE returns WT_ENOTSUP.
  * wt_batch_set_state / get_state: tank i's eta [Nx], u, w [Nz+1][Nx].
  * wt_batch_step: nsteps full steps, dt[i] for tank i (host array); returns
  * after all tanks finished; WT_EBREAK / WT_ENOCONV if any tank failed.
@@ -282,6 +291,10 @@ int wt_batch_set_state(wt_batch* b, int i, const double* eta, const double* u, c
 int wt_batch_get_state(const wt_batch* b, int i, double* eta, double* u, double* w, double* time);
 int wt_batch_step(wt_batch* b, const double* dt, int nsteps);
 int wt_batch_stats(const wt_batch* b, int i, long* solves, long* iterations, double* last_rel);
+/* Launch later wt_batch_step calls on the given cudaStream_t (passed as
+ * void*; NULL returns to the batch's own stream), e.g. to bracket them with
+ * the caller's CUDA events.  The call still returns after the step. */
+int wt_batch_set_stream(wt_batch* b, void* stream);
 int wt_batch_destroy(wt_batch* b);
 
 /*
@@ -311,6 +324,23 @@ int wt_profile(wt_tank* t, unsigned mask);
 int wt_profile_read(wt_tank* t, int kernel_class, double* ms, long* launches, double* bytes,
                     double* flops);
 int wt_get_launches(const wt_tank* t, long* launches);
+
+/*
+ * Device time of one unit of the solve, for roofline measurements (no
+ * counterpart in the paper).  With the geometry of (eta_a, eta_b) set up as
+ * for a solve, reps back-to-back units on a fixed input are captured into one
+ * CUDA graph, replayed once to warm up and once between two CUDA events on
+ * the tank's stream: *ms_per_call = elapsed / reps, *launches_per_call (may
+ * be NULL) = kernels per unit.  No per-launch events, so the figure is not
+ * inflated by event overhead.  what: WT_TIME_OPERATOR (Ap = A_{a,b} p on the
+ * finest level, Eq. poissonp: the unit whose algorithmic traffic is read p +
+ * write Ap) or WT_TIME_VCYCLE (one V-cycle, Algorithm 1).  precision:
+ * WT_FP64 or WT_FP32.  reps in [1, 10000].  WT_EINVAL while wt_profile
+ * timing is on.
+ */
+enum wt_time_unit { WT_TIME_OPERATOR = 0, WT_TIME_VCYCLE = 1 };
+int wt_time_kernel(wt_tank* t, const double* eta_a, const double* eta_b, int what, int precision, int reps,
+                   double* ms_per_call, long* launches_per_call);
 
 /*
  * Allocation-free operator apply (the paper has no counterpart; this is a

@@ -32,7 +32,8 @@ class wt_options(ctypes.Structure):
                 ("filter", ctypes.c_int), ("linear", ctypes.c_int), ("coarsest_max", ctypes.c_int),
                 ("bc_transfer", ctypes.c_int), ("tail_max", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_ir", ctypes.c_int), ("vcycle_grid", ctypes.c_int),
-                ("tail_cluster", ctypes.c_int), ("barrier_cycles", ctypes.c_longlong)]
+                ("tail_cluster", ctypes.c_int), ("barrier_cycles", ctypes.c_longlong),
+                ("cycle", ctypes.c_int)]
 
 
 class wt_solve_info(ctypes.Structure):
@@ -85,6 +86,8 @@ def _load():
         "wt_batch_stats": [P, I, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long),
                            ctypes.POINTER(D)],
         "wt_batch_destroy": [P],
+        "wt_batch_set_stream": [P, P],
+        "wt_time_kernel": [P, P, P, I, I, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long)],
         "wt_last_error": [ctypes.c_char_p, ctypes.c_size_t],
     }
     for name, args in sig.items():
@@ -248,6 +251,16 @@ def wt_apply_operator_static(Nx, Nz, L, h, eta_a, eta_b, p, Ap, stream_handle=0)
                                          _ptr(p), _ptr(Ap), ctypes.c_void_p(int(stream_handle)))
 
 
+WT_TIME_OPERATOR, WT_TIME_VCYCLE = 0, 1
+
+
+def wt_time_kernel(t, eta_a, eta_b, what, precision, reps):
+    ms, n = ctypes.c_double(), ctypes.c_long()
+    st = _lib.wt_time_kernel(t, _ptr(eta_a), _ptr(eta_b), int(what), int(precision), int(reps),
+                             ctypes.byref(ms), ctypes.byref(n))
+    return st, ms.value, n.value
+
+
 def wt_set_bathymetry(t, h):
     return _lib.wt_set_bathymetry(t, _ptr(h))
 
@@ -324,6 +337,10 @@ def wt_batch_stats(b, i):
 
 def wt_batch_destroy(b):
     return _lib.wt_batch_destroy(b)
+
+
+def wt_batch_set_stream(b, stream_handle):
+    return _lib.wt_batch_set_stream(b, ctypes.c_void_p(int(stream_handle)))
 
 
 def wt_get_launches(t):
@@ -472,6 +489,13 @@ class Tank:
         _check(st)
         return dict(ms=ms, launches=n, bytes=b, flops=f)
 
+    def time_kernel(self, eta_a, eta_b, what=WT_TIME_OPERATOR, precision=WT_FP32, reps=200):
+        """(ms per unit, kernels per unit) of the operator apply or the V-cycle,
+        timed as one CUDA graph of `reps` units between two events."""
+        st, ms, n = wt_time_kernel(self.handle, eta_a, eta_b, what, precision, reps)
+        _check(st)
+        return ms, n
+
     def launches(self):
         st, n = wt_get_launches(self.handle)
         _check(st)
@@ -533,6 +557,9 @@ class Batch:
     def step(self, dt, nsteps=1):
         dt = np.broadcast_to(np.asarray(dt, dtype=np.float64), (len(self),))
         _check(wt_batch_step(self.handle, dt, nsteps))
+
+    def set_stream(self, stream_handle):
+        _check(wt_batch_set_stream(self.handle, stream_handle))
 
     def stats(self, i):
         st, s, it, r = wt_batch_stats(self.handle, i)

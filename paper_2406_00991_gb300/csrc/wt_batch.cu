@@ -5,8 +5,10 @@
 // (Eq. kinematicFS), the sigma metric of every multigrid level (Eq. 1_Scoef),
 // the smoother's block inverses and the coarsest inverse, the forcing and
 // right-hand side (Eq. forc1, poissonp, bcpdneu), the mixed-stage Poisson
-// solve - FP64 flexible GMRES (Sec. 4.4) preconditioned by the FP32
-// p-multigrid V-cycle (Algorithm 1) - and the projection (Eq. rkforc1).
+// solve - FP64 flexible GMRES (Sec. 4.4) preconditioned by the p-multigrid
+// V-cycle (Algorithm 1) in FP32 (mixed form) or in FP64 (plain form: every
+// level, smoother block and transfer in FP64) - and the projection
+// (Eq. rkforc1).
 // Tanks are launched in decreasing order of size (longest-processing-time
 // first) so the large ones start first.  The phases are the device bodies of
 // wt_dev.cuh / wt_cta.cuh; no CTA waits on another.
@@ -77,7 +79,10 @@ __device__ void cta_update(double* w, const double* V, long ld, int nvec, long n
   __syncthreads();
 }
 
-// FP64 flexible GMRES(m) with the FP32 V-cycle as preconditioner, in this CTA.
+// FP64 flexible GMRES(m) with the V-cycle as preconditioner, in this CTA:
+// the FP32 V-cycle on the rounded Arnoldi vector (P64 = false) or the FP64
+// V-cycle on the vector itself (P64 = true).
+template <bool P64>
 __device__ void fgmres_cta(const BatchTankDesc& B, const double* b, double* x, int smem,
                            unsigned char* sm, KrylovSmem& K) {
   const TailLevel<double>& F = B.lv64[0];
@@ -123,11 +128,28 @@ __device__ void fgmres_cta(const BatchTankDesc& B, const double* b, double* x, i
         double* vj = V + (long)j * n;
         double* zj = Z + (long)j * n;
         double* w = V + (long)(j + 1) * n;
-        for (long e = threadIdx.x; e < n; e += blockDim.x) B.b32[e] = (float)vj[e];
-        __syncthreads();
-        vcycle_cta<float, 2>(A, sm);                              // e32 = M^{-1} v_j (FP32)
-        for (long e = threadIdx.x; e < n; e += blockDim.x) zj[e] = (double)B.e32[e];
-        __syncthreads();
+        if (P64) {
+          TailArgs<double> A64;
+          A64.lv = B.lv64;
+          A64.l0 = 0;
+          A64.nl = B.nl;
+          A64.f0 = vj;
+          A64.x0 = zj;
+          A64.f0_nyq = 1;
+          A64.omega = B.omega;
+          A64.nu1 = B.nu1;
+          A64.nu2 = B.nu2;
+          A64.AinvT = B.AinvT;
+          A64.smem = smem;
+          vcycle_cta<double, 2>(A64, sm);                         // z_j = M^{-1} v_j (FP64)
+          __syncthreads();
+        } else {
+          for (long e = threadIdx.x; e < n; e += blockDim.x) B.b32[e] = (float)vj[e];
+          __syncthreads();
+          vcycle_cta<float, 2>(A, sm);                            // e32 = M^{-1} v_j (FP32)
+          for (long e = threadIdx.x; e < n; e += blockDim.x) zj[e] = (double)B.e32[e];
+          __syncthreads();
+        }
         t_apply_op<double, 2>(F, zj, w, nullptr, false, smem, sm);   // w = A z_j
         cta_dots(w, V, n, j + 1, n, false, K);                    // classical Gram-Schmidt, twice
         if (threadIdx.x <= j) K.H[j * (m + 1) + threadIdx.x] = K.h[threadIdx.x];
@@ -199,6 +221,7 @@ __device__ RowPass<double> pass64(const BatchTankDesc& B, const double* in, doub
 
 // One Runge-Kutta stage k of one tank (the same sequence as the host-driven
 // stage in wt_capi.cu, linear = free-surface and advection terms dropped).
+template <bool P64>
 __device__ void stage_cta(const BatchTankDesc& B, int k, double dt, int smem, unsigned char* sm,
                           KrylovSmem& K) {
   const double a = c_alpha[k - 1], b = c_beta[k - 1];
@@ -245,15 +268,24 @@ __device__ void stage_cta(const BatchTankDesc& B, int k, double dt, int smem, un
     metric_body(t0, ts, V.ncols, S.h, S.hx, nullptr, S.ea, S.eax, nullptr, S.eb, S.ebx, nullptr,
                 const_cast<double*>(V.meta), B.flag);
     __syncthreads();
-    float* m32 = const_cast<float*>(B.lv32[l].V.meta);
-    for (long i = t0; i < (long)kMeta * V.ncols; i += ts) m32[i] = (float)V.meta[i];
-    __syncthreads();
+    if (!P64) {
+      float* m32 = const_cast<float*>(B.lv32[l].V.meta);
+      for (long i = t0; i < (long)kMeta * V.ncols; i += ts) m32[i] = (float)V.meta[i];
+      __syncthreads();
+    }
   }
   for (int l = 0; l + 1 < B.nl; ++l) {
-    const TailLevel<float>& L = B.lv32[l];
-    const int per_warp = L.V.M1 * (2 * L.V.M1 + 1) * (int)sizeof(float);
-    blockinv_body<float>(L.V, const_cast<float*>(L.Binv), L.nclass, L.cxx, L.cyy, B.flag, 0, 1,
-                         smem / per_warp, sm);
+    if (P64) {
+      const TailLevel<double>& L = B.lv64[l];
+      const int per_warp = L.V.M1 * (2 * L.V.M1 + 1) * (int)sizeof(double);
+      blockinv_body<double>(L.V, const_cast<double*>(L.Binv), L.nclass, L.cxx, L.cyy, B.flag, 0, 1,
+                            smem / per_warp, sm);
+    } else {
+      const TailLevel<float>& L = B.lv32[l];
+      const int per_warp = L.V.M1 * (2 * L.V.M1 + 1) * (int)sizeof(float);
+      blockinv_body<float>(L.V, const_cast<float*>(L.Binv), L.nclass, L.cxx, L.cyy, B.flag, 0, 1,
+                           smem / per_warp, sm);
+    }
     __syncthreads();
   }
   coarse_factor_body(B.lv64[B.nl - 1].V, B.cDx, B.cDy, B.AinvT, B.flag, sm);
@@ -279,7 +311,7 @@ __device__ void stage_cta(const BatchTankDesc& B, int k, double dt, int smem, un
   colmat_body<double>(Dm, M1, M1, ws, Dws, nc, 0, 0, 1, sm);
   stage_rhs_body(t0, ts, sa, us, nullptr, ws, usx, nullptr, Dus, nullptr, Dws, rhs);
   __syncthreads();
-  fgmres_cta(B, rhs, B.p, smem, sm, K);
+  fgmres_cta<P64>(B, rhs, B.p, smem, sm, K);
   // projection
   t_rowpass(pass64(B, B.p, px, M1, Nx, lx, Nx, lx, XOP_DERIV), smem, sm);
   colmat_body<double>(Dm, M1, M1, B.p, Dp, nc, 0, 0, 1, sm);
@@ -290,6 +322,7 @@ __device__ void stage_cta(const BatchTankDesc& B, int k, double dt, int smem, un
   (void)n;
 }
 
+template <bool P64>
 __global__ void __launch_bounds__(512) k_batch_step(const BatchTankDesc* descs, const int* order,
                                                     const double* dt, int nsteps, int smem) {
   extern __shared__ __align__(16) unsigned char sm[];
@@ -297,14 +330,18 @@ __global__ void __launch_bounds__(512) k_batch_step(const BatchTankDesc* descs, 
   const int tank = order[blockIdx.x];
   const BatchTankDesc& B = descs[tank];
   for (int s = 0; s < nsteps; ++s)
-    for (int k = 1; k <= 5; ++k) stage_cta(B, k, dt[tank], smem, sm, K);
+    for (int k = 1; k <= 5; ++k) stage_cta<P64>(B, k, dt[tank], smem, sm, K);
 }
 
 cudaError_t launch_batch_step(const BatchTankDesc* descs, const int* order, int ntanks, const double* dt,
-                              int nsteps, int smem, cudaStream_t s) {
-  cudaError_t e = ensure_dyn_smem((const void*)k_batch_step, (size_t)smem);
+                              int nsteps, int smem, int fp64, cudaStream_t s) {
+  const void* fn = fp64 ? (const void*)k_batch_step<true> : (const void*)k_batch_step<false>;
+  cudaError_t e = ensure_dyn_smem(fn, (size_t)smem);
   if (e != cudaSuccess) return e;
-  k_batch_step<<<ntanks, 512, smem, s>>>(descs, order, dt, nsteps, smem);
+  if (fp64)
+    k_batch_step<true><<<ntanks, 512, smem, s>>>(descs, order, dt, nsteps, smem);
+  else
+    k_batch_step<false><<<ntanks, 512, smem, s>>>(descs, order, dt, nsteps, smem);
   return cudaGetLastError();
 }
 

@@ -322,6 +322,7 @@ int check_options(const wt_options& o) {
   if (o.coarsest_max < 1 || o.coarsest_max > 128) return fail(WT_EINVAL, "coarsest_max must be in [1, 128]");
   if (o.tail_max < 0) return fail(WT_EINVAL, "tail_max must be >= 0");
   if (o.barrier_cycles < 0) return fail(WT_EINVAL, "barrier_cycles must be >= 0");
+  if (o.cycle != 0 && o.cycle != 1) return fail(WT_EINVAL, "cycle must be 0 (V-cycle) or 1 (full multigrid)");
   if ((o.filter != 0 && o.filter != 1) || (o.linear != 0 && o.linear != 1) ||
       (o.bc_transfer != 0 && o.bc_transfer != 1))
     return fail(WT_EINVAL, "filter, linear, bc_transfer are 0 or 1");
@@ -561,6 +562,7 @@ int wt_default_options(wt_options* o) {
   o->vcycle_grid = 0;
   o->tail_cluster = 0;
   o->barrier_cycles = 0;
+  o->cycle = 0;
   return WT_OK;
 }
 
@@ -815,6 +817,75 @@ int wt_apply_operator(wt_tank* t, const double* eta_a, const double* eta_b, cons
   });
 }
 
+int wt_time_kernel(wt_tank* t, const double* eta_a, const double* eta_b, int what, int precision, int reps,
+                   double* ms_per_call, long* launches_per_call) {
+  if (!t || !eta_a || !eta_b || !ms_per_call) return fail(WT_EINVAL, "NULL argument");
+  if (precision != WT_FP64 && precision != WT_FP32) return fail(WT_EINVAL, "precision must be WT_FP64 or WT_FP32");
+  if (what != WT_TIME_OPERATOR && what != WT_TIME_VCYCLE) return fail(WT_EINVAL, "unknown unit to time");
+  if (reps < 1 || reps > 10000) return fail(WT_EINVAL, "reps must be in [1, 10000]");
+  if (t->prof.mask != 0) return fail(WT_EINVAL, "per-launch timing (wt_profile) is on");
+  return guarded([&]() -> int {
+    enter(*t);
+    const long n = t->n;
+    const double* ea = in_dev(*t, eta_a, t->io_s1, t->ncols);
+    const double* eb = in_dev(*t, eta_b, t->io_s2, t->ncols);
+    setup_geometry(*t, ea, eb, precision, what == WT_TIME_VCYCLE, what == WT_TIME_VCYCLE);
+    // a smooth non-zero input (the timing does not depend on its values)
+    std::vector<double> hx(n);
+    for (long i = 0; i < n; ++i) hx[i] = std::sin(0.001 * (double)i) + 0.5;
+    WT_CK(cudaMemcpyAsync(t->b64, hx.data(), sizeof(double) * n, cudaMemcpyHostToDevice, t->s));
+    WT_CK((launch_convert<double, float>(t->b64, t->b32, n, nullptr, 0, t->s)));
+    auto unit = [&]() {
+      if (what == WT_TIME_OPERATOR) {
+        if (precision == WT_FP64) apply_op<double>(*t, 0, t->b64, t->x64, nullptr, false);
+        else apply_op<float>(*t, 0, t->b32, t->e32, nullptr, false);
+      } else {
+        if (precision == WT_FP64) mg_cycle<double>(*t, t->b64, t->x64);
+        else mg_cycle<float>(*t, t->b32, t->e32);
+      }
+    };
+    unit();                                   // warm-up (and any one-time set-up)
+    WT_CK(cudaStreamSynchronize(t->s));
+    const long l0 = t->prof.launches;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    WT_CK(cudaStreamBeginCapture(t->s, cudaStreamCaptureModeThreadLocal));
+    try {
+      for (int r = 0; r < reps; ++r) unit();
+    } catch (...) {
+      cudaStreamEndCapture(t->s, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    WT_CK(cudaStreamEndCapture(t->s, &graph));
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    WT_CK(ei);
+    const long per = (t->prof.launches - l0) / reps;
+    t->prof.launches = l0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = 0.f;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, t->s);          // warm replay
+    if (e == cudaSuccess) e = cudaEventRecord(e0, t->s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, t->s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, t->s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaGraphExecDestroy(exec);
+    WT_CK(e);
+    t->prof.launches += 2 * per * reps;
+    *ms_per_call = (double)ms / reps;
+    if (launches_per_call) *launches_per_call = per;
+    const int fl = read_flags(*t);
+    if (fl) return fail(WT_EBREAK, "water depth d <= 0 or non-finite surface");
+    return WT_OK;
+  });
+}
+
 int wt_precondition(wt_tank* t, const double* eta_a, const double* eta_b, const double* r, double* z,
                     int precision) {
   if (!t || !eta_a || !eta_b || !r || !z) return fail(WT_EINVAL, "NULL argument");
@@ -828,11 +899,11 @@ int wt_precondition(wt_tank* t, const double* eta_a, const double* eta_b, const 
     const double* rd = in_dev(*t, r, t->io_f1, n);
     if (precision == WT_FP64) {
       WT_CK(cudaMemcpyAsync(t->b64, rd, sizeof(double) * n, cudaMemcpyDeviceToDevice, t->s));
-      vcycle<double>(*t, 0, t->b64, t->x64);
+      mg_cycle<double>(*t, t->b64, t->x64);
       out_copy(*t, z, t->x64, n);
     } else {
       WT_LAUNCH(*t, K_KRYLOV, 12.0 * n, 0.0, (launch_convert<double, float>(rd, t->b32, n, nullptr, 0, t->s)));
-      vcycle<float>(*t, 0, t->b32, t->e32);
+      mg_cycle<float>(*t, t->b32, t->e32);
       WT_LAUNCH(*t, K_KRYLOV, 12.0 * n, 0.0, (launch_convert<float, double>(t->e32, t->io_f2, n, nullptr, 0, t->s)));
       out_copy(*t, z, t->io_f2, n);
     }
@@ -1072,7 +1143,8 @@ struct wt_batch {
   int* d_order = nullptr;
   double* d_dt = nullptr;
   double* d_stats = nullptr;      // 4 doubles per tank
-  cudaStream_t s = nullptr;
+  cudaStream_t s = nullptr;       // the stream launches go to (own_s unless the caller set one)
+  cudaStream_t own_s = nullptr;
   int smem = 96 * 1024;
   std::vector<int> order;
 };
@@ -1109,10 +1181,11 @@ void fill_desc(wt_batch& b) {
 // the smoother per warp.
 int check_batch_tank(const wt_tank& t, int smem) {
   if (t.Ny != 1) return fail(WT_EINVAL, "batched tanks are 2D (Ny = 1)");
-  if (t.opt.mode != WT_MIXED) return fail(WT_ENOTSUP, "batched tanks run the mixed solver only");
+  if (t.opt.mode != WT_MIXED && t.opt.mode != WT_FP64)
+    return fail(WT_ENOTSUP, "batched tanks run the mixed or the FP64 solver (not WT_REFINE)");
   const size_t row = (2 * (size_t)t.Nx + t.Nx / 2) * 2 * sizeof(double);
   const size_t coarse = (size_t)t.ncoarse * (t.ncoarse + 1) * sizeof(double) + (t.ncoarse + 1) * sizeof(int);
-  const size_t blk = (size_t)t.M1 * (2 * t.M1 + 1) * sizeof(float);
+  const size_t blk = (size_t)t.M1 * (2 * t.M1 + 1) * (t.opt.mode == WT_FP64 ? sizeof(double) : sizeof(float));
   if (row > (size_t)smem) return fail(WT_ENOTSUP, "batched tanks need Nx <= 2048");
   if (coarse > (size_t)smem) return fail(WT_ENOTSUP, "batched tank's coarsest level is too large (coarsest_max)");
   if (blk > (size_t)smem) return fail(WT_ENOTSUP, "batched tank's Nz is too large");
@@ -1143,7 +1216,8 @@ int wt_create_batch(int ntanks, const int* Nx, const int* Nz, const double* L, d
     }
   }
   const int rc = guarded([&]() -> int {
-    WT_CK(cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking));
+    WT_CK(cudaStreamCreateWithFlags(&b->own_s, cudaStreamNonBlocking));
+    b->s = b->own_s;
     b->d_desc = b->ar.alloc<BatchTankDesc>(ntanks);
     b->d_order = b->ar.alloc<int>(ntanks);
     b->d_dt = b->ar.alloc<double>(ntanks);
@@ -1160,7 +1234,7 @@ int wt_create_batch(int ntanks, const int* Nx, const int* Nz, const double* L, d
   });
   if (rc != WT_OK) {
     for (wt_tank* q : b->tanks) wt_destroy(q);
-    if (b->s) cudaStreamDestroy(b->s);
+    if (b->own_s) cudaStreamDestroy(b->own_s);
     return rc;
   }
   *out = b.release();
@@ -1169,7 +1243,8 @@ int wt_create_batch(int ntanks, const int* Nx, const int* Nz, const double* L, d
 
 int wt_batch_set_options(wt_batch* b, const wt_options* o) {
   if (!b || !o) return fail(WT_EINVAL, "NULL argument");
-  if (o->mode != WT_MIXED) return fail(WT_ENOTSUP, "batched tanks run the mixed solver only");
+  if (o->mode != WT_MIXED && o->mode != WT_FP64)
+    return fail(WT_ENOTSUP, "batched tanks run the mixed or the FP64 solver (not WT_REFINE)");
   for (wt_tank* t : b->tanks) {
     const int st = wt_set_options(t, o);
     if (st != WT_OK) return st;
@@ -1206,7 +1281,8 @@ int wt_batch_step(wt_batch* b, const double* dt, int nsteps) {
     fill_desc(*b);
     for (wt_tank* t : b->tanks) WT_CK(cudaStreamSynchronize(t->s));   // pending state uploads
     WT_CK(cudaMemcpyAsync(b->d_dt, dt, sizeof(double) * nt, cudaMemcpyHostToDevice, b->s));
-    WT_CK(launch_batch_step(b->d_desc, b->d_order, nt, b->d_dt, nsteps, b->smem, b->s));
+    const int fp64 = b->tanks[0]->opt.mode == WT_FP64;   // one option set for every tank
+    WT_CK(launch_batch_step(b->d_desc, b->d_order, nt, b->d_dt, nsteps, b->smem, fp64, b->s));
     WT_CK(cudaStreamSynchronize(b->s));
     int bad = 0;
     for (int i = 0; i < nt; ++i) {
@@ -1239,9 +1315,18 @@ int wt_batch_destroy(wt_batch* b) {
   if (!b) return WT_OK;
   if (b->s) cudaStreamSynchronize(b->s);
   for (wt_tank* t : b->tanks) wt_destroy(t);
-  if (b->s) cudaStreamDestroy(b->s);
+  if (b->own_s) cudaStreamDestroy(b->own_s);
   delete b;
   return WT_OK;
+}
+
+int wt_batch_set_stream(wt_batch* b, void* stream) {
+  if (!b) return fail(WT_EINVAL, "NULL batch");
+  return guarded([&]() -> int {
+    WT_CK(cudaStreamSynchronize(b->s));
+    b->s = stream ? static_cast<cudaStream_t>(stream) : b->own_s;
+    return WT_OK;
+  });
 }
 
 int wt_destroy(wt_tank* t) {

@@ -247,17 +247,15 @@ __device__ inline bool grid_sync(GridBar* b, int* flag) {
       const long long t0 = clock64();
       unsigned polls = 0;
       while (ld_acquire_u64(&b->count) < target) {
-        if ((++polls & 63u) == 0u) {
-          if (ld_relaxed_s32(&b->abort)) {
-            ok = 0;
-            break;
-          }
-          if (clock64() - t0 > lim) {
-            atomicExch(&b->abort, 1);
-            atomicOr(flag, 32);
-            ok = 0;
-            break;
-          }
+        if (clock64() - t0 > lim) {
+          atomicExch(&b->abort, 1);
+          atomicOr(flag, 32);
+          ok = 0;
+          break;
+        }
+        if ((++polls & 63u) == 0u && ld_relaxed_s32(&b->abort)) {
+          ok = 0;
+          break;
         }
       }
     } else if (ld_relaxed_s32(&b->abort)) {

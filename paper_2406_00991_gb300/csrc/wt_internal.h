@@ -220,8 +220,9 @@ struct BatchTankDesc {
   double tol, omega;
   int nu1, nu2, restart, max_it, filter, linear;
 };
+// fp64: the FP64 V-cycle as preconditioner (plain form), else the FP32 one.
 cudaError_t launch_batch_step(const BatchTankDesc* descs, const int* order, int ntanks, const double* dt,
-                              int nsteps, int smem, cudaStream_t s);
+                              int nsteps, int smem, int fp64, cudaStream_t s);
 template <typename T>
 struct TailArgs {
   const TailLevel<T>* lv;   // device array, all levels of the hierarchy

@@ -353,12 +353,16 @@ static int tail_level(wt_tank& t, bool tr) {
   return -1;
 }
 
+// x0_given: x holds an initial state (the full-multigrid cycle), so the
+// first smoothing sweep works on the residual f - A x instead of assuming
+// x = 0, and the one-launch schedules (which assume x = 0) are not used at
+// this level.
 template <typename T>
-void vcycle(wt_tank& t, int l, const T* f, T* x, bool tr) {
+void vcycle(wt_tank& t, int l, const T* f, T* x, bool tr, bool x0_given) {
   auto& lev = levels<T>(t);
   const int nl = (int)lev.size();
   auto& L = lev[l];
-  if (l == 0 && !tr && t.opt.vcycle_grid) {
+  if (l == 0 && !tr && t.opt.vcycle_grid && !x0_given) {
     // the whole cycle in one cooperative launch; the dynamic shared memory
     // holds the largest unprefetched row pair (twice the finest row plus
     // half a row of twiddles) and the small per-phase tables
@@ -382,7 +386,7 @@ void vcycle(wt_tank& t, int l, const T* f, T* x, bool tr) {
       return;
     }
   }
-  if (l == tail_level<T>(t, tr)) {
+  if (l == tail_level<T>(t, tr) && !x0_given) {
     TailArgs<T> a;
     a.lv = tail_desc<T>(t);
     a.l0 = l;
@@ -415,7 +419,7 @@ void vcycle(wt_tank& t, int l, const T* f, T* x, bool tr) {
   // the finest level and levels reached by sigma-only coarsening may have some.
   const bool f_nyq = (l == 0) || (lev[l - 1].Nx == L.Nx);
   if (t.opt.nu1 > 0) {
-    smooth<T>(t, l, x, f, true, f_nyq, tr);
+    smooth<T>(t, l, x, f, !x0_given, f_nyq, tr);
     for (int i = 1; i < t.opt.nu1; ++i) smooth<T>(t, l, x, f, false, false, tr);
     auto& C = lev[l + 1];
     if (L.Ny == 1 && C.Nx != L.Nx) {
@@ -432,13 +436,48 @@ void vcycle(wt_tank& t, int l, const T* f, T* x, bool tr) {
       apply_op<T>(t, l, x, L.r, f, false, tr);  // r = f - A u
       restrict_to<T>(t, l, L.r);
     }
+  } else if (x0_given) {
+    apply_op<T>(t, l, x, L.r, f, false, tr);  // r = f - A u
+    restrict_to<T>(t, l, L.r);
   } else {
     WT_CK(cudaMemsetAsync(x, 0, sizeof(T) * L.n, t.s));
     restrict_to<T>(t, l, f);
   }
-  vcycle<T>(t, l + 1, lev[l + 1].f, lev[l + 1].x, tr);
+  vcycle<T>(t, l + 1, lev[l + 1].f, lev[l + 1].x, tr, false);
   const bool dx = prolong_add<T>(t, l, x, t.opt.nu2 > 0 ? L.t1 : nullptr);   // u = u + P e_c
   for (int i = 0; i < t.opt.nu2; ++i) smooth<T>(t, l, x, f, false, false, tr, dx && i == 0);
+}
+
+// Full multigrid (Algorithm 2): the right-hand side restricted to every
+// level, the coarsest level solved, then on each finer level the prolongated
+// coarse result as the initial state of one V-cycle.  Linear in f, so it is
+// a fixed preconditioner like the V-cycle.
+template <typename T>
+void fmg(wt_tank& t, const T* f, T* x, bool tr) {
+  auto& lev = levels<T>(t);
+  const int nl = (int)lev.size();
+  if (nl == 1) {
+    vcycle<T>(t, 0, f, x, tr, false);
+    return;
+  }
+  restrict_to<T>(t, 0, f);                                   // f_1 = R f_0
+  for (int l = 1; l < nl - 1; ++l) restrict_to<T>(t, l, lev[l].f);   // f_{l+1} = R f_l
+  vcycle<T>(t, nl - 1, lev[nl - 1].f, lev[nl - 1].x, tr, false);   // coarsest: direct solve
+  for (int l = nl - 2; l >= 0; --l) {
+    T* xl = l == 0 ? x : lev[l].x;
+    const T* fl = l == 0 ? f : lev[l].f;
+    WT_CK(cudaMemsetAsync(xl, 0, sizeof(T) * lev[l].n, t.s));
+    prolong_add<T>(t, l, xl);                                // u_l = P u_{l+1}
+    vcycle<T>(t, l, fl, xl, tr, true);                       // u_l = Vcycle(l, u_l, f_l)
+  }
+}
+
+// The preconditioner of the Krylov solver: one V-cycle (Algorithm 1) or one
+// full-multigrid cycle (Algorithm 2), as the options select.
+template <typename T>
+void mg_cycle(wt_tank& t, const T* f, T* x, bool tr) {
+  if (t.opt.cycle == 1) fmg<T>(t, f, x, tr);
+  else vcycle<T>(t, 0, f, x, tr, false);
 }
 
 // ------------------------------------------------------------------ norms
@@ -467,16 +506,16 @@ template <typename T>
 static void precondition(wt_tank& t, const T* v, T* z, bool pre32, bool tr);
 template <>
 void precondition<float>(wt_tank& t, const float* v, float* z, bool, bool tr) {
-  vcycle<float>(t, 0, v, z, tr);
+  mg_cycle<float>(t, v, z, tr);
 }
 template <>
 void precondition<double>(wt_tank& t, const double* v, double* z, bool pre32, bool tr) {
   if (!pre32) {
-    vcycle<double>(t, 0, v, z, tr);
+    mg_cycle<double>(t, v, z, tr);
     return;
   }
   const long n = t.n;
-  vcycle<float>(t, 0, t.b32, t.e32, tr);
+  mg_cycle<float>(t, t.b32, t.e32, tr);
   WT_LAUNCH(t, K_KRYLOV, 12.0 * n, 0.0, (launch_convert<float, double>(t.e32, z, n, nullptr, 0, t.s)));
 }
 
@@ -676,7 +715,9 @@ template void apply_op<double>(wt_tank&, int, const double*, double*, const doub
                                const OpExtra<double>&);
 template void apply_op<float>(wt_tank&, int, const float*, float*, const float*, bool, bool,
                               const OpExtra<float>&);
-template void vcycle<double>(wt_tank&, int, const double*, double*, bool);
-template void vcycle<float>(wt_tank&, int, const float*, float*, bool);
+template void vcycle<double>(wt_tank&, int, const double*, double*, bool, bool);
+template void vcycle<float>(wt_tank&, int, const float*, float*, bool, bool);
+template void mg_cycle<double>(wt_tank&, const double*, double*, bool);
+template void mg_cycle<float>(wt_tank&, const float*, float*, bool);
 
 }  // namespace wt

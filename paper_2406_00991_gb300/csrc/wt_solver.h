@@ -93,7 +93,9 @@ struct OpExtra {
 };
 template <typename T> void apply_op(wt_tank& t, int l, const T* x, T* out, const T* f, bool nyq,
                                     bool tr = false, const OpExtra<T>& ex = OpExtra<T>());
-template <typename T> void vcycle(wt_tank& t, int l, const T* f, T* x, bool tr = false);
+template <typename T> void vcycle(wt_tank& t, int l, const T* f, T* x, bool tr = false, bool x0_given = false);
+// The preconditioner cycle the options select (V-cycle or full multigrid).
+template <typename T> void mg_cycle(wt_tank& t, const T* f, T* x, bool tr = false);
 template <typename T>
 double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit, int* its_out,
               bool pre32, bool tr = false);

@@ -1,6 +1,7 @@
 """Batched uneven 2D tanks (one persistent launch, one CTA per tank) against
 the host-driven single-tank path and against the oracle's Runge-Kutta step
-(Sec. 4.1 low-storage RK4, Eq. kinematicFS, forc1, poissonp, rkforc1)."""
+(Sec. 4.1 low-storage RK4, Eq. kinematicFS, forc1, poissonp, rkforc1), in the
+mixed form (FP32 V-cycle) and the plain FP64 form."""
 
 import math
 
@@ -55,7 +56,7 @@ SHAPES = [(64, 12, 2 * math.pi, 0.03, 1), (256, 24, 8.0, 0.05, 2), (128, 16, 4.0
           (1024, 24, 32.0, 0.15, 5), (32, 8, 1.0, 0.004, 1)]
 
 
-@pytest.mark.parametrize("opts", [dict(), dict(filter=1), dict(linear=1)])
+@pytest.mark.parametrize("opts", [dict(), dict(filter=1), dict(linear=1), dict(mode=0), dict(mode=0, filter=1)])
 def test_batch_matches_single_tanks(wt, opts):
     # uneven tanks, including the 1024 x 24 tank and a 32 x 8 one; 1e-10 is the
     # method's solve tolerance (1e-12 lies below the FP64 rounding floor of the
@@ -69,8 +70,9 @@ def test_batch_matches_single_tanks(wt, opts):
     B.step(dts, 2)
     for i, ((Nx, Nz, L, _, _), (h, eta, u, w)) in enumerate(zip(SHAPES, tanks)):
         e1, u1, w1, t1 = B.get_state(i)
-        e2, u2, w2, t2, (solves, its) = single(wt, Nx, Nz, L, h, eta, u, w, dts[i], 2, mode=1, tol=1e-10,
-                                               **opts)
+        o = dict(opts)
+        o.setdefault("mode", 1)
+        e2, u2, w2, t2, (solves, its) = single(wt, Nx, Nz, L, h, eta, u, w, dts[i], 2, tol=1e-10, **o)
         assert abs(t1 - 2 * dts[i]) < 1e-14 and abs(t2 - t1) < 1e-14
         assert close(e1, e2, 1e-10), (i, np.abs(e1 - e2).max())
         assert close(u1, u2, 1e-8), (i, np.abs(u1 - u2).max())
@@ -82,11 +84,12 @@ def test_batch_matches_single_tanks(wt, opts):
     B.close()
 
 
-def test_batch_matches_oracle_step(wt):
+@pytest.mark.parametrize("mode", [1, 0])
+def test_batch_matches_oracle_step(wt, mode):
     Nx, Nz, L = 64, 12, 2 * math.pi
     h, eta, u, w = wave_tank(Nx, Nz, L, 0.03)
     dt = 0.01
-    B = wt.Batch([Nx], [Nz], [L], [h], tol=1e-12)
+    B = wt.Batch([Nx], [Nz], [L], [h], tol=1e-12, mode=mode)
     B.set_state(0, eta, u, w)
     B.step([dt], 1)
     e1, u1, w1, _ = B.get_state(0)
@@ -139,7 +142,7 @@ def test_batch_errors(wt):
         B.step(-0.01, 1)
     assert e.value.code == wt.WT_EINVAL
     with pytest.raises(wt.WtError) as e:
-        B.set_options(mode=wt.WT_FP64)
+        B.set_options(mode=wt.WT_REFINE)
     assert e.value.code == wt.WT_ENOTSUP
     # still water stays still; zero right-hand sides take zero iterations
     B.step(0.01, 3)

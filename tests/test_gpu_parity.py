@@ -287,3 +287,38 @@ def test_rk_stages_parity_3d(wt, mode):
         assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
     dv, bot = rk.divergence_residual(tank_o, rk.State(g, eta, u, v, w))
     assert np.abs(dv).max() < 1e-7 and np.abs(bot).max() < 1e-9
+
+
+@pytest.mark.parametrize("Nx,Ny,Nz", [(64, 1, 16), (1024, 1, 24), (16, 16, 8), (32, 32, 12)])
+def test_fmg_parity(wt, Nx, Ny, Nz):
+    # one full-multigrid cycle (Algorithm 2) as the preconditioner: the GPU's
+    # cycle against the oracle's on the same hierarchy and smoother
+    L = 2 * math.pi
+    g, h, ea, eb = curved(Nx, Ny, Nz, L)
+    r = np.random.default_rng(4).standard_normal(g.shape)
+    levels = pmg.build_levels(Nx, Ny, Nz, L, h, ea, eb, coarsest_max=64)
+    ref = pmg.fmg(levels, r, 2, 2, "jacobi", 0.4, "inject")
+    T = wt.Tank(Nx, Ny, Nz, L, h, cycle=1)
+    got = T.precondition(ea, eb, r, wt.WT_FP64)
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-9 * scale
+    got32 = T.precondition(ea, eb, r, wt.WT_FP32)
+    assert np.abs(got32 - ref).max() <= 5e-3 * scale
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fmg_solve_takes_no_more_iterations_than_vcycle(wt, mode):
+    # Table 1: FMG + GMRES needs slightly fewer iterations than V-cycle +
+    # GMRES for the same tolerance (and costs more per iteration)
+    Nx, Nz, L = 256, 24, 8.0
+    g, h, ea, eb = curved(Nx, 1, Nz, L)
+    b = np.random.default_rng(9).standard_normal(g.shape)
+    its = {}
+    for cyc in (0, 1):
+        T = wt.Tank(Nx, 1, Nz, L, h, mode=mode, tol=1e-10, cycle=cyc)
+        p, info = T.poisson_solve(ea, eb, b)
+        r = b - op.apply_A(g, op.Geometry(g, h, ea), op.Geometry(g, h, eb), p)
+        assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(b)
+        its[cyc] = info.iterations
+    print("iterations V-cycle %d, FMG %d (mode %d)" % (its[0], its[1], mode))
+    assert its[1] <= its[0]

@@ -105,7 +105,9 @@ def test_sea3d_full_step_invariants(wt):
     # times the derivative scale (kappa_max ~ 12.6, CGL ~ Nz^2): a few 1e-8 vel
     assert np.abs(dv).max() < 1e-6 * vel
     assert np.abs(bot).max() < 1e-8 * vel
-    assert abs(eta.mean() - eta0.mean()) < 1e-12
+    # mass: the mean of eta moves only by the surface flux that the solve
+    # tolerance leaves, five stages of ~tol * |eta|
+    assert abs(eta.mean() - eta0.mean()) < 1e-9 * np.abs(eta0).max()
     assert np.isfinite(eta).all() and np.abs(eta - eta0).max() < 0.1
 
 
@@ -135,7 +137,7 @@ def test_batch_workload_full_step(wt):
         e1, u1, w1, tm = B.get_state(i)
         assert abs(tm - q["dt"]) < 1e-14
         assert B.stats(i)[2] <= 1e-10
-        assert abs(e1.mean() - st[i][0].mean()) < 1e-12
+        assert abs(e1.mean() - st[i][0].mean()) < 1e-9 * np.abs(st[i][0]).max()
         if i in order[:64:8]:
             tank_o = rk.Tank(q["Nx"], 1, q["Nz"], q["L"], hs[i], tol=1e-10, filter=False)
             dv, bot = rk.divergence_residual(tank_o, rk.State(tank_o.grid, e1, u1, np.zeros_like(u1), w1))

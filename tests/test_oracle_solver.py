@@ -105,3 +105,42 @@ def test_sigma_transfers_between_equal_degrees_are_the_identity():
     assert np.abs(r - sp.fourier_resample(b, 16, axis=2)).max() < 1e-12 * np.abs(b).max()
     e = np.random.default_rng(2).standard_normal(coarse.shape)
     assert np.abs(pmg.prolong(coarse, fine, e) - sp.fourier_resample(e, 32, axis=2)).max() < 1e-12 * np.abs(e).max()
+
+
+def test_fmg_on_two_levels_is_a_vcycle_from_the_prolongated_coarse_solve():
+    # Algorithm 2 with two grids: the coarse problem for the restricted
+    # right-hand side solved exactly (dense LU), prolongated, and one V-cycle
+    # on the fine grid from that state
+    g, h, ea, eb, b = problem(16, 1, 8)
+    levels = pmg.build_levels(16, 1, 8, g.L, h, ea, eb, coarsest_max=100)
+    assert len(levels) == 2
+    fc = pmg.restrict(levels[0].grid, levels[1].grid, b)
+    uc = np.linalg.solve(levels[1].dense, fc.ravel()).reshape(levels[1].grid.shape)
+    u0 = pmg.prolong(levels[1].grid, levels[0].grid, uc)
+    want = pmg.vcycle(levels, 0, u0, b, 2, 2, "jacobi", 0.4, "inject")
+    got = pmg.fmg(levels, b, 2, 2, "jacobi", 0.4, "inject")
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    # with one level it is the direct solve
+    one = pmg.build_levels(8, 1, 4, g.L, h[:, ::2], ea[:, ::2], eb[:, ::2], coarsest_max=64)
+    assert len(one) == 1
+    f1 = b[::2, :, ::2].copy()
+    assert np.allclose(pmg.fmg(one, f1), np.linalg.solve(one[0].dense, f1.ravel()).reshape(f1.shape),
+                       rtol=0, atol=1e-12 * np.abs(f1).max() * 1e3)
+
+
+def test_fmg_is_linear_and_beats_one_vcycle():
+    g, h, ea, eb, b = problem(64, 1, 12)
+    levels = pmg.build_levels(64, 1, 12, g.L, h, ea, eb, coarsest_max=64)
+    lev = levels[0]
+    b2 = np.random.default_rng(11).standard_normal(g.shape)
+    a = pmg.fmg(levels, 2.0 * b - 3.0 * b2)
+    c = 2.0 * pmg.fmg(levels, b) - 3.0 * pmg.fmg(levels, b2)
+    assert np.abs(a - c).max() <= 1e-11 * np.abs(c).max()
+    # a smooth right-hand side: FMG's error is below one V-cycle's from zero
+    X = np.broadcast_to(g.x[None, None, :], g.shape)
+    S = np.broadcast_to(g.sigma[:, None, None], g.shape)
+    f = np.cos(X) * (1 + S ** 2)
+    exact = np.linalg.solve(lev.dense, f.ravel()).reshape(g.shape)
+    e_fmg = np.linalg.norm(pmg.fmg(levels, f) - exact)
+    e_v = np.linalg.norm(pmg.vcycle(levels, 0, np.zeros(g.shape), f) - exact)
+    assert e_fmg < e_v
