@@ -77,21 +77,23 @@ def solve_dense(level, b):
 
 def solve_pmg(Nx, Ny, Nz, L, h, eta_a, eta_b, b, tol=1e-12, x0=None, restart=30,
               maxit=500, cycle="v", nu1=2, nu2=2, smoother="jacobi", omega=0.4,
-              coarsest_max=256, precondition=True, bc_transfer="inject"):
+              coarsest_max=256, precondition=True, bc_transfer="inject", omega_s=1.0):
     """GMRES + one p-multigrid cycle per preconditioner application (Sec. 4.4).
 
-    ``cycle`` is "v" (Algorithm 1) or "fmg" (Algorithm 2).  Returns
-    (p, iterations, relres_history, levels).
+    ``cycle`` is "v" (Algorithm 1) or "fmg" (Algorithm 2).  The spectral
+    smoothers use the reference depth min(h) of the fine bathymetry.
+    Returns (p, iterations, relres_history, levels).
     """
     levels = pmg.build_levels(Nx, Ny, Nz, L, h, eta_a, eta_b, coarsest_max)
     fine = levels[0]
+    dref = float(np.min(h))
     if not precondition:
         pre = None
     elif cycle == "fmg":
-        pre = lambda r: pmg.fmg(levels, r, nu1, nu2, smoother, omega, bc_transfer)
+        pre = lambda r: pmg.fmg(levels, r, nu1, nu2, smoother, omega, bc_transfer, omega_s, dref)
     else:
         pre = lambda r: pmg.vcycle(levels, 0, np.zeros_like(r), r, nu1, nu2, smoother, omega,
-                                   bc_transfer)
+                                   bc_transfer, omega_s, dref)
     x, its, hist = gmres(fine.apply, np.asarray(b, dtype=np.float64).reshape(fine.grid.shape),
                          x0=x0, precond=pre, tol=tol, restart=restart, maxit=maxit)
     return x, its, hist, levels

@@ -217,12 +217,76 @@ def block_gauss_seidel(level, x, f):
     return x
 
 
-def smooth(level, x, f, sweeps, smoother, omega):
+def reference_column_matrix(grid, kappa2, dref):
+    """Column matrix of the flat reference operator for one horizontal
+    Fourier mode: the operator with eta = 0 and h = dref (so sigma_x =
+    sigma_y = 0, sigma_z = 1/dref) acting on p(sigma) exp(i kappa . x):
+    interior rows D D / dref^2 - kappa^2 I, surface row e_0 (Eq. bcpd),
+    bottom row D[Nz, :] / dref (Eq. bcpdneu with n = (0, 0, 1)).  kappa^2
+    is the discrete second-derivative symbol: the Nyquist mode, which the
+    composite D_x(D_x .) annihilates, has kappa^2 = 0 along that axis."""
+    D = grid.Ds
+    A = (D @ D) / dref ** 2 - kappa2 * np.eye(grid.M1)
+    A[0, :] = 0.0
+    A[0, 0] = 1.0
+    A[-1, :] = D[-1, :] / dref
+    return A
+
+
+def reference_kappa2(grid):
+    """kappa_x^2 + kappa_y^2 of every (y, x) Fourier mode, numpy FFT order,
+    with the Nyquist wavenumber of each axis counted as 0."""
+    def k2(N):
+        if N == 1:
+            return np.zeros(1)
+        k = sp.fourier_wavenumbers(N, grid.L)
+        k2 = k ** 2
+        k2[N // 2] = 0.0
+        return k2
+    return k2(grid.Ny)[:, None] + k2(grid.Nx)[None, :]
+
+
+def spectral_smooth(level, x, f, omega_s, dref, transpose=False):
+    """One sweep of the mean-depth spectral smoother (the stronger smoother
+    row of the build's plan; the paper's Sec. 4.3 leaves the smoother open
+    beyond block relaxation): x <- x + omega_s S (f - A x), where S solves
+    the flat reference problem of depth dref exactly, mode by mode: the
+    residual is Fourier transformed along x (and y), each mode's column is
+    solved with ``reference_column_matrix``, and the result transformed
+    back.  ``transpose`` uses the transposed column matrices (the smoother
+    of A^T; the modal transform is symmetric)."""
+    g = level.grid
+    r = f - (level.apply(x) if not transpose else level.dense.T @ x.ravel()).reshape(g.shape)
+    R = np.fft.fft(r, axis=2)
+    if g.Ny > 1:
+        R = np.fft.fft(R, axis=1)
+    K2 = reference_kappa2(g)
+    out = np.zeros_like(R)
+    for iy in range(g.Ny):
+        for ix in range(g.Nx):
+            A = reference_column_matrix(g, K2[iy, ix], dref)
+            out[:, iy, ix] = np.linalg.solve(A.T if transpose else A, R[:, iy, ix])
+    if g.Ny > 1:
+        out = np.fft.ifft(out, axis=1)
+    out = np.real(np.fft.ifft(out, axis=2))
+    return x + omega_s * out
+
+
+def smooth(level, x, f, sweeps, smoother, omega, omega_s=1.0, dref=None):
+    """``sweeps`` sweeps of the chosen smoother: "jacobi" (damped block-Jacobi
+    with the Nyquist split), "jacobi-plain", "gs" (forward block
+    Gauss-Seidel), "spectral" (mean-depth spectral smoother of depth dref),
+    "jacobi+spectral" (a block-Jacobi sweep then a spectral sweep)."""
     for _ in range(sweeps):
         if smoother == "gs":
             x = block_gauss_seidel(level, x, f)
         elif smoother == "jacobi-plain":
             x = block_jacobi(level, x, f, omega, nyquist_split=False)
+        elif smoother == "spectral":
+            x = spectral_smooth(level, x, f, omega_s, dref)
+        elif smoother == "jacobi+spectral":
+            x = block_jacobi(level, x, f, omega)
+            x = spectral_smooth(level, x, f, omega_s, dref)
         else:
             x = block_jacobi(level, x, f, omega)
     return x
@@ -234,21 +298,23 @@ def coarse_solve(level, f):
 
 
 def vcycle(levels, l, x, f, nu1=2, nu2=2, smoother="jacobi", omega=0.4,
-           bc_transfer="inject"):
+           bc_transfer="inject", omega_s=1.0, dref=None):
     """Recursive V-cycle (Algorithm 1), level index l = 0 is the finest."""
     lev = levels[l]
     if l == len(levels) - 1:
         return coarse_solve(lev, f)
-    x = smooth(lev, x, f, nu1, smoother, omega)
+    x = smooth(lev, x, f, nu1, smoother, omega, omega_s, dref)
     r = f - lev.apply(x)
     rc = restrict(lev.grid, levels[l + 1].grid, r, bc_transfer)
-    ec = vcycle(levels, l + 1, np.zeros_like(rc), rc, nu1, nu2, smoother, omega, bc_transfer)
+    ec = vcycle(levels, l + 1, np.zeros_like(rc), rc, nu1, nu2, smoother, omega, bc_transfer,
+                omega_s, dref)
     x = x + prolong(levels[l + 1].grid, lev.grid, ec)
-    x = smooth(lev, x, f, nu2, smoother, omega)
+    x = smooth(lev, x, f, nu2, smoother, omega, omega_s, dref)
     return x
 
 
-def fmg(levels, f, nu1=2, nu2=2, smoother="jacobi", omega=0.4, bc_transfer="inject"):
+def fmg(levels, f, nu1=2, nu2=2, smoother="jacobi", omega=0.4, bc_transfer="inject", omega_s=1.0,
+        dref=None):
     """Full multigrid (Algorithm 2): V-cycles from the coarsest grid upwards,
     prolongating each result as the next level's initial state."""
     fs = [f]
@@ -257,6 +323,6 @@ def fmg(levels, f, nu1=2, nu2=2, smoother="jacobi", omega=0.4, bc_transfer="inje
     P = len(levels)
     u = np.zeros_like(fs[-1])
     for l in range(P - 1, 0, -1):
-        u = vcycle(levels, l, u, fs[l], nu1, nu2, smoother, omega, bc_transfer)
+        u = vcycle(levels, l, u, fs[l], nu1, nu2, smoother, omega, bc_transfer, omega_s, dref)
         u = prolong(levels[l].grid, levels[l - 1].grid, u)
-    return vcycle(levels, 0, u, fs[0], nu1, nu2, smoother, omega, bc_transfer)
+    return vcycle(levels, 0, u, fs[0], nu1, nu2, smoother, omega, bc_transfer, omega_s, dref)

@@ -144,3 +144,37 @@ def test_fmg_is_linear_and_beats_one_vcycle():
     e_fmg = np.linalg.norm(pmg.fmg(levels, f) - exact)
     e_v = np.linalg.norm(pmg.vcycle(levels, 0, np.zeros(g.shape), f) - exact)
     assert e_fmg < e_v
+
+
+@pytest.mark.parametrize("Nx,Ny,Nz,dref", [(32, 1, 10, 1.0), (16, 1, 8, 0.7), (8, 8, 6, 1.3)])
+def test_spectral_smoother_is_exact_on_the_flat_reference_tank(Nx, Ny, Nz, dref):
+    # on a flat tank of depth dref at rest the reference operator is the
+    # operator itself, so one undamped sweep from zero is the dense solve
+    L = 2 * math.pi
+    g = op.Grid(Nx, Ny, Nz, L)
+    h = np.full((Ny, Nx), dref)
+    z = np.zeros((Ny, Nx))
+    lev = pmg.Level(Nx, Ny, Nz, L, h, z, z)
+    b = np.random.default_rng(2).standard_normal(g.shape)
+    want = np.linalg.solve(lev.dense, b.ravel()).reshape(g.shape)
+    got = pmg.spectral_smooth(lev, np.zeros(g.shape), b, 1.0, dref)
+    assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+    wantT = np.linalg.solve(lev.dense.T, b.ravel()).reshape(g.shape)
+    gotT = pmg.spectral_smooth(lev, np.zeros(g.shape), b, 1.0, dref, transpose=True)
+    assert np.abs(gotT - wantT).max() <= 1e-10 * np.abs(wantT).max()
+    # a wrong reference depth is no longer exact
+    off = pmg.spectral_smooth(lev, np.zeros(g.shape), b, 1.0, 1.1 * dref)
+    assert np.abs(off - want).max() > 1e-3 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("smoother", ["spectral", "jacobi+spectral"])
+def test_spectral_smoothers_solve_to_dense_lu(smoother):
+    g, h, ea, eb, b = problem(32, 1, 10)
+    lev = pmg.Level(32, 1, 10, g.L, h, ea, eb)
+    p_lu = krylov.solve_dense(lev, b)
+    p, its, hist, levels = krylov.solve_pmg(32, 1, 10, g.L, h, ea, eb, b, tol=1e-13, smoother=smoother,
+                                            coarsest_max=64, nu1=1, nu2=1)
+    assert np.abs(p - p_lu).max() < 1e-9 * np.abs(p_lu).max()
+    _, its_bj, _, _ = krylov.solve_pmg(32, 1, 10, g.L, h, ea, eb, b, tol=1e-13, coarsest_max=64, nu1=1, nu2=1)
+    if smoother == "jacobi+spectral":
+        assert its < its_bj
