@@ -112,6 +112,16 @@ typedef struct wt_options {
                         (Algorithm 2: the right-hand side restricted to every
                         level, the coarsest solved, and on each finer level a
                         V-cycle from the prolongated coarse result)         */
+  int smoother;      /* 0 = damped block-Jacobi over the columns (default);
+                        1 = mean-depth spectral smoother: x += omega_s S
+                        (f - A x), S the exact solve of the flat reference
+                        problem (eta = 0, depth = min h) by horizontal
+                        Fourier mode - the modes' (Nz+1)^2 inverses are
+                        built once per bathymetry; 2 = a block-Jacobi sweep
+                        followed by a spectral sweep.  With 1 or 2 every
+                        level runs launch per phase (tail_max and
+                        vcycle_grid are not used)                           */
+  double omega_s;    /* damping of the spectral smoother (1.0)               */
 } wt_options;
 
 typedef struct wt_solve_info {

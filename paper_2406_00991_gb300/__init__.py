@@ -33,7 +33,7 @@ class wt_options(ctypes.Structure):
                 ("bc_transfer", ctypes.c_int), ("tail_max", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_ir", ctypes.c_int), ("vcycle_grid", ctypes.c_int),
                 ("tail_cluster", ctypes.c_int), ("barrier_cycles", ctypes.c_longlong),
-                ("cycle", ctypes.c_int)]
+                ("cycle", ctypes.c_int), ("smoother", ctypes.c_int), ("omega_s", ctypes.c_double)]
 
 
 class wt_solve_info(ctypes.Structure):

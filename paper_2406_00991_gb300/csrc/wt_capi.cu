@@ -6,6 +6,7 @@
 #include "wt_solver.h"
 
 #include <algorithm>
+#include <map>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -205,7 +206,120 @@ void alloc_level(Arena& ar, Level<T>& L, int Nx, int Ny, int Nz, double Ldom, bo
   if (!coarsest) L.Binv = ar.alloc<T>((size_t)L.nclass * L.M1 * L.M1 * L.ncols);
 }
 
+// In-place inverse of the n x n row-major matrix A (Gauss-Jordan with
+// partial pivoting, FP64); false if A is singular.
+bool invert_host(std::vector<double>& A, int n) {
+  std::vector<double> I((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[(size_t)r * n + c]) > std::fabs(A[(size_t)piv * n + c])) piv = r;
+    if (!(std::fabs(A[(size_t)piv * n + c]) > 0.0)) return false;
+    if (piv != c)
+      for (int j = 0; j < n; ++j) {
+        std::swap(A[(size_t)piv * n + j], A[(size_t)c * n + j]);
+        std::swap(I[(size_t)piv * n + j], I[(size_t)c * n + j]);
+      }
+    const double d = 1.0 / A[(size_t)c * n + c];
+    for (int j = 0; j < n; ++j) {
+      A[(size_t)c * n + j] *= d;
+      I[(size_t)c * n + j] *= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = A[(size_t)r * n + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j) {
+        A[(size_t)r * n + j] -= f * A[(size_t)c * n + j];
+        I[(size_t)r * n + j] -= f * I[(size_t)c * n + j];
+      }
+    }
+  }
+  A.swap(I);
+  return true;
+}
+
+// Tables of the mean-depth spectral smoother on every level above the
+// coarsest: for each distinct kappa^2 = (2 pi / L)^2 (n^2 + m^2) (n, m the
+// x and y mode numbers, 0 at an axis' Nyquist mode) the inverse of the flat
+// reference column matrix of depth dref = min h:
+//   rows 1..Nz-1: D D / dref^2 - kappa^2 I,  row 0: e_0,  row Nz: D[Nz, :] / dref.
+// 2D: table n for kx = n (the Nyquist column uses table 0).  3D: an index
+// per mode (ky, kx), kx <= Nx/2.
+void build_spectral(wt_tank& t) {
+  t.spar.release();
+  t.spec_ready = false;
+  const int nl = (int)t.L64.size();
+  const double dref = t.hmin;
+  const double k0 = 2.0 * M_PI / t.L;
+  for (int l = 0; l + 1 < nl; ++l) {
+    auto& L64 = t.L64[l];
+    auto& L32 = t.L32[l];
+    const int Nx = L64.Nx, Ny = L64.Ny, M1 = L64.M1, Nz = L64.Nz;
+    const int H = Nx / 2, Nh = H + 1;
+    auto D = cheb_D(Nz);
+    auto D2 = matmul(D, D, M1, M1, M1);
+    auto modeno = [](int k, int N) {            // |mode number|, 0 at Nyquist
+      if (N == 1) return 0;
+      const int m = k <= N / 2 ? k : N - k;
+      return m == N / 2 ? 0 : m;
+    };
+    std::vector<long> keys;                     // n^2 + m^2 of each table
+    std::vector<int> idx;
+    if (Ny == 1) {
+      for (int n = 0; n < H; ++n) keys.push_back((long)n * n);
+    } else {
+      std::map<long, int> where;
+      idx.resize((size_t)Ny * Nh);
+      for (int ky = 0; ky < Ny; ++ky)
+        for (int kx = 0; kx < Nh; ++kx) {
+          const long mx = modeno(kx, Nx), my = modeno(ky, Ny);
+          const long key = mx * mx + my * my;
+          auto it = where.find(key);
+          if (it == where.end()) {
+            it = where.emplace(key, (int)keys.size()).first;
+            keys.push_back(key);
+          }
+          idx[(size_t)ky * Nh + kx] = it->second;
+        }
+    }
+    std::vector<double> tab(keys.size() * (size_t)M1 * M1);
+    for (size_t q = 0; q < keys.size(); ++q) {
+      const double kap2 = k0 * k0 * (double)keys[q];
+      std::vector<double> A((size_t)M1 * M1, 0.0);
+      for (int i = 1; i < Nz; ++i)
+        for (int j = 0; j < M1; ++j)
+          A[(size_t)i * M1 + j] = D2[(size_t)i * M1 + j] / (dref * dref) - (i == j ? kap2 : 0.0);
+      A[0] = 1.0;
+      for (int j = 0; j < M1; ++j) A[(size_t)Nz * M1 + j] = D[(size_t)Nz * M1 + j] / dref;
+      if (!invert_host(A, M1)) throw WtError{WT_EINVAL, "singular reference column matrix"};
+      std::copy(A.begin(), A.end(), tab.begin() + q * (size_t)M1 * M1);
+    }
+    L64.Stab = upload<double>(t.spar, tab);
+    L32.Stab = upload<float>(t.spar, tab);
+    int* di = nullptr;
+    if (Ny > 1) {
+      di = t.spar.alloc<int>(idx.size());
+      WT_CK(cudaMemcpy(di, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice));
+    }
+    L64.sidx = L32.sidx = di;
+    L64.spec = t.spar.alloc<double2>((size_t)M1 * Ny * Nh);
+    L32.spec = t.spar.alloc<float2>((size_t)M1 * Ny * Nh);
+  }
+  t.spec_ready = true;
+}
+
+// Build the spectral tables if the options use the spectral smoother.
+void ensure_spectral(wt_tank& t) {
+  if (t.opt.smoother != 0 && !t.spec_ready) build_spectral(t);
+}
+
 void build_hierarchy(wt_tank& t) {
+  t.spar.release();
+  t.spec_ready = false;
+  for (auto& L : t.L64) L.Stab = nullptr, L.sidx = nullptr, L.spec = nullptr;
+  for (auto& L : t.L32) L.Stab = nullptr, L.sidx = nullptr, L.spec = nullptr;
   t.har.release();
   t.L64.clear();
   t.L32.clear();
@@ -323,6 +437,9 @@ int check_options(const wt_options& o) {
   if (o.tail_max < 0) return fail(WT_EINVAL, "tail_max must be >= 0");
   if (o.barrier_cycles < 0) return fail(WT_EINVAL, "barrier_cycles must be >= 0");
   if (o.cycle != 0 && o.cycle != 1) return fail(WT_EINVAL, "cycle must be 0 (V-cycle) or 1 (full multigrid)");
+  if (o.smoother < 0 || o.smoother > 2)
+    return fail(WT_EINVAL, "smoother must be 0 (block-Jacobi), 1 (spectral) or 2 (both)");
+  if (!(o.omega_s > 0) || !(o.omega_s < 2)) return fail(WT_EINVAL, "omega_s must be in (0, 2)");
   if ((o.filter != 0 && o.filter != 1) || (o.linear != 0 && o.linear != 1) ||
       (o.bc_transfer != 0 && o.bc_transfer != 1))
     return fail(WT_EINVAL, "filter, linear, bc_transfer are 0 or 1");
@@ -563,6 +680,8 @@ int wt_default_options(wt_options* o) {
   o->tail_cluster = 0;
   o->barrier_cycles = 0;
   o->cycle = 0;
+  o->smoother = 0;
+  o->omega_s = 1.0;
   return WT_OK;
 }
 
@@ -662,6 +781,7 @@ int wt_create(int Nx, int Ny, int Nz, double L, double g, double nu, const doubl
     WT_CK(cudaStreamSynchronize(t->s));
     for (double v : hh)
       if (!(v > 0) || !std::isfinite(v)) return fail(WT_EINVAL, "bathymetry must be positive and finite");
+    t->hmin = *std::min_element(hh.begin(), hh.end());
     WT_CK(cudaMemcpyAsync(t->io_s2, hh.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, t->s));
     setup_bathymetry(*t, t->io_s2);
     WT_CK(cudaStreamSynchronize(t->s));
@@ -691,6 +811,7 @@ int wt_set_options(wt_tank* t, const wt_options* o) {
       setup_bathymetry(*t, t->io_s2);
       WT_CK(cudaStreamSynchronize(t->s));
     }
+    ensure_spectral(*t);
     return WT_OK;
   });
 }
@@ -1013,8 +1134,19 @@ int wt_set_bathymetry(wt_tank* t, const double* h) {
   return guarded([&]() -> int {
     enter(*t);
     const double* hd = in_dev(*t, h, t->io_s1, t->ncols);
+    std::vector<double> hh(t->ncols);
+    WT_CK(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * t->ncols, cudaMemcpyDefault, t->s));
+    WT_CK(cudaStreamSynchronize(t->s));
+    for (double v : hh)
+      if (!(v > 0) || !std::isfinite(v)) return fail(WT_EINVAL, "bathymetry must be positive and finite");
     setup_bathymetry(*t, hd);
     WT_CK(cudaStreamSynchronize(t->s));
+    const double hmin = *std::min_element(hh.begin(), hh.end());
+    if (hmin != t->hmin) {                       // the spectral smoother's reference depth moved
+      t->hmin = hmin;
+      t->spec_ready = false;
+      ensure_spectral(*t);
+    }
     return WT_OK;
   });
 }
@@ -1183,6 +1315,8 @@ int check_batch_tank(const wt_tank& t, int smem) {
   if (t.Ny != 1) return fail(WT_EINVAL, "batched tanks are 2D (Ny = 1)");
   if (t.opt.mode != WT_MIXED && t.opt.mode != WT_FP64)
     return fail(WT_ENOTSUP, "batched tanks run the mixed or the FP64 solver (not WT_REFINE)");
+  if (t.opt.smoother != 0 || t.opt.cycle != 0)
+    return fail(WT_ENOTSUP, "batched tanks use the block-Jacobi smoother and the V-cycle");
   const size_t row = (2 * (size_t)t.Nx + t.Nx / 2) * 2 * sizeof(double);
   const size_t coarse = (size_t)t.ncoarse * (t.ncoarse + 1) * sizeof(double) + (t.ncoarse + 1) * sizeof(int);
   const size_t blk = (size_t)t.M1 * (2 * t.M1 + 1) * (t.opt.mode == WT_FP64 ? sizeof(double) : sizeof(float));

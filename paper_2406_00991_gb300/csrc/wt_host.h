@@ -63,6 +63,11 @@ struct Level {
   T *rhoX = nullptr, *rhoY = nullptr, *rhoXY = nullptr;
   T *Rsig = nullptr, *Psig = nullptr;   // to / from the next coarser level
   bool sig_id = false;                   // both are the identity (same sigma nodes)
+  // mean-depth spectral smoother: reference column inverses, table index
+  // per mode (3D), half-spectrum work array (built when the option asks)
+  T* Stab = nullptr;
+  int* sidx = nullptr;
+  c2_t<T>* spec = nullptr;
   LevelView<T> view(const c2_t<T>* tw, int logNtw, double Ld) const {
     LevelView<T> v;
     v.Nx = Nx; v.Ny = Ny; v.Nz = Nz; v.M1 = M1; v.logNx = logNx; v.logNy = logNy;
@@ -158,6 +163,9 @@ struct wt_tank {
 
   wt::Arena ar;       // sizes fixed at creation
   wt::Arena har;      // level hierarchy (rebuilt when coarsest_max changes)
+  wt::Arena spar;     // spectral smoother tables (rebuilt with the hierarchy or the bathymetry)
+  double hmin = 1.0;  // reference depth of the spectral smoother: min h of the fine bathymetry
+  bool spec_ready = false;
 
   std::vector<std::array<int, 3>> dims;
   std::vector<wt::Level<double>> L64;

@@ -258,6 +258,23 @@ cudaError_t launch_vcycle_grid(const TailArgs<T>& a, int dim, GridBar* bar, int*
 template <typename T>
 cudaError_t launch_vcycle_cluster(const TailArgs<T>& a, int dim, int csize, cudaStream_t s);
 
+// Mean-depth spectral smoother (wt_spec.cu): x = scale S r (first) or
+// x += scale S r, S the exact solve of the flat reference problem mode by mode.
+template <typename T>
+struct SpecArgs {
+  int Nx = 0, Ny = 1, M1 = 0, logNx = 0, logNy = 0;
+  const T* r = nullptr;          // residual [M1][Ny][Nx]
+  T* x = nullptr;                // iterate [M1][Ny][Nx]
+  c2_t<T>* spec = nullptr;       // work: half spectra [M1][Ny][Nx/2+1]
+  const T* tab = nullptr;        // inverses of the reference column matrices [ntab][M1][M1]
+  const int* sidx = nullptr;     // 3D: table of each mode [Ny][Nx/2+1]; NULL in 2D (table = kx)
+  T scale = 1;                   // omega_s / (Nx Ny)
+  int first = 0, tr = 0;         // x = (first) or x += ; transposed tables (smoother of A^T)
+  const c2_t<T>* tw = nullptr;
+  int logNtw = 0;
+};
+template <typename T> cudaError_t launch_spectral_smooth(const SpecArgs<T>& a, cudaStream_t s);
+
 // Dense coarsest level (wt_coarse.cu), always FP64 arithmetic.
 cudaError_t launch_coarse_factor(const LevelView<double>& L, const double* Dx, const double* Dy,
                                  double* LU, int* piv, int* flag, cudaStream_t s);

@@ -262,9 +262,56 @@ static void nyquist_of(wt_tank& t, Level<T>& L, const T* f) {
 }
 
 // ------------------------------------------------------------------ V-cycle
+// One sweep of the mean-depth spectral smoother: x = omega_s S f from x = 0
+// (first) or x += omega_s S (f - A x) (wt_spec.cu).
+template <typename T>
+static void spectral_sweep(wt_tank& t, int l, T* x, const T* f, bool first, bool tr, bool have_dx) {
+  auto& L = levels<T>(t)[l];
+  if (!L.Stab) throw WtError{WT_EINVAL, "spectral smoother tables are not built"};
+  const T* r = f;
+  if (!first) {
+    OpExtra<T> ex;
+    ex.have_dx = have_dx;
+    apply_op<T>(t, l, x, L.r, f, false, tr, ex);
+    r = L.r;
+  }
+  SpecArgs<T> a;
+  a.Nx = L.Nx; a.Ny = L.Ny; a.M1 = L.M1; a.logNx = L.logNx; a.logNy = L.logNy;
+  a.r = r; a.x = x; a.spec = L.spec; a.tab = L.Stab; a.sidx = L.sidx;
+  a.scale = (T)(t.opt.omega_s / ((double)L.Nx * L.Ny));
+  a.first = first ? 1 : 0;
+  a.tr = tr ? 1 : 0;
+  a.tw = twiddles<T>(t);
+  a.logNtw = t.logNtw;
+  const double nh = (double)L.M1 * L.Ny * (L.Nx / 2 + 1);
+  WT_LAUNCH(t, K_SMOOTH, sizeof(T) * (3.0 * L.n + 8.0 * nh), 2.0 * 8.0 * nh * L.M1,
+            launch_spectral_smooth<T>(a, t.s));
+  // kernels of the pass: x forward, y forward and inverse (3D), columns, x inverse
+  t.prof.launches += (L.Ny > 1 ? 5 : 3) - 1;
+}
+
+template <typename T>
+static void smooth_bj(wt_tank& t, int l, T* x, const T* f, bool first, bool f_has_nyq, bool tr,
+                      bool have_dx);
+
+// One smoothing sweep of the kind the options select: damped block-Jacobi
+// (0), the mean-depth spectral smoother (1), or a block-Jacobi sweep then a
+// spectral sweep (2).  first: x = 0 on entry.
 template <typename T>
 static void smooth(wt_tank& t, int l, T* x, const T* f, bool first, bool f_has_nyq, bool tr,
                    bool have_dx = false) {
+  const int kind = t.opt.smoother;
+  if (kind == 1) {
+    spectral_sweep<T>(t, l, x, f, first, tr, have_dx);
+    return;
+  }
+  smooth_bj<T>(t, l, x, f, first, f_has_nyq, tr, have_dx);
+  if (kind == 2) spectral_sweep<T>(t, l, x, f, false, tr, false);
+}
+
+template <typename T>
+static void smooth_bj(wt_tank& t, int l, T* x, const T* f, bool first, bool f_has_nyq, bool tr,
+                      bool have_dx) {
   auto& L = levels<T>(t)[l];
   const auto V = L.view(twiddles<T>(t), t.logNtw, t.L);
   const T om = (T)t.opt.omega;
@@ -346,7 +393,7 @@ template <> TailLevel<float>* tail_desc<float>(wt_tank& t) { return t.tl32; }
 // one thread-block cluster with tail_cluster >= 2); -1: none.
 template <typename T>
 static int tail_level(wt_tank& t, bool tr) {
-  if (t.opt.tail_max <= 0 || tr) return -1;
+  if (t.opt.tail_max <= 0 || tr || t.opt.smoother != 0) return -1;
   auto& lev = levels<T>(t);
   for (size_t l = 0; l < lev.size(); ++l)
     if (lev[l].n <= t.opt.tail_max) return (int)l;
@@ -362,7 +409,7 @@ void vcycle(wt_tank& t, int l, const T* f, T* x, bool tr, bool x0_given) {
   auto& lev = levels<T>(t);
   const int nl = (int)lev.size();
   auto& L = lev[l];
-  if (l == 0 && !tr && t.opt.vcycle_grid && !x0_given) {
+  if (l == 0 && !tr && t.opt.vcycle_grid && !x0_given && t.opt.smoother == 0) {
     // the whole cycle in one cooperative launch; the dynamic shared memory
     // holds the largest unprefetched row pair (twice the finest row plus
     // half a row of twiddles) and the small per-phase tables
