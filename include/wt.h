@@ -252,6 +252,25 @@ int wt_adjoint_step(wt_tank* t, double dt, const double* eta, const double* u, c
                     double* lam_eta, double* lam_u, double* lam_w, double* dJ_dh);
 
 /*
+ * Steady nonlinear periodic wave by the Fourier stream-function method of
+ * Rienecker & Fenton (1981), which the paper uses to initialise its
+ * nonlinear accuracy study (Sec. 5.2) and its bar case (Sec. 5.5): nwaves
+ * wavelengths in the periodic domain (k = 2 pi nwaves / L), height H over
+ * the tank's flat bottom (h constant, else WT_EINVAL), nmodes Fourier modes
+ * (2..128).  Solved on the host in FP64 (Newton's method on the surface
+ * kinematic and Bernoulli conditions at nmodes + 1 points, zero mean level,
+ * crest-to-trough height H, no mean Eulerian current; the height raised in
+ * steps of 0.005 in steepness; the last solution is cached per tank) and
+ * evaluated at the tank's nodes at time `time`: eta [Nx] and the fixed-frame
+ * u, w [Nz+1][Nx] at z = sigma (h + eta) - h (each may be NULL; host or
+ * device arrays), *c = phase speed (may be NULL).  H is limited to 0.85 x
+ * the Battjes steepness 0.1401 tanh(0.8863 k h) (WT_EINVAL above it);
+ * WT_ENOCONV if Newton's method fails.  2D tanks only.
+ */
+int wt_stream_function_wave(wt_tank* t, int nwaves, double H, int nmodes, double time, double* eta,
+                            double* u, double* w, double* c);
+
+/*
  * Solver autotuner.  Times wt_poisson_solve on this tank's problem
  * A_{a,b} p = rhs (eta_a, eta_b [Ny][Nx], rhs [Nz+1][Ny][Nx]; host or device)
  * from a zero initial guess under a grid of settings - omega in {0.3, 0.4,
@@ -259,6 +278,7 @@ int wt_adjoint_step(wt_tank* t, double dt, const double* eta, const double* u, c
  * 128}, and mode in {WT_MIXED, WT_REFINE} unless the tank is in WT_FP64 - one
  * warm-up solve plus the median of reps (1..100) timed solves each, and keeps
  * the fastest setting that reaches the tolerance; then, on that setting, the
+ * spectral smoothers (smoother 1 and 2, nu1 = nu2 in {1, 2}), the
  * full-multigrid cycle (cycle = 1) and the V-cycle's launch schedule (tail_max 2048 or 8192 with tail_cluster 0 or
  * 16, or vcycle_grid = 1).  The paper leaves these
  * choices open (Sec. 4.1).  On success the tank uses the winner, *best holds

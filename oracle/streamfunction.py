@@ -21,7 +21,7 @@ frame moving with the wave speed c over a flat bed at y = 0 (still depth d):
 * no mean Eulerian current in the fixed frame: c = U.
 
 Unknowns U, Q, R, eta_0..eta_N, B_1..B_N (2N + 4) against 2N + 4 equations,
-solved by Newton's method with a forward-difference Jacobian; the height is
+solved by Newton's method with a central-difference Jacobian; the height is
 raised in steps from a linear-theory start (continuation).  In the fixed
 frame the fields are eta(x, t) = sum_j E_j cos(j k (x - c t)) (the cosine
 interpolant of the eta_m) and, at height z above the still level,
@@ -68,10 +68,18 @@ class Wave:
         w = np.zeros(X.shape)
         for j in range(1, self.N + 1):
             jk = j * self.k
-            a = jk * self.B[j - 1] / math.cosh(jk * self.d)
-            u += a * np.cosh(jk * y) * np.cos(jk * X)
-            w += a * np.sinh(jk * y) * np.sin(jk * X)
+            sh, ch = _sh_ch(jk, y, self.d)
+            u += jk * self.B[j - 1] * ch * np.cos(jk * X)
+            w += jk * self.B[j - 1] * sh * np.sin(jk * X)
         return u, w
+
+
+def _sh_ch(jk, y, d):
+    """sinh(jk y) / cosh(jk d) and cosh(jk y) / cosh(jk d) without overflow."""
+    e1 = np.exp(jk * (y - d))
+    e2 = np.exp(-jk * (y + d))
+    e3 = math.exp(-2.0 * jk * d)
+    return (e1 - e2) / (1.0 + e3), (e1 + e2) / (1.0 + e3)
 
 
 def _residual(z, k, d, H, g, N):
@@ -85,10 +93,10 @@ def _residual(z, k, d, H, g, N):
     w = np.zeros(N + 1)
     for j in range(1, N + 1):
         jk = j * k
-        ch = math.cosh(jk * d)
-        psi += B[j - 1] * np.sinh(jk * y) / ch * np.cos(jk * Xm)
-        u += B[j - 1] * jk * np.cosh(jk * y) / ch * np.cos(jk * Xm)
-        w += B[j - 1] * jk * np.sinh(jk * y) / ch * np.sin(jk * Xm)
+        sh, ch = _sh_ch(jk, y, d)
+        psi += B[j - 1] * sh * np.cos(jk * Xm)
+        u += B[j - 1] * jk * ch * np.cos(jk * Xm)
+        w += B[j - 1] * jk * sh * np.sin(jk * Xm)
     kin = psi + Q
     dyn = 0.5 * (u * u + w * w) + g * eta - R
     wts = np.ones(N + 1)
@@ -103,7 +111,7 @@ def solve(k, d, H, g=9.81, N=24, steps=None, tol=1e-13, maxit=60):
     with continuation in H).  Returns a ``Wave``."""
     if steps is None:
         steep = H * k / (2 * math.pi)
-        steps = max(1, int(math.ceil(steep / 0.01)))
+        steps = max(1, int(math.ceil(steep / 0.005)))
     c0 = math.sqrt(g / k * math.tanh(k * d))
     n = 2 * N + 4
     Xm = np.arange(N + 1) * math.pi / (N * k)
@@ -124,11 +132,13 @@ def solve(k, d, H, g=9.81, N=24, steps=None, tol=1e-13, maxit=60):
         for _ in range(maxit):
             F = _residual(cur, k, d, Hs, g, N)
             J = np.zeros((n, n))
-            for i in range(n):
-                hstep = 1e-7 * max(1.0, abs(cur[i]))
+            for i in range(n):                     # central differences
+                hstep = 1e-6 * max(1e-3, abs(cur[i]))
                 zp = cur.copy()
+                zm = cur.copy()
                 zp[i] += hstep
-                J[:, i] = (_residual(zp, k, d, Hs, g, N) - F) / hstep
+                zm[i] -= hstep
+                J[:, i] = (_residual(zp, k, d, Hs, g, N) - _residual(zm, k, d, Hs, g, N)) / (2 * hstep)
             dz = np.linalg.solve(J, -F)
             cur = cur + dz
             if np.abs(dz).max() < tol * max(1.0, np.abs(cur).max()):

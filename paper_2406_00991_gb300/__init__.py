@@ -88,6 +88,7 @@ def _load():
         "wt_batch_destroy": [P],
         "wt_batch_set_stream": [P, P],
         "wt_time_kernel": [P, P, P, I, I, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long)],
+        "wt_stream_function_wave": [P, I, D, I, D, P, P, P, ctypes.POINTER(D)],
         "wt_last_error": [ctypes.c_char_p, ctypes.c_size_t],
     }
     for name, args in sig.items():
@@ -249,6 +250,13 @@ def wt_apply_operator_static(Nx, Nz, L, h, eta_a, eta_b, p, Ap, stream_handle=0)
     """Allocation-free 2D FP64 operator apply; every array must be a CUDA tensor."""
     return _lib.wt_apply_operator_static(int(Nx), int(Nz), float(L), _ptr(h), _ptr(eta_a), _ptr(eta_b),
                                          _ptr(p), _ptr(Ap), ctypes.c_void_p(int(stream_handle)))
+
+
+def wt_stream_function_wave(t, nwaves, H, nmodes, time, eta, u, w):
+    c = ctypes.c_double()
+    st = _lib.wt_stream_function_wave(t, int(nwaves), float(H), int(nmodes), float(time), _ptr(eta), _ptr(u),
+                                      _ptr(w), ctypes.byref(c))
+    return st, c.value
 
 
 WT_TIME_OPERATOR, WT_TIME_VCYCLE = 0, 1
@@ -488,6 +496,14 @@ class Tank:
         st, ms, n, b, f = wt_profile_read(self.handle, kernel_class)
         _check(st)
         return dict(ms=ms, launches=n, bytes=b, flops=f)
+
+    def stream_function_wave(self, nwaves, H, nmodes=32, time=0.0):
+        """(eta, u, w, c) of the stream-function wave at the tank's nodes (2D, flat bottom)."""
+        eta = np.zeros((1, self.Nx))
+        u, w = np.zeros(self.shape), np.zeros(self.shape)
+        st, c = wt_stream_function_wave(self.handle, nwaves, H, nmodes, time, eta, u, w)
+        _check(st)
+        return eta, u, w, c
 
     def time_kernel(self, eta_a, eta_b, what=WT_TIME_OPERATOR, precision=WT_FP32, reps=200):
         """(ms per unit, kernels per unit) of the operator apply or the V-cycle,

@@ -782,6 +782,7 @@ int wt_create(int Nx, int Ny, int Nz, double L, double g, double nu, const doubl
     for (double v : hh)
       if (!(v > 0) || !std::isfinite(v)) return fail(WT_EINVAL, "bathymetry must be positive and finite");
     t->hmin = *std::min_element(hh.begin(), hh.end());
+    t->hmax = *std::max_element(hh.begin(), hh.end());
     WT_CK(cudaMemcpyAsync(t->io_s2, hh.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, t->s));
     setup_bathymetry(*t, t->io_s2);
     WT_CK(cudaStreamSynchronize(t->s));
@@ -1142,11 +1143,49 @@ int wt_set_bathymetry(wt_tank* t, const double* h) {
     setup_bathymetry(*t, hd);
     WT_CK(cudaStreamSynchronize(t->s));
     const double hmin = *std::min_element(hh.begin(), hh.end());
+    t->hmax = *std::max_element(hh.begin(), hh.end());
     if (hmin != t->hmin) {                       // the spectral smoother's reference depth moved
       t->hmin = hmin;
       t->spec_ready = false;
       ensure_spectral(*t);
     }
+    return WT_OK;
+  });
+}
+
+int wt_stream_function_wave(wt_tank* t, int nwaves, double H, int nmodes, double time, double* eta,
+                            double* u, double* w, double* c) {
+  if (!t) return fail(WT_EINVAL, "NULL tank");
+  if (t->Ny != 1) return fail(WT_ENOTSUP, "stream-function waves are set on 2D tanks");
+  if (nwaves < 1 || nwaves > t->Nx / 4) return fail(WT_EINVAL, "nwaves must be in [1, Nx/4]");
+  if (nmodes < 2 || nmodes > 128) return fail(WT_EINVAL, "nmodes must be in [2, 128]");
+  if (!(H > 0) || !std::isfinite(H) || !std::isfinite(time)) return fail(WT_EINVAL, "H must be positive");
+  if (t->hmax - t->hmin > 1e-12 * t->hmax) return fail(WT_EINVAL, "stream-function waves need a flat bottom");
+  const double k = 2.0 * M_PI * nwaves / t->L, d = t->hmax;
+  if (H * k / (2.0 * M_PI) > 0.85 * 0.1401 * std::tanh(0.8863 * k * d))
+    return fail(WT_EINVAL, "H above 0.85 x the Battjes breaking steepness");
+  return guarded([&]() -> int {
+    SfWave& W = t->sf;
+    if (!(W.k == k && W.d == d && W.H == H && W.g == t->g && W.N == nmodes)) {
+      SfWave nw;
+      if (!sf_solve(k, d, H, t->g, nmodes, nw)) return fail(WT_ENOCONV, "stream-function Newton iteration failed");
+      W = nw;
+    }
+    const int Nx = t->Nx, M1 = t->M1;
+    std::vector<double> he(Nx), hu((size_t)M1 * Nx), hw((size_t)M1 * Nx);
+    for (int j = 0; j < Nx; ++j) {
+      const double x = j * t->L / Nx;
+      he[j] = sf_eta(W, x, time);
+      for (int m = 0; m < M1; ++m) {
+        const double sig = 0.5 * (std::cos(M_PI * m / t->Nz) + 1.0);
+        const double z = sig * (d + he[j]) - d;
+        sf_velocity(W, x, z, time, hu[(size_t)m * Nx + j], hw[(size_t)m * Nx + j]);
+      }
+    }
+    if (eta) WT_CK(cudaMemcpy(eta, he.data(), sizeof(double) * Nx, cudaMemcpyDefault));
+    if (u) WT_CK(cudaMemcpy(u, hu.data(), sizeof(double) * hu.size(), cudaMemcpyDefault));
+    if (w) WT_CK(cudaMemcpy(w, hw.data(), sizeof(double) * hw.size(), cudaMemcpyDefault));
+    if (c) *c = W.c;
     return WT_OK;
   });
 }

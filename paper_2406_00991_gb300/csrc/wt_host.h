@@ -140,6 +140,19 @@ struct AdjBufs {
   double last_rel = 0.0;
   double* col(int i) { return cols + (long)i * ncols; }
 };
+// A solved stream-function wave (wt_sfwave.cu): wavenumber k, still depth d,
+// height H, gravity g, N Fourier modes, speed c = U, flux Q, Bernoulli R,
+// stream-function coefficients B_1..B_N, surface cosine coefficients E_0..E_N.
+struct SfWave {
+  double k = 0, d = 0, H = 0, g = 0;
+  int N = 0;
+  double c = 0, U = 0, Q = 0, R = 0;
+  std::vector<double> B, E;
+};
+bool sf_solve(double k, double d, double H, double g, int N, SfWave& out);
+double sf_eta(const SfWave& W, double x, double t);
+// fixed-frame velocity at x, height z above the still water level, time t
+void sf_velocity(const SfWave& W, double x, double z, double t, double& u, double& w);
 }  // namespace wt
 
 struct wt_tank {
@@ -165,6 +178,8 @@ struct wt_tank {
   wt::Arena har;      // level hierarchy (rebuilt when coarsest_max changes)
   wt::Arena spar;     // spectral smoother tables (rebuilt with the hierarchy or the bathymetry)
   double hmin = 1.0;  // reference depth of the spectral smoother: min h of the fine bathymetry
+  double hmax = 1.0;  // max h of the fine bathymetry (flat-bottom checks)
+  wt::SfWave sf;      // last stream-function wave solved for this tank (cache)
   bool spec_ready = false;
 
   std::vector<std::array<int, 3>> dims;

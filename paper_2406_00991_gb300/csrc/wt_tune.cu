@@ -28,12 +28,33 @@ double now_ms() {
   return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
-// Second stage on the winner: the full-multigrid cycle instead of the
-// V-cycle, then the launch schedule of the V-cycles - the levels below
+// Second stage on the winner: the spectral smoothers, the full-multigrid
+// cycle instead of the V-cycle, then the launch schedule of the V-cycles - the levels below
 // tail_max unknowns in one launch (one CTA, or a cluster of 16 CTAs), or the
 // whole cycle as one cooperative launch - each kept only where it is faster.
 template <typename F>
 void refine_schedule(wt_options& bo, double& bms, F&& measure) {
+  {
+    // the mean-depth spectral smoother, alone or after block-Jacobi, with
+    // one or two sweeps each way
+    const wt_options base = bo;
+    const int kinds[] = {1, 2};
+    const int nus[] = {1, 2};
+    for (int kind : kinds)
+      for (int nu : nus) {
+        wt_options o = base;
+        o.smoother = kind;
+        o.nu1 = o.nu2 = nu;
+        o.tail_max = 0;
+        o.tail_cluster = 0;
+        o.vcycle_grid = 0;
+        const double ms = measure(o, bms);
+        if (ms > 0 && ms < bms) {
+          bms = ms;
+          bo = o;
+        }
+      }
+  }
   {
     // the full-multigrid cycle (Algorithm 2) as the preconditioner
     wt_options o = bo;
@@ -47,6 +68,7 @@ void refine_schedule(wt_options& bo, double& bms, F&& measure) {
       bo = o;
     }
   }
+  if (bo.smoother != 0) return;             // the one-launch schedules smooth by block-Jacobi only
   const wt_options base = bo;
   const int tails[] = {2048, 8192};
   const int clusters[] = {0, 16};
