@@ -340,6 +340,7 @@ def run_ours(args):
     if not args.no_extras:
         line["batch"] = bench_batch(w, torch, args)
         line["table1_cycles"] = bench_cycles(w, torch, p, h, st0)
+        line["e2_convergence"] = bench_e2(w)
         line["adjoint"] = bench_adjoint(w, torch, args)
         line["sea3d"] = bench_sea3d(w, torch, args)
     print(json.dumps(line), flush=True)
@@ -481,6 +482,36 @@ def bench_cycles(w, torch, p, h, st0):
                                      "rel_residual": info.rel_residual}
             T.close()
             out["%s_%s" % (mname, cname)] = row
+    return out
+
+
+def bench_e2(w):
+    """The paper's Sec. 5.2 accuracy study: error in u after one Runge-Kutta
+    step (dt = T / 1000) from an exact stream-function wave, for kh in {0.5,
+    2, 2 pi} and H/L at 0.1, 0.4, 0.7 of the Battjes limit, refining Nx at
+    Nz = 24 and Nz at Nx = 64 (FP64 solver at 1e-12)."""
+    out = {"workload": "stream-function waves, one wavelength per tank, flat bed h = 1, FP64 solver at 1e-12",
+           "error": "max |u - u_exact(dt)| / max |u_exact|", "cases": []}
+    for kh in (0.5, 2.0, 2 * math.pi):
+        for frac in (0.1, 0.4, 0.7):
+            k = kh
+            L = 2 * math.pi / k
+            H = frac * 0.1401 * math.tanh(0.8863 * kh) * 2 * math.pi / k
+            row = {"kh": kh, "H_over_L_battjes_fraction": frac, "Nx_at_Nz24": {}, "Nz_at_Nx64": {}}
+            for key, sizes in (("Nx_at_Nz24", [(8, 24), (16, 24), (32, 24), (64, 24)]),
+                               ("Nz_at_Nx64", [(64, 4), (64, 8), (64, 12), (64, 16), (64, 24)])):
+                for Nx, Nz in sizes:
+                    T = w.Tank(Nx, 1, Nz, L, np.ones((1, Nx)), mode=w.WT_FP64, tol=1e-12, max_it=400)
+                    eta, u, ww, c = T.stream_function_wave(1, H, 48, time=0.0)
+                    dt = L / c / 1000.0
+                    T.set_state(eta, u, np.zeros_like(u), ww)
+                    T.step(dt, 1)
+                    u1 = T.get_state()[1]
+                    _, ux, _, _ = T.stream_function_wave(1, H, 48, time=dt)
+                    T.close()
+                    row[key][str(Nx if key.startswith("Nx") else Nz)] = float(np.abs(u1 - ux).max() /
+                                                                             np.abs(ux).max())
+            out["cases"].append(row)
     return out
 
 

@@ -137,9 +137,12 @@ int wt_default_options(wt_options* opt);
 /*
  * Create a tank on the current CUDA device.  Sec. 2 (geometry), Sec. 3.4
  * (grids), Sec. 4.1 (level hierarchy).  bathymetry: h(x, y) > 0, [Ny][Nx].
- * g: gravity (9.81 in the paper), nu: kinematic viscosity (only nu = 0 is
- * supported by this build: WT_ENOTSUP otherwise).  On success *out owns all
- * device memory of the tank until wt_destroy.
+ * g: gravity (9.81 in the paper), nu >= 0: kinematic viscosity.  With nu > 0
+ * the forcing carries nu Div_b Grad_b q for every velocity component
+ * (Eq. sigmom1, forc1) and the bed is no-slip (Sec. 5.4): after every stage
+ * the velocity and its stage registers are zero on the bottom nodes.  The
+ * adjoint calls and the batched tanks cover nu = 0 only (WT_ENOTSUP).  On
+ * success *out owns all device memory of the tank until wt_destroy.
  */
 int wt_create(int Nx, int Ny, int Nz, double L, double g, double nu,
               const double* bathymetry, wt_tank** out);
@@ -250,6 +253,22 @@ int wt_adjoint_solve(wt_tank* t, const double* eta_a, const double* eta_b, const
                      double tol, wt_solve_info* info);
 int wt_adjoint_step(wt_tank* t, double dt, const double* eta, const double* u, const double* w,
                     double* lam_eta, double* lam_u, double* lam_w, double* dJ_dh);
+
+/*
+ * Relaxation zone (Sec. 5.5: the wave generation and absorption zones of the
+ * bar case, after Larsen & Dancy): for every column in the zone between x0
+ * and x1 (either order; no wrap-around), with xi = (x - x0) / (x1 - x0) in
+ * [0, 1], the state is blended towards the targets,
+ *   q <- (1 - w) q + w q_target,  w = (exp(xi^3.5) - 1) / (e - 1),
+ * so w = 0 at x0 (the zone's inner edge) and 1 at x1 (full target).  Apply
+ * it between steps, with targets taken at the state's time (for instance
+ * wt_stream_function_wave at that time for generation, zero for
+ * absorption).  eta_target [Ny][Nx], u/v/w_target [Nz+1][Ny][Nx]: host or
+ * device; a NULL target leaves that field alone (v_target is ignored in 2D).
+ * Needs a state (WT_EINVAL otherwise).
+ */
+int wt_relax(wt_tank* t, double x0, double x1, const double* eta_target, const double* u_target,
+             const double* v_target, const double* w_target);
 
 /*
  * Steady nonlinear periodic wave by the Fourier stream-function method of

@@ -22,12 +22,21 @@ Readings of the paper:
 * Filter placement (Sec. 3.6 says "every stage"): on the stage input
   (eta^(k-1), u^(k-1)) before anything else, so the projected u^(k) stays
   discretely divergence-free.  Off unless ``filter=True``.
+* Viscosity (nu > 0, Sec. 5.4): the forcing carries nu Div_b Grad_b q for
+  every velocity component, the composite discrete Laplacian of the
+  operator's interior rows, at every node (the surface rows use the same
+  collocation derivatives; no stress condition is printed); the bed is
+  no-slip: after each stage the velocity and its registers K are set to
+  zero on the bottom nodes.  The projection only zeroes the normal
+  velocity there, so the tangential part is reset explicitly (the
+  divergence invariant then holds up to that slip's size).
 * ``linear=True`` is the linearised model of Sec. 5.3 (Eq. NSElin, linFS):
   no advection, d eta/dt = w~, and the sigma-map frozen at the still-water
   level (eta = 0 in every metric), since linearising about rest also
   linearises the moving domain (otherwise O(kA) geometry terms remain).
 """
 
+import math
 from fractions import Fraction
 
 import numpy as np
@@ -188,6 +197,9 @@ def stage(tank, st, k, dt):
     st.u = st.u + b * st.Ku
     st.v = st.v + b * st.Kv
     st.w = st.w + b * st.Kw
+    if tank.nu != 0.0:                      # no-slip bed
+        for q in (st.u, st.v, st.w, st.Ku, st.Kv, st.Kw):
+            q[-1] = 0.0
     st.eta = eta_new
     st.p = p
     return st
@@ -198,6 +210,29 @@ def step(tank, st, dt):
     for k in range(1, STAGES + 1):
         stage(tank, st, k, dt)
     st.t += dt
+    return st
+
+
+def relaxation_weight(x, x0, x1):
+    """Target weight of a relaxation zone (Sec. 5.5, after Larsen & Dancy):
+    with xi = (x - x0) / (x1 - x0), w = (exp(xi^3.5) - 1) / (e - 1) inside the
+    zone (0 at its inner edge x0, 1 at x1), 0 outside."""
+    x = np.asarray(x, dtype=np.float64)
+    lo, hi = min(x0, x1), max(x0, x1)
+    xi = np.clip((x - x0) / (x1 - x0), 0.0, 1.0)
+    w = (np.exp(xi ** 3.5) - 1.0) / (math.e - 1.0)
+    return np.where((x >= lo) & (x <= hi), w, 0.0)
+
+
+def relax(tank, st, x0, x1, eta_t=None, u_t=None, v_t=None, w_t=None):
+    """q <- (1 - w) q + w q_target for the given targets (columns of the zone)."""
+    wgt = relaxation_weight(tank.grid.x, x0, x1)[None, :]
+    if eta_t is not None:
+        st.eta = (1.0 - wgt) * st.eta + wgt * eta_t
+    for name, tgt in (("u", u_t), ("v", v_t), ("w", w_t)):
+        if tgt is not None and not (name == "v" and tank.grid.Ny == 1):
+            q = getattr(st, name)
+            setattr(st, name, (1.0 - wgt[None]) * q + wgt[None] * tgt)
     return st
 
 

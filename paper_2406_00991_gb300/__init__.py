@@ -89,6 +89,7 @@ def _load():
         "wt_batch_set_stream": [P, P],
         "wt_time_kernel": [P, P, P, I, I, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long)],
         "wt_stream_function_wave": [P, I, D, I, D, P, P, P, ctypes.POINTER(D)],
+        "wt_relax": [P, D, D, P, P, P, P],
         "wt_last_error": [ctypes.c_char_p, ctypes.c_size_t],
     }
     for name, args in sig.items():
@@ -257,6 +258,11 @@ def wt_stream_function_wave(t, nwaves, H, nmodes, time, eta, u, w):
     st = _lib.wt_stream_function_wave(t, int(nwaves), float(H), int(nmodes), float(time), _ptr(eta), _ptr(u),
                                       _ptr(w), ctypes.byref(c))
     return st, c.value
+
+
+def wt_relax(t, x0, x1, eta_target, u_target, v_target, w_target):
+    return _lib.wt_relax(t, float(x0), float(x1), _ptr(eta_target), _ptr(u_target), _ptr(v_target),
+                         _ptr(w_target))
 
 
 WT_TIME_OPERATOR, WT_TIME_VCYCLE = 0, 1
@@ -496,6 +502,11 @@ class Tank:
         st, ms, n, b, f = wt_profile_read(self.handle, kernel_class)
         _check(st)
         return dict(ms=ms, launches=n, bytes=b, flops=f)
+
+    def relax(self, x0, x1, eta_target=None, u_target=None, w_target=None, v_target=None):
+        """Blend the state towards the targets inside the zone from x0 (weight 0)
+        to x1 (weight 1)."""
+        _check(wt_relax(self.handle, x0, x1, eta_target, u_target, v_target, w_target))
 
     def stream_function_wave(self, nwaves, H, nmodes=32, time=0.0):
         """(eta, u, w, c) of the stream-function wave at the tank's nodes (2D, flat bottom)."""

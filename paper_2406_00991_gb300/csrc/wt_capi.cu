@@ -584,6 +584,28 @@ int rk_stage(wt_tank& t, int k, double dt, AdjStage* rec = nullptr) {
   dds(t, t.u, us);
   dds(t, t.w, ws);
   if (y) dds(t, t.v, vs);
+  if (t.nu != 0.0) {
+    // nu Div_b Grad_b q for q = u, (v,) w with the derivatives just taken
+    auto& Vb = t.visc;
+    double *Gx = Vb[3], *Gy = Vb[4], *Gz = Vb[5], *dGx = Vb[6], *dGy = Vb[7], *sGx = Vb[8], *sGy = Vb[9],
+           *sGz = Vb[10];
+    auto lap = [&](const double* qx, const double* qy, const double* qs, double* out) {
+      WT_LAUNCH(t, K_STAGE, 8.0 * t.n * (y ? 6 : 4), 6.0 * t.n, launch_visc_grad(sa, qx, y ? qy : nullptr, qs, Gx, y ? Gy : nullptr, Gz, t.s));
+      ddx(t, Gx, dGx, M1);
+      if (y) ddy(t, Gy, dGy, M1);
+      dds(t, Gx, sGx);
+      if (y) dds(t, Gy, sGy);
+      dds(t, Gz, sGz);
+      WT_LAUNCH(t, K_STAGE, 8.0 * t.n * (y ? 6 : 4), 8.0 * t.n, launch_visc_div(sa, dGx, sGx, y ? dGy : nullptr, y ? sGy : nullptr, sGz, out, t.s));
+    };
+    lap(ux, uy, us, Vb[0]);
+    if (y) lap(vx, vy, vs, Vb[1]);
+    lap(wx, wy, ws, Vb[2]);
+    sa.nu = t.nu;
+    sa.lap_u = Vb[0];
+    sa.lap_v = y ? Vb[1] : nullptr;
+    sa.lap_w = Vb[2];
+  }
   WT_LAUNCH(t, K_STAGE, 8.0 * t.n * (y ? 24 : 14), 30.0 * t.n, launch_stage_forcing(sa, t.u, y ? t.v : nullptr, t.w, ux, uy, vx, vy, wx, wy, t.eta_x,
                              y ? t.eta_y : t.zero_s, t.f_eta, t.Ku, t.Kv, t.Kw, us, vs, ws, t.s));
   if (rec) {
@@ -611,6 +633,14 @@ int rk_stage(wt_tank& t, int k, double dt, AdjStage* rec = nullptr) {
   if (y) ddy(t, t.p, py, M1);
   dds(t, t.p, Dp);
   WT_LAUNCH(t, K_STAGE, 8.0 * t.n * (y ? 12 : 9), 16.0 * t.n, launch_stage_project(sa, px, py, Dp, t.Ku, t.Kv, t.Kw, t.u, y ? t.v : nullptr, t.w, t.dflag, t.s));
+  if (t.nu != 0.0) {
+    // no-slip bed (Sec. 5.4): the velocity and its stage registers vanish on
+    // the bottom nodes
+    const size_t off = (size_t)(M1 - 1) * t.ncols, bytes = sizeof(double) * t.ncols;
+    double* rows[] = {t.u, t.w, t.Ku, t.Kw, y ? t.v : nullptr, y ? t.Kv : nullptr};
+    for (double* q : rows)
+      if (q) WT_CK(cudaMemsetAsync(q + off, 0, bytes, t.s));
+  }
   std::swap(t.eta, t.eta_new);
   if (k == 5) t.time += dt;
   const int fl = read_flags(t);
@@ -695,7 +725,7 @@ int wt_create(int Nx, int Ny, int Nz, double L, double g, double nu, const doubl
   if (Nz < 2 || Nz > 32) return fail(WT_EINVAL, "Nz must be in [2, 32]");
   if (!(L > 0) || !std::isfinite(L)) return fail(WT_EINVAL, "L must be positive");
   if (!(g > 0) || !std::isfinite(g)) return fail(WT_EINVAL, "g must be positive");
-  if (nu != 0.0) return fail(WT_ENOTSUP, "viscosity nu != 0 is not supported by this build");
+  if (!(nu >= 0.0) || !std::isfinite(nu)) return fail(WT_EINVAL, "nu must be >= 0 and finite");
   if (!bathymetry) return fail(WT_EINVAL, "bathymetry pointer is NULL");
   return guarded([&]() -> int {
     std::unique_ptr<wt_tank> t(new wt_tank());
@@ -768,6 +798,8 @@ int wt_create(int Nx, int Ny, int Nz, double L, double g, double nu, const doubl
     t->Ku = ar.alloc<double>(n); t->Kv = ar.alloc<double>(n); t->Kw = ar.alloc<double>(n);
     t->p = ar.alloc<double>(n);
     for (int i = 0; i < 18; ++i) t->work.push_back(ar.alloc<double>(n));
+    if (nu != 0.0)                     // viscous term: three Laplacians and eight temporaries
+      for (int i = 0; i < 11; ++i) t->visc.push_back(ar.alloc<double>(n));
     t->io_s1 = ar.alloc<double>(nc); t->io_s2 = ar.alloc<double>(nc);
     t->io_f1 = ar.alloc<double>(n); t->io_f2 = ar.alloc<double>(n);
     t->dflag = ar.alloc<int>(4);
@@ -1153,6 +1185,42 @@ int wt_set_bathymetry(wt_tank* t, const double* h) {
   });
 }
 
+int wt_relax(wt_tank* t, double x0, double x1, const double* eta_target, const double* u_target,
+             const double* v_target, const double* w_target) {
+  if (!t) return fail(WT_EINVAL, "NULL tank");
+  if (!std::isfinite(x0) || !std::isfinite(x1) || x0 == x1) return fail(WT_EINVAL, "the zone needs x0 != x1");
+  if (!t->have_state) return fail(WT_EINVAL, "no state: call wt_set_state first");
+  return guarded([&]() -> int {
+    enter(*t);
+    const int Nx = t->Nx, nc = t->ncols;
+    const double lo = std::min(x0, x1), hi = std::max(x0, x1);
+    std::vector<double> wg(nc, 0.0);
+    for (int j = 0; j < Nx; ++j) {
+      const double x = j * t->L / Nx;
+      if (x < lo || x > hi) continue;
+      const double xi = (x - x0) / (x1 - x0);               // 0 at x0, 1 at x1
+      const double g = (std::exp(std::pow(xi, 3.5)) - 1.0) / (std::exp(1.0) - 1.0);
+      for (int jy = 0; jy < t->Ny; ++jy) wg[(size_t)jy * Nx + j] = g;
+    }
+    if (!t->relax_w) t->relax_w = t->ar.alloc<double>(nc);
+    WT_CK(cudaMemcpyAsync(t->relax_w, wg.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, t->s));
+    const long n = t->n;
+    // targets: device arrays as they are, host arrays through the staging buffers
+    const double* et = eta_target ? in_dev(*t, eta_target, t->io_s1, nc) : nullptr;
+    const double* ut = u_target ? in_dev(*t, u_target, t->io_f1, n) : nullptr;
+    const double* wt_ = w_target ? in_dev(*t, w_target, t->io_f2, n) : nullptr;
+    const double* vt = nullptr;
+    if (v_target && t->Ny > 1) {
+      vt = in_dev(*t, v_target, t->work[0], n);
+    }
+    WT_CK(launch_relax(nc, t->M1, t->relax_w, et, ut, vt, wt_, t->eta, t->u, t->Ny > 1 ? t->v : nullptr, t->w,
+                       t->s));
+    WT_CK(cudaStreamSynchronize(t->s));
+    t->prof.launches += 1;
+    return WT_OK;
+  });
+}
+
 int wt_stream_function_wave(wt_tank* t, int nwaves, double H, int nmodes, double time, double* eta,
                             double* u, double* w, double* c) {
   if (!t) return fail(WT_EINVAL, "NULL tank");
@@ -1246,6 +1314,7 @@ int wt_adjoint_solve(wt_tank* t, const double* eta_a, const double* eta_b, const
 
 int wt_adjoint_step(wt_tank* t, double dt, const double* eta, const double* u, const double* w,
                     double* lam_eta, double* lam_u, double* lam_w, double* dJ_dh) {
+  if (t && t->nu != 0.0) return fail(WT_ENOTSUP, "the adjoint step covers the inviscid model (nu = 0)");
   if (!t || !eta || !u || !w || !lam_eta || !lam_u || !lam_w) return fail(WT_EINVAL, "NULL argument");
   if (t->Ny != 1) return fail(WT_ENOTSUP, "the adjoint step is 2D only");
   if (!(dt > 0) || !std::isfinite(dt)) return fail(WT_EINVAL, "dt must be positive");
@@ -1373,6 +1442,7 @@ int wt_create_batch(int ntanks, const int* Nx, const int* Nz, const double* L, d
   if (!out || !Nx || !Nz || !L || !bathymetry) return fail(WT_EINVAL, "NULL argument");
   *out = nullptr;
   if (ntanks < 1 || ntanks > 65535) return fail(WT_EINVAL, "ntanks must be in [1, 65535]");
+  if (nu != 0.0) return fail(WT_ENOTSUP, "batched tanks run the inviscid model (nu = 0)");
   std::unique_ptr<wt_batch> b(new wt_batch());
   for (int i = 0; i < ntanks; ++i) {
     wt_tank* t = nullptr;

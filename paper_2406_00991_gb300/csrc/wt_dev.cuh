@@ -1041,6 +1041,11 @@ __device__ inline void stage_forcing_body(long t0, long ts, StageArgs a, const d
         Fv -= uu * vx[e] + vv * vy[e] + wsig * vs[e];
       }
     }
+    if (a.nu != 0.0) {                   // nu Div_b Grad_b q (Eq. sigmom1, forc1)
+      Fu += a.nu * a.lap_u[e];
+      Fw += a.nu * a.lap_w[e];
+      if (v) Fv += a.nu * a.lap_v[e];
+    }
     const double ku = a.alpha * Ku[e] + a.dt * Fu;
     const double kw = a.alpha * Kw[e] + a.dt * Fw;
     Ku[e] = ku;

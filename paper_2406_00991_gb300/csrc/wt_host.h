@@ -212,6 +212,8 @@ struct wt_tank {
   double *u = nullptr, *v = nullptr, *w = nullptr, *Ku = nullptr, *Kv = nullptr, *Kw = nullptr;
   double *p = nullptr;
   std::vector<double*> work;       // fine-level FP64 temporaries
+  std::vector<double*> visc;       // viscous term (nu != 0): laplacians of u, v, w and temporaries
+  double* relax_w = nullptr;       // relaxation-zone weights per column (first wt_relax)
   double *io_s1 = nullptr, *io_s2 = nullptr, *io_f1 = nullptr, *io_f2 = nullptr;
   double time = 0;
   bool have_state = false;

@@ -331,7 +331,23 @@ struct StageArgs {
   const double* sigma;
   const double* D;        // d/dsigma [M1*M1]
   const double* meta;     // finest-level metric (a = new, b = old)
+  // viscous term nu Div_b Grad_b q of each velocity component (NULL: none)
+  double nu = 0.0;
+  const double *lap_u = nullptr, *lap_v = nullptr, *lap_w = nullptr;
 };
+// Viscous term, two pointwise halves around the derivative passes (geometry
+// b of the stage's metric): grad: Gx = qx + sigma_x qs, Gy = qy + sigma_y qs
+// (Gy NULL in 2D), Gz = sigma_z qs; div: lap = dGx + sigma_x sGx + dGy +
+// sigma_y sGy + sigma_z sGz (x- / y-derivatives d, sigma-derivatives s).
+cudaError_t launch_visc_grad(const StageArgs& a, const double* qx, const double* qy, const double* qs,
+                             double* Gx, double* Gy, double* Gz, cudaStream_t s);
+cudaError_t launch_visc_div(const StageArgs& a, const double* dGx, const double* sGx, const double* dGy,
+                            const double* sGy, const double* sGz, double* lap, cudaStream_t s);
+// Relaxation zone: q = (1 - wgt) q + wgt q_target for eta (per column) and
+// the velocity fields (every sigma row), wgt per column.
+cudaError_t launch_relax(int ncols, int M1, const double* wgt, const double* eta_t, const double* u_t,
+                         const double* v_t, const double* w_t, double* eta, double* u, double* v, double* w,
+                         cudaStream_t s);
 cudaError_t launch_stage_forcing(const StageArgs& a, const double* u, const double* v,
                                  const double* w, const double* ux, const double* uy,
                                  const double* vx, const double* vy, const double* wx,

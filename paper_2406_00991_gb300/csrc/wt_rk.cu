@@ -77,6 +77,70 @@ __global__ void k_stage_project(StageArgs a, const double* __restrict__ px, cons
   stage_project_body(TLOOP, a, px, py, Dp, Ku, Kv, Kw, u, v, w, flag);
 }
 
+__global__ void k_visc_grad(StageArgs a, const double* __restrict__ qx, const double* __restrict__ qy,
+                            const double* __restrict__ qs, double* __restrict__ Gx, double* __restrict__ Gy,
+                            double* __restrict__ Gz) {
+  const long nc = a.ncols;
+  GRID_LOOP(e, (long)a.M1 * nc) {
+    const int m = (int)(e / nc);
+    const long c = e - m * nc;
+    const double s = a.sigma[m];
+    const double* meta = a.meta;
+    const double sxb = meta[M_AXb * nc + c] - s * meta[M_BXb * nc + c];
+    const double q = qs[e];
+    Gx[e] = qx[e] + sxb * q;
+    if (Gy) Gy[e] = qy[e] + (meta[M_AYb * nc + c] - s * meta[M_BYb * nc + c]) * q;
+    Gz[e] = meta[M_Zb * nc + c] * q;
+  }
+}
+
+__global__ void k_visc_div(StageArgs a, const double* __restrict__ dGx, const double* __restrict__ sGx,
+                           const double* __restrict__ dGy, const double* __restrict__ sGy,
+                           const double* __restrict__ sGz, double* __restrict__ lap) {
+  const long nc = a.ncols;
+  GRID_LOOP(e, (long)a.M1 * nc) {
+    const int m = (int)(e / nc);
+    const long c = e - m * nc;
+    const double s = a.sigma[m];
+    const double* meta = a.meta;
+    double v = dGx[e] + (meta[M_AXb * nc + c] - s * meta[M_BXb * nc + c]) * sGx[e] + meta[M_Zb * nc + c] * sGz[e];
+    if (dGy) v += dGy[e] + (meta[M_AYb * nc + c] - s * meta[M_BYb * nc + c]) * sGy[e];
+    lap[e] = v;
+  }
+}
+
+__global__ void k_relax(int ncols, int M1, const double* __restrict__ wgt, const double* __restrict__ eta_t,
+                        const double* __restrict__ u_t, const double* __restrict__ v_t,
+                        const double* __restrict__ w_t, double* __restrict__ eta, double* __restrict__ u,
+                        double* __restrict__ v, double* __restrict__ w) {
+  GRID_LOOP(e, (long)M1 * ncols) {
+    const long c = e % ncols;
+    const double g = wgt[c];
+    if (g == 0.0) continue;
+    if (e < ncols && eta_t) eta[c] = (1.0 - g) * eta[c] + g * eta_t[c];
+    if (u_t) u[e] = (1.0 - g) * u[e] + g * u_t[e];
+    if (v && v_t) v[e] = (1.0 - g) * v[e] + g * v_t[e];
+    if (w_t) w[e] = (1.0 - g) * w[e] + g * w_t[e];
+  }
+}
+
+cudaError_t launch_visc_grad(const StageArgs& a, const double* qx, const double* qy, const double* qs,
+                             double* Gx, double* Gy, double* Gz, cudaStream_t s) {
+  k_visc_grad<<<blocks_n((long)a.M1 * a.ncols), 256, 0, s>>>(a, qx, qy, qs, Gx, Gy, Gz);
+  return cudaGetLastError();
+}
+cudaError_t launch_visc_div(const StageArgs& a, const double* dGx, const double* sGx, const double* dGy,
+                            const double* sGy, const double* sGz, double* lap, cudaStream_t s) {
+  k_visc_div<<<blocks_n((long)a.M1 * a.ncols), 256, 0, s>>>(a, dGx, sGx, dGy, sGy, sGz, lap);
+  return cudaGetLastError();
+}
+cudaError_t launch_relax(int ncols, int M1, const double* wgt, const double* eta_t, const double* u_t,
+                         const double* v_t, const double* w_t, double* eta, double* u, double* v, double* w,
+                         cudaStream_t s) {
+  k_relax<<<blocks_n((long)M1 * ncols), 256, 0, s>>>(ncols, M1, wgt, eta_t, u_t, v_t, w_t, eta, u, v, w);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_metric_fill(int ncols, const double* h, const double* hx, const double* hy,
                                const double* ea, const double* eax, const double* eay,
                                const double* eb, const double* ebx, const double* eby, double* meta,

@@ -51,10 +51,10 @@ def test_argument_checks_without_gpu():
     assert st == w.WT_EINVAL
     st, h = w.wt_create(64, 1, 40, 1.0, 9.81, 0.0, np.ones(64))
     assert st == w.WT_EINVAL
-    st, h = w.wt_create(64, 1, 16, 1.0, 9.81, 1e-6, np.ones(64))
-    assert st == w.WT_ENOTSUP
+    st, h = w.wt_create(64, 1, 16, 1.0, 9.81, -1e-6, np.ones(64))
+    assert st == w.WT_EINVAL
     code, msg = w.wt_last_error()
-    assert code == w.WT_ENOTSUP and "viscosity" in msg
+    assert code == w.WT_EINVAL and "nu" in msg
     assert w.wt_destroy(None) == w.WT_OK
 
 

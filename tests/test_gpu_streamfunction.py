@@ -1,0 +1,87 @@
+"""Stream-function waves on the GPU path: the library's host solver
+(wt_stream_function_wave, analytic Jacobian) against the oracle's
+(central-difference Jacobian) at the tank's nodes, and the paper's Sec. 5.2
+accuracy study - one Runge-Kutta step from the exact steady wave, error of u
+against the exact translated wave - converging spectrally in Nx and in Nz.
+The exact wave solves the inviscid nonlinear problem, so this also checks the
+nonlinear forcing, the free-surface update and the projection end to end."""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import operator as op
+from oracle import streamfunction as sf
+
+pytestmark = pytest.mark.gpu
+
+G = 9.81
+
+
+@pytest.fixture(scope="module")
+def wt():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2406_00991_gb300 as w
+    return w
+
+
+def battjes_height(kh, frac, k):
+    return frac * 0.1401 * math.tanh(0.8863 * kh) * 2 * math.pi / k
+
+
+@pytest.mark.parametrize("kh,frac", [(0.5, 0.5), (2.0, 0.5), (2 * math.pi, 0.5), (2.0, 0.7)])
+def test_library_wave_matches_oracle(wt, kh, frac):
+    d = 1.0
+    k = kh / d
+    L = 2 * math.pi / k
+    H = battjes_height(kh, frac, k)
+    Nx, Nz = 64, 16
+    T = wt.Tank(Nx, 1, Nz, L, np.full((1, Nx), d))
+    for t in (0.0, 0.37):
+        eta, u, w, c = T.stream_function_wave(1, H, 32, time=t)
+        W = sf.solve(k, d, H, N=32)
+        g = op.Grid(Nx, 1, Nz, L)
+        eref = W.eta(g.x, t)
+        z = g.sigma[:, None] * (d + eref[None, :]) - d
+        uref, wref = W.velocity(g.x[None, :], z, t)
+        assert abs(c - W.c) < 1e-12 * W.c
+        assert np.abs(eta[0] - eref).max() < 1e-10 * H
+        scale = np.abs(uref).max()
+        assert np.abs(u[:, 0] - uref).max() < 1e-10 * scale
+        assert np.abs(w[:, 0] - wref).max() < 1e-10 * scale
+    with pytest.raises(wt.WtError) as e:
+        T.stream_function_wave(1, battjes_height(kh, 0.95, k), 32)       # above 0.85 x Battjes
+    assert e.value.code == wt.WT_EINVAL
+
+
+def one_step_error(wt, kh, frac, Nx, Nz, nmodes=48):
+    d = 1.0
+    k = kh / d
+    L = 2 * math.pi / k
+    H = battjes_height(kh, frac, k)
+    T = wt.Tank(Nx, 1, Nz, L, np.full((1, Nx), d), mode=0, tol=1e-12, max_it=400)
+    eta, u, w, c = T.stream_function_wave(1, H, nmodes, time=0.0)
+    period = L / c
+    dt = period / 1000.0
+    T.set_state(eta, u, np.zeros_like(u), w)
+    T.step(dt, 1)
+    e1, u1, _, w1, _ = T.get_state()
+    eta_x, u_x, w_x, _ = T.stream_function_wave(1, H, nmodes, time=dt)
+    T.close()
+    return np.abs(u1 - u_x).max() / np.abs(u_x).max()
+
+
+@pytest.mark.parametrize("kh", [0.5, 2.0, 2 * math.pi])
+def test_spectral_convergence_one_step(wt, kh):
+    frac = 0.4
+    ex = [one_step_error(wt, kh, frac, Nx, 24) for Nx in (8, 16, 32)]
+    ez = [one_step_error(wt, kh, frac, 64, Nz) for Nz in (4, 8, 12)]
+    print("kh %.3f: error in u after one step, Nx 8/16/32 (Nz 24):" % kh, ex, " Nz 4/8/12 (Nx 64):", ez)
+    floor = 1e-9
+    for seq in (ex, ez):
+        for a, b in zip(seq, seq[1:]):
+            assert b < 0.1 * a or b < floor, seq
+    assert min(ex[-1], ez[-1]) < 1e-6

@@ -1,0 +1,162 @@
+"""Viscous model and relaxation zones on the GPU path (paper Sec. 5.4 and 5.5):
+
+* five stages with nu > 0 against the oracle's (nu Div_b Grad_b q in the
+  forcing, no-slip bed), at the RK-parity bounds (1e-10 eta, 1e-8 u, w);
+* the oscillatory wave boundary layer of Sec. 5.4: the linearised model
+  started from the analytic solution (outer linear-wave flow plus the Stokes
+  layer U_0m exp(-zeta/delta_1) cos(wt - kx - zeta/delta_1), delta_1 =
+  sqrt(2 nu / w)) keeps it, to a few percent of U_0m, over two and a quarter
+  periods, while the inviscid model loses it;
+* relaxation zones against the oracle's blend, and an absorbing zone that
+  drains a wave's energy."""
+
+import math
+
+import numpy as np
+import pytest
+
+import seeded_inputs as si
+from oracle import operator as op
+from oracle import rk
+
+pytestmark = pytest.mark.gpu
+
+G = 9.81
+
+
+@pytest.fixture(scope="module")
+def wt():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_2406_00991_gb300 as w
+    return w
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_viscous_stages_parity(wt, mode):
+    Nx, Nz, L, nu = 64, 12, 2 * math.pi, 5e-3
+    x = np.arange(Nx) * L / Nx
+    h = (1.0 - 0.3 * np.exp(-((x - L / 2) / 1.0) ** 2))[None]
+    g = op.Grid(Nx, 1, Nz, L)
+    eta0 = si.stokes2_eta(x, 0.03, 1.0, 1.0)[None]
+    geo = op.Geometry(g, h, eta0)
+    u0, w0 = si.linear_velocity(x[None, None, :], geo.z_nodes(g), 0.03, 1.0, 1.0)
+    tank_o = rk.Tank(Nx, 1, Nz, L, h, nu=nu, tol=1e-13, coarsest_max=64)
+    st = rk.State(g, eta0, u0, np.zeros_like(u0), w0)
+    T = wt.Tank(Nx, 1, Nz, L, h, nu=nu, mode=mode, tol=1e-12)
+    T.set_state(np.ascontiguousarray(eta0), np.ascontiguousarray(u0), np.zeros_like(u0),
+                np.ascontiguousarray(w0))
+    dt = 0.01
+    for k in range(1, 6):
+        rk.stage(tank_o, st, k, dt)
+        T.rk_stage(k, dt)
+    eta, u, v, w, tm = T.get_state()
+    assert np.abs(eta - st.eta).max() <= 1e-10 * np.abs(st.eta).max()
+    assert np.abs(u - st.u).max() <= 1e-8 * np.abs(st.u).max()
+    assert np.abs(w - st.w).max() <= 1e-8 * np.abs(st.w).max()
+    assert np.all(u[-1] == 0.0) and np.all(w[-1] == 0.0)
+    # the viscous term matters at this size: the inviscid step differs
+    st0 = rk.State(g, eta0, u0, np.zeros_like(u0), w0)
+    tank_i = rk.Tank(Nx, 1, Nz, L, h, tol=1e-13, coarsest_max=64)
+    rk.step(tank_i, st0, dt)
+    assert np.abs(u - st0.u).max() > 1e-4 * np.abs(st.u).max()
+    T.close()
+
+
+def boundary_layer(x, zeta, t, H, k, h, omega, nu):
+    """Linear wave (amplitude H/2) over a flat bed with its Stokes layer."""
+    d1 = math.sqrt(2.0 * nu / omega)
+    U0m = 0.5 * H * omega / math.sinh(k * h)
+    ph = omega * t - k * x
+    z = zeta - h
+    u = 0.5 * H * omega * np.cosh(k * (z + h)) / math.sinh(k * h) * np.cos(ph) \
+        - U0m * np.exp(-zeta / d1) * np.cos(ph - zeta / d1)
+    w = -0.5 * H * omega * np.sinh(k * (z + h)) / math.sinh(k * h) * np.sin(ph)
+    eta = 0.5 * H * np.cos(ph)
+    return eta, u, w, U0m, d1
+
+
+@pytest.mark.parametrize("nu", [1e-4])
+def test_oscillatory_boundary_layer(wt, nu):
+    h, kh, H = 0.4, 0.6725, 0.02
+    k = kh / h
+    L = 2 * math.pi / k
+    omega = math.sqrt(G * k * math.tanh(kh))
+    Tp = 2 * math.pi / omega
+    Nx, Nz = 16, 32
+    g = op.Grid(Nx, 1, Nz, L)
+    zeta = (g.sigma * h)[:, None, None] * np.ones((1, 1, Nx))       # linear model: still-water nodes
+    X = np.broadcast_to(g.x[None, None, :], g.shape)
+    eta0, u0, w0, U0m, d1 = boundary_layer(g.x[None, :], zeta, 0.0, H, k, h, omega, nu)
+    nsteps = 900                                                    # 2.25 periods
+    dt = 2.25 * Tp / nsteps
+    _, uex, _, _, _ = boundary_layer(X, zeta, nsteps * dt, H, k, h, omega, nu)
+    near = (zeta[:, 0, 0] > 0) & (zeta[:, 0, 0] < 5 * d1)
+    assert near.sum() >= 3
+    errs = {}
+    for nu_run in (nu, 0.0):
+        T = wt.Tank(Nx, 1, Nz, L, np.full((1, Nx), h), nu=nu_run, mode=0, tol=1e-12, linear=1)
+        T.set_state(np.ascontiguousarray(eta0), np.ascontiguousarray(u0), np.zeros_like(u0),
+                    np.ascontiguousarray(w0))
+        T.step(dt, nsteps)
+        _, u, _, _, _ = T.get_state()
+        errs[nu_run] = np.abs(u[near] - uex[near]).max() / U0m
+        T.close()
+    print("boundary layer: max |u - u_exact| / U0m within 5 delta_1 of the bed, viscous %.3e, inviscid %.3e"
+          % (errs[nu], errs[0.0]))
+    assert errs[nu] < 0.05
+    assert errs[0.0] > 0.3
+
+
+def test_relaxation_matches_oracle_and_absorbs(wt):
+    Nx, Nz, L = 128, 12, 8 * math.pi
+    g = op.Grid(Nx, 1, Nz, L)
+    h = np.ones((1, Nx))
+    A = 0.01
+    eta0 = si.airy(g.x, None, A=A)[None]
+    geo = op.Geometry(g, h[0], np.zeros(Nx))
+    _, u0, w0 = si.airy(g.x[None, None, :], geo.z_nodes(g), A=A)
+    r = np.random.default_rng(4)
+    tgt = [r.standard_normal((1, Nx)) * 0.01, r.standard_normal(g.shape), r.standard_normal(g.shape)]
+    x0, x1 = 0.75 * L, L - L / Nx
+    # one blend against the oracle's
+    T = wt.Tank(Nx, 1, Nz, L, h, mode=0, tol=1e-12, linear=1)
+    T.set_state(np.ascontiguousarray(eta0), np.ascontiguousarray(u0), np.zeros_like(u0), np.ascontiguousarray(w0))
+    T.relax(x0, x1, *tgt)
+    e1, u1, _, w1, _ = T.get_state()
+    tank_o = rk.Tank(Nx, 1, Nz, L, h, linear=True)
+    so = rk.State(g, eta0, u0, np.zeros_like(u0), w0)
+    rk.relax(tank_o, so, x0, x1, tgt[0], tgt[1], None, tgt[2])
+    for a, b in ((e1, so.eta), (u1, so.u), (w1, so.w)):
+        assert np.abs(a - b).max() <= 1e-14 * max(1.0, np.abs(b).max())
+    # an absorbing zone (target: rest) drains the wave; without it the energy stays
+    Tp = 2 * math.pi / si.omega(1.0, 1.0)
+    dt = Tp / 40
+    energy = {}
+    for absorb in (False, True):
+        T.set_state(np.ascontiguousarray(eta0), np.ascontiguousarray(u0), np.zeros_like(u0),
+                    np.ascontiguousarray(w0))
+        for _ in range(160):                               # four periods
+            T.step(dt, 1)
+            if absorb:
+                T.relax(x0, x1, np.zeros((1, Nx)), np.zeros(g.shape), np.zeros(g.shape))
+        energy[absorb] = float(np.sum(T.get_state()[0] ** 2))
+    e0 = float(np.sum(eta0 ** 2))
+    print("wave energy after four periods / initial: free %.4f, absorbing zone %.4f"
+          % (energy[False] / e0, energy[True] / e0))
+    assert abs(energy[False] / e0 - 1.0) < 0.01
+    assert energy[True] < 0.2 * e0
+    T.close()
+
+
+def test_viscous_limits(wt):
+    with pytest.raises(wt.WtError) as e:
+        wt.Batch([64], [8], [1.0], [np.ones((1, 64))], nu=1e-3)
+    assert e.value.code == wt.WT_ENOTSUP
+    T = wt.Tank(32, 1, 8, 1.0, np.ones((1, 32)), nu=1e-3)
+    z = np.zeros((1, 32))
+    f = np.zeros(T.shape)
+    with pytest.raises(wt.WtError) as e:
+        T.adjoint_step(0.01, z, f, f, z.copy(), f.copy(), f.copy())
+    assert e.value.code == wt.WT_ENOTSUP

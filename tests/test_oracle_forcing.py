@@ -138,3 +138,44 @@ def test_forcing_spectral_convergence_in_nz():
         _, F = rk.forcing(tank, op.Geometry(g, h, st.eta), st)
         errs.append(np.abs(F[0] - F_ref[0]).max())
     assert errs[1] < 1e-2 * errs[0] and errs[2] < 1e-2 * errs[1]
+
+
+def test_viscous_term_is_the_physical_laplacian():
+    # q = sin(x) z^2 with z = sigma d - h on a curved, moving geometry: the
+    # composite Div_b Grad_b q must equal the physical Laplacian
+    # (2 - z^2) sin(x) at every node (q is band-limited in x and quadratic in
+    # sigma, so the discrete derivatives are exact to rounding)
+    g, L, h, eta, ex, ey, d, s, X, Y, Z = _setup(32, 1, 12)
+    q = np.sin(X) * Z ** 2
+    geo = op.Geometry(g, h, eta)
+    lap = op.div(g, geo, op.grad(g, geo, q))
+    want = (2.0 - Z ** 2) * np.sin(X)
+    assert np.abs(lap - want).max() <= 1e-10 * np.abs(want).max()
+    # and it enters the forcing with the factor nu
+    tank0 = rk.Tank(32, 1, 12, L, h, g=9.81)
+    tank1 = rk.Tank(32, 1, 12, L, h, g=9.81, nu=0.3)
+    st = rk.State(g, eta, q, np.zeros_like(q), np.zeros_like(q))
+    _, F0 = rk.forcing(tank0, geo, st)
+    _, F1 = rk.forcing(tank1, geo, st)
+    assert np.abs((F1[0] - F0[0]) - 0.3 * want).max() <= 1e-10 * 0.3 * np.abs(want).max()
+
+
+def test_viscous_stage_is_no_slip_and_relaxation_weights():
+    Nx, Nz, L = 32, 10, 2 * math.pi
+    g = op.Grid(Nx, 1, Nz, L)
+    h = np.ones((1, Nx))
+    eta = 0.01 * np.cos(g.x)[None]
+    u = np.broadcast_to(0.05 * np.cos(g.x)[None, None, :], g.shape).copy()
+    w = np.zeros(g.shape)
+    tank = rk.Tank(Nx, 1, Nz, L, h, nu=1e-3, solver="dense")
+    st = rk.State(g, eta, u, np.zeros_like(u), w)
+    rk.stage(tank, st, 1, 1e-3)
+    assert np.all(st.u[-1] == 0.0) and np.all(st.w[-1] == 0.0) and np.all(st.Ku[-1] == 0.0)
+    assert np.abs(st.u[0]).max() > 0.04
+    x = np.linspace(0.0, 4.0, 401)
+    wg = rk.relaxation_weight(x, 1.0, 3.0)
+    assert wg[x < 1.0].max() == 0.0 and wg[x > 3.0].max() == 0.0
+    assert abs(wg[100]) < 1e-15 and abs(wg[300] - 1.0) < 1e-15
+    inside = wg[(x >= 1.0) & (x <= 3.0)]
+    assert np.all(np.diff(inside) >= 0.0)
+    assert np.allclose(rk.relaxation_weight(x, 3.0, 1.0), rk.relaxation_weight(4.0 - x, 1.0, 3.0))
