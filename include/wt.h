@@ -139,8 +139,10 @@ int wt_default_options(wt_options* opt);
  * (grids), Sec. 4.1 (level hierarchy).  bathymetry: h(x, y) > 0, [Ny][Nx].
  * g: gravity (9.81 in the paper), nu >= 0: kinematic viscosity.  With nu > 0
  * the forcing carries nu Div_b Grad_b q for every velocity component
- * (Eq. sigmom1, forc1) and the bed is no-slip (Sec. 5.4): after every stage
- * the velocity and its stage registers are zero on the bottom nodes.  The
+ * (Eq. sigmom1, forc1) with the vertical component of Grad_b q set to zero on
+ * the surface nodes (a stress-free surface), and the bed is no-slip
+ * (Sec. 5.4): after every stage the velocity and its stage registers are
+ * zero on the bottom nodes.  The
  * adjoint calls and the batched tanks cover nu = 0 only (WT_ENOTSUP).  On
  * success *out owns all device memory of the tank until wt_destroy.
  */

@@ -24,12 +24,15 @@ Readings of the paper:
   discretely divergence-free.  Off unless ``filter=True``.
 * Viscosity (nu > 0, Sec. 5.4): the forcing carries nu Div_b Grad_b q for
   every velocity component, the composite discrete Laplacian of the
-  operator's interior rows, at every node (the surface rows use the same
-  collocation derivatives; no stress condition is printed); the bed is
-  no-slip: after each stage the velocity and its registers K are set to
-  zero on the bottom nodes.  The projection only zeroes the normal
-  velocity there, so the tangential part is reset explicitly (the
-  divergence invariant then holds up to that slip's size).
+  operator's interior rows, at every node.  No surface condition is
+  printed; the reading is a stress-free surface: the vertical component of
+  Grad_b q is zero on the surface nodes before the divergence (without a
+  condition there the collocation Laplacian is not dissipative and the
+  explicit stages blow up).  The bed is no-slip: after each stage the
+  velocity and its registers K are set to zero on the bottom nodes.  The
+  projection only zeroes the normal velocity there, so the tangential part
+  is reset explicitly (the divergence invariant then holds up to that
+  slip's size).
 * ``linear=True`` is the linearised model of Sec. 5.3 (Eq. NSElin, linFS):
   no advection, d eta/dt = w~, and the sigma-map frozen at the still-water
   level (eta = 0 in every metric), since linearising about rest also
@@ -142,7 +145,9 @@ def forcing(tank, geo_b, st):
             F[i] -= st.u * gr.dx(q) + st.v * gr.dy(q) + wsig * gr.ds(q)
     if tank.nu != 0.0:
         for i, q in enumerate((st.u, st.v, st.w)):
-            F[i] += tank.nu * div(gr, geo_b, grad(gr, geo_b, q))
+            G = grad(gr, geo_b, q)
+            G[2][0] = 0.0                     # stress-free surface: no vertical flux
+            F[i] += tank.nu * div(gr, geo_b, G)
     return f_eta, F
 
 

@@ -337,8 +337,10 @@ struct StageArgs {
 };
 // Viscous term, two pointwise halves around the derivative passes (geometry
 // b of the stage's metric): grad: Gx = qx + sigma_x qs, Gy = qy + sigma_y qs
-// (Gy NULL in 2D), Gz = sigma_z qs; div: lap = dGx + sigma_x sGx + dGy +
-// sigma_y sGy + sigma_z sGz (x- / y-derivatives d, sigma-derivatives s).
+// (Gy NULL in 2D), Gz = sigma_z qs except Gz = 0 on the surface row (the
+// stress-free surface: no vertical viscous flux there); div: lap = dGx +
+// sigma_x sGx + dGy + sigma_y sGy + sigma_z sGz (x- / y-derivatives d,
+// sigma-derivatives s).
 cudaError_t launch_visc_grad(const StageArgs& a, const double* qx, const double* qy, const double* qs,
                              double* Gx, double* Gy, double* Gz, cudaStream_t s);
 cudaError_t launch_visc_div(const StageArgs& a, const double* dGx, const double* sGx, const double* dGy,

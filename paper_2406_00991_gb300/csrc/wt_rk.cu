@@ -90,7 +90,7 @@ __global__ void k_visc_grad(StageArgs a, const double* __restrict__ qx, const do
     const double q = qs[e];
     Gx[e] = qx[e] + sxb * q;
     if (Gy) Gy[e] = qy[e] + (meta[M_AYb * nc + c] - s * meta[M_BYb * nc + c]) * q;
-    Gz[e] = meta[M_Zb * nc + c] * q;
+    Gz[e] = m == 0 ? 0.0 : meta[M_Zb * nc + c] * q;     // stress-free surface: no vertical flux
   }
 }
 
