@@ -502,12 +502,12 @@ def bench_e2(w):
                                ("Nz_at_Nx64", [(64, 4), (64, 8), (64, 12), (64, 16), (64, 24)])):
                 for Nx, Nz in sizes:
                     T = w.Tank(Nx, 1, Nz, L, np.ones((1, Nx)), mode=w.WT_FP64, tol=1e-12, max_it=400)
-                    eta, u, ww, c = T.stream_function_wave(1, H, 48, time=0.0)
+                    eta, u, ww, c = T.stream_function_wave(1, H, 32, time=0.0)
                     dt = L / c / 1000.0
                     T.set_state(eta, u, np.zeros_like(u), ww)
                     T.step(dt, 1)
                     u1 = T.get_state()[1]
-                    _, ux, _, _ = T.stream_function_wave(1, H, 48, time=dt)
+                    _, ux, _, _ = T.stream_function_wave(1, H, 32, time=dt)
                     T.close()
                     row[key][str(Nx if key.startswith("Nx") else Nz)] = float(np.abs(u1 - ux).max() /
                                                                              np.abs(ux).max())
