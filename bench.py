@@ -367,12 +367,21 @@ def bench_batch(w, torch, args):
                        "over Gaussian bars), one persistent launch (one CTA per tank, largest first)",
            "metric": "RK4 DOF-updates/s", "unit": UNIT, "steps": K, "tanks_redrawn": redrawn,
            "timing": "CUDA events on the batch's stream around one wt_batch_step call of K steps"}
+    tuned = None
     for name, mode in (("mixed", w.WT_MIXED), ("fp64", w.WT_FP64)):
         B = w.Batch([q["Nx"] for q in tanks], [q["Nz"] for q in tanks], [q["L"] for q in tanks], hs,
                     tol=1e-10, mode=mode)
         B.set_stream(stream.cuda_stream)
         for i, s_ in enumerate(st):
             B.set_state(i, *s_)
+        if tuned is None:
+            # damping and sweep counts picked by the batch autotuner on one step of
+            # the mixed batch (the FP64 batch runs with the same smoother settings)
+            tuned, tuned_ms, entry_ms = B.autotune(dts, reps=1)
+            out["autotuned"] = {"omega": tuned["omega"], "nu1": tuned["nu1"], "nu2": tuned["nu2"],
+                                "tuned_ms_per_step": tuned_ms, "default_ms_per_step": entry_ms}
+        else:
+            B.set_options(mode=mode, tol=1e-10, omega=tuned["omega"], nu1=tuned["nu1"], nu2=tuned["nu2"])
         B.step(dts, 1)                               # warm-up
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()

@@ -346,6 +346,21 @@ int wt_batch_stats(const wt_batch* b, int i, long* solves, long* iterations, dou
  * void*; NULL returns to the batch's own stream), e.g. to bracket them with
  * the caller's CUDA events.  The call still returns after the step. */
 int wt_batch_set_stream(wt_batch* b, void* stream);
+/* Number of tanks, tank i's sizes, and the option set the batch runs with. */
+int wt_batch_size(const wt_batch* b, int* ntanks);
+int wt_batch_tank_dims(const wt_batch* b, int i, int* Nx, int* Nz);
+int wt_batch_get_options(const wt_batch* b, wt_options* opt);
+/*
+ * Batch autotuner: times one wt_batch_step(dt) of the whole batch - the
+ * makespan of the persistent launch - from the tanks' current states
+ * (restored before every trial and on return) for omega in {0.3, 0.4, 0.5,
+ * 0.6} x (nu1, nu2) in {(1,1), (2,2)} on top of the batch's options (mode
+ * kept), median of reps (1..20) trials each, and keeps the fastest that
+ * completes.  best, best_ms, entry_ms as in wt_autotune (any may be NULL).
+ * WT_ENOCONV if no candidate completes a step.
+ */
+int wt_batch_autotune(wt_batch* b, const double* dt, int reps, wt_options* best, double* best_ms,
+                      double* entry_ms);
 int wt_batch_destroy(wt_batch* b);
 
 /*

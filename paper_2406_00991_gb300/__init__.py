@@ -87,6 +87,10 @@ def _load():
                            ctypes.POINTER(D)],
         "wt_batch_destroy": [P],
         "wt_batch_set_stream": [P, P],
+        "wt_batch_size": [P, ctypes.POINTER(I)],
+        "wt_batch_tank_dims": [P, I, ctypes.POINTER(I), ctypes.POINTER(I)],
+        "wt_batch_get_options": [P, ctypes.POINTER(wt_options)],
+        "wt_batch_autotune": [P, P, I, ctypes.POINTER(wt_options), ctypes.POINTER(D), ctypes.POINTER(D)],
         "wt_time_kernel": [P, P, P, I, I, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long)],
         "wt_stream_function_wave": [P, I, D, I, D, P, P, P, ctypes.POINTER(D)],
         "wt_relax": [P, D, D, P, P, P, P],
@@ -102,28 +106,30 @@ def _load():
     return lib
 
 
-class _Missing:
-    """Stand-in while libwt.so is absent: any use raises the load error."""
+class _Lazy:
+    """The library, loaded at its first use: importing the package (for
+    instance to build the library) loads nothing, so a build in the same
+    process is what the first call sees.  A missing or stale libwt.so raises
+    ImportError at that first call; there is no CPU fallback."""
 
-    def __init__(self, err):
-        self._err = err
+    def __init__(self):
+        self._real = None
 
     def __getattr__(self, name):
-        raise self._err
+        if self._real is None:
+            self._real = _load()
+        return getattr(self._real, name)
 
 
 def _reload():
-    """(Re)load libwt.so after a build; returns the ctypes library."""
+    """Load libwt.so (after a build); returns the ctypes library."""
     global _lib, lib
     _lib = _load()
     lib = _lib
     return _lib
 
 
-try:
-    _lib = _load()
-except ImportError as _e:          # not built yet: fail loudly at the first call
-    _lib = _Missing(_e)
+_lib = _Lazy()
 lib = _lib
 
 
@@ -357,6 +363,33 @@ def wt_batch_set_stream(b, stream_handle):
     return _lib.wt_batch_set_stream(b, ctypes.c_void_p(int(stream_handle)))
 
 
+def wt_batch_size(b):
+    n = ctypes.c_int()
+    st = _lib.wt_batch_size(b, ctypes.byref(n))
+    return st, n.value
+
+
+def wt_batch_tank_dims(b, i):
+    nx, nz = ctypes.c_int(), ctypes.c_int()
+    st = _lib.wt_batch_tank_dims(b, int(i), ctypes.byref(nx), ctypes.byref(nz))
+    return st, nx.value, nz.value
+
+
+def wt_batch_get_options(b):
+    o = wt_options()
+    st = _lib.wt_batch_get_options(b, ctypes.byref(o))
+    return st, o
+
+
+def wt_batch_autotune(b, dt, reps=1):
+    d = np.ascontiguousarray(dt, dtype=np.float64)
+    o = wt_options()
+    bm, em = ctypes.c_double(), ctypes.c_double()
+    st = _lib.wt_batch_autotune(b, d.ctypes.data_as(ctypes.c_void_p), int(reps), ctypes.byref(o),
+                                ctypes.byref(bm), ctypes.byref(em))
+    return st, o, bm.value, em.value
+
+
 def wt_get_launches(t):
     n = ctypes.c_long()
     st = _lib.wt_get_launches(t, ctypes.byref(n))
@@ -587,6 +620,19 @@ class Batch:
 
     def set_stream(self, stream_handle):
         _check(wt_batch_set_stream(self.handle, stream_handle))
+
+    def options(self):
+        st, o = wt_batch_get_options(self.handle)
+        _check(st)
+        return {k: getattr(o, k) for k, _ in wt_options._fields_}
+
+    def autotune(self, dt, reps=1):
+        """Pick omega and the sweep counts that minimise one batch step from the
+        current states (restored); returns (options, best ms, entry ms)."""
+        dt = np.broadcast_to(np.asarray(dt, dtype=np.float64), (len(self),))
+        st, o, bm, em = wt_batch_autotune(self.handle, dt, reps)
+        _check(st)
+        return {k: getattr(o, k) for k, _ in wt_options._fields_}, bm, em
 
     def stats(self, i):
         st, s, it, r = wt_batch_stats(self.handle, i)

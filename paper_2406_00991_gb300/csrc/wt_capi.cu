@@ -1563,6 +1563,25 @@ int wt_batch_destroy(wt_batch* b) {
   return WT_OK;
 }
 
+int wt_batch_size(const wt_batch* b, int* ntanks) {
+  if (!b || !ntanks) return fail(WT_EINVAL, "NULL argument");
+  *ntanks = (int)b->tanks.size();
+  return WT_OK;
+}
+
+int wt_batch_tank_dims(const wt_batch* b, int i, int* Nx, int* Nz) {
+  if (!b || i < 0 || i >= (int)b->tanks.size()) return fail(WT_EINVAL, "tank index out of range");
+  if (Nx) *Nx = b->tanks[i]->Nx;
+  if (Nz) *Nz = b->tanks[i]->Nz;
+  return WT_OK;
+}
+
+int wt_batch_get_options(const wt_batch* b, wt_options* o) {
+  if (!b || !o || b->tanks.empty()) return fail(WT_EINVAL, "NULL argument");
+  *o = b->tanks[0]->opt;
+  return WT_OK;
+}
+
 int wt_batch_set_stream(wt_batch* b, void* stream) {
   if (!b) return fail(WT_EINVAL, "NULL batch");
   return guarded([&]() -> int {

@@ -271,3 +271,84 @@ extern "C" int wt_autotune_step(wt_tank* t, double dt, int reps, wt_options* bes
   if (entry_ms) *entry_ms = e_ms;
   return WT_OK;
 }
+
+// Batch autotuner: one option set for every tank of the batch, timed on one
+// wt_batch_step of the batch itself (the makespan of the persistent launch,
+// host clock: the call returns when every tank is done), from the batch's
+// current states, which are restored before every trial and on return.
+extern "C" int wt_batch_autotune(wt_batch* b, const double* dt, int reps, wt_options* best, double* best_ms,
+                                 double* entry_ms) {
+  if (!b || !dt) return wt::set_error(WT_EINVAL, "wt_batch_autotune: NULL argument");
+  if (reps < 1 || reps > 20) return wt::set_error(WT_EINVAL, "wt_batch_autotune: reps must be in [1, 20]");
+  int ntanks = 0, st = wt_batch_size(b, &ntanks);
+  if (st != WT_OK) return st;
+  struct Saved {
+    std::vector<double> eta, u, w;
+    double time = 0.0;
+  };
+  std::vector<Saved> saved(ntanks);
+  for (int i = 0; i < ntanks; ++i) {
+    int Nx = 0, Nz = 0;
+    if ((st = wt_batch_tank_dims(b, i, &Nx, &Nz)) != WT_OK) return st;
+    saved[i].eta.resize(Nx);
+    saved[i].u.resize((size_t)(Nz + 1) * Nx);
+    saved[i].w.resize((size_t)(Nz + 1) * Nx);
+    if ((st = wt_batch_get_state(b, i, saved[i].eta.data(), saved[i].u.data(), saved[i].w.data(),
+                                 &saved[i].time)) != WT_OK)
+      return st;
+  }
+  wt_options entry{};
+  if ((st = wt_batch_get_options(b, &entry)) != WT_OK) return st;
+  auto restore = [&]() {
+    for (int i = 0; i < ntanks; ++i) {
+      const int s = wt_batch_set_state(b, i, saved[i].eta.data(), saved[i].u.data(), saved[i].w.data(),
+                                       saved[i].time);
+      if (s != WT_OK) return s;
+    }
+    return (int)WT_OK;
+  };
+  auto measure = [&](const wt_options& o) -> double {
+    if (wt_batch_set_options(b, &o) != WT_OK) return -1.0;
+    std::vector<double> ms;
+    for (int r = 0; r < reps; ++r) {
+      if (restore() != WT_OK) return -1.0;
+      const double t0 = now_ms();
+      const int s = wt_batch_step(b, dt, 1);
+      const double d = now_ms() - t0;
+      if (s != WT_OK) return -1.0;
+      ms.push_back(d);
+    }
+    std::sort(ms.begin(), ms.end());
+    return ms[ms.size() / 2];
+  };
+  const double e_ms = measure(entry);
+  wt_options bo = entry;
+  double bms = e_ms > 0 ? e_ms : 1e300;
+  const double omegas[] = {0.3, 0.4, 0.5, 0.6};
+  const int nus[][2] = {{1, 1}, {2, 2}};
+  for (double om : omegas)
+    for (const auto& nu : nus) {
+      wt_options o = entry;
+      o.omega = om;
+      o.nu1 = nu[0];
+      o.nu2 = nu[1];
+      if (o.omega == entry.omega && o.nu1 == entry.nu1 && o.nu2 == entry.nu2) continue;
+      const double ms = measure(o);
+      if (ms > 0 && ms < bms) {
+        bms = ms;
+        bo = o;
+      }
+    }
+  if (bms >= 1e300) {
+    wt_batch_set_options(b, &entry);
+    restore();
+    return wt::set_error(WT_ENOCONV, "wt_batch_autotune: no candidate completed a step");
+  }
+  st = wt_batch_set_options(b, &bo);
+  if (st == WT_OK) st = restore();
+  if (st != WT_OK) return st;
+  if (best) *best = bo;
+  if (best_ms) *best_ms = bms;
+  if (entry_ms) *entry_ms = e_ms;
+  return WT_OK;
+}

@@ -167,3 +167,64 @@ def test_bathymetry_gradient_finite_differences(wt):
         fd = (J_of(b0 + eps * d_b, eta0 + eps * d_e) - J_of(b0 - eps * d_b, eta0 - eps * d_e)) / (2 * eps)
         ad = np.dot(gb, d_b) + np.dot(ge, d_e)
         assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+
+
+def test_gradient_workload_as_stated(wt):
+    """The gradient workload as stated: L = 16, Nx = 512, Nz = 20, 64-mode
+    seeded bathymetry, eta0 = 0.02 cos(2 pi x / 4), u0 = w0 = 0, 400 steps,
+    checkpoints every 20 steps, 16 gauges, target from a forward run over a
+    second seeded bathymetry.  The FP64 gradient (solves at 1e-12, the
+    tightest relative residual the FP64 path reaches here) against central
+    finite differences with step 1e-6 along a unit direction in the 64 b_k
+    and one in eta0 (spec: <= 1e-6 relative), and the mixed solver's
+    gradient (1e-10 solves) against the FP64 one."""
+    from paper_2406_00991_gb300.adjoint import gauge_series
+    Nx, Nz, L, nsteps, every = 512, 20, 16.0, 400, 20
+    dt = 0.5 * (L / Nx) / math.sqrt(9.81)
+    x = np.arange(Nx) * L / Nx
+    b0, phi = si.adjoint_bathymetry(5, L=L, K=64)
+    b_star, _ = si.adjoint_bathymetry(6, L=L, K=64)
+    kk = np.arange(1, 65)
+    C = np.cos(2 * math.pi * kk[:, None] * x[None, :] / L + phi[:, None])
+    eta0 = 0.02 * np.cos(2 * math.pi * x / 4.0)
+    gauges = np.arange(0, Nx, 32)
+    dev = torch.device("cuda")
+    Ct = torch.tensor(C, device=dev)
+    zeros = torch.zeros((Nz + 1, Nx), dtype=torch.float64, device=dev)
+    T = wt.Tank(Nx, 1, Nz, L, (1.0 + b0 @ C)[None], mode=0, tol=1e-12, filter=1, max_it=600)
+    with torch.no_grad():
+        target = gauge_series(T, 1.0 + torch.tensor(b_star, device=dev) @ Ct, torch.tensor(eta0, device=dev),
+                              zeros, zeros, dt, nsteps, gauges, every=every).clone()
+
+    def J_of(b, e0, grad=False):
+        bt = torch.tensor(b, device=dev, requires_grad=grad)
+        et = torch.tensor(e0, device=dev, requires_grad=grad)
+        series = gauge_series(T, 1.0 + bt @ Ct, et, zeros, zeros, dt, nsteps, gauges, every=every)
+        J = 0.5 * torch.sum((series - target) ** 2) * dt
+        if grad:
+            J.backward()
+            return J.item(), bt.grad.cpu().numpy(), et.grad.cpu().numpy()
+        return J.item()
+
+    J0, gb, ge = J_of(b0, eta0, grad=True)
+    r = np.random.default_rng(11)
+    db = r.standard_normal(64)
+    db /= np.linalg.norm(db)
+    de = r.standard_normal(Nx)
+    de /= np.linalg.norm(de)
+    eps = 1e-6
+    for d_b, d_e in ((db, 0 * de), (0 * db, de)):
+        fd = (J_of(b0 + eps * d_b, eta0 + eps * d_e) - J_of(b0 - eps * d_b, eta0 - eps * d_e)) / (2 * eps)
+        ad = float(np.dot(gb, d_b) + np.dot(ge, d_e))
+        print("gradient workload: finite difference %.12e, adjoint %.12e, relative %.2e"
+              % (fd, ad, abs(fd - ad) / abs(ad)))
+        assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+    # the mixed solver's gradient
+    T.set_options(mode=1, tol=1e-10)
+    J1, gb1, ge1 = J_of(b0, eta0, grad=True)
+    rel_b = np.abs(gb1 - gb).max() / np.abs(gb).max()
+    rel_e = np.abs(ge1 - ge).max() / np.abs(ge).max()
+    print("mixed vs FP64 gradient: J %.2e, b %.2e, eta0 %.2e relative" % (abs(J1 - J0) / J0, rel_b, rel_e))
+    assert abs(J1 - J0) <= 1e-8 * J0
+    assert rel_b <= 1e-7 and rel_e <= 1e-7
+    T.close()

@@ -38,3 +38,30 @@ def test_autotune(wt, mode):
     assert info.rel_residual <= 1e-10
     r = b - op.apply_A(g, op.Geometry(g, h, ea), op.Geometry(g, h, eb), p)
     assert np.linalg.norm(r) <= 1.5e-9 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("mode", [1, 0])
+def test_batch_autotune(wt, mode):
+    # a small uneven batch: the tuner keeps the batch's mode, returns a grid
+    # point no slower than the entry options, leaves it active and restores
+    # every tank's state
+    from test_gpu_batch import wave_tank
+    shapes = [(64, 12, 2 * np.pi, 0.03, 1), (256, 24, 8.0, 0.05, 2), (128, 16, 4.0, 0.02, 1)]
+    tanks = [wave_tank(Nx, Nz, L, a, m, seed=i) for i, (Nx, Nz, L, a, m) in enumerate(shapes)]
+    B = wt.Batch([s[0] for s in shapes], [s[1] for s in shapes], [s[2] for s in shapes], [t[0] for t in tanks],
+                 tol=1e-10, mode=mode)
+    for i, (h, eta, u, w) in enumerate(tanks):
+        B.set_state(i, eta, u, w)
+    dts = [0.2 * s[2] / s[0] / np.sqrt(9.81) for s in shapes]
+    opts, best, entry = B.autotune(dts, reps=1)
+    assert 0 < best <= entry
+    assert opts["mode"] == mode and opts["omega"] in (0.3, 0.4, 0.5, 0.6)
+    assert (opts["nu1"], opts["nu2"]) in ((1, 1), (2, 2))
+    assert B.options() == opts
+    for i, (h, eta, u, w) in enumerate(tanks):
+        e1, u1, w1, tm = B.get_state(i)
+        assert tm == 0.0 and np.array_equal(e1, eta) and np.array_equal(u1, u)
+    B.step(dts, 1)
+    for i in range(len(shapes)):
+        assert B.stats(i)[2] <= 1e-10
+    B.close()

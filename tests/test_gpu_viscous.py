@@ -91,22 +91,32 @@ def test_oscillatory_boundary_layer(wt, nu):
     eta0, u0, w0, U0m, d1 = boundary_layer(g.x[None, :], zeta, 0.0, H, k, h, omega, nu)
     nsteps = 900                                                    # 2.25 periods
     dt = 2.25 * Tp / nsteps
-    _, uex, _, _, _ = boundary_layer(X, zeta, nsteps * dt, H, k, h, omega, nu)
     near = (zeta[:, 0, 0] > 0) & (zeta[:, 0, 0] < 5 * d1)
     assert near.sum() >= 3
-    errs = {}
+    errs, decay = {}, {}
     for nu_run in (nu, 0.0):
         T = wt.Tank(Nx, 1, Nz, L, np.full((1, Nx), h), nu=nu_run, mode=0, tol=1e-12, linear=1)
         T.set_state(np.ascontiguousarray(eta0), np.ascontiguousarray(u0), np.zeros_like(u0),
                     np.ascontiguousarray(w0))
         T.step(dt, nsteps)
-        _, u, _, _, _ = T.get_state()
-        errs[nu_run] = np.abs(u[near] - uex[near]).max() / U0m
+        e, u, _, _, _ = T.get_state()
         T.close()
-    print("boundary layer: max |u - u_exact| / U0m within 5 delta_1 of the bed, viscous %.3e, inviscid %.3e"
-          % (errs[nu], errs[0.0]))
-    assert errs[nu] < 0.05
+        # the bed layer dissipates the wave (amplitude decay of a few percent
+        # over two periods, which the analytic profile leaves out): take the
+        # wave's amplitude and phase from the computed surface, then compare
+        # the velocity profile near the bed with the analytic one for them
+        a = 2.0 / Nx * np.sum(e[0] * np.cos(k * g.x))
+        b = 2.0 / Nx * np.sum(e[0] * np.sin(k * g.x))
+        amp, ph = math.hypot(a, b), math.atan2(b, a)             # eta = amp cos(kx - ph)
+        _, uex, _, U0, _ = boundary_layer(X, zeta, ph / omega, 2 * amp, k, h, omega, nu)
+        errs[nu_run] = np.abs(u[near] - uex[near]).max() / U0
+        decay[nu_run] = amp / (0.5 * H)
+    print("boundary layer: max |u - u_exact| / U0m within 5 delta_1 of the bed, viscous %.3e, inviscid %.3e;"
+          " wave amplitude after 2.25 periods / initial: %.4f, %.4f" % (errs[nu], errs[0.0], decay[nu], decay[0.0]))
+    assert errs[nu] < 0.02
     assert errs[0.0] > 0.3
+    # the viscous wave loses a few percent of its amplitude, the inviscid one none
+    assert 0.9 < decay[nu] < 0.99 and abs(decay[0.0] - 1.0) < 1e-3
 
 
 def test_relaxation_matches_oracle_and_absorbs(wt):
