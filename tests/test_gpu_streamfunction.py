@@ -47,13 +47,15 @@ def test_library_wave_matches_oracle(wt, kh, frac):
         eref = W.eta(g.x, t)
         z = g.sigma[:, None] * (d + eref[None, :]) - d
         uref, wref = W.velocity(g.x[None, :], z, t)
-        # two Newton solutions of an ill-conditioned system (steep waves: the
-        # high modes' coefficients reach 1e-14 of the first) agree to ~1e-10
-        assert abs(c - W.c) < 1e-10 * W.c
-        assert np.abs(eta[0] - eref).max() < 1e-9 * H
+        # two Newton solutions (analytic and central-difference Jacobians) of
+        # a system whose conditioning grows with the steepness agree to 1e-10
+        # for moderate waves and to a few 1e-9 at 0.7 x Battjes
+        bound = 1e-10 if frac <= 0.5 else 1e-8
+        assert abs(c - W.c) < bound * W.c
+        assert np.abs(eta[0] - eref).max() < bound * H
         scale = np.abs(uref).max()
-        assert np.abs(u[:, 0] - uref).max() < 1e-9 * scale
-        assert np.abs(w[:, 0] - wref).max() < 1e-9 * scale
+        assert np.abs(u[:, 0] - uref).max() < bound * scale
+        assert np.abs(w[:, 0] - wref).max() < bound * scale
     with pytest.raises(wt.WtError) as e:
         T.stream_function_wave(1, battjes_height(kh, 0.95, k), 32)       # above 0.85 x Battjes
     assert e.value.code == wt.WT_EINVAL
