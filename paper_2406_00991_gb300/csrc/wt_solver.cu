@@ -139,7 +139,8 @@ void setup_geometry(wt_tank& t, const double* ea, const double* eb, int precisio
 
 void setup_blocks(wt_tank& t, int precision, bool blocks, bool coarse, cudaStream_t s) {
   const int nl = (int)t.L64.size();
-  if (blocks && nl > 1) {
+  // the spectral smoother alone (smoother = 1) needs no column-block inverses
+  if (blocks && nl > 1 && t.opt.smoother != 1) {
     // every level's column blocks in one launch
     auto fill = [&](auto& lev, auto tw, auto& m, double wbytes) {
       double bytes = 0.0, flops = 0.0;
