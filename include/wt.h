@@ -299,7 +299,8 @@ int wt_stream_function_wave(wt_tank* t, int nwaves, double H, int nmodes, double
  * 128}, and mode in {WT_MIXED, WT_REFINE} unless the tank is in WT_FP64 - one
  * warm-up solve plus the median of reps (1..100) timed solves each, and keeps
  * the fastest setting that reaches the tolerance; then, on that setting, the
- * spectral smoothers (smoother 1 and 2, nu1 = nu2 in {1, 2}), the
+ * WT_REFINE with inner_tol 1e-4 and 1e-3 (unless the tank is in WT_FP64),
+ * the spectral smoothers (smoother 1 and 2, nu1 = nu2 in {1, 2}), the
  * full-multigrid cycle (cycle = 1) and the V-cycle's launch schedule (tail_max 2048 or 8192 with tail_cluster 0 or
  * 16, or vcycle_grid = 1).  The paper leaves these
  * choices open (Sec. 4.1).  On success the tank uses the winner, *best holds
@@ -319,14 +320,17 @@ int wt_autotune_step(wt_tank* t, double dt, int reps, wt_options* best, double* 
  * Batches of independent 2D tanks of uneven size, advanced together by one
  * persistent kernel launch per wt_batch_step: one CTA owns one tank and runs
  * all of its Runge-Kutta stages (free surface, metric, smoother set-up,
- * forcing, mixed-stage Poisson solve with FP64 flexible GMRES and the FP32
- * or FP64 p-multigrid V-cycle, projection); the largest tanks start first.
+ * forcing, mixed-stage Poisson solve - FP64 flexible GMRES with the FP32 or
+ * FP64 p-multigrid V-cycle, or FP64 refinement around an FP32 one - and the
+ * projection); the largest tanks start first.
  * wt_create_batch: tank i has Nx[i], Nz[i], L[i] and bathymetry[i] ([Nx[i]],
  * host or device), Ny = 1; g and nu as in wt_create.  Each tank's coarsest
  * level must have at most 64 unknowns.  The batch owns its tanks.
  * wt_batch_set_options applies one option set to every tank: WT_MIXED (FP64
- * GMRES, FP32 V-cycle; the default) or WT_FP64 (FP64 GMRES, FP64 V-cycle, the
- * plain method); WT_REFINE returns WT_ENOTSUP.
+ * GMRES, FP32 V-cycle; the default), WT_FP64 (FP64 GMRES, FP64 V-cycle, the
+ * plain method) or WT_REFINE (FP64 residual, FP32 GMRES + FP32 V-cycle to
+ * inner_tol, at most max_ir refinements per solve); block-Jacobi V-cycles
+ * only (smoother 0, cycle 0; WT_ENOTSUP otherwise).
  * wt_batch_set_state / get_state: tank i's eta [Nx], u, w [Nz+1][Nx].
  * wt_batch_step: nsteps full steps, dt[i] for tank i (host array); returns
  * after all tanks finished; WT_EBREAK / WT_ENOCONV if any tank failed.
@@ -354,9 +358,10 @@ int wt_batch_get_options(const wt_batch* b, wt_options* opt);
  * Batch autotuner: times one wt_batch_step(dt) of the whole batch - the
  * makespan of the persistent launch - from the tanks' current states
  * (restored before every trial and on return) for omega in {0.3, 0.4, 0.5,
- * 0.6} x (nu1, nu2) in {(1,1), (2,2)} on top of the batch's options (mode
- * kept), median of reps (1..20) trials each, and keeps the fastest that
- * completes.  best, best_ms, entry_ms as in wt_autotune (any may be NULL).
+ * 0.6} x (nu1, nu2) in {(1,1), (2,2)} on top of the batch's options, then,
+ * unless the batch runs WT_FP64, the refinement form with inner_tol 1e-4 and
+ * 1e-3 on the winner; median of reps (1..20) trials each; keeps the fastest
+ * that completes.  best, best_ms, entry_ms as in wt_autotune (any may be NULL).
  * WT_ENOCONV if no candidate completes a step.
  */
 int wt_batch_autotune(wt_batch* b, const double* dt, int reps, wt_options* best, double* best_ms,

@@ -7,13 +7,15 @@
 // right-hand side (Eq. forc1, poissonp, bcpdneu), the mixed-stage Poisson
 // solve - FP64 flexible GMRES (Sec. 4.4) preconditioned by the p-multigrid
 // V-cycle (Algorithm 1) in FP32 (mixed form) or in FP64 (plain form: every
-// level, smoother block and transfer in FP64) - and the projection
-// (Eq. rkforc1).
+// level, smoother block and transfer in FP64), or FP64 iterative refinement
+// around an FP32 flexible GMRES with the FP32 V-cycle (refinement form) - and
+// the projection (Eq. rkforc1).
 // Tanks are launched in decreasing order of size (longest-processing-time
 // first) so the large ones start first.  The phases are the device bodies of
 // wt_dev.cuh / wt_cta.cuh; no CTA waits on another.
 #define WT_DEV_RESTRICT
 #include "wt_cta.cuh"
+#include "../../include/wt.h"
 
 namespace wt {
 
@@ -35,17 +37,18 @@ struct KrylovSmem {
   double scal[4];
 };
 
-// out[i] = sum_e w[e] V_i[e] for i < nvec (and out[nvec] = ||w||^2 if norm).
-__device__ void cta_dots(const double* w, const double* V, long ld, int nvec, long n, bool norm,
-                         KrylovSmem& K) {
+// out[i] = sum_e w[e] V_i[e] for i < nvec (and out[nvec] = ||w||^2 if norm),
+// accumulated in FP64 whatever the vectors' precision.
+template <typename K>
+__device__ void cta_dots(const K* w, const K* V, long ld, int nvec, long n, bool norm, KrylovSmem& KS) {
   double acc[33];
 #pragma unroll
   for (int i = 0; i < 33; ++i) acc[i] = 0.0;
   for (long e = threadIdx.x; e < n; e += blockDim.x) {
-    const double wv = w[e];
+    const double wv = (double)w[e];
 #pragma unroll
     for (int i = 0; i < 32; ++i)
-      if (i < nvec) acc[i] += wv * V[i * ld + e];
+      if (i < nvec) acc[i] += wv * (double)V[i * ld + e];
     acc[32] += wv * wv;
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -54,156 +57,188 @@ __device__ void cta_dots(const double* w, const double* V, long ld, int nvec, lo
     if (!(i < nvec || (i == 32 && norm))) continue;
     double v = acc[i];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) K.red[warp][i] = v;
+    if (lane == 0) KS.red[warp][i] = v;
   }
   __syncthreads();
   if (threadIdx.x < 33) {
     const int i = threadIdx.x;
     if (i < nvec || (i == 32 && norm)) {
       double s = 0.0;
-      for (int k = 0; k < nw; ++k) s += K.red[k][i];
-      K.h[i] = s;
+      for (int k = 0; k < nw; ++k) s += KS.red[k][i];
+      KS.h[i] = s;
     }
   }
   __syncthreads();
 }
 
-// w -= sum_i c_i V_i (c from K.h), optionally scaled into out.
-__device__ void cta_update(double* w, const double* V, long ld, int nvec, long n, const double* c,
-                           double scale, double* out) {
+// w -= sum_i c_i V_i (c from KS.h), optionally scaled into out.
+template <typename K>
+__device__ void cta_update(K* w, const K* V, long ld, int nvec, long n, const double* c, double scale, K* out) {
   for (long e = threadIdx.x; e < n; e += blockDim.x) {
-    double wv = w[e];
-    for (int i = 0; i < nvec; ++i) wv -= c[i] * V[i * ld + e];
-    out[e] = wv * scale;
+    double wv = (double)w[e];
+    for (int i = 0; i < nvec; ++i) wv -= c[i] * (double)V[i * ld + e];
+    out[e] = (K)(wv * scale);
   }
   __syncthreads();
 }
 
-// FP64 flexible GMRES(m) with the V-cycle as preconditioner, in this CTA:
-// the FP32 V-cycle on the rounded Arnoldi vector (P64 = false) or the FP64
-// V-cycle on the vector itself (P64 = true).
-template <bool P64>
-__device__ void fgmres_cta(const BatchTankDesc& B, const double* b, double* x, int smem,
-                           unsigned char* sm, KrylovSmem& K) {
-  const TailLevel<double>& F = B.lv64[0];
+// Preconditioners of the CTA's flexible GMRES.
+enum BatchPre {
+  PRE_F32_OF_F64 = 0,   // FP64 Krylov vectors, the FP32 V-cycle on their rounding
+  PRE_F64 = 1,          // FP64 Krylov vectors, the FP64 V-cycle
+  PRE_F32 = 2           // FP32 Krylov vectors, the FP32 V-cycle
+};
+
+// Flexible GMRES(m) on the finest level of precision K, in this CTA: x is the
+// initial guess and the result, bn the norm the residual is measured against;
+// returns the last true relative residual ||b - A x|| / bn (precision K).
+template <typename K, int PRE>
+__device__ double fgmres_cta(const BatchTankDesc& B, const TailLevel<K>& F, const K* b, K* x, K* V, K* Z,
+                             double bn, double tol, int maxit, int* its_out, int smem, unsigned char* sm,
+                             KrylovSmem& KS) {
   const long n = B.n;
   const int m = B.restart;
-  double* V = B.V64;
-  double* Z = B.Z64;
-  TailArgs<float> A;
-  A.lv = B.lv32;
-  A.l0 = 0;
-  A.nl = B.nl;
-  A.f0 = B.b32;
-  A.x0 = B.e32;
-  A.f0_nyq = 1;
-  A.omega = (float)B.omega;
-  A.nu1 = B.nu1;
-  A.nu2 = B.nu2;
-  A.AinvT = B.AinvT;
-  A.smem = smem;
-  cta_dots(b, nullptr, 0, 0, n, true, K);
-  const double bn = sqrt(K.h[32]);
+  int its = 0;
+  double rel = 1.0;
+  for (;;) {
+    t_apply_op<K, 2>(F, x, V, b, false, smem, sm);            // r = b - A x
+    cta_dots<K>(V, nullptr, 0, 0, n, true, KS);
+    const double beta = sqrt(KS.h[32]);
+    rel = beta / bn;
+    if (rel <= tol || its >= maxit || !isfinite(rel)) break;
+    for (long e = threadIdx.x; e < n; e += blockDim.x) V[e] = (K)((double)V[e] / beta);
+    if (threadIdx.x == 0) {
+      for (int i = 0; i <= m; ++i) KS.g[i] = 0.0;
+      KS.g[0] = beta;
+    }
+    __syncthreads();
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      K* vj = V + (long)j * n;
+      K* zj = Z + (long)j * n;
+      K* w = V + (long)(j + 1) * n;
+      if constexpr (PRE == PRE_F64) {
+        TailArgs<double> A;
+        A.lv = B.lv64; A.l0 = 0; A.nl = B.nl;
+        A.f0 = reinterpret_cast<const double*>(vj);
+        A.x0 = reinterpret_cast<double*>(zj);
+        A.f0_nyq = 1; A.omega = B.omega; A.nu1 = B.nu1; A.nu2 = B.nu2; A.AinvT = B.AinvT; A.smem = smem;
+        vcycle_cta<double, 2>(A, sm);                            // z_j = M^{-1} v_j (FP64)
+        __syncthreads();
+      } else {
+        TailArgs<float> A;
+        A.lv = B.lv32; A.l0 = 0; A.nl = B.nl;
+        A.f0_nyq = 1; A.omega = (float)B.omega; A.nu1 = B.nu1; A.nu2 = B.nu2; A.AinvT = B.AinvT; A.smem = smem;
+        if constexpr (PRE == PRE_F32) {                          // z_j = M^{-1} v_j (FP32)
+          A.f0 = reinterpret_cast<const float*>(vj);
+          A.x0 = reinterpret_cast<float*>(zj);
+          vcycle_cta<float, 2>(A, sm);
+          __syncthreads();
+        } else {                                                 // the FP32 V-cycle on (float) v_j
+          A.f0 = B.b32;
+          A.x0 = B.e32;
+          for (long e = threadIdx.x; e < n; e += blockDim.x) B.b32[e] = (float)vj[e];
+          __syncthreads();
+          vcycle_cta<float, 2>(A, sm);
+          for (long e = threadIdx.x; e < n; e += blockDim.x) zj[e] = (K)B.e32[e];
+          __syncthreads();
+        }
+      }
+      t_apply_op<K, 2>(F, zj, w, nullptr, false, smem, sm);     // w = A z_j
+      cta_dots<K>(w, V, n, j + 1, n, false, KS);                 // classical Gram-Schmidt, twice
+      if (threadIdx.x <= j) KS.H[j * (m + 1) + threadIdx.x] = KS.h[threadIdx.x];
+      __syncthreads();
+      cta_update<K>(w, V, n, j + 1, n, KS.h, 1.0, w);
+      cta_dots<K>(w, V, n, j + 1, n, true, KS);
+      if (threadIdx.x == 0) {
+        double* H = KS.H + j * (m + 1);
+        double hh = KS.h[32];
+        for (int i = 0; i <= j; ++i) {
+          H[i] += KS.h[i];
+          hh -= KS.h[i] * KS.h[i];
+        }
+        const double hn = hh > 0 ? sqrt(hh) : 0.0;
+        for (int i = 0; i < j; ++i) {
+          const double t = KS.cs[i] * H[i] + KS.sn[i] * H[i + 1];
+          H[i + 1] = -KS.sn[i] * H[i] + KS.cs[i] * H[i + 1];
+          H[i] = t;
+        }
+        const double den = hypot(H[j], hn);
+        const double c = den > 0 ? H[j] / den : 1.0, sg = den > 0 ? hn / den : 0.0;
+        KS.cs[j] = c;
+        KS.sn[j] = sg;
+        H[j] = den;
+        const double gj = KS.g[j];
+        KS.g[j + 1] = -sg * gj;
+        KS.g[j] = c * gj;
+        const bool breakdown = !(hn > 1e-14 * den);
+        KS.scal[0] = breakdown ? 0.0 : 1.0 / hn;
+        KS.scal[1] = (fabs(KS.g[j + 1]) <= tol * bn || breakdown) ? 1.0 : 0.0;
+      }
+      __syncthreads();
+      cta_update<K>(w, V, n, j + 1, n, KS.h, KS.scal[0], w);      // v_{j+1}
+      ++its;
+      k = j + 1;
+      if (KS.scal[1] != 0.0 || its >= maxit) break;
+    }
+    if (threadIdx.x == 0) {
+      for (int i = k - 1; i >= 0; --i) {
+        double sacc = KS.g[i];
+        for (int l = i + 1; l < k; ++l) sacc -= KS.H[l * (m + 1) + i] * KS.y[l];
+        KS.y[i] = sacc / KS.H[i * (m + 1) + i];
+      }
+    }
+    __syncthreads();
+    for (long e = threadIdx.x; e < n; e += blockDim.x) {
+      double acc = (double)x[e];
+      for (int i = 0; i < k; ++i) acc += KS.y[i] * (double)Z[(long)i * n + e];
+      x[e] = (K)acc;
+    }
+    __syncthreads();
+  }
+  *its_out = its;
+  return rel;
+}
+
+// The stage's pressure solve in this CTA, in the batch's form: FP64 GMRES with
+// the FP32 V-cycle (MODE 0) or the FP64 V-cycle (MODE 1); or FP64 iterative
+// refinement (MODE 2): r = b - A x in FP64, an FP32 flexible GMRES with the
+// FP32 V-cycle solves A e = r / |r| to inner_tol, x += |r| e.
+template <int MODE>
+__device__ void solve_cta(const BatchTankDesc& B, const double* b, double* x, int smem, unsigned char* sm,
+                          KrylovSmem& KS) {
+  const long n = B.n;
+  cta_dots<double>(b, nullptr, 0, 0, n, true, KS);
+  const double bn = sqrt(KS.h[32]);
   int its = 0;
   double rel = 0.0;
   if (bn == 0.0) {
     for (long e = threadIdx.x; e < n; e += blockDim.x) x[e] = 0.0;
     __syncthreads();
-  } else {
+  } else if constexpr (MODE == 2) {
+    int refinements = 0;
     for (;;) {
-      t_apply_op<double, 2>(F, x, V, b, false, smem, sm);       // r = b - A x
-      cta_dots(V, nullptr, 0, 0, n, true, K);
-      const double beta = sqrt(K.h[32]);
-      rel = beta / bn;
-      if (rel <= B.tol || its >= B.max_it) break;
-      for (long e = threadIdx.x; e < n; e += blockDim.x) V[e] /= beta;
-      if (threadIdx.x == 0) {
-        for (int i = 0; i <= m; ++i) K.g[i] = 0.0;
-        K.g[0] = beta;
-      }
-      __syncthreads();
-      int k = 0;
-      bool done = false;
-      for (int j = 0; j < m; ++j) {
-        double* vj = V + (long)j * n;
-        double* zj = Z + (long)j * n;
-        double* w = V + (long)(j + 1) * n;
-        if (P64) {
-          TailArgs<double> A64;
-          A64.lv = B.lv64;
-          A64.l0 = 0;
-          A64.nl = B.nl;
-          A64.f0 = vj;
-          A64.x0 = zj;
-          A64.f0_nyq = 1;
-          A64.omega = B.omega;
-          A64.nu1 = B.nu1;
-          A64.nu2 = B.nu2;
-          A64.AinvT = B.AinvT;
-          A64.smem = smem;
-          vcycle_cta<double, 2>(A64, sm);                         // z_j = M^{-1} v_j (FP64)
-          __syncthreads();
-        } else {
-          for (long e = threadIdx.x; e < n; e += blockDim.x) B.b32[e] = (float)vj[e];
-          __syncthreads();
-          vcycle_cta<float, 2>(A, sm);                            // e32 = M^{-1} v_j (FP32)
-          for (long e = threadIdx.x; e < n; e += blockDim.x) zj[e] = (double)B.e32[e];
-          __syncthreads();
-        }
-        t_apply_op<double, 2>(F, zj, w, nullptr, false, smem, sm);   // w = A z_j
-        cta_dots(w, V, n, j + 1, n, false, K);                    // classical Gram-Schmidt, twice
-        if (threadIdx.x <= j) K.H[j * (m + 1) + threadIdx.x] = K.h[threadIdx.x];
-        __syncthreads();
-        cta_update(w, V, n, j + 1, n, K.h, 1.0, w);
-        cta_dots(w, V, n, j + 1, n, true, K);
-        double hh = 0.0;
-        if (threadIdx.x == 0) {
-          double* H = K.H + j * (m + 1);
-          hh = K.h[32];
-          for (int i = 0; i <= j; ++i) {
-            H[i] += K.h[i];
-            hh -= K.h[i] * K.h[i];
-          }
-          const double hn = hh > 0 ? sqrt(hh) : 0.0;
-          for (int i = 0; i < j; ++i) {
-            const double t = K.cs[i] * H[i] + K.sn[i] * H[i + 1];
-            H[i + 1] = -K.sn[i] * H[i] + K.cs[i] * H[i + 1];
-            H[i] = t;
-          }
-          const double den = hypot(H[j], hn);
-          const double c = den > 0 ? H[j] / den : 1.0, s = den > 0 ? hn / den : 0.0;
-          K.cs[j] = c;
-          K.sn[j] = s;
-          H[j] = den;
-          const double gj = K.g[j];
-          K.g[j + 1] = -s * gj;
-          K.g[j] = c * gj;
-          const bool breakdown = !(hn > 1e-14 * den);
-          K.scal[0] = breakdown ? 0.0 : 1.0 / hn;
-          K.scal[1] = (fabs(K.g[j + 1]) <= B.tol * bn || breakdown) ? 1.0 : 0.0;
-        }
-        __syncthreads();
-        cta_update(w, V, n, j + 1, n, K.h, K.scal[0], w);        // v_{j+1}
-        ++its;
-        k = j + 1;
-        done = K.scal[1] != 0.0;
-        if (done || its >= B.max_it) break;
-      }
-      if (threadIdx.x == 0) {
-        for (int i = k - 1; i >= 0; --i) {
-          double s = K.g[i];
-          for (int l = i + 1; l < k; ++l) s -= K.H[l * (m + 1) + i] * K.y[l];
-          K.y[i] = s / K.H[i * (m + 1) + i];
-        }
-      }
-      __syncthreads();
+      t_apply_op<double, 2>(B.lv64[0], x, B.r64, b, false, smem, sm);   // r = b - A x (FP64)
+      cta_dots<double>(B.r64, nullptr, 0, 0, n, true, KS);
+      const double rn = sqrt(KS.h[32]);
+      rel = rn / bn;
+      if (rel <= B.tol || refinements >= B.max_ir || its >= B.max_it || !isfinite(rel)) break;
       for (long e = threadIdx.x; e < n; e += blockDim.x) {
-        double acc = x[e];
-        for (int i = 0; i < k; ++i) acc += K.y[i] * Z[(long)i * n + e];
-        x[e] = acc;
+        B.b32[e] = (float)(B.r64[e] / rn);
+        B.e32[e] = 0.0f;
       }
       __syncthreads();
+      int it = 0;
+      const int cap = min(B.restart, B.max_it - its);
+      fgmres_cta<float, PRE_F32>(B, B.lv32[0], B.b32, B.e32, B.V32, B.Z32, 1.0, B.inner_tol, cap, &it, smem, sm, KS);
+      its += it;
+      for (long e = threadIdx.x; e < n; e += blockDim.x) x[e] += rn * (double)B.e32[e];
+      __syncthreads();
+      ++refinements;
     }
+  } else {
+    rel = fgmres_cta<double, MODE == 1 ? PRE_F64 : PRE_F32_OF_F64>(B, B.lv64[0], b, x, B.V64, B.Z64, bn, B.tol,
+                                                                   B.max_it, &its, smem, sm, KS);
   }
   if (threadIdx.x == 0) {
     B.stats[0] += 1.0;
@@ -221,9 +256,10 @@ __device__ RowPass<double> pass64(const BatchTankDesc& B, const double* in, doub
 
 // One Runge-Kutta stage k of one tank (the same sequence as the host-driven
 // stage in wt_capi.cu, linear = free-surface and advection terms dropped).
-template <bool P64>
+template <int MODE>
 __device__ void stage_cta(const BatchTankDesc& B, int k, double dt, int smem, unsigned char* sm,
                           KrylovSmem& K) {
+  constexpr bool P64 = MODE == 1;                 // FP64 V-cycle: FP64 blocks, no FP32 metric
   const double a = c_alpha[k - 1], b = c_beta[k - 1];
   const int M1 = B.M1, Nx = B.Nx, lx = B.logNx;
   const long n = B.n;
@@ -311,7 +347,7 @@ __device__ void stage_cta(const BatchTankDesc& B, int k, double dt, int smem, un
   colmat_body<double>(Dm, M1, M1, ws, Dws, nc, 0, 0, 1, sm);
   stage_rhs_body(t0, ts, sa, us, nullptr, ws, usx, nullptr, Dus, nullptr, Dws, rhs);
   __syncthreads();
-  fgmres_cta<P64>(B, rhs, B.p, smem, sm, K);
+  solve_cta<MODE>(B, rhs, B.p, smem, sm, K);
   // projection
   t_rowpass(pass64(B, B.p, px, M1, Nx, lx, Nx, lx, XOP_DERIV), smem, sm);
   colmat_body<double>(Dm, M1, M1, B.p, Dp, nc, 0, 0, 1, sm);
@@ -322,7 +358,7 @@ __device__ void stage_cta(const BatchTankDesc& B, int k, double dt, int smem, un
   (void)n;
 }
 
-template <bool P64>
+template <int MODE>
 __global__ void __launch_bounds__(512) k_batch_step(const BatchTankDesc* descs, const int* order,
                                                     const double* dt, int nsteps, int smem) {
   extern __shared__ __align__(16) unsigned char sm[];
@@ -330,19 +366,23 @@ __global__ void __launch_bounds__(512) k_batch_step(const BatchTankDesc* descs, 
   const int tank = order[blockIdx.x];
   const BatchTankDesc& B = descs[tank];
   for (int s = 0; s < nsteps; ++s)
-    for (int k = 1; k <= 5; ++k) stage_cta<P64>(B, k, dt[tank], smem, sm, K);
+    for (int k = 1; k <= 5; ++k) stage_cta<MODE>(B, k, dt[tank], smem, sm, K);
+}
+
+template <int MODE>
+static cudaError_t launch_mode(const BatchTankDesc* descs, const int* order, int ntanks, const double* dt,
+                               int nsteps, int smem, cudaStream_t s) {
+  cudaError_t e = ensure_dyn_smem((const void*)k_batch_step<MODE>, (size_t)smem);
+  if (e != cudaSuccess) return e;
+  k_batch_step<MODE><<<ntanks, 512, smem, s>>>(descs, order, dt, nsteps, smem);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_batch_step(const BatchTankDesc* descs, const int* order, int ntanks, const double* dt,
-                              int nsteps, int smem, int fp64, cudaStream_t s) {
-  const void* fn = fp64 ? (const void*)k_batch_step<true> : (const void*)k_batch_step<false>;
-  cudaError_t e = ensure_dyn_smem(fn, (size_t)smem);
-  if (e != cudaSuccess) return e;
-  if (fp64)
-    k_batch_step<true><<<ntanks, 512, smem, s>>>(descs, order, dt, nsteps, smem);
-  else
-    k_batch_step<false><<<ntanks, 512, smem, s>>>(descs, order, dt, nsteps, smem);
-  return cudaGetLastError();
+                              int nsteps, int smem, int mode, cudaStream_t s) {
+  if (mode == WT_FP64) return launch_mode<1>(descs, order, ntanks, dt, nsteps, smem, s);
+  if (mode == WT_REFINE) return launch_mode<2>(descs, order, ntanks, dt, nsteps, smem, s);
+  return launch_mode<0>(descs, order, ntanks, dt, nsteps, smem, s);
 }
 
 }  // namespace wt

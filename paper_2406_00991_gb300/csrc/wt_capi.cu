@@ -1402,14 +1402,16 @@ void fill_desc(wt_batch& b) {
     D.lv32 = t.tl32; D.lv64 = t.tl64; D.S = t.sd;
     D.AinvT = t.cLU; D.cDx = t.cDx; D.cDy = t.cDy;
     D.V64 = t.V64; D.Z64 = t.Z64; D.b32 = t.b32; D.e32 = t.e32;
+    D.V32 = t.V32; D.Z32 = t.Z32; D.r64 = t.r64;
     D.eta = t.eta; D.eta_new = t.eta_new; D.Keta = t.Keta; D.f_eta = t.f_eta; D.eta_x = t.eta_x;
     D.u = t.u; D.w = t.w; D.Ku = t.Ku; D.Kw = t.Kw; D.p = t.p; D.zero_s = t.zero_s;
     for (int k = 0; k < 18; ++k) D.work[k] = t.work[k];
     D.filt_x = t.filt_x; D.Fcheb = t.Fcheb;
     D.flag = t.dflag;
     D.stats = b.d_stats + 4 * i;
-    D.tol = t.opt.tol; D.omega = t.opt.omega;
+    D.tol = t.opt.tol; D.omega = t.opt.omega; D.inner_tol = t.opt.inner_tol;
     D.nu1 = t.opt.nu1; D.nu2 = t.opt.nu2; D.restart = t.opt.restart; D.max_it = t.opt.max_it;
+    D.max_ir = t.opt.max_ir;
     D.filter = t.opt.filter; D.linear = t.opt.linear;
   }
   WT_CK(cudaMemcpy(b.d_desc, d.data(), sizeof(BatchTankDesc) * nt, cudaMemcpyHostToDevice));
@@ -1421,8 +1423,6 @@ void fill_desc(wt_batch& b) {
 // the smoother per warp.
 int check_batch_tank(const wt_tank& t, int smem) {
   if (t.Ny != 1) return fail(WT_EINVAL, "batched tanks are 2D (Ny = 1)");
-  if (t.opt.mode != WT_MIXED && t.opt.mode != WT_FP64)
-    return fail(WT_ENOTSUP, "batched tanks run the mixed or the FP64 solver (not WT_REFINE)");
   if (t.opt.smoother != 0 || t.opt.cycle != 0)
     return fail(WT_ENOTSUP, "batched tanks use the block-Jacobi smoother and the V-cycle");
   const size_t row = (2 * (size_t)t.Nx + t.Nx / 2) * 2 * sizeof(double);
@@ -1486,8 +1486,6 @@ int wt_create_batch(int ntanks, const int* Nx, const int* Nz, const double* L, d
 
 int wt_batch_set_options(wt_batch* b, const wt_options* o) {
   if (!b || !o) return fail(WT_EINVAL, "NULL argument");
-  if (o->mode != WT_MIXED && o->mode != WT_FP64)
-    return fail(WT_ENOTSUP, "batched tanks run the mixed or the FP64 solver (not WT_REFINE)");
   for (wt_tank* t : b->tanks) {
     const int st = wt_set_options(t, o);
     if (st != WT_OK) return st;
@@ -1524,8 +1522,8 @@ int wt_batch_step(wt_batch* b, const double* dt, int nsteps) {
     fill_desc(*b);
     for (wt_tank* t : b->tanks) WT_CK(cudaStreamSynchronize(t->s));   // pending state uploads
     WT_CK(cudaMemcpyAsync(b->d_dt, dt, sizeof(double) * nt, cudaMemcpyHostToDevice, b->s));
-    const int fp64 = b->tanks[0]->opt.mode == WT_FP64;   // one option set for every tank
-    WT_CK(launch_batch_step(b->d_desc, b->d_order, nt, b->d_dt, nsteps, b->smem, fp64, b->s));
+    const int mode = b->tanks[0]->opt.mode;              // one option set for every tank
+    WT_CK(launch_batch_step(b->d_desc, b->d_order, nt, b->d_dt, nsteps, b->smem, mode, b->s));
     WT_CK(cudaStreamSynchronize(b->s));
     int bad = 0;
     for (int i = 0; i < nt; ++i) {

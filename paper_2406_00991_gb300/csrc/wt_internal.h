@@ -211,18 +211,21 @@ struct BatchTankDesc {
   const SurfDesc* S;
   double *AinvT, *cDx, *cDy;
   double *V64, *Z64;
+  float *V32, *Z32;         // FP32 Krylov vectors of the refinement form's inner solve
+  double* r64;              // FP64 residual of the refinement form
   float *b32, *e32;
   double *eta, *eta_new, *Keta, *f_eta, *eta_x, *u, *w, *Ku, *Kw, *p, *zero_s;
   double* work[18];
   const double *filt_x, *Fcheb;
   int* flag;
   double* stats;            // [0] solves, [1] Krylov iterations, [2] last relative residual
-  double tol, omega;
-  int nu1, nu2, restart, max_it, filter, linear;
+  double tol, omega, inner_tol;
+  int nu1, nu2, restart, max_it, max_ir, filter, linear;
 };
-// fp64: the FP64 V-cycle as preconditioner (plain form), else the FP32 one.
+// mode: WT_MIXED (FP64 GMRES, FP32 V-cycle), WT_FP64 (FP64 GMRES, FP64
+// V-cycle) or WT_REFINE (FP64 refinement around FP32 GMRES + FP32 V-cycle).
 cudaError_t launch_batch_step(const BatchTankDesc* descs, const int* order, int ntanks, const double* dt,
-                              int nsteps, int smem, int fp64, cudaStream_t s);
+                              int nsteps, int smem, int mode, cudaStream_t s);
 template <typename T>
 struct TailArgs {
   const TailLevel<T>* lv;   // device array, all levels of the hierarchy

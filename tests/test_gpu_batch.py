@@ -56,7 +56,8 @@ SHAPES = [(64, 12, 2 * math.pi, 0.03, 1), (256, 24, 8.0, 0.05, 2), (128, 16, 4.0
           (1024, 24, 32.0, 0.15, 5), (32, 8, 1.0, 0.004, 1)]
 
 
-@pytest.mark.parametrize("opts", [dict(), dict(filter=1), dict(linear=1), dict(mode=0), dict(mode=0, filter=1)])
+@pytest.mark.parametrize("opts", [dict(), dict(filter=1), dict(linear=1), dict(mode=0), dict(mode=0, filter=1),
+                                  dict(mode=3, inner_tol=1e-4), dict(mode=3, filter=1)])
 def test_batch_matches_single_tanks(wt, opts):
     # uneven tanks, including the 1024 x 24 tank and a 32 x 8 one; 1e-10 is the
     # method's solve tolerance (1e-12 lies below the FP64 rounding floor of the
@@ -84,7 +85,7 @@ def test_batch_matches_single_tanks(wt, opts):
     B.close()
 
 
-@pytest.mark.parametrize("mode", [1, 0])
+@pytest.mark.parametrize("mode", [1, 0, 3])
 def test_batch_matches_oracle_step(wt, mode):
     Nx, Nz, L = 64, 12, 2 * math.pi
     h, eta, u, w = wave_tank(Nx, Nz, L, 0.03)
@@ -142,7 +143,7 @@ def test_batch_errors(wt):
         B.step(-0.01, 1)
     assert e.value.code == wt.WT_EINVAL
     with pytest.raises(wt.WtError) as e:
-        B.set_options(mode=wt.WT_REFINE)
+        B.set_options(smoother=1)
     assert e.value.code == wt.WT_ENOTSUP
     # still water stays still; zero right-hand sides take zero iterations
     B.step(0.01, 3)
