@@ -81,7 +81,9 @@ def test_batch_matches_single_tanks(wt, opts):
         bs, bits, brel = B.stats(i)
         assert bs == 10 == solves
         assert brel <= 1e-10
-        assert abs(bits - its) <= 10           # same method, reductions in another order
+        # same method, reductions in another order; the refinement form's FP32
+        # inner solves react more to that order (they restart every refinement)
+        assert abs(bits - its) <= (10 if o["mode"] != 3 else max(10, its // 2))
     B.close()
 
 
