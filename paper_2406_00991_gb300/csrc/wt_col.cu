@@ -95,7 +95,7 @@ constexpr long kTpcMinCols = 8192;
 
 static inline int grid_cols(long ncols, int threads) {
   const long w = threads / 32;
-  return (int)std::min<long>(std::max<long>(1, (ncols + w - 1) / w), 152L * 64);
+  return (int)std::min<long>(std::max<long>(1, (ncols + w - 1) / w), (long)sm_count() * 64);
 }
 
 // Warp-per-column operator with the column length fixed at compile time where
@@ -200,7 +200,7 @@ cudaError_t launch_block_inverse_multi(const BlockInvMulti<T>& m, int* flag, cud
     if (e != cudaSuccess) return e;
   }
   const long total = m.start[m.nlev];
-  const int g = (int)std::min<long>(std::max<long>(1, (total + 3) / 4), 152 * 8);
+  const int g = (int)std::min<long>(std::max<long>(1, (total + 3) / 4), sm_count() * 8);
   return launch_k(k_block_inverse_multi<T>, dim3(g), dim3(128), smem, s, m, flag);
 }
 

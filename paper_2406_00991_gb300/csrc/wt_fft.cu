@@ -176,7 +176,7 @@ cudaError_t launch_rowpass(const RowPass<T>& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   int grid = (npairs + ppc - 1) / ppc;
-  grid = std::min(grid, 152 * 16);
+  grid = std::min(grid, sm_count() * 16);
   return launch_k(k_rowpass<T>, dim3(grid), dim3(256), smem, s, a, ppc);
 }
 

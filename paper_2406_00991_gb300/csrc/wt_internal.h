@@ -109,6 +109,10 @@ cudaError_t ensure_dyn_smem(const void* fn, size_t bytes);
 // device (cached per (kernel, device) likewise).
 cudaError_t ensure_nonportable_cluster(const void* fn);
 
+// Streaming multiprocessors of the current device (cached per device): grid
+// caps are multiples of it.
+int sm_count();
+
 // Launch through cudaLaunchKernelEx (grid, block, dynamic shared memory,
 // stream); returns the launch status.
 template <typename... KArgs, typename... Args>

@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(256) k_update_dots_arnoldi(T* __restrict__ w, 
 
 // ------------------------------------------------------------------ launchers
 static inline int blocks_for(long n) {
-  return (int)std::min<long>(std::max<long>(1, (n + 255) / 256), 152 * 4);
+  return (int)std::min<long>(std::max<long>(1, (n + 255) / 256), (long)sm_count() * 4);
 }
 
 template <typename T>

@@ -1,6 +1,7 @@
 // Per-device launch configuration shared by the launchers.
 #include "wt_internal.h"
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -33,6 +34,23 @@ cudaError_t ensure_nonportable_cluster(const void* fn) {
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e == cudaSuccess) have = true;
   return e;
+}
+
+int sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 152;                                   // GB300's count if the query fails
+  }
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+    cudaGetLastError();
+    v = 152;
+  }
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
 }
 
 }  // namespace wt

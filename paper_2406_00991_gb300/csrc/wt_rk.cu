@@ -9,7 +9,7 @@
 
 namespace wt {
 
-static inline int blocks_n(long n) { return (int)std::min<long>(std::max<long>(1, (n + 255) / 256), 152 * 8); }
+static inline int blocks_n(long n) { return (int)std::min<long>(std::max<long>(1, (n + 255) / 256), (long)sm_count() * 8); }
 
 #define GRID_LOOP(i, n) for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (long)gridDim.x * blockDim.x)
 
