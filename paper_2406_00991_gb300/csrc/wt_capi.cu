@@ -440,6 +440,7 @@ int check_options(const wt_options& o) {
   if (o.smoother < 0 || o.smoother > 2)
     return fail(WT_EINVAL, "smoother must be 0 (block-Jacobi), 1 (spectral) or 2 (both)");
   if (!(o.omega_s > 0) || !(o.omega_s < 2)) return fail(WT_EINVAL, "omega_s must be in (0, 2)");
+  if (o.warp_fft != 0 && o.warp_fft != 1) return fail(WT_EINVAL, "warp_fft must be 0 or 1");
   if ((o.filter != 0 && o.filter != 1) || (o.linear != 0 && o.linear != 1) ||
       (o.bc_transfer != 0 && o.bc_transfer != 1))
     return fail(WT_EINVAL, "filter, linear, bc_transfer are 0 or 1");
@@ -489,6 +490,7 @@ RowPass<double> dpass(wt_tank& t, const double* in, double* out, int nrows, int 
   a.in = in; a.out = out; a.nrows = nrows; a.Nin = N; a.Nout = N;
   a.logNin = ilog2(N); a.logNout = ilog2(N); a.op = op;
   a.kscale = 2.0 * M_PI / t.L; a.tw = t.tw64; a.logNtw = t.logNtw;
+  a.warp = t.opt.warp_fft;
   return a;
 }
 // d/dx of a field with `planes` sigma levels (planes = 1: a surface)
@@ -712,6 +714,7 @@ int wt_default_options(wt_options* o) {
   o->cycle = 0;
   o->smoother = 0;
   o->omega_s = 1.0;
+  o->warp_fft = 1;
   return WT_OK;
 }
 

@@ -154,6 +154,7 @@ __global__ void __launch_bounds__(256) k_rowpass_real(RowPass<T> a) {
 template <typename T>
 cudaError_t launch_rowpass(const RowPass<T>& a, cudaStream_t s) {
   if (a.nrows <= 0) return cudaSuccess;
+  if (a.warp && warp_deriv_fits(a)) return launch_deriv_warp(a, s);
   if (!a.ylines && a.Nin >= 8 && a.Nout >= 8 && (!a.out2 || (a.Nout2 >= 8 && a.Nout2 <= a.Nout))) {
     const int Nt = std::max(a.Nin, a.Nout);
     const size_t smem = (size_t)(2 * (Nt / 2 + 1) + Nt / 2) * sizeof(c2_t<T>);

@@ -99,6 +99,7 @@ struct RowPass {
   int Nout2 = 0, logNout2 = 0;
   int op2 = XOP_RESAMPLE;
   int write_out = 1;
+  int warp = 1;                // derivative passes over many lines may use the warp kernels
 };
 
 // Raise kernel `fn`'s dynamic shared-memory limit to at least `bytes` on the
@@ -127,6 +128,10 @@ inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_
 }
 
 template <typename T> cudaError_t launch_rowpass(const RowPass<T>& a, cudaStream_t s);
+// Derivative passes with one warp per line pair and the transform in
+// registers (wt_wfft.cu); warp_deriv_fits says whether a pass qualifies.
+template <typename T> bool warp_deriv_fits(const RowPass<T>& a);
+template <typename T> cudaError_t launch_deriv_warp(const RowPass<T>& a, cudaStream_t s);
 
 // Independent row passes in one launch (one pair of rows per CTA): the
 // passes must not read what another pass of the same launch writes.

@@ -39,6 +39,7 @@ static RowPass<T> xpass(wt_tank& t, const T* in, T* out, int nrows, int Nin, int
   a.kscale = (T)(2.0 * M_PI / t.L);
   a.tw = twiddles<T>(t);
   a.logNtw = t.logNtw;
+  a.warp = t.opt.warp_fft;
   return a;
 }
 

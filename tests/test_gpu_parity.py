@@ -82,7 +82,7 @@ def test_levels_match_oracle_hierarchy(wt):
 @pytest.mark.parametrize("tail_max,grid,cluster", [(0, 0, 0), (8192, 0, 0), (100000, 0, 0), (0, 1, 0),
                                                    (8192, 0, 16), (100000, 0, 8), (2048, 0, 2)])
 @pytest.mark.parametrize("Nx,Ny,Nz", [(64, 1, 16), (256, 1, 24), (1024, 1, 24), (16, 16, 8),
-                                      (32, 32, 12)])
+                                      (32, 32, 12), (64, 64, 16)])
 def test_vcycle_parity(wt, Nx, Ny, Nz, tail_max, grid, cluster):
     # same algorithm on both sides (block Jacobi with Nyquist split, omega 0.4,
     # nu1 = nu2 = 2, injected boundary rows, coarsest <= 64 unknowns): the
@@ -322,3 +322,25 @@ def test_fmg_solve_takes_no_more_iterations_than_vcycle(wt, mode):
         its[cyc] = info.iterations
     print("iterations V-cycle %d, FMG %d (mode %d)" % (its[0], its[1], mode))
     assert its[1] <= its[0]
+
+
+@pytest.mark.parametrize("Nx,Ny,Nz", [(256, 64, 12), (64, 256, 12), (1024, 16, 8), (512, 32, 6)])
+def test_operator_parity_warp_passes(wt, Nx, Ny, Nz):
+    # 3D levels with many lines run their x- and y-derivative passes one warp
+    # per line pair (transform in registers): against the oracle, and against
+    # the CTA-per-line passes (warp_fft = 0) on the same tank
+    L = 2 * math.pi
+    g, h, ea, eb = curved(Nx, Ny, Nz, L)
+    p = np.random.default_rng(2).standard_normal(g.shape)
+    ref = op.apply_A(g, op.Geometry(g, h, ea), op.Geometry(g, h, eb), p)
+    scale = np.abs(ref).max()
+    T = wt.Tank(Nx, Ny, Nz, L, h)
+    got = T.apply_operator(ea, eb, p, wt.WT_FP64)
+    got32 = T.apply_operator(ea, eb, p, wt.WT_FP32)
+    assert np.abs(got - ref).max() <= 1e-11 * scale
+    assert np.abs(got32 - ref).max() <= 2e-4 * scale
+    T.set_options(warp_fft=0)
+    old = T.apply_operator(ea, eb, p, wt.WT_FP64)
+    old32 = T.apply_operator(ea, eb, p, wt.WT_FP32)
+    assert np.abs(got - old).max() <= 1e-12 * scale
+    assert np.abs(got32 - old32).max() <= 1e-4 * scale
