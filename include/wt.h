@@ -122,11 +122,11 @@ typedef struct wt_options {
                         level runs launch per phase (tail_max and
                         vcycle_grid are not used)                           */
   double omega_s;    /* damping of the spectral smoother (1.0)               */
-  int warp_fft;      /* 1 (default): x- and y-derivative passes over many
-                        lines (>= 512 x-rows, or y-lines of >= 16 columns;
-                        32..1024 points, FP64 up to 512) run one warp per
-                        line pair with the transform in registers; 0: every
-                        pass one CTA per line (pair)                          */
+  int warp_fft;      /* 1 (default): FP32 x- and y-derivative passes over
+                        many lines (>= 512 x-rows, or y-lines of >= 16
+                        columns; 32..1024 points) run one warp per line pair
+                        with the transform in registers; 0: every pass one
+                        CTA per line (pair)                                  */
 } wt_options;
 
 typedef struct wt_solve_info {

@@ -242,13 +242,18 @@ __global__ void __launch_bounds__(256) k_yderiv_warp(RowPass<T> a) {
   }
 }
 
-// Whether the warp passes take this row pass: a derivative with equal in/out
-// lengths of 32..1024 points (FP64: ..512), a plain epilogue (store, add or
+// Whether the warp passes take this row pass: FP32, a derivative with equal
+// in/out lengths of 32..1024 points, a plain epilogue (store, add or
 // residual), no Nyquist coefficient and no second transform, and enough lines
 // to fill the GPU (x-rows: >= 512; y-lines: >= 16 x-columns).
 template <typename T>
 bool warp_deriv_fits(const RowPass<T>& a) {
-  const int maxN = sizeof(T) == 4 ? 1024 : 512;
+  // FP32 only: at FP64 the transform is bound by the FP64 rate, and the
+  // register-resident form (up to 186 registers a thread) measured slower
+  // than the CTA-per-line passes (FP64 operator apply on 256 x 256 x 16:
+  // 692 against 599 us)
+  if (sizeof(T) != 4) return false;
+  const int maxN = 1024;
   if (a.op != XOP_DERIV || a.Nin != a.Nout || a.Nin < 32 || a.Nin > maxN) return false;
   if (a.nyq || a.out2 || !a.write_out) return false;
   if (a.epi != EPI_STORE && a.epi != EPI_ADD && a.epi != EPI_RESID) return false;
@@ -277,6 +282,9 @@ static cudaError_t launch_r(const RowPass<T>& a, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_deriv_warp(const RowPass<T>& a, cudaStream_t s) {
+  if constexpr (sizeof(T) != 4) {
+    return cudaErrorInvalidValue;
+  } else {
   switch (a.Nin) {
     case 32: return launch_r<T, 1>(a, s);
     case 64: return launch_r<T, 2>(a, s);
@@ -285,10 +293,9 @@ cudaError_t launch_deriv_warp(const RowPass<T>& a, cudaStream_t s) {
     case 512: return launch_r<T, 16>(a, s);
     default: break;
   }
-  if constexpr (sizeof(T) == 4) {
-    if (a.Nin == 1024) return launch_r<T, 32>(a, s);
-  }
+  if (a.Nin == 1024) return launch_r<T, 32>(a, s);
   return cudaErrorInvalidValue;
+  }
 }
 
 template bool warp_deriv_fits<float>(const RowPass<float>&);
