@@ -41,10 +41,12 @@ import seeded_inputs as si  # noqa: E402
 
 METRIC = "RK4 DOF-updates/s (mixed FP32/FP64 p-MG Poisson solves at 1e-10 residual)"
 # DRAM bytes (read + write) of one FP32 operator apply, summed over its
-# kernels, from one ncu capture of the same build and size (see profiles/);
-# None until measured
-OP_TRAFFIC_2D = None
-OP_TRAFFIC_3D = None
+# kernels, from one ncu capture of the same build and size (the operator-apply
+# traffic summary under profiles/): 2D 1024 x 24, 3 launches; 3D 256 x 256 x 16,
+# 5 launches.  The writes read 0 there: each output stays dirty in L2 past the
+# end of its kernel.
+OP_TRAFFIC_2D = 154368 + 259072 + 256512
+OP_TRAFFIC_3D = 4488960 + 4491776 + 16568320 + 8944640 + 8947712
 UNIT = "DOF-updates/s"
 STAGES = 5
 
