@@ -127,6 +127,12 @@ typedef struct wt_options {
                         columns; 32..1024 points) run one warp per line pair
                         with the transform in registers; 0: every pass one
                         CTA per line (pair)                                  */
+  int pdl;           /* 1 (default): kernels are launched with programmatic
+                        dependent launch - the next kernel of the stream is
+                        made resident while its predecessor runs and waits
+                        (griddepcontrol.wait) for the predecessor's completion
+                        before touching memory, so results are unchanged and
+                        only launch latency is hidden; 0: plain stream order */
 } wt_options;
 
 typedef struct wt_solve_info {

@@ -34,7 +34,8 @@ class wt_options(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("max_ir", ctypes.c_int), ("vcycle_grid", ctypes.c_int),
                 ("tail_cluster", ctypes.c_int), ("barrier_cycles", ctypes.c_longlong),
                 ("cycle", ctypes.c_int), ("smoother", ctypes.c_int), ("omega_s", ctypes.c_double),
-                ("warp_fft", ctypes.c_int)]
+                ("warp_fft", ctypes.c_int),
+                ("pdl", ctypes.c_int)]
 
 
 class wt_solve_info(ctypes.Structure):

@@ -66,6 +66,7 @@ __global__ void k_adj_proj(AdjArgs A, const double* __restrict__ Lu, const doubl
                            const double* __restrict__ p, double* __restrict__ LKu1,
                            double* __restrict__ LKw1, double* __restrict__ LGx, double* __restrict__ q,
                            double* __restrict__ lut, double* __restrict__ lwt, double* __restrict__ gB) {
+  pdl_enter();
   const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long nc = A.nc;
   if (c >= nc) return;
@@ -107,6 +108,7 @@ __global__ void k_adj_rhs(AdjArgs A, const double* __restrict__ lam, const doubl
                           double* __restrict__ lwt, double* __restrict__ LKu, double* __restrict__ LKw,
                           double* __restrict__ lFu, double* __restrict__ lFw, double* __restrict__ gA,
                           double* __restrict__ gB, double* __restrict__ gHX) {
+  pdl_enter();
   const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long nc = A.nc;
   if (c >= nc) return;
@@ -188,6 +190,7 @@ __global__ void k_adj_forcing(AdjArgs A, const double* __restrict__ ut, const do
                               double* __restrict__ lwt, double* __restrict__ lux, double* __restrict__ lwx,
                               double* __restrict__ lex, double* __restrict__ lfe, double* __restrict__ ldb,
                               double* __restrict__ gB) {
+  pdl_enter();
   const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long nc = A.nc;
   if (c >= nc) return;
@@ -249,6 +252,7 @@ __global__ void k_adj_metric(long nc, const double* __restrict__ meta, const dou
                              const double* __restrict__ ldb, double* __restrict__ lea,
                              double* __restrict__ leax, double* __restrict__ leb, double* __restrict__ lebx,
                              double* __restrict__ lh0, double* __restrict__ lhx) {
+  pdl_enter();
   const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
   const double hx = meta[M_HX * nc + c];
@@ -275,6 +279,7 @@ __global__ void k_adj_eta(AdjArgs A, const double* __restrict__ Le, double* __re
                           const double* __restrict__ ex, const double* __restrict__ ut,
                           double* __restrict__ lut, double* __restrict__ lwt, double* __restrict__ lh,
                           double* __restrict__ let, double* __restrict__ lex) {
+  pdl_enter();
   const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= A.nc) return;
   const double LN = Le[c] + (A.linear ? 0.0 : lea[c] - tA[c]);      // adjoint of eta^(k)
@@ -295,6 +300,7 @@ __global__ void k_adj_eta(AdjArgs A, const double* __restrict__ Le, double* __re
 inline int blocks(long n) { return (int)std::max<long>(1, (n + 127) / 128); }
 
 __global__ void k_add(double* __restrict__ y, const double* __restrict__ x, long n) {
+  pdl_enter();
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] += x[i];
 }
@@ -302,8 +308,7 @@ __global__ void k_add(double* __restrict__ y, const double* __restrict__ x, long
 }  // namespace
 
 cudaError_t launch_add(double* y, const double* x, long n, cudaStream_t s) {
-  k_add<<<blocks(n), 128, 0, s>>>(y, x, n);
-  return cudaGetLastError();
+  return launch_k(k_add, dim3(blocks(n)), dim3(128), 0, s, y, x, n);
 }
 
 // One stage reversed.  The forward stage k was recorded in t.adj->st[k-1].
@@ -351,7 +356,7 @@ int adjoint_stage(wt_tank& t, int k, double dt, const double* alpha, const doubl
          *leb = B.col(12), *lebx = B.col(13), *lh0 = B.col(14), *lhx = B.col(15), *tA = B.col(16),
          *tB = B.col(17), *tH = B.col(18), *ex = B.col(19), *let = B.col(20), *lex = B.col(21);
   // projection
-  WT_LAUNCH(t, K_STAGE, 8.0 * n * 10, 8.0 * n * 4 * M1, (k_adj_proj<<<blocks(nc), 128, 0, s>>>(A, B.Lu, B.Lw, B.LKu, B.LKw, R.p, B.LKu1, B.LKw1, B.LGx, B.q, B.lut, B.lwt, gB), cudaGetLastError()));
+  WT_LAUNCH(t, K_STAGE, 8.0 * n * 10, 8.0 * n * 4 * M1, launch_k(k_adj_proj, dim3(blocks(nc)), dim3(128), 0, s, A, B.Lu, B.Lw, B.LKu, B.LKw, R.p, B.LKu1, B.LKw1, B.LGx, B.q, B.lut, B.lwt, gB));
   {
     RowPass<double> a = pass(B.LGx, B.lp, M1, XOP_DERIV);
     a.scale = -1.0;
@@ -368,13 +373,13 @@ int adjoint_stage(wt_tank& t, int k, double dt, const double* alpha, const doubl
   if (st != WT_OK && st != WT_ENOCONV) return st;
   run_rowpass(t, pass(B.lrhs, B.t1, M1, XOP_DERIV));
   run_rowpass(t, pass(R.p, B.px, M1, XOP_DERIV));
-  WT_LAUNCH(t, K_STAGE, 8.0 * n * 16, 8.0 * n * 12 * M1, (k_adj_rhs<<<blocks(nc), 128, 0, s>>>(A, B.lrhs, B.t1, R.p, B.px, R.us, R.ws, B.LKu1, B.LKw1, B.lut, B.lwt, B.LKu, B.LKw, B.lFu, B.lFw, gA, gB, gHX), cudaGetLastError()));
+  WT_LAUNCH(t, K_STAGE, 8.0 * n * 16, 8.0 * n * 12 * M1, launch_k(k_adj_rhs, dim3(blocks(nc)), dim3(128), 0, s, A, B.lrhs, B.t1, R.p, B.px, R.us, R.ws, B.LKu1, B.LKw1, B.lut, B.lwt, B.LKu, B.LKw, B.lFu, B.lFw, gA, gB, gHX));
   // forcing
   if (!lin) {
     run_rowpass(t, pass(R.u_f, B.ux, M1, XOP_DERIV));
     run_rowpass(t, pass(R.w_f, B.wx, M1, XOP_DERIV));
   }
-  WT_LAUNCH(t, K_STAGE, 8.0 * n * 12, 8.0 * n * 4 * M1, (k_adj_forcing<<<blocks(nc), 128, 0, s>>>(A, R.u_f, R.w_f, B.ux, B.wx, R.f_eta, B.lFu, B.lFw, B.lut, B.lwt, B.lux, B.lwx, lexf, lfe, ldb, gB), cudaGetLastError()));
+  WT_LAUNCH(t, K_STAGE, 8.0 * n * 12, 8.0 * n * 4 * M1, launch_k(k_adj_forcing, dim3(blocks(nc)), dim3(128), 0, s, A, R.u_f, R.w_f, B.ux, B.wx, R.f_eta, B.lFu, B.lFw, B.lut, B.lwt, B.lux, B.lwx, lexf, lfe, ldb, gB));
   if (!lin) {
     RowPass<double> a = pass(B.lux, B.lut, M1, XOP_DERIV);
     a.scale = -1.0;
@@ -386,12 +391,12 @@ int adjoint_stage(wt_tank& t, int k, double dt, const double* alpha, const doubl
     run_rowpass(t, b);
   }
   // metric of both geometries, then the free surface
-  WT_LAUNCH(t, K_STAGE, 8.0 * nc * 20, 0.0, (k_adj_metric<<<blocks(nc), 128, 0, s>>>(nc, A.meta, gA, gB, gHX, ldb, lea, leax, leb, lebx, lh0, lhx), cudaGetLastError()));
+  WT_LAUNCH(t, K_STAGE, 8.0 * nc * 20, 0.0, launch_k(k_adj_metric, dim3(blocks(nc)), dim3(128), 0, s, nc, A.meta, gA, gB, gHX, ldb, lea, leax, leb, lebx, lh0, lhx));
   run_rowpass(t, pass(leax, tA, 1, XOP_DERIV));
   run_rowpass(t, pass(lebx, tB, 1, XOP_DERIV));
   run_rowpass(t, pass(lhx, tH, 1, XOP_DERIV));
   run_rowpass(t, pass(R.eta_f, ex, 1, XOP_DERIV));
-  WT_LAUNCH(t, K_STAGE, 8.0 * nc * 16, 0.0, (k_adj_eta<<<blocks(nc), 128, 0, s>>>(A, B.Le, B.LKe, lea, tA, leb, tB, lh0, tH, lfe, lexf, ex, R.u_f, B.lut, B.lwt, B.lh, let, lex), cudaGetLastError()));
+  WT_LAUNCH(t, K_STAGE, 8.0 * nc * 16, 0.0, launch_k(k_adj_eta, dim3(blocks(nc)), dim3(128), 0, s, A, B.Le, B.LKe, lea, tA, leb, tB, lh0, tH, lfe, lexf, ex, R.u_f, B.lut, B.lwt, B.lh, let, lex));
   {
     RowPass<double> a = pass(lex, let, 1, XOP_DERIV);
     a.scale = -1.0;

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <utility>
 
 using namespace wt;
 
@@ -441,6 +442,7 @@ int check_options(const wt_options& o) {
     return fail(WT_EINVAL, "smoother must be 0 (block-Jacobi), 1 (spectral) or 2 (both)");
   if (!(o.omega_s > 0) || !(o.omega_s < 2)) return fail(WT_EINVAL, "omega_s must be in (0, 2)");
   if (o.warp_fft != 0 && o.warp_fft != 1) return fail(WT_EINVAL, "warp_fft must be 0 or 1");
+  if (o.pdl != 0 && o.pdl != 1) return fail(WT_EINVAL, "pdl must be 0 or 1");
   if ((o.filter != 0 && o.filter != 1) || (o.linear != 0 && o.linear != 1) ||
       (o.bc_transfer != 0 && o.bc_transfer != 1))
     return fail(WT_EINVAL, "filter, linear, bc_transfer are 0 or 1");
@@ -456,6 +458,14 @@ int guarded(F&& f) {
   } catch (const std::exception& e) {
     return fail(WT_ENOMEM, e.what());
   }
+}
+
+// guarded() with the tank's programmatic-dependent-launch option in force for
+// the launches of the call.
+template <typename F>
+int guarded_t(const wt_tank* t, F&& f) {
+  PdlScope pdl(t->opt.pdl != 0);
+  return guarded(std::forward<F>(f));
 }
 
 // Order the tank's own stream after work already queued on the legacy
@@ -715,6 +725,7 @@ int wt_default_options(wt_options* o) {
   o->smoother = 0;
   o->omega_s = 1.0;
   o->warp_fft = 1;
+  o->pdl = 1;
   return WT_OK;
 }
 
@@ -892,7 +903,7 @@ int wt_get_levels(const wt_tank* t, int* nlevels, int* dims) {
 int wt_set_state(wt_tank* t, const double* eta, const double* u, const double* v, const double* w,
                  double time) {
   if (!t || !eta || !u || !w || (t->Ny > 1 && !v)) return fail(WT_EINVAL, "NULL state array");
-  return guarded([&]() -> int {
+  return guarded_t(t, [&]() -> int {
     enter(*t);
     const long n = t->n;
     const int nc = t->ncols;
@@ -952,7 +963,7 @@ int wt_apply_operator(wt_tank* t, const double* eta_a, const double* eta_b, cons
                       int precision) {
   if (!t || !eta_a || !eta_b || !p || !Ap) return fail(WT_EINVAL, "NULL argument");
   if (precision != WT_FP64 && precision != WT_FP32) return fail(WT_EINVAL, "precision must be WT_FP64 or WT_FP32");
-  return guarded([&]() -> int {
+  return guarded_t(t, [&]() -> int {
     enter(*t);
     const long n = t->n;
     const double* ea = in_dev(*t, eta_a, t->io_s1, t->ncols);
@@ -981,7 +992,7 @@ int wt_time_kernel(wt_tank* t, const double* eta_a, const double* eta_b, int wha
   if (what != WT_TIME_OPERATOR && what != WT_TIME_VCYCLE) return fail(WT_EINVAL, "unknown unit to time");
   if (reps < 1 || reps > 10000) return fail(WT_EINVAL, "reps must be in [1, 10000]");
   if (t->prof.mask != 0) return fail(WT_EINVAL, "per-launch timing (wt_profile) is on");
-  return guarded([&]() -> int {
+  return guarded_t(t, [&]() -> int {
     enter(*t);
     const long n = t->n;
     const double* ea = in_dev(*t, eta_a, t->io_s1, t->ncols);
@@ -1047,7 +1058,7 @@ int wt_precondition(wt_tank* t, const double* eta_a, const double* eta_b, const 
                     int precision) {
   if (!t || !eta_a || !eta_b || !r || !z) return fail(WT_EINVAL, "NULL argument");
   if (precision != WT_FP64 && precision != WT_FP32) return fail(WT_EINVAL, "precision must be WT_FP64 or WT_FP32");
-  return guarded([&]() -> int {
+  return guarded_t(t, [&]() -> int {
     enter(*t);
     const long n = t->n;
     const double* ea = in_dev(*t, eta_a, t->io_s1, t->ncols);
@@ -1074,7 +1085,7 @@ int wt_poisson_solve(wt_tank* t, const double* eta_a, const double* eta_b, const
                      double tol, wt_solve_info* info) {
   if (!t || !eta_a || !eta_b || !rhs || !p) return fail(WT_EINVAL, "NULL argument");
   if (tol <= 0) tol = t->opt.tol;
-  return guarded([&]() -> int {
+  return guarded_t(t, [&]() -> int {
     enter(*t);
     const long n = t->n;
     const double* ea = in_dev(*t, eta_a, t->io_s1, t->ncols);
@@ -1102,7 +1113,7 @@ int wt_rk_stage(wt_tank* t, int k, double dt) {
   if (k < 1 || k > 5) return fail(WT_EINVAL, "stage k must be in [1, 5]");
   if (!(dt > 0) || !std::isfinite(dt)) return fail(WT_EINVAL, "dt must be positive");
   if (!t->have_state) return fail(WT_EINVAL, "no state: call wt_set_state first");
-  return guarded([&]() -> int { return rk_stage(*t, k, dt); });
+  return guarded_t(t, [&]() -> int { return rk_stage(*t, k, dt); });
 }
 
 int wt_step(wt_tank* t, double dt, int nsteps) {
@@ -1167,7 +1178,7 @@ int wt_get_launches(const wt_tank* t, long* launches) {
 // ================================================================ adjoint
 int wt_set_bathymetry(wt_tank* t, const double* h) {
   if (!t || !h) return fail(WT_EINVAL, "NULL argument");
-  return guarded([&]() -> int {
+  return guarded_t(t, [&]() -> int {
     enter(*t);
     const double* hd = in_dev(*t, h, t->io_s1, t->ncols);
     std::vector<double> hh(t->ncols);
@@ -1193,7 +1204,7 @@ int wt_relax(wt_tank* t, double x0, double x1, const double* eta_target, const d
   if (!t) return fail(WT_EINVAL, "NULL tank");
   if (!std::isfinite(x0) || !std::isfinite(x1) || x0 == x1) return fail(WT_EINVAL, "the zone needs x0 != x1");
   if (!t->have_state) return fail(WT_EINVAL, "no state: call wt_set_state first");
-  return guarded([&]() -> int {
+  return guarded_t(t, [&]() -> int {
     enter(*t);
     const int Nx = t->Nx, nc = t->ncols;
     const double lo = std::min(x0, x1), hi = std::max(x0, x1);
@@ -1235,7 +1246,7 @@ int wt_stream_function_wave(wt_tank* t, int nwaves, double H, int nmodes, double
   const double k = 2.0 * M_PI * nwaves / t->L, d = t->hmax;
   if (H * k / (2.0 * M_PI) > 0.85 * 0.1401 * std::tanh(0.8863 * k * d))
     return fail(WT_EINVAL, "H above 0.85 x the Battjes breaking steepness");
-  return guarded([&]() -> int {
+  return guarded_t(t, [&]() -> int {
     SfWave& W = t->sf;
     if (!(W.k == k && W.d == d && W.H == H && W.g == t->g && W.N == nmodes)) {
       SfWave nw;
@@ -1266,7 +1277,7 @@ int wt_apply_operator_transposed(wt_tank* t, const double* eta_a, const double* 
   if (!t || !eta_a || !eta_b || !lam || !out) return fail(WT_EINVAL, "NULL argument");
   if (precision != WT_FP64 && precision != WT_FP32) return fail(WT_EINVAL, "precision must be WT_FP64 or WT_FP32");
   if (t->Ny != 1) return fail(WT_ENOTSUP, "the transposed operator is 2D only");
-  return guarded([&]() -> int {
+  return guarded_t(t, [&]() -> int {
     enter(*t);
     const long n = t->n;
     const double* ea = in_dev(*t, eta_a, t->io_s1, t->ncols);
@@ -1293,7 +1304,7 @@ int wt_adjoint_solve(wt_tank* t, const double* eta_a, const double* eta_b, const
   if (!t || !eta_a || !eta_b || !rhs || !lam) return fail(WT_EINVAL, "NULL argument");
   if (t->Ny != 1) return fail(WT_ENOTSUP, "the transposed problem is 2D only");
   if (tol <= 0) tol = t->opt.tol;
-  return guarded([&]() -> int {
+  return guarded_t(t, [&]() -> int {
     enter(*t);
     const long n = t->n;
     const double* ea = in_dev(*t, eta_a, t->io_s1, t->ncols);
@@ -1321,7 +1332,7 @@ int wt_adjoint_step(wt_tank* t, double dt, const double* eta, const double* u, c
   if (!t || !eta || !u || !w || !lam_eta || !lam_u || !lam_w) return fail(WT_EINVAL, "NULL argument");
   if (t->Ny != 1) return fail(WT_ENOTSUP, "the adjoint step is 2D only");
   if (!(dt > 0) || !std::isfinite(dt)) return fail(WT_EINVAL, "dt must be positive");
-  return guarded([&]() -> int {
+  return guarded_t(t, [&]() -> int {
     enter(*t);
     alloc_adj(*t);
     AdjBufs& B = *t->adj;

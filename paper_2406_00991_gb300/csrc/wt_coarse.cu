@@ -24,6 +24,7 @@ __global__ void __launch_bounds__(256) k_coarse_factor(LevelView<double> L, cons
                                                       const double* __restrict__ Dy,
                                                       double* __restrict__ LUout, int* __restrict__ piv,
                                                       int* flag) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smraw[];
   coarse_factor_body(L, Dx, Dy, LUout, flag, smraw);
   (void)piv;
@@ -35,6 +36,7 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_coarse_solve(int n, const double* __restrict__ AinvT,
                                                      const int* __restrict__ piv, int tr,
                                                      const T* __restrict__ f, T* __restrict__ x) {
+  pdl_enter();
   __shared__ double b[128];
   for (int i = threadIdx.x; i < n; i += blockDim.x) b[i] = (double)f[i];
   __syncthreads();
@@ -56,8 +58,7 @@ cudaError_t launch_coarse_factor(const LevelView<double>& L, const double* Dx, c
     cudaError_t e = ensure_dyn_smem((const void*)k_coarse_factor, smem);
     if (e != cudaSuccess) return e;
   }
-  k_coarse_factor<<<1, 256, smem, s>>>(L, Dx, Dy, LU, piv, flag);
-  return cudaGetLastError();
+  return launch_k(k_coarse_factor, dim3(1), dim3(256), smem, s, L, Dx, Dy, LU, piv, flag);
 }
 
 template <typename T>

@@ -22,6 +22,7 @@ __global__ void __launch_bounds__(256) k_op_cols(LevelView<T> L, const T* __rest
                                                  const T* __restrict__ Px, const T* __restrict__ Py,
                                                  T* __restrict__ Gx, T* __restrict__ Gy,
                                                  T* __restrict__ part) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smraw[];
   opcols_body<T, DIM, KM>(L, p, Px, Py, Gx, Gy, part, blockIdx.x, gridDim.x, smraw);
 }
@@ -31,6 +32,7 @@ __global__ void __launch_bounds__(128) k_op_cols_tpc(LevelView<T> L, const T* __
                                                      const T* __restrict__ Px, const T* __restrict__ Py,
                                                      T* __restrict__ Gx, T* __restrict__ Gy,
                                                      T* __restrict__ part) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smraw[];
   opcols_tpc_body<T, DIM, MAXM>(L, p, Px, Py, Gx, Gy, part, smraw);
 }
@@ -39,6 +41,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_op_cols_T(LevelView<T> L, const T* __restrict__ lam,
                                                    const T* __restrict__ Dlam, T* __restrict__ Mx,
                                                    T* __restrict__ part) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smraw[];
   opcolsT_body<T>(L, lam, Dlam, Mx, part, blockIdx.x, gridDim.x, smraw);
 }
@@ -53,6 +56,7 @@ __global__ void __launch_bounds__(256) k_smooth_cols(LevelView<T> L, const T* __
                                                      const T* __restrict__ rhoXY,
                                                      const T* __restrict__ Binv,
                                                      T* __restrict__ x, T omega, int first) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smraw[];
   smooth_body<T, DIM, MAXM, TR, EXACT>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first, blockIdx.x, gridDim.x, smraw);
 }
@@ -61,6 +65,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_col_matrix(const T* __restrict__ M, int Mo, int Mi,
                                                     const T* __restrict__ in, T* __restrict__ out,
                                                     int ncols, int accumulate) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smraw[];
   colmat_body<T>(M, Mo, Mi, in, out, ncols, accumulate, blockIdx.x, gridDim.x, smraw);
 }
@@ -69,6 +74,7 @@ __global__ void __launch_bounds__(256) k_col_matrix(const T* __restrict__ M, int
 // cost one level's latency (a warp's Gauss-Jordan) instead of the sum.
 template <typename T>
 __global__ void __launch_bounds__(128) k_block_inverse_multi(const __grid_constant__ BlockInvMulti<T> m, int* flag) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smraw[];
   const int wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
   T* A = reinterpret_cast<T*>(smraw) + wib * (m.maxM1 * (2 * m.maxM1 + 1));

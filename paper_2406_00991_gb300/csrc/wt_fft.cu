@@ -20,6 +20,7 @@ namespace wt {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_rowpass(RowPass<T> a, int ppc) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smraw[];
   rowpass_body<T>(a, ppc, blockIdx.x, gridDim.x, smraw);
 }
@@ -92,6 +93,7 @@ __device__ c2_t<T>* real_spectral(c2_t<T>* A, c2_t<T>* B, int logNin, int logNou
 // and the optional second transform of the result into out2.
 template <typename T>
 __global__ void __launch_bounds__(256) k_rowpass_real(RowPass<T> a) {
+  pdl_enter();
   using c2 = c2_t<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int Nin = a.Nin, Nout = a.Nout;
@@ -186,6 +188,7 @@ template cudaError_t launch_rowpass<double>(const RowPass<double>&, cudaStream_t
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_rowpass_multi(const __grid_constant__ MultiPass<T> m) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smraw[];
   int i = 0;
   while (i + 1 < m.n && (int)blockIdx.x >= m.start[i + 1]) ++i;
@@ -210,8 +213,7 @@ cudaError_t launch_rowpass_multi(const MultiPass<T>& m0, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   if (m.start[m.n] <= 0) return cudaSuccess;
-  k_rowpass_multi<T><<<m.start[m.n], 256, smem, s>>>(m);
-  return cudaGetLastError();
+  return launch_k(k_rowpass_multi<T>, dim3(m.start[m.n]), dim3(256), smem, s, m);
 }
 
 template cudaError_t launch_rowpass_multi<float>(const MultiPass<float>&, cudaStream_t);

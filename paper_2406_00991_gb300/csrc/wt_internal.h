@@ -114,8 +114,42 @@ cudaError_t ensure_nonportable_cluster(const void* fn);
 // caps are multiples of it.
 int sm_count();
 
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream-serialisation attribute may be scheduled while its predecessor in
+// the stream still runs; every kernel that launch_k starts therefore begins
+// with pdl_enter(): griddepcontrol.wait (returns once every prerequisite grid
+// has completed and its memory operations are visible, and at once when the
+// kernel was launched without the attribute) before it touches global
+// memory.  A grid of at most half as many CTAs as the device has SMs then
+// signals griddepcontrol.launch_dependents, so that the next kernel's CTAs
+// are made resident on the idle SMs while it runs; a wider grid does not
+// (its dependent would be packed onto the SMs that free up first and share
+// them with the primary's last CTAs: measured slower on 3D levels).  The
+// stream's serialisation is kept either way: only launch latency overlaps.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() {
+  pdl_wait();
+  unsigned nsm;
+  asm("mov.u32 %0, %%nsmid;" : "=r"(nsm));
+  if (2ull * gridDim.x * gridDim.y * gridDim.z <= nsm) pdl_trigger();
+}
+
+// Whether launch_k sets the attribute on the calling host thread; the C-ABI
+// entry points scope it from the tank's `pdl` option (off elsewhere).
+bool pdl_enabled();
+struct PdlScope {
+  bool prev;
+  explicit PdlScope(bool on);
+  ~PdlScope();
+  PdlScope(const PdlScope&) = delete;
+  PdlScope& operator=(const PdlScope&) = delete;
+};
+
 // Launch through cudaLaunchKernelEx (grid, block, dynamic shared memory,
-// stream); returns the launch status.
+// stream), with the programmatic-serialisation attribute when pdl_enabled();
+// returns the launch status.  Every kernel started here calls pdl_enter()
+// first.
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                             Args... args) {
@@ -124,6 +158,13 @@ inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_
   cfg.blockDim = block;
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  if (pdl_enabled()) {
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 

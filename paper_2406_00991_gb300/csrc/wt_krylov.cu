@@ -22,6 +22,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_dots(const T* __restrict__ w, const T* __restrict__ V,
                                              long ldv, int nvec, long n, double* __restrict__ partial,
                                              int with_norm) {
+  pdl_enter();
   __shared__ double red[8][33];
   T acc[33];
 #pragma unroll
@@ -61,6 +62,7 @@ __global__ void __launch_bounds__(256) k_update_normalize(const T* w, const T* _
                                                          const double* __restrict__ h,
                                                          const double* __restrict__ inv_norm,
                                                          T* vout, float* __restrict__ v32) {
+  pdl_enter();
   __shared__ T sh[32];
   for (int i = threadIdx.x; i < 32; i += blockDim.x) sh[i] = i < nvec ? (T)h[i] : T(0);
   __syncthreads();
@@ -80,6 +82,7 @@ __global__ void __launch_bounds__(256) k_update_normalize(const T* w, const T* _
 template <typename T>
 __global__ void __launch_bounds__(256) k_lincomb(T* __restrict__ x, const T* __restrict__ Z, long ldz,
                                                 int nvec, long n, const double* __restrict__ y) {
+  pdl_enter();
   __shared__ T sy[32];
   for (int i = threadIdx.x; i < 32; i += blockDim.x) sy[i] = i < nvec ? (T)y[i] : T(0);
   __syncthreads();
@@ -95,6 +98,7 @@ __global__ void __launch_bounds__(256) k_lincomb(T* __restrict__ x, const T* __r
 template <typename Ti, typename To>
 __global__ void k_convert(const Ti* __restrict__ in, To* __restrict__ out, long n,
                           const double* __restrict__ scale, int invert) {
+  pdl_enter();
   double s = 1.0;
   if (scale) s = invert ? 1.0 / *scale : *scale;
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
@@ -104,12 +108,14 @@ __global__ void k_convert(const Ti* __restrict__ in, To* __restrict__ out, long 
 template <typename T>
 __global__ void k_axpy_from(double* __restrict__ x, const T* __restrict__ e, long n,
                             const double* __restrict__ scale) {
+  pdl_enter();
   const double s = *scale;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     x[i] += s * (double)e[i];
 }
 
 __global__ void k_nyquist_coef_f(const float* __restrict__ r, int nrows, int N, float* __restrict__ rho) {
+  pdl_enter();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= nrows) return;
   float s = 0;
@@ -118,6 +124,7 @@ __global__ void k_nyquist_coef_f(const float* __restrict__ r, int nrows, int N, 
   if (lane == 0) rho[warp] = s / (float)N;
 }
 __global__ void k_nyquist_coef_d(const double* __restrict__ r, int nrows, int N, double* __restrict__ rho) {
+  pdl_enter();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= nrows) return;
   double s = 0;
@@ -135,6 +142,7 @@ __device__ double block_sum_partial(const double* partial, int nblk, int nvals, 
 
 __global__ void k_gmres_init(double* st, const double* __restrict__ partial, int nblk, int m,
                              double bnorm, double tol) {
+  pdl_enter();
   if (threadIdx.x != 0) return;
   const double ww = block_sum_partial(partial, nblk, 1, 0);
   const double beta = sqrt(ww);
@@ -185,6 +193,7 @@ __device__ void arnoldi_update(double* st, const double* h2, double ww, int j, i
 }
 
 __global__ void k_gmres_solve_y(double* st, int k, int m) {
+  pdl_enter();
   if (threadIdx.x != 0) return;
   for (int i = k - 1; i >= 0; --i) {
     double s = st[OFF_G + i];
@@ -214,6 +223,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_dots_sum(const T* __restrict__ w, const T* __restrict__ V, long ldv,
                                                  int nvec, long n, double* __restrict__ partial, int with_norm,
                                                  double* __restrict__ out, unsigned* ticket) {
+  pdl_enter();
   __shared__ double red[8][33];
   T acc[33];
 #pragma unroll
@@ -258,6 +268,7 @@ __global__ void __launch_bounds__(256) k_update_dots_arnoldi(T* __restrict__ w, 
                                                             long ldv, int nvec, long n, double* st,
                                                             double* __restrict__ partial, int j, int m,
                                                             unsigned* ticket) {
+  pdl_enter();
   __shared__ double red[8][33];
   __shared__ T sh[32];
   const double* h = st + OFF_H1;

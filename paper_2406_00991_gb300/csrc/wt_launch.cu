@@ -36,6 +36,14 @@ cudaError_t ensure_nonportable_cluster(const void* fn) {
   return e;
 }
 
+namespace {
+thread_local bool tl_pdl = false;
+}
+
+bool pdl_enabled() { return tl_pdl; }
+PdlScope::PdlScope(bool on) : prev(tl_pdl) { tl_pdl = on; }
+PdlScope::~PdlScope() { tl_pdl = prev; }
+
 int sm_count() {
   static std::atomic<int> cache[64];
   int dev = 0;

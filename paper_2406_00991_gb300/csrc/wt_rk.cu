@@ -20,11 +20,13 @@ __global__ void k_metric_fill(int ncols, const double* __restrict__ h, const dou
                               const double* __restrict__ eax, const double* __restrict__ eay,
                               const double* __restrict__ eb, const double* __restrict__ ebx,
                               const double* __restrict__ eby, double* __restrict__ meta, int* flag) {
+  pdl_enter();
   metric_body(TLOOP, ncols, h, hx, hy, ea, eax, eay, eb, ebx, eby, meta, flag);
 }
 
 // Every level's metric in one launch: blockIdx.y = level.
 __global__ void k_metric_multi(const __grid_constant__ MetricMulti m) {
+  pdl_enter();
   const MetricLevel& L = m.lv[blockIdx.y];
   const long t0 = (long)blockIdx.x * blockDim.x + threadIdx.x, ts = (long)gridDim.x * blockDim.x;
   metric_body(t0, ts, L.ncols, L.h, L.hx, L.hy, L.ea, L.eax, L.eay, L.eb, L.ebx, L.eby, L.meta, m.flag);
@@ -37,6 +39,7 @@ __global__ void k_metric_multi(const __grid_constant__ MetricMulti m) {
 
 template <typename Ti, typename To>
 __global__ void k_cast(const Ti* __restrict__ in, To* __restrict__ out, long n) {
+  pdl_enter();
   GRID_LOOP(i, n) out[i] = (To)in[i];
 }
 
@@ -46,6 +49,7 @@ __global__ void k_stage_eta(int ncols, int linear, double alpha, double beta, do
                             const double* __restrict__ ey, double* __restrict__ Keta,
                             const double* __restrict__ eta, double* __restrict__ eta_new,
                             double* __restrict__ f_eta, int* flag) {
+  pdl_enter();
   stage_eta_body(TLOOP, ncols, linear, alpha, beta, dt, u, v, w, ex, ey, Keta, eta, eta_new, f_eta, flag);
 }
 
@@ -58,6 +62,7 @@ __global__ void k_stage_forcing(StageArgs a, const double* __restrict__ u, const
                                 double* __restrict__ Ku, double* __restrict__ Kv,
                                 double* __restrict__ Kw, double* __restrict__ us,
                                 double* __restrict__ vs, double* __restrict__ ws) {
+  pdl_enter();
   stage_forcing_body(TLOOP, a, u, v, w, ux, uy, vx, vy, wx, wy, ex, ey, f_eta, Ku, Kv, Kw, us, vs, ws);
 }
 
@@ -66,6 +71,7 @@ __global__ void k_stage_rhs(StageArgs a, const double* __restrict__ us, const do
                             const double* __restrict__ vsy, const double* __restrict__ Dus,
                             const double* __restrict__ Dvs, const double* __restrict__ Dws,
                             double* __restrict__ rhs) {
+  pdl_enter();
   stage_rhs_body(TLOOP, a, us, vs, ws, usx, vsy, Dus, Dvs, Dws, rhs);
 }
 
@@ -74,12 +80,14 @@ __global__ void k_stage_project(StageArgs a, const double* __restrict__ px, cons
                                 double* __restrict__ Kv, double* __restrict__ Kw,
                                 double* __restrict__ u, double* __restrict__ v, double* __restrict__ w,
                                 int* flag) {
+  pdl_enter();
   stage_project_body(TLOOP, a, px, py, Dp, Ku, Kv, Kw, u, v, w, flag);
 }
 
 __global__ void k_visc_grad(StageArgs a, const double* __restrict__ qx, const double* __restrict__ qy,
                             const double* __restrict__ qs, double* __restrict__ Gx, double* __restrict__ Gy,
                             double* __restrict__ Gz) {
+  pdl_enter();
   const long nc = a.ncols;
   GRID_LOOP(e, (long)a.M1 * nc) {
     const int m = (int)(e / nc);
@@ -97,6 +105,7 @@ __global__ void k_visc_grad(StageArgs a, const double* __restrict__ qx, const do
 __global__ void k_visc_div(StageArgs a, const double* __restrict__ dGx, const double* __restrict__ sGx,
                            const double* __restrict__ dGy, const double* __restrict__ sGy,
                            const double* __restrict__ sGz, double* __restrict__ lap) {
+  pdl_enter();
   const long nc = a.ncols;
   GRID_LOOP(e, (long)a.M1 * nc) {
     const int m = (int)(e / nc);
@@ -113,6 +122,7 @@ __global__ void k_relax(int ncols, int M1, const double* __restrict__ wgt, const
                         const double* __restrict__ u_t, const double* __restrict__ v_t,
                         const double* __restrict__ w_t, double* __restrict__ eta, double* __restrict__ u,
                         double* __restrict__ v, double* __restrict__ w) {
+  pdl_enter();
   GRID_LOOP(e, (long)M1 * ncols) {
     const long c = e % ncols;
     const double g = wgt[c];
@@ -126,27 +136,23 @@ __global__ void k_relax(int ncols, int M1, const double* __restrict__ wgt, const
 
 cudaError_t launch_visc_grad(const StageArgs& a, const double* qx, const double* qy, const double* qs,
                              double* Gx, double* Gy, double* Gz, cudaStream_t s) {
-  k_visc_grad<<<blocks_n((long)a.M1 * a.ncols), 256, 0, s>>>(a, qx, qy, qs, Gx, Gy, Gz);
-  return cudaGetLastError();
+  return launch_k(k_visc_grad, dim3(blocks_n((long)a.M1 * a.ncols)), dim3(256), 0, s, a, qx, qy, qs, Gx, Gy, Gz);
 }
 cudaError_t launch_visc_div(const StageArgs& a, const double* dGx, const double* sGx, const double* dGy,
                             const double* sGy, const double* sGz, double* lap, cudaStream_t s) {
-  k_visc_div<<<blocks_n((long)a.M1 * a.ncols), 256, 0, s>>>(a, dGx, sGx, dGy, sGy, sGz, lap);
-  return cudaGetLastError();
+  return launch_k(k_visc_div, dim3(blocks_n((long)a.M1 * a.ncols)), dim3(256), 0, s, a, dGx, sGx, dGy, sGy, sGz, lap);
 }
 cudaError_t launch_relax(int ncols, int M1, const double* wgt, const double* eta_t, const double* u_t,
                          const double* v_t, const double* w_t, double* eta, double* u, double* v, double* w,
                          cudaStream_t s) {
-  k_relax<<<blocks_n((long)M1 * ncols), 256, 0, s>>>(ncols, M1, wgt, eta_t, u_t, v_t, w_t, eta, u, v, w);
-  return cudaGetLastError();
+  return launch_k(k_relax, dim3(blocks_n((long)M1 * ncols)), dim3(256), 0, s, ncols, M1, wgt, eta_t, u_t, v_t, w_t, eta, u, v, w);
 }
 
 cudaError_t launch_metric_fill(int ncols, const double* h, const double* hx, const double* hy,
                                const double* ea, const double* eax, const double* eay,
                                const double* eb, const double* ebx, const double* eby, double* meta,
                                int* flag, cudaStream_t s) {
-  k_metric_fill<<<blocks_n(ncols), 256, 0, s>>>(ncols, h, hx, hy, ea, eax, eay, eb, ebx, eby, meta, flag);
-  return cudaGetLastError();
+  return launch_k(k_metric_fill, dim3(blocks_n(ncols)), dim3(256), 0, s, ncols, h, hx, hy, ea, eax, eay, eb, ebx, eby, meta, flag);
 }
 
 cudaError_t launch_metric_multi(const MetricMulti& m, cudaStream_t s) {
@@ -154,14 +160,12 @@ cudaError_t launch_metric_multi(const MetricMulti& m, cudaStream_t s) {
   if (m.n > kMaxMetricLevels) return cudaErrorInvalidValue;
   int maxc = 1;
   for (int i = 0; i < m.n; ++i) maxc = std::max(maxc, m.lv[i].ncols);
-  k_metric_multi<<<dim3(blocks_n(maxc), m.n), 256, 0, s>>>(m);
-  return cudaGetLastError();
+  return launch_k(k_metric_multi, dim3(blocks_n(maxc), m.n), dim3(256), 0, s, m);
 }
 
 template <typename Ti, typename To>
 cudaError_t launch_cast(const Ti* in, To* out, long n, cudaStream_t s) {
-  k_cast<Ti, To><<<blocks_n(n), 256, 0, s>>>(in, out, n);
-  return cudaGetLastError();
+  return launch_k(k_cast<Ti, To>, dim3(blocks_n(n)), dim3(256), 0, s, in, out, n);
 }
 template cudaError_t launch_cast<double, float>(const double*, float*, long, cudaStream_t);
 template cudaError_t launch_cast<float, double>(const float*, double*, long, cudaStream_t);
@@ -172,9 +176,8 @@ cudaError_t launch_stage_eta(int ncols, int M1, int linear, double alpha, double
                              const double* eta_y, double* Keta, const double* eta, double* eta_new,
                              double* f_eta, int* flag, cudaStream_t s) {
   (void)M1;
-  k_stage_eta<<<blocks_n(ncols), 256, 0, s>>>(ncols, linear, alpha, beta, dt, u, v, w, eta_x, eta_y,
+  return launch_k(k_stage_eta, dim3(blocks_n(ncols)), dim3(256), 0, s, ncols, linear, alpha, beta, dt, u, v, w, eta_x, eta_y,
                                               Keta, eta, eta_new, f_eta, flag);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_stage_forcing(const StageArgs& a, const double* u, const double* v, const double* w,
@@ -182,22 +185,19 @@ cudaError_t launch_stage_forcing(const StageArgs& a, const double* u, const doub
                                  const double* wx, const double* wy, const double* eta_x,
                                  const double* eta_y, const double* f_eta, double* Ku, double* Kv,
                                  double* Kw, double* us, double* vs, double* ws, cudaStream_t s) {
-  k_stage_forcing<<<blocks_n((long)a.M1 * a.ncols), 256, 0, s>>>(a, u, v, w, ux, uy, vx, vy, wx, wy,
+  return launch_k(k_stage_forcing, dim3(blocks_n((long)a.M1 * a.ncols)), dim3(256), 0, s, a, u, v, w, ux, uy, vx, vy, wx, wy,
                                                                   eta_x, eta_y, f_eta, Ku, Kv, Kw, us,
                                                                   vs, ws);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_stage_rhs(const StageArgs& a, const double* us, const double* vs, const double* ws,
                               const double* usx, const double* vsy, const double* Dus,
                               const double* Dvs, const double* Dws, double* rhs, cudaStream_t s) {
-  k_stage_rhs<<<blocks_n((long)a.M1 * a.ncols), 256, 0, s>>>(a, us, vs, ws, usx, vsy, Dus, Dvs, Dws, rhs);
-  return cudaGetLastError();
+  return launch_k(k_stage_rhs, dim3(blocks_n((long)a.M1 * a.ncols)), dim3(256), 0, s, a, us, vs, ws, usx, vsy, Dus, Dvs, Dws, rhs);
 }
 cudaError_t launch_stage_project(const StageArgs& a, const double* px, const double* py,
                                   const double* Dp, double* Ku, double* Kv, double* Kw, double* u,
                                   double* v, double* w, int* flag, cudaStream_t s) {
-  k_stage_project<<<blocks_n((long)a.M1 * a.ncols), 256, 0, s>>>(a, px, py, Dp, Ku, Kv, Kw, u, v, w, flag);
-  return cudaGetLastError();
+  return launch_k(k_stage_project, dim3(blocks_n((long)a.M1 * a.ncols)), dim3(256), 0, s, a, px, py, Dp, Ku, Kv, Kw, u, v, w, flag);
 }
 }  // namespace wt

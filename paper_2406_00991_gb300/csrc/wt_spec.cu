@@ -36,6 +36,7 @@ __device__ __forceinline__ void stage_twiddles(c2_t<T>* tws, const c2_t<T>* tw, 
 template <typename T>
 __global__ void __launch_bounds__(256) k_spec_fwd_x(const T* __restrict__ in, c2_t<T>* __restrict__ out,
                                                     int logN, const c2_t<T>* __restrict__ tw, int logNtw) {
+  pdl_enter();
   using c2 = c2_t<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = 1 << logN, H = N >> 1;
@@ -71,6 +72,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_spec_inv_x(const c2_t<T>* __restrict__ in, T* __restrict__ x,
                                                     int logN, T scale, int first,
                                                     const c2_t<T>* __restrict__ tw, int logNtw) {
+  pdl_enter();
   using c2 = c2_t<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = 1 << logN, H = N >> 1;
@@ -113,6 +115,7 @@ __global__ void __launch_bounds__(256) k_spec_inv_x(const c2_t<T>* __restrict__ 
 template <typename T>
 __global__ void __launch_bounds__(256) k_spec_y(c2_t<T>* __restrict__ S, int Ny, int logNy, int Nh, int tx,
                                                 int inverse, const c2_t<T>* __restrict__ tw, int logNtw) {
+  pdl_enter();
   using c2 = c2_t<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   c2* A = reinterpret_cast<c2*>(smraw);          // tx sequences of Ny
@@ -141,6 +144,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_spec_cols(c2_t<T>* __restrict__ S, const T* __restrict__ Tab,
                                                    const int* __restrict__ sidx, int M1, int Ny, int Nh,
                                                    int tr) {
+  pdl_enter();
   using c2 = c2_t<T>;
   const int lane = threadIdx.x & 31;
   const long nmodes = (long)Ny * Nh;
@@ -184,8 +188,7 @@ cudaError_t launch_spectral_smooth(const SpecArgs<T>& a, cudaStream_t s) {
   {
     const size_t smem = (size_t)(2 * H + H) * sizeof(c2);
     if ((e = ensure_dyn_smem((const void*)k_spec_fwd_x<T>, smem)) != cudaSuccess) return e;
-    k_spec_fwd_x<T><<<nrows, 256, smem, s>>>(a.r, a.spec, a.logNx, a.tw, a.logNtw);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_k(k_spec_fwd_x<T>, dim3(nrows), dim3(256), smem, s, a.r, a.spec, a.logNx, a.tw, a.logNtw)) != cudaSuccess) return e;
   }
   // kx per CTA: 8 (a 64-byte FP32 / 128-byte FP64 segment per y row) as long
   // as both ping-pong buffers stay within 192 KB of shared memory
@@ -195,25 +198,21 @@ cudaError_t launch_spectral_smooth(const SpecArgs<T>& a, cudaStream_t s) {
   const dim3 ygrid((Nh + tx - 1) / tx, a.M1);
   if (a.Ny > 1) {
     if ((e = ensure_dyn_smem((const void*)k_spec_y<T>, ysmem)) != cudaSuccess) return e;
-    k_spec_y<T><<<ygrid, 256, ysmem, s>>>(a.spec, a.Ny, a.logNy, Nh, tx, 0, a.tw, a.logNtw);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_k(k_spec_y<T>, dim3(ygrid), dim3(256), ysmem, s, a.spec, a.Ny, a.logNy, Nh, tx, 0, a.tw, a.logNtw)) != cudaSuccess) return e;
   }
   {
     const long nmodes = (long)a.Ny * Nh;
     const int wpb = 8;
     const long blocks = std::min<long>((nmodes + wpb - 1) / wpb, 65535L);
-    k_spec_cols<T><<<(unsigned)blocks, 32 * wpb, 0, s>>>(a.spec, a.tab, a.sidx, a.M1, a.Ny, Nh, a.tr);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_k(k_spec_cols<T>, dim3((unsigned)blocks), dim3(32 * wpb), 0, s, a.spec, a.tab, a.sidx, a.M1, a.Ny, Nh, a.tr)) != cudaSuccess) return e;
   }
   if (a.Ny > 1) {
-    k_spec_y<T><<<ygrid, 256, ysmem, s>>>(a.spec, a.Ny, a.logNy, Nh, tx, 1, a.tw, a.logNtw);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_k(k_spec_y<T>, dim3(ygrid), dim3(256), ysmem, s, a.spec, a.Ny, a.logNy, Nh, tx, 1, a.tw, a.logNtw)) != cudaSuccess) return e;
   }
   {
     const size_t smem = (size_t)((H + 1) + H + H + H) * sizeof(c2);
     if ((e = ensure_dyn_smem((const void*)k_spec_inv_x<T>, smem)) != cudaSuccess) return e;
-    k_spec_inv_x<T><<<nrows, 256, smem, s>>>(a.spec, a.x, a.logNx, a.scale, a.first, a.tw, a.logNtw);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_k(k_spec_inv_x<T>, dim3(nrows), dim3(256), smem, s, a.spec, a.x, a.logNx, a.scale, a.first, a.tw, a.logNtw)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

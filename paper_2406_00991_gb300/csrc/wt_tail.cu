@@ -17,6 +17,7 @@ namespace wt {
 
 template <typename T, int DIM>
 __global__ void __launch_bounds__(512) k_vcycle_tail(TailArgs<T> A) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char sm[];
   vcycle_cta<T, DIM>(A, sm);
 }
@@ -26,11 +27,8 @@ cudaError_t launch_vcycle_tail(const TailArgs<T>& a, int dim, cudaStream_t s) {
   cudaError_t e = dim == 3 ? ensure_dyn_smem((const void*)k_vcycle_tail<T, 3>, (size_t)a.smem)
                            : ensure_dyn_smem((const void*)k_vcycle_tail<T, 2>, (size_t)a.smem);
   if (e != cudaSuccess) return e;
-  if (dim == 3)
-    k_vcycle_tail<T, 3><<<1, 512, a.smem, s>>>(a);
-  else
-    k_vcycle_tail<T, 2><<<1, 512, a.smem, s>>>(a);
-  return cudaGetLastError();
+  if (dim == 3) return launch_k(k_vcycle_tail<T, 3>, dim3(1), dim3(512), a.smem, s, a);
+  return launch_k(k_vcycle_tail<T, 2>, dim3(1), dim3(512), a.smem, s, a);
 }
 
 template cudaError_t launch_vcycle_tail<float>(const TailArgs<float>&, int, cudaStream_t);

@@ -162,6 +162,7 @@ __device__ __forceinline__ void stage_tw(c2_t<T>* tws, const RowPass<T>& a, int 
 // x-rows: rows r (of a [rows][N] array), row m = r / Ny for the boundary rows
 template <typename T, int R>
 __global__ void __launch_bounds__(256) k_xderiv_warp(RowPass<T> a) {
+  pdl_enter();
   using c2 = c2_t<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   c2* tws = reinterpret_cast<c2*>(smraw);
@@ -201,6 +202,7 @@ __global__ void __launch_bounds__(256) k_xderiv_warp(RowPass<T> a) {
 // [N][17]; warp w transforms columns 2w and 2w + 1.
 template <typename T, int R>
 __global__ void __launch_bounds__(256) k_yderiv_warp(RowPass<T> a) {
+  pdl_enter();
   using c2 = c2_t<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = 32 * R;
@@ -271,13 +273,12 @@ static cudaError_t launch_r(const RowPass<T>& a, cudaStream_t s) {
     if ((e = ensure_dyn_smem((const void*)k_yderiv_warp<T, R>, smem)) != cudaSuccess) return e;
     const int planes = a.nrows / a.Nxl;
     const dim3 grid((a.Nxl + 15) / 16, planes);
-    k_yderiv_warp<T, R><<<grid, 256, smem, s>>>(a);
+    return launch_k(k_yderiv_warp<T, R>, grid, dim3(256), smem, s, a);
   } else {
     const size_t smem = (size_t)(N / 2) * sizeof(c2);
     const long pairs = ((long)a.nrows + 1) / 2;
-    k_xderiv_warp<T, R><<<(unsigned)((pairs + 7) / 8), 256, smem, s>>>(a);
+    return launch_k(k_xderiv_warp<T, R>, dim3((unsigned)((pairs + 7) / 8)), dim3(256), smem, s, a);
   }
-  return cudaGetLastError();
 }
 
 template <typename T>
