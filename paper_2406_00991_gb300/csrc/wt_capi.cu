@@ -797,7 +797,7 @@ int wt_create(int Nx, int Ny, int Nz, double L, double g, double nu, const doubl
     t->Z64 = ar.alloc<double>((size_t)31 * n);
     t->V32 = ar.alloc<float>((size_t)32 * n);
     t->Z32 = ar.alloc<float>((size_t)31 * n);
-    t->nblk = (int)std::min<long>(296, std::max<long>(1, (n + 511) / 512));
+    t->nblk = (int)std::min<long>(2L * sm_count(), std::max<long>(1, (n + 511) / 512));
     t->partial = ar.alloc<double>((size_t)t->nblk * 40);
     t->st = ar.alloc<double>(4608);
     t->stN = ar.alloc<double>(4608);

@@ -61,6 +61,34 @@ __global__ void __launch_bounds__(256) k_smooth_cols(LevelView<T> L, const T* __
   smooth_body<T, DIM, MAXM, TR, EXACT>(L, r, rhoX, rhoY, rhoXY, Binv, x, omega, first, blockIdx.x, gridDim.x, smraw);
 }
 
+// out = M in (accumulate: out += M in) column by column with one thread per
+// column: the column's Mi values in registers, M (Mo x Mi, row-major) in
+// shared memory read as warp-wide broadcasts, loads and stores coalesced
+// across the threads' consecutive columns.  Every input of a column is read
+// before its first output is written, so out may be in (the filter).
+template <typename T, int MI>
+__global__ void __launch_bounds__(128) k_col_matrix_tpc(const T* __restrict__ M, int Mo, const T* in,
+                                                        T* out, int ncols, int accumulate) {
+  pdl_enter();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sM = reinterpret_cast<T*>(smraw);
+  for (int i = threadIdx.x; i < Mo * MI; i += blockDim.x) sM[i] = M[i];
+  __syncthreads();
+  const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncols) return;
+  const long nc = ncols;
+  T v[MI];
+#pragma unroll
+  for (int j = 0; j < MI; ++j) v[j] = in[j * nc + c];
+  for (int i = 0; i < Mo; ++i) {
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < MI; ++j) acc = fma(sM[i * MI + j], v[j], acc);
+    const long o = i * nc + c;
+    out[o] = accumulate ? out[o] + acc : acc;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_col_matrix(const T* __restrict__ M, int Mo, int Mi,
                                                     const T* __restrict__ in, T* __restrict__ out,
@@ -191,6 +219,22 @@ cudaError_t launch_smooth_cols(const LevelView<T>& L, const T* r, const T* rhoX,
 template <typename T>
 cudaError_t launch_col_matrix(const T* M, int Mo, int Mi, const T* in, T* out, int ncols,
                               int accumulate, cudaStream_t s) {
+  if (ncols >= kTpcMinCols && Mo <= kMaxM1) {
+    // many columns (3D levels): one thread per column
+    const dim3 G((unsigned)((ncols + 127) / 128)), B(128);
+    const size_t sm = sizeof(T) * (size_t)Mo * Mi;
+#define WT_CMT(MI) launch_k(k_col_matrix_tpc<T, MI>, G, B, sm, s, M, Mo, in, out, ncols, accumulate)
+    switch (Mi) {
+      case 5: return WT_CMT(5);
+      case 9: return WT_CMT(9);
+      case 13: return WT_CMT(13);
+      case 17: return WT_CMT(17);
+      case 25: return WT_CMT(25);
+      case 33: return WT_CMT(33);
+      default: break;
+    }
+#undef WT_CMT
+  }
   const int g = grid_cols(ncols, 256);
   const size_t smem = sizeof(T) * (size_t)Mo * Mi;
   return launch_k(k_col_matrix<T>, dim3(g), dim3(256), smem, s, M, Mo, Mi, in, out, ncols, accumulate);

@@ -133,18 +133,32 @@ __global__ void k_nyquist_coef_d(const double* __restrict__ r, int nrows, int N,
   if (lane == 0) rho[warp] = s / (double)N;
 }
 
-// ---- small dense GMRES part (one CTA)
-__device__ double block_sum_partial(const double* partial, int nblk, int nvals, int i) {
-  double s = 0;
-  for (int b = 0; b < nblk; ++b) s += partial[(long)b * nvals + i];
+// ---- small dense GMRES part
+// Sum over b < nblk of partial[b * nvals + i], by one warp: the lanes stride
+// over the blocks with four accumulators in flight, then a shuffle tree; the
+// result is returned in every lane.  __ldcg: the partials were written by
+// other CTAs of the same (or the previous) launch.
+__device__ double warp_sum_partials(const double* partial, int nblk, int nvals, int i, int lane) {
+  double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  int b = lane;
+  for (; b + 96 < nblk; b += 128) {
+    s0 += __ldcg(partial + (long)b * nvals + i);
+    s1 += __ldcg(partial + (long)(b + 32) * nvals + i);
+    s2 += __ldcg(partial + (long)(b + 64) * nvals + i);
+    s3 += __ldcg(partial + (long)(b + 96) * nvals + i);
+  }
+  for (; b < nblk; b += 32) s0 += __ldcg(partial + (long)b * nvals + i);
+  double s = (s0 + s1) + (s2 + s3);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return s;
 }
 
+// One warp.
 __global__ void k_gmres_init(double* st, const double* __restrict__ partial, int nblk, int m,
                              double bnorm, double tol) {
   pdl_enter();
+  const double ww = warp_sum_partials(partial, nblk, 1, 0, threadIdx.x & 31);
   if (threadIdx.x != 0) return;
-  const double ww = block_sum_partial(partial, nblk, 1, 0);
   const double beta = sqrt(ww);
   st[0] = beta;
   st[1] = beta;
@@ -253,10 +267,9 @@ __global__ void __launch_bounds__(256) k_dots_sum(const T* __restrict__ w, const
     partial[(long)blockIdx.x * nvals + i] = s;
   }
   if (!last_block(ticket)) return;
-  for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
-    double s = 0;
-    for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partial + (long)b * nvals + i);
-    out[i] = s;
+  for (int i = warp; i < nvals; i += (int)(blockDim.x >> 5)) {
+    const double s = warp_sum_partials(partial, (int)gridDim.x, nvals, i, lane);
+    if (lane == 0) out[i] = s;
   }
 }
 
@@ -308,10 +321,11 @@ __global__ void __launch_bounds__(256) k_update_dots_arnoldi(T* __restrict__ w, 
   if (!last_block(ticket)) return;
   __shared__ double h2[64];
   __shared__ double ww;
-  for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
-    double s = 0;
-    for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partial + (long)b * nvals + i);
-    if (i < j + 1) h2[i] = s; else ww = s;
+  for (int i = warp; i < nvals; i += (int)(blockDim.x >> 5)) {
+    const double s = warp_sum_partials(partial, (int)gridDim.x, nvals, i, lane);
+    if (lane == 0) {
+      if (i < j + 1) h2[i] = s; else ww = s;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) arnoldi_update(st, h2, ww, j, m);

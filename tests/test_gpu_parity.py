@@ -289,6 +289,30 @@ def test_rk_stages_parity_3d(wt, mode):
     assert np.abs(dv).max() < 1e-7 and np.abs(bot).max() < 1e-9
 
 
+@pytest.mark.parametrize("N,Nz,stages", [(128, 4, 5), (128, 16, 1)])
+def test_rk_stages_parity_3d_many_columns(wt, N, Nz, stages):
+    # 16,384 columns: the FP64 sigma derivatives and the Chebyshev filter of
+    # the stage run one thread per column (the column-matrix kernel for
+    # levels of at least 8,192 columns), filter on, against the oracle
+    L = 2 * math.pi
+    g = op.Grid(N, N, Nz, L)
+    X, Y = np.meshgrid(g.x, g.y, indexing="xy")
+    h = 1.0 - 0.1 * np.cos(X) * np.sin(Y)
+    sea = si.jonswap_sea(seed=2, L=L, ncomp=48, kp=4.0, hs_over_lp=0.01)
+    eta0, u0, v0, w0 = si.jonswap_fields(sea, N, g.sigma)
+    tank_o = rk.Tank(N, N, Nz, L, h, tol=1e-13, coarsest_max=64, filter=True)
+    st = rk.State(g, eta0, u0, v0, w0)
+    dt = 0.005
+    T = wt.Tank(N, N, Nz, L, h, mode=wt.WT_MIXED, tol=1e-12, max_it=400, filter=1)
+    T.set_state(*(np.ascontiguousarray(a) for a in (eta0, u0, v0, w0)))
+    for k in range(1, stages + 1):
+        rk.stage(tank_o, st, k, dt)
+        T.rk_stage(k, dt)
+    eta, u, v, w, tm = T.get_state()
+    for got, ref in ((eta, st.eta), (u, st.u), (v, st.v), (w, st.w)):
+        assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("Nx,Ny,Nz", [(64, 1, 16), (1024, 1, 24), (16, 16, 8), (32, 32, 12)])
 def test_fmg_parity(wt, Nx, Ny, Nz):
     # one full-multigrid cycle (Algorithm 2) as the preconditioner: the GPU's
