@@ -18,27 +18,30 @@ namespace wt {
 constexpr int OFF_H1 = 8, OFF_H2 = 72, OFF_CS = 136, OFF_SN = 200, OFF_G = 264, OFF_Y = 328,
               OFF_H = 392;
 
-template <typename T>
+// Per-CTA partial sums of V_i^T w (i < nvec) and, with with_norm, ||w||^2.
+// NV >= nvec bounds the unrolled vector loops at compile time (0, 4, 8, 16,
+// 32), so that short bases keep few registers and a high occupancy.
+template <typename T, int NV>
 __global__ void __launch_bounds__(256) k_dots(const T* __restrict__ w, const T* __restrict__ V,
                                              long ldv, int nvec, long n, double* __restrict__ partial,
                                              int with_norm) {
   pdl_enter();
-  __shared__ double red[8][33];
-  T acc[33];
+  __shared__ double red[8][NV + 1];
+  T acc[NV + 1];
 #pragma unroll
-  for (int i = 0; i < 33; ++i) acc[i] = T(0);
+  for (int i = 0; i <= NV; ++i) acc[i] = T(0);
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
     const T wv = w[e];
 #pragma unroll
-    for (int i = 0; i < 32; ++i)
+    for (int i = 0; i < NV; ++i)
       if (i < nvec) acc[i] += wv * V[i * ldv + e];
-    acc[32] += wv * wv;
+    acc[NV] += wv * wv;
   }
   const int nvals = nvec + with_norm;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-  for (int i = 0; i < 33; ++i) {
-    const bool used = (i < nvec) || (i == 32 && with_norm);
+  for (int i = 0; i <= NV; ++i) {
+    const bool used = (i < nvec) || (i == NV && with_norm);
     if (!used) continue;
     double v = (double)acc[i];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -46,7 +49,7 @@ __global__ void __launch_bounds__(256) k_dots(const T* __restrict__ w, const T* 
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
-    const int src = (i < nvec) ? i : 32;
+    const int src = (i < nvec) ? i : NV;
     double s = 0;
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k][src];
     partial[(long)blockIdx.x * nvals + i] = s;
@@ -56,21 +59,21 @@ __global__ void __launch_bounds__(256) k_dots(const T* __restrict__ w, const T* 
 // vout = (w - V h) * inv_norm, h = st[OFF_H2..], inv_norm = st[2]; vout may
 // be w itself (each element is read and written by one thread), and v32, if
 // given, receives the FP32 rounding of vout (the FP32 V-cycle's input).
-template <typename T>
+template <typename T, int NV>
 __global__ void __launch_bounds__(256) k_update_normalize(const T* w, const T* __restrict__ V,
                                                          long ldv, int nvec, long n,
                                                          const double* __restrict__ h,
                                                          const double* __restrict__ inv_norm,
                                                          T* vout, float* __restrict__ v32) {
   pdl_enter();
-  __shared__ T sh[32];
-  for (int i = threadIdx.x; i < 32; i += blockDim.x) sh[i] = i < nvec ? (T)h[i] : T(0);
+  __shared__ T sh[NV + 1];
+  for (int i = threadIdx.x; i < NV; i += blockDim.x) sh[i] = i < nvec ? (T)h[i] : T(0);
   __syncthreads();
   const T s = (T)(*inv_norm);
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
     T wv = w[e];
 #pragma unroll
-    for (int i = 0; i < 32; ++i)
+    for (int i = 0; i < NV; ++i)
       if (i < nvec) wv -= sh[i] * V[i * ldv + e];
     wv *= s;
     vout[e] = wv;
@@ -79,17 +82,17 @@ __global__ void __launch_bounds__(256) k_update_normalize(const T* w, const T* _
 }
 
 // x += sum_i y_i Z_i, y = st[OFF_Y..]
-template <typename T>
+template <typename T, int NV>
 __global__ void __launch_bounds__(256) k_lincomb(T* __restrict__ x, const T* __restrict__ Z, long ldz,
                                                 int nvec, long n, const double* __restrict__ y) {
   pdl_enter();
-  __shared__ T sy[32];
-  for (int i = threadIdx.x; i < 32; i += blockDim.x) sy[i] = i < nvec ? (T)y[i] : T(0);
+  __shared__ T sy[NV + 1];
+  for (int i = threadIdx.x; i < NV; i += blockDim.x) sy[i] = i < nvec ? (T)y[i] : T(0);
   __syncthreads();
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
     T acc = x[e];
 #pragma unroll
-    for (int i = 0; i < 32; ++i)
+    for (int i = 0; i < NV; ++i)
       if (i < nvec) acc += sy[i] * Z[i * ldz + e];
     x[e] = acc;
   }
@@ -233,27 +236,27 @@ __device__ inline bool last_block(unsigned* ticket) {
 }
 
 // k_dots followed (in the last CTA) by the sum of the partials into out.
-template <typename T>
+template <typename T, int NV>
 __global__ void __launch_bounds__(256) k_dots_sum(const T* __restrict__ w, const T* __restrict__ V, long ldv,
                                                  int nvec, long n, double* __restrict__ partial, int with_norm,
                                                  double* __restrict__ out, unsigned* ticket) {
   pdl_enter();
-  __shared__ double red[8][33];
-  T acc[33];
+  __shared__ double red[8][NV + 1];
+  T acc[NV + 1];
 #pragma unroll
-  for (int i = 0; i < 33; ++i) acc[i] = T(0);
+  for (int i = 0; i <= NV; ++i) acc[i] = T(0);
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
     const T wv = w[e];
 #pragma unroll
-    for (int i = 0; i < 32; ++i)
+    for (int i = 0; i < NV; ++i)
       if (i < nvec) acc[i] += wv * V[i * ldv + e];
-    acc[32] += wv * wv;
+    acc[NV] += wv * wv;
   }
   const int nvals = nvec + with_norm;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-  for (int i = 0; i < 33; ++i) {
-    const bool used = (i < nvec) || (i == 32 && with_norm);
+  for (int i = 0; i <= NV; ++i) {
+    const bool used = (i < nvec) || (i == NV && with_norm);
     if (!used) continue;
     double v = (double)acc[i];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(256) k_dots_sum(const T* __restrict__ w, const
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
-    const int src = (i < nvec) ? i : 32;
+    const int src = (i < nvec) ? i : NV;
     double s = 0;
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k][src];
     partial[(long)blockIdx.x * nvals + i] = s;
@@ -275,45 +278,45 @@ __global__ void __launch_bounds__(256) k_dots_sum(const T* __restrict__ w, const
 
 // w -= V h1 (h1 = st[OFF_H1..]) and the per-CTA sums of (V^T w, ||w||^2);
 // the last CTA adds them up and performs the Arnoldi / Givens update of
-// column j (arnoldi_update).
-template <typename T>
+// column j (arnoldi_update).  NV >= nvec >= 1.
+template <typename T, int NV>
 __global__ void __launch_bounds__(256) k_update_dots_arnoldi(T* __restrict__ w, const T* __restrict__ V,
                                                             long ldv, int nvec, long n, double* st,
                                                             double* __restrict__ partial, int j, int m,
                                                             unsigned* ticket) {
   pdl_enter();
-  __shared__ double red[8][33];
-  __shared__ T sh[32];
+  __shared__ double red[8][NV + 1];
+  __shared__ T sh[NV];
   const double* h = st + OFF_H1;
-  for (int i = threadIdx.x; i < 32; i += blockDim.x) sh[i] = i < nvec ? (T)h[i] : T(0);
+  for (int i = threadIdx.x; i < NV; i += blockDim.x) sh[i] = i < nvec ? (T)h[i] : T(0);
   __syncthreads();
-  T acc[33];
+  T acc[NV + 1];
 #pragma unroll
-  for (int i = 0; i < 33; ++i) acc[i] = T(0);
+  for (int i = 0; i <= NV; ++i) acc[i] = T(0);
   for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
-    T v[32];
+    T v[NV];
     T wv = w[e];
 #pragma unroll
-    for (int i = 0; i < 32; ++i)
+    for (int i = 0; i < NV; ++i)
       if (i < nvec) { v[i] = V[i * ldv + e]; wv -= sh[i] * v[i]; }
     w[e] = wv;
 #pragma unroll
-    for (int i = 0; i < 32; ++i)
+    for (int i = 0; i < NV; ++i)
       if (i < nvec) acc[i] += wv * v[i];
-    acc[32] += wv * wv;
+    acc[NV] += wv * wv;
   }
   const int nvals = nvec + 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-  for (int i = 0; i < 33; ++i) {
-    if (!(i < nvec || i == 32)) continue;
+  for (int i = 0; i <= NV; ++i) {
+    if (!(i < nvec || i == NV)) continue;
     double v = (double)acc[i];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) red[warp][i] = v;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nvals; i += blockDim.x) {
-    const int src = (i < nvec) ? i : 32;
+    const int src = (i < nvec) ? i : NV;
     double s = 0;
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k][src];
     partial[(long)blockIdx.x * nvals + i] = s;
@@ -336,21 +339,34 @@ static inline int blocks_for(long n) {
   return (int)std::min<long>(std::max<long>(1, (n + 255) / 256), (long)sm_count() * 4);
 }
 
+// The compile-time bound NV of the basis loops: the smallest of 0 (no
+// vectors), 4, 8, 16, 32 that holds nvec.
+#define WT_NV_DISPATCH(nvec, CALL) \
+  ((nvec) <= 0 ? CALL(0) : (nvec) <= 4 ? CALL(4) : (nvec) <= 8 ? CALL(8) : (nvec) <= 16 ? CALL(16) : CALL(32))
+#define WT_NV1_DISPATCH(nvec, CALL) \
+  ((nvec) <= 4 ? CALL(4) : (nvec) <= 8 ? CALL(8) : (nvec) <= 16 ? CALL(16) : CALL(32))
+
 template <typename T>
 cudaError_t launch_dots(const T* w, const T* V, long ldv, int nvec, long n, double* partial, int nblk,
                         int with_norm, cudaStream_t s) {
-  return launch_k(k_dots<T>, dim3(nblk), dim3(256), 0, s, w, V, ldv, nvec, n, partial, with_norm);
+#define WT_C(NV) launch_k(k_dots<T, NV>, dim3(nblk), dim3(256), 0, s, w, V, ldv, nvec, n, partial, with_norm)
+  return WT_NV_DISPATCH(nvec, WT_C);
+#undef WT_C
 }
 template <typename T>
 cudaError_t launch_update_normalize(const T* w, const T* V, long ldv, int nvec, long n, const double* h,
                                     const double* inv_norm, T* vout, float* v32, cudaStream_t s) {
-  return launch_k(k_update_normalize<T>, dim3(blocks_for(n)), dim3(256), 0, s, w, V, ldv, nvec, n, h, inv_norm, vout,
-                  v32);
+#define WT_C(NV) launch_k(k_update_normalize<T, NV>, dim3(blocks_for(n)), dim3(256), 0, s, w, V, ldv, nvec, n, h, \
+                          inv_norm, vout, v32)
+  return WT_NV_DISPATCH(nvec, WT_C);
+#undef WT_C
 }
 template <typename T>
 cudaError_t launch_lincomb(T* x, const T* Z, long ldz, int nvec, long n, const double* y,
                            cudaStream_t s) {
-  return launch_k(k_lincomb<T>, dim3(blocks_for(n)), dim3(256), 0, s, x, Z, ldz, nvec, n, y);
+#define WT_C(NV) launch_k(k_lincomb<T, NV>, dim3(blocks_for(n)), dim3(256), 0, s, x, Z, ldz, nvec, n, y)
+  return WT_NV_DISPATCH(nvec, WT_C);
+#undef WT_C
 }
 template <typename Ti, typename To>
 cudaError_t launch_convert(const Ti* in, To* out, long n, const double* scale, int invert,
@@ -381,15 +397,19 @@ cudaError_t launch_gmres_solve_y(double* st, int k, int m, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_dots_sum(const T* w, const T* V, long ldv, int nvec, long n, double* partial, int nblk,
                             int with_norm, double* out, unsigned* ticket, cudaStream_t s) {
-  return launch_k(k_dots_sum<T>, dim3(nblk), dim3(256), 0, s, w, V, ldv, nvec, n, partial, with_norm, out,
-                  ticket);
+#define WT_C(NV) launch_k(k_dots_sum<T, NV>, dim3(nblk), dim3(256), 0, s, w, V, ldv, nvec, n, partial, with_norm, \
+                          out, ticket)
+  return WT_NV_DISPATCH(nvec, WT_C);
+#undef WT_C
 }
 template <typename T>
 cudaError_t launch_update_dots_arnoldi(T* w, const T* V, long ldv, int nvec, long n, double* st,
                                        double* partial, int nblk, int j, int m, unsigned* ticket,
                                        cudaStream_t s) {
-  return launch_k(k_update_dots_arnoldi<T>, dim3(nblk), dim3(256), 0, s, w, V, ldv, nvec, n, st, partial, j, m,
-                  ticket);
+#define WT_C(NV) launch_k(k_update_dots_arnoldi<T, NV>, dim3(nblk), dim3(256), 0, s, w, V, ldv, nvec, n, st, \
+                          partial, j, m, ticket)
+  return WT_NV1_DISPATCH(nvec, WT_C);
+#undef WT_C
 }
 
 #define WT_KINST(T)                                                                                  \
