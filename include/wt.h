@@ -133,6 +133,15 @@ typedef struct wt_options {
                         (griddepcontrol.wait) for the predecessor's completion
                         before touching memory, so results are unchanged and
                         only launch latency is hidden; 0: plain stream order */
+  int df64;          /* 1 (default): the FP64 x- and y-derivative and filter
+                        passes over many lines (32..256 points, 3D levels)
+                        run in double-float arithmetic (each value the
+                        unevaluated sum of two floats, about 48 significant
+                        bits, from error-free float transformations) on the
+                        FP32 units, which GB300 runs at 64 times its FP64
+                        rate; the data stay FP64 in memory (measured operator
+                        error 2e-15 of max |Ap| against 1e-15 in FP64).
+                        0: FP64 arithmetic                                   */
 } wt_options;
 
 typedef struct wt_solve_info {

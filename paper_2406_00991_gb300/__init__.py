@@ -35,7 +35,8 @@ class wt_options(ctypes.Structure):
                 ("tail_cluster", ctypes.c_int), ("barrier_cycles", ctypes.c_longlong),
                 ("cycle", ctypes.c_int), ("smoother", ctypes.c_int), ("omega_s", ctypes.c_double),
                 ("warp_fft", ctypes.c_int),
-                ("pdl", ctypes.c_int)]
+                ("pdl", ctypes.c_int),
+                ("df64", ctypes.c_int)]
 
 
 class wt_solve_info(ctypes.Structure):

@@ -443,6 +443,7 @@ int check_options(const wt_options& o) {
   if (!(o.omega_s > 0) || !(o.omega_s < 2)) return fail(WT_EINVAL, "omega_s must be in (0, 2)");
   if (o.warp_fft != 0 && o.warp_fft != 1) return fail(WT_EINVAL, "warp_fft must be 0 or 1");
   if (o.pdl != 0 && o.pdl != 1) return fail(WT_EINVAL, "pdl must be 0 or 1");
+  if (o.df64 != 0 && o.df64 != 1) return fail(WT_EINVAL, "df64 must be 0 or 1");
   if ((o.filter != 0 && o.filter != 1) || (o.linear != 0 && o.linear != 1) ||
       (o.bc_transfer != 0 && o.bc_transfer != 1))
     return fail(WT_EINVAL, "filter, linear, bc_transfer are 0 or 1");
@@ -501,6 +502,7 @@ RowPass<double> dpass(wt_tank& t, const double* in, double* out, int nrows, int 
   a.logNin = ilog2(N); a.logNout = ilog2(N); a.op = op;
   a.kscale = 2.0 * M_PI / t.L; a.tw = t.tw64; a.logNtw = t.logNtw;
   a.warp = t.opt.warp_fft;
+  a.df = t.opt.df64;
   return a;
 }
 // d/dx of a field with `planes` sigma levels (planes = 1: a surface)
@@ -726,6 +728,7 @@ int wt_default_options(wt_options* o) {
   o->omega_s = 1.0;
   o->warp_fft = 1;
   o->pdl = 1;
+  o->df64 = 1;
   return WT_OK;
 }
 

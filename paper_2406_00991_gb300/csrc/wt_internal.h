@@ -100,6 +100,7 @@ struct RowPass {
   int op2 = XOP_RESAMPLE;
   int write_out = 1;
   int warp = 1;                // derivative passes over many lines may use the warp kernels
+  int df = 0;                  // FP64 derivative passes may run in double-float arithmetic
 };
 
 // Raise kernel `fn`'s dynamic shared-memory limit to at least `bytes` on the

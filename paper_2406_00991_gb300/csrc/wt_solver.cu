@@ -40,6 +40,7 @@ static RowPass<T> xpass(wt_tank& t, const T* in, T* out, int nrows, int Nin, int
   a.tw = twiddles<T>(t);
   a.logNtw = t.logNtw;
   a.warp = t.opt.warp_fft;
+  a.df = t.opt.df64;
   return a;
 }
 

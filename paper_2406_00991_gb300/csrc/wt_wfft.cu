@@ -1,6 +1,7 @@
-// Spectral x- and y-derivative passes with one warp per pair of real lines,
-// the transform held in registers (paper Sec. 3.5: D f = F^{-1}(i kappa F f),
-// the Nyquist coefficient multiplied by 0).  For passes over many lines (the
+// Spectral x- and y-derivative and filter passes with one warp per pair of
+// real lines, the transform held in registers (paper Sec. 3.5: D f =
+// F^{-1}(i kappa F f), the Nyquist coefficient multiplied by 0; Sec. 3.6: the
+// exponential cut-off filter F^{-1}(F_S F f)).  For passes over many lines (the
 // 3D levels) the CTA-per-line Stockham passes of wt_fft.cu spend most of
 // their instructions on idle threads, barriers and shared-memory index
 // arithmetic; here a warp transforms two real lines packed as one complex
@@ -12,19 +13,33 @@
 //   3. a 32-point DFT across the lanes per slot by __shfl_xor_sync butterflies
 //      (decimation in frequency: lane l then holds k1 = brev_32(l)),
 // so lane l, slot q holds Z[k2 + R k1]; the derivative multiplies it by
-// i kappa(k); the inverse runs the three steps backwards (decimation in time
-// from the bit-reversed orders, conjugate twiddles), leaving N z' in natural
-// order.  The derivative is a real operator, so the real and imaginary parts
-// of z' are the two lines' derivatives.  x-rows are loaded and stored
-// coalesced (lane-consecutive); y-lines go through a shared-memory tile of
-// 16 x-columns per CTA (one column pair per warp).
+// i kappa(k) (the filter by its real response at |k|); the inverse runs the
+// three steps backwards (decimation in time from the bit-reversed orders,
+// conjugate twiddles), leaving N z' in natural order.  Both operators are
+// real, so the real and imaginary parts of z' are the two lines' results.
+// x-rows are loaded and stored coalesced (lane-consecutive); y-lines go
+// through a shared-memory tile of 16 x-columns per CTA (one column pair per
+// warp).  FP32 data are transformed in FP32; FP64 data (option df64) in
+// double-float arithmetic (wt_ff.cuh).
 #include "wt_dev.cuh"
+#include "wt_ff.cuh"
 
 #include <algorithm>
 
 namespace wt {
 
+template <> __device__ __forceinline__ ff2 mk<ff>(ff re, ff im) {
+  ff2 r;
+  r.x = re;
+  r.y = im;
+  return r;
+}
+
 namespace {
+
+template <typename A> __device__ __forceinline__ A a_int(int v);
+template <> __device__ __forceinline__ float a_int<float>(int v) { return (float)v; }
+template <> __device__ __forceinline__ ff a_int<ff>(int v) { return ff(v); }
 
 template <int R>
 struct Log2 {
@@ -57,7 +72,7 @@ __device__ __forceinline__ c2_t<T> cconj(c2_t<T> a) { return mk<T>(a.x, -a.y); }
 
 template <typename T>
 __device__ __forceinline__ c2_t<T> shfl_xor_c(c2_t<T> v, int m) {
-  return mk<T>(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+  return mk<T>(shfl_xor_a(v.x, m), shfl_xor_a(v.y, m));
 }
 
 // Forward transform of the warp's sequence (see the file comment).
@@ -140,8 +155,22 @@ __device__ __forceinline__ void warp_deriv(c2_t<T> (&x)[R], int N, int lane, T k
   for (int q = 0; q < R; ++q) {
     const int k = brev_const<R>(q) + R * k1;
     const int sk = k < N / 2 ? k : k - N;
-    const T kap = (k == N / 2) ? T(0) : kscale * T(sk) * s;
+    const T kap = (k == N / 2) ? a_zero<T>() : kscale * a_int<T>(sk) * s;
     x[q] = mk<T>(-kap * x[q].y, kap * x[q].x);
+  }
+}
+
+// The exponential filter in the spectrum: Z[k] *= s filt[|signed k|] (the
+// table in the storage type T, read through the read-only path).
+template <typename T, typename A, int R>
+__device__ __forceinline__ void warp_filter(c2_t<A> (&x)[R], int N, int lane, const T* __restrict__ filt, A s) {
+  const int k1 = (int)(__brev((unsigned)lane) >> 27);
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    const int k = brev_const<R>(q) + R * k1;
+    const int an = k <= N / 2 ? k : N - k;
+    const A f = to_arith<A, T>(__ldg(filt + an)) * s;
+    x[q] = mk<A>(f * x[q].x, f * x[q].y);
   }
 }
 
@@ -152,22 +181,28 @@ __device__ __forceinline__ T epilogue(const RowPass<T>& a, long o, T v) {
   return v;
 }
 
-template <typename T>
-__device__ __forceinline__ void stage_tw(c2_t<T>* tws, const RowPass<T>& a, int N, int logN) {
-  for (int t = threadIdx.x; t < N / 2; t += blockDim.x) tws[t] = a.tw[t << (a.logNtw - logN)];
+// The half twiddle table of an N-point transform in the arithmetic type A.
+template <typename T, typename A>
+__device__ __forceinline__ void stage_tw(c2_t<A>* tws, const RowPass<T>& a, int N, int logN) {
+  for (int t = threadIdx.x; t < N / 2; t += blockDim.x) {
+    const c2_t<T> w = a.tw[t << (a.logNtw - logN)];
+    tws[t] = mk<A>(to_arith<A, T>(w.x), to_arith<A, T>(w.y));
+  }
 }
 
 }  // namespace
 
-// x-rows: rows r (of a [rows][N] array), row m = r / Ny for the boundary rows
-template <typename T, int R>
+// x-rows: rows r (of a [rows][N] array), row m = r / Ny for the boundary
+// rows.  T: the storage type; A: the arithmetic type of the transform (T
+// itself for FP32, double-float for FP64 data).
+template <typename T, typename A, int R>
 __global__ void __launch_bounds__(256) k_xderiv_warp(RowPass<T> a) {
   pdl_enter();
-  using c2 = c2_t<T>;
+  using c2 = c2_t<A>;
   extern __shared__ __align__(16) unsigned char smraw[];
   c2* tws = reinterpret_cast<c2*>(smraw);
   const int N = 32 * R;
-  stage_tw<T>(tws, a, N, a.logNin);
+  stage_tw<T, A>(tws, a, N, a.logNin);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const long pair = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -178,21 +213,24 @@ __global__ void __launch_bounds__(256) k_xderiv_warp(RowPass<T> a) {
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     const int j = lane + 32 * q;
-    x[q] = mk<T>(a.in[r0 * N + j], has1 ? a.in[r1 * N + j] : T(0));
+    x[q] = mk<A>(to_arith<A, T>(a.in[r0 * N + j]), has1 ? to_arith<A, T>(a.in[r1 * N + j]) : a_zero<A>());
   }
-  warp_fft_forward<T, R>(x, tws, N, lane);
-  warp_deriv<T, R>(x, N, lane, a.kscale, a.scale / T(N));
-  warp_fft_inverse<T, R>(x, tws, N, lane);
+  warp_fft_forward<A, R>(x, tws, N, lane);
+  if (a.op == XOP_FILTER)
+    warp_filter<T, A, R>(x, N, lane, a.filt, to_arith<A, T>(a.scale / T(N)));
+  else
+    warp_deriv<A, R>(x, N, lane, to_arith<A, T>(a.kscale), to_arith<A, T>(a.scale / T(N)));
+  warp_fft_inverse<A, R>(x, tws, N, lane);
   const bool z0 = a.skip_bc && ((r0 / a.Ny) == 0 || (r0 / a.Ny) == a.M1 - 1);
   const bool z1 = a.skip_bc && ((r1 / a.Ny) == 0 || (r1 / a.Ny) == a.M1 - 1);
 #pragma unroll
   for (int q = 0; q < R; ++q) {
     const int j = lane + 32 * q;
     const long o0 = r0 * N + j;
-    a.out[o0] = epilogue<T>(a, o0, z0 ? T(0) : x[q].x);
+    a.out[o0] = epilogue<T>(a, o0, z0 ? T(0) : from_arith<T, A>(x[q].x));
     if (has1) {
       const long o1 = r1 * N + j;
-      a.out[o1] = epilogue<T>(a, o1, z1 ? T(0) : x[q].y);
+      a.out[o1] = epilogue<T>(a, o1, z1 ? T(0) : from_arith<T, A>(x[q].y));
     }
   }
 }
@@ -200,15 +238,15 @@ __global__ void __launch_bounds__(256) k_xderiv_warp(RowPass<T> a) {
 // y-lines of a [planes][N][Nxl] array: CTA (blockIdx.x, blockIdx.y) takes
 // columns 16 blockIdx.x .. + 15 of plane blockIdx.y through a shared tile
 // [N][17]; warp w transforms columns 2w and 2w + 1.
-template <typename T, int R>
+template <typename T, typename A, int R>
 __global__ void __launch_bounds__(256) k_yderiv_warp(RowPass<T> a) {
   pdl_enter();
-  using c2 = c2_t<T>;
+  using c2 = c2_t<A>;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = 32 * R;
   c2* tws = reinterpret_cast<c2*>(smraw);
   T* tile = reinterpret_cast<T*>(tws + N / 2);          // [N][17]
-  stage_tw<T>(tws, a, N, a.logNin);
+  stage_tw<T, A>(tws, a, N, a.logNin);
   const int plane = blockIdx.y, jx0 = blockIdx.x * 16, Nxl = a.Nxl;
   const long base = (long)plane * N * Nxl;
   for (int i = threadIdx.x; i < N * 16; i += blockDim.x) {
@@ -222,16 +260,19 @@ __global__ void __launch_bounds__(256) k_yderiv_warp(RowPass<T> a) {
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const int j = lane + 32 * q;
-      x[q] = mk<T>(tile[j * 17 + 2 * w], tile[j * 17 + 2 * w + 1]);
+      x[q] = mk<A>(to_arith<A, T>(tile[j * 17 + 2 * w]), to_arith<A, T>(tile[j * 17 + 2 * w + 1]));
     }
-    warp_fft_forward<T, R>(x, tws, N, lane);
-    warp_deriv<T, R>(x, N, lane, a.kscale, a.scale / T(N));
-    warp_fft_inverse<T, R>(x, tws, N, lane);
+    warp_fft_forward<A, R>(x, tws, N, lane);
+    if (a.op == XOP_FILTER)
+      warp_filter<T, A, R>(x, N, lane, a.filt, to_arith<A, T>(a.scale / T(N)));
+    else
+      warp_deriv<A, R>(x, N, lane, to_arith<A, T>(a.kscale), to_arith<A, T>(a.scale / T(N)));
+    warp_fft_inverse<A, R>(x, tws, N, lane);
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const int j = lane + 32 * q;
-      tile[j * 17 + 2 * w] = x[q].x;
-      tile[j * 17 + 2 * w + 1] = x[q].y;
+      tile[j * 17 + 2 * w] = from_arith<T, A>(x[q].x);
+      tile[j * 17 + 2 * w + 1] = from_arith<T, A>(x[q].y);
     }
   }
   __syncthreads();
@@ -244,58 +285,64 @@ __global__ void __launch_bounds__(256) k_yderiv_warp(RowPass<T> a) {
   }
 }
 
-// Whether the warp passes take this row pass: FP32, a derivative with equal
-// in/out lengths of 32..1024 points, a plain epilogue (store, add or
-// residual), no Nyquist coefficient and no second transform, and enough lines
-// to fill the GPU (x-rows: >= 512; y-lines: >= 16 x-columns).
+// Whether the warp passes take this row pass: a derivative or the filter with equal in/out
+// lengths of 32..1024 points (FP32) or 32..256 points (FP64 data, option
+// df64: double-float arithmetic), a plain epilogue (store, add or residual),
+// no Nyquist coefficient and no second transform, and enough lines to fill
+// the GPU (x-rows: >= 512; y-lines: >= 16 x-columns).
 template <typename T>
 bool warp_deriv_fits(const RowPass<T>& a) {
-  // FP32 only: at FP64 the transform is bound by the FP64 rate, and the
-  // register-resident form (up to 186 registers a thread) measured slower
-  // than the CTA-per-line passes (FP64 operator apply on 256 x 256 x 16:
-  // 692 against 599 us)
-  if (sizeof(T) != 4) return false;
-  const int maxN = 1024;
-  if (a.op != XOP_DERIV || a.Nin != a.Nout || a.Nin < 32 || a.Nin > maxN) return false;
+  // FP64 in FP64 arithmetic is bound by the FP64 rate: the register-resident
+  // form (up to 186 registers a thread) measured slower than the CTA-per-line
+  // passes (FP64 operator apply on 256 x 256 x 16: 692 against 599 us), so
+  // FP64 data take the warp passes only in double-float
+  const int maxN = sizeof(T) == 4 ? 1024 : 256;
+  if (sizeof(T) != 4 && !a.df) return false;
+  if (!(a.op == XOP_DERIV || (a.op == XOP_FILTER && a.filt))) return false;
+  if (a.Nin != a.Nout || a.Nin < 32 || a.Nin > maxN) return false;
   if (a.nyq || a.out2 || !a.write_out) return false;
   if (a.epi != EPI_STORE && a.epi != EPI_ADD && a.epi != EPI_RESID) return false;
   if (a.ylines) return a.Nxl >= 16 && a.nrows >= 32 * 16;
   return a.nrows >= 512;
 }
 
-template <typename T, int R>
+template <typename T, typename A, int R>
 static cudaError_t launch_r(const RowPass<T>& a, cudaStream_t s) {
-  using c2 = c2_t<T>;
   const int N = 32 * R;
   cudaError_t e;
   if (a.ylines) {
-    const size_t smem = (size_t)(N / 2) * sizeof(c2) + (size_t)N * 17 * sizeof(T);
-    if ((e = ensure_dyn_smem((const void*)k_yderiv_warp<T, R>, smem)) != cudaSuccess) return e;
+    const size_t smem = (size_t)(N / 2) * sizeof(c2_t<A>) + (size_t)N * 17 * sizeof(T);
+    if ((e = ensure_dyn_smem((const void*)k_yderiv_warp<T, A, R>, smem)) != cudaSuccess) return e;
     const int planes = a.nrows / a.Nxl;
     const dim3 grid((a.Nxl + 15) / 16, planes);
-    return launch_k(k_yderiv_warp<T, R>, grid, dim3(256), smem, s, a);
+    return launch_k(k_yderiv_warp<T, A, R>, grid, dim3(256), smem, s, a);
   } else {
-    const size_t smem = (size_t)(N / 2) * sizeof(c2);
+    const size_t smem = (size_t)(N / 2) * sizeof(c2_t<A>);
     const long pairs = ((long)a.nrows + 1) / 2;
-    return launch_k(k_xderiv_warp<T, R>, dim3((unsigned)((pairs + 7) / 8)), dim3(256), smem, s, a);
+    return launch_k(k_xderiv_warp<T, A, R>, dim3((unsigned)((pairs + 7) / 8)), dim3(256), smem, s, a);
   }
 }
 
 template <typename T>
 cudaError_t launch_deriv_warp(const RowPass<T>& a, cudaStream_t s) {
   if constexpr (sizeof(T) != 4) {
-    return cudaErrorInvalidValue;
+    switch (a.Nin) {
+      case 32: return launch_r<T, ff, 1>(a, s);
+      case 64: return launch_r<T, ff, 2>(a, s);
+      case 128: return launch_r<T, ff, 4>(a, s);
+      case 256: return launch_r<T, ff, 8>(a, s);
+      default: return cudaErrorInvalidValue;
+    }
   } else {
-  switch (a.Nin) {
-    case 32: return launch_r<T, 1>(a, s);
-    case 64: return launch_r<T, 2>(a, s);
-    case 128: return launch_r<T, 4>(a, s);
-    case 256: return launch_r<T, 8>(a, s);
-    case 512: return launch_r<T, 16>(a, s);
-    default: break;
-  }
-  if (a.Nin == 1024) return launch_r<T, 32>(a, s);
-  return cudaErrorInvalidValue;
+    switch (a.Nin) {
+      case 32: return launch_r<T, T, 1>(a, s);
+      case 64: return launch_r<T, T, 2>(a, s);
+      case 128: return launch_r<T, T, 4>(a, s);
+      case 256: return launch_r<T, T, 8>(a, s);
+      case 512: return launch_r<T, T, 16>(a, s);
+      case 1024: return launch_r<T, T, 32>(a, s);
+      default: return cudaErrorInvalidValue;
+    }
   }
 }
 
