@@ -154,7 +154,12 @@ static cudaError_t launch_op_cols_m(const LevelView<T>& L, int g, size_t smem, c
 
 template <typename T>
 cudaError_t launch_op_cols(const LevelView<T>& L, const T* p, const T* Px, const T* Py, T* Gx,
-                           T* Gy, T* part, cudaStream_t s) {
+                           T* Gy, T* part, cudaStream_t s, int df) {
+  if constexpr (sizeof(T) == 8) {
+    if (df && L.ncols >= kTpcMinCols && col_df_fits(L.M1))
+      return launch_op_cols_df(L, p, Px, Py, Gx, Gy, part, s);
+  }
+  (void)df;
   const size_t smem = opcols_smem<T>(L.M1);
   if (L.ncols >= kTpcMinCols && L.M1 <= 17) {
     // many columns: one thread per column, coalesced sigma rows
@@ -218,7 +223,12 @@ cudaError_t launch_smooth_cols(const LevelView<T>& L, const T* r, const T* rhoX,
 
 template <typename T>
 cudaError_t launch_col_matrix(const T* M, int Mo, int Mi, const T* in, T* out, int ncols,
-                              int accumulate, cudaStream_t s) {
+                              int accumulate, cudaStream_t s, int df) {
+  if constexpr (sizeof(T) == 8) {
+    if (df && ncols >= kTpcMinCols && Mo <= kMaxM1 && col_df_fits(Mi))
+      return launch_col_matrix_df(M, Mo, Mi, in, out, ncols, accumulate, s);
+  }
+  (void)df;
   if (ncols >= kTpcMinCols && Mo <= kMaxM1) {
     // many columns (3D levels): one thread per column
     const dim3 G((unsigned)((ncols + 127) / 128)), B(128);
@@ -256,14 +266,14 @@ cudaError_t launch_block_inverse_multi(const BlockInvMulti<T>& m, int* flag, cud
 
 #define WT_INST(T)                                                                              \
   template cudaError_t launch_op_cols<T>(const LevelView<T>&, const T*, const T*, const T*, T*,  \
-                                         T*, T*, cudaStream_t);                                 \
+                                         T*, T*, cudaStream_t, int);                            \
   template cudaError_t launch_smooth_cols<T>(const LevelView<T>&, const T*, const T*, const T*,  \
                                              const T*, const T*, int, T*, T, int, int,          \
                                              cudaStream_t);                                      \
   template cudaError_t launch_op_cols_T<T>(const LevelView<T>&, const T*, const T*, T*, T*,      \
                                            cudaStream_t);                                        \
   template cudaError_t launch_col_matrix<T>(const T*, int, int, const T*, T*, int, int,         \
-                                            cudaStream_t);                                      \
+                                            cudaStream_t, int);                                 \
   template cudaError_t launch_block_inverse_multi<T>(const BlockInvMulti<T>&, int*, cudaStream_t);
 WT_INST(float)
 WT_INST(double)

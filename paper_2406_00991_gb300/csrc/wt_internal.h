@@ -201,10 +201,11 @@ struct MetricMulti {
 };
 cudaError_t launch_metric_multi(const MetricMulti& m, cudaStream_t s);
 
-// Column kernels (wt_col.cu).
+// Column kernels (wt_col.cu).  df != 0: FP64 levels of many columns run the
+// double-float kernels of wt_dfcol.cu where they fit.
 template <typename T>
 cudaError_t launch_op_cols(const LevelView<T>& L, const T* p, const T* Px, const T* Py,
-                           T* Gx, T* Gy, T* part, cudaStream_t s);
+                           T* Gx, T* Gy, T* part, cudaStream_t s, int df = 0);
 // Column part of A^T (2D only): Mx = mu_x, part as in opcolsT_body.
 template <typename T>
 cudaError_t launch_op_cols_T(const LevelView<T>& L, const T* lam, const T* Dlam, T* Mx, T* part,
@@ -217,7 +218,14 @@ cudaError_t launch_smooth_cols(const LevelView<T>& L, const T* r, const T* rhoX,
 // out[mo][c] = sum_mi M[mo][mi] in[mi][c] for c < ncols (sigma transfers, filter)
 template <typename T>
 cudaError_t launch_col_matrix(const T* M, int Mo, int Mi, const T* in, T* out, int ncols,
-                              int accumulate, cudaStream_t s);
+                              int accumulate, cudaStream_t s, int df = 0);
+// Double-float FP64 column kernels (wt_dfcol.cu) for column lengths 5, 9, 13,
+// 17 (col_df_fits).
+bool col_df_fits(int M1);
+cudaError_t launch_op_cols_df(const LevelView<double>& L, const double* p, const double* Px, const double* Py,
+                              double* Gx, double* Gy, double* part, cudaStream_t s);
+cudaError_t launch_col_matrix_df(const double* M, int Mo, int Mi, const double* in, double* out, int ncols,
+                                 int accumulate, cudaStream_t s);
 // The block inverses of several levels in one launch: the (column, class)
 // tasks of level l are start[l] .. start[l+1]-1, one warp each.
 template <typename T>

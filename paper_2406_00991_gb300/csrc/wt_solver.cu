@@ -211,7 +211,7 @@ void apply_op(wt_tank& t, int l, const T* x, T* out, const T* f, bool nyq, bool 
   }
   if (L.Ny == 1) {
     if (!ex.have_dx) run_rowpass(t, xpass<T>(t, x, L.t1, L.M1, L.Nx, L.Nx, XOP_DERIV));
-    WT_LAUNCH(t, K_OPCOLS, sizeof(T) * (4.0 * L.n + 7.0 * L.ncols), 6.0 * L.M1 * L.M1 * L.ncols, launch_op_cols<T>(V, x, L.t1, nullptr, L.t2, nullptr, L.t3, s));
+    WT_LAUNCH(t, K_OPCOLS, sizeof(T) * (4.0 * L.n + 7.0 * L.ncols), 6.0 * L.M1 * L.M1 * L.ncols, launch_op_cols<T>(V, x, L.t1, nullptr, L.t2, nullptr, L.t3, s, t.opt.df64));
     RowPass<T> a = xpass<T>(t, L.t2, out, L.M1, L.Nx, L.Nx, XOP_DERIV);
     a.skip_bc = 1;
     a.Ny = 1;
@@ -225,7 +225,7 @@ void apply_op(wt_tank& t, int l, const T* x, T* out, const T* f, bool nyq, bool 
   } else {
     run_rowpass(t, xpass<T>(t, x, L.t1, L.M1 * L.Ny, L.Nx, L.Nx, XOP_DERIV));
     run_rowpass(t, ypass<T>(t, x, L.t4, L.M1, L.Nx, L.Ny, L.Ny, XOP_DERIV));
-    WT_LAUNCH(t, K_OPCOLS, sizeof(T) * (6.0 * L.n + 12.0 * L.ncols), 8.0 * L.M1 * L.M1 * L.ncols, launch_op_cols<T>(V, x, L.t1, L.t4, L.t2, L.t5, L.t3, s));
+    WT_LAUNCH(t, K_OPCOLS, sizeof(T) * (6.0 * L.n + 12.0 * L.ncols), 8.0 * L.M1 * L.M1 * L.ncols, launch_op_cols<T>(V, x, L.t1, L.t4, L.t2, L.t5, L.t3, s, t.opt.df64));
     RowPass<T> a = xpass<T>(t, L.t2, L.t6, L.M1 * L.Ny, L.Nx, L.Nx, XOP_DERIV);
     a.skip_bc = 1;
     a.Ny = L.Ny;
