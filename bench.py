@@ -48,6 +48,7 @@ METRIC = "RK4 DOF-updates/s (mixed FP32/FP64 p-MG Poisson solves at 1e-10 residu
 OP_TRAFFIC_2D = 154368 + 259072 + 256512
 OP_TRAFFIC_3D = 4488960 + 4491776 + 16568320 + 8944640 + 8947712
 UNIT = "DOF-updates/s"
+SMOOTHERS = {0: "damped block-Jacobi", 1: "mean-depth spectral", 2: "block-Jacobi then mean-depth spectral"}
 STAGES = 5
 
 
@@ -300,10 +301,16 @@ def run_ours(args):
                              "solver": ("mixed: FP64 flexible GMRES(30) preconditioned by the FP32 p-multigrid V-cycle"
                                         if tuned["mode"] == w.WT_MIXED else
                                         "refine: FP64 iterative refinement around FP32 FGMRES + FP32 V-cycle"),
+                             "smoother": SMOOTHERS.get(tuned["smoother"], "?") + (
+                                 " (spectral on levels of >= %d unknowns, block-Jacobi below)" % tuned["spectral_min"]
+                                 if tuned["smoother"] and tuned["spectral_min"] else ""),
                              "autotuned": {"omega": tuned["omega"], "nu1": tuned["nu1"], "nu2": tuned["nu2"],
                                            "coarsest_max": tuned["coarsest_max"], "mode": tuned["mode"],
                                            "tail_max": tuned["tail_max"], "tail_cluster": tuned["tail_cluster"],
-                                           "vcycle_grid": tuned["vcycle_grid"],
+                                           "vcycle_grid": tuned["vcycle_grid"], "smoother": tuned["smoother"],
+                                           "omega_s": tuned["omega_s"], "spectral_min": tuned["spectral_min"],
+                                           "cycle": tuned["cycle"], "inner_tol": tuned["inner_tol"],
+                                           "pdl": tuned["pdl"],
                                            "tuned_ms_per_step": tuned_ms, "default_ms_per_step": entry_ms}}),
         "solves_per_s": solves_s,
         "krylov_iterations_per_solve": iters / max(1, solves),

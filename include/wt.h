@@ -88,9 +88,8 @@ typedef struct wt_options {
                         through the Chebyshev truncation as printed          */
   int tail_max;      /* levels with at most this many unknowns run in one
                         V-cycle launch of one CTA (or of the cluster that
-                        tail_cluster sets); 0: never, the default - graph
-                        replay of the multi-CTA levels is faster at the
-                        sizes measured so far                               */
+                        tail_cluster sets), smoothed by block-Jacobi; 0:
+                        never, the default (the autotuners try it)          */
   double inner_tol;  /* WT_REFINE: relative residual of each FP32 inner
                         solve (1e-5)                                         */
   int max_ir;        /* WT_REFINE: refinement steps per solve (30)           */
@@ -118,9 +117,10 @@ typedef struct wt_options {
                         problem (eta = 0, depth = min h) by horizontal
                         Fourier mode - the modes' (Nz+1)^2 inverses are
                         built once per bathymetry; 2 = a block-Jacobi sweep
-                        followed by a spectral sweep.  With 1 or 2 every
-                        level runs launch per phase (tail_max and
-                        vcycle_grid are not used)                           */
+                        followed by a spectral sweep.  With 1 or 2
+                        vcycle_grid is not used, and the levels at or below
+                        tail_max (if set) run the one-launch tail with
+                        block-Jacobi sweeps, the finer levels spectral ones */
   double omega_s;    /* damping of the spectral smoother (1.0)               */
   int warp_fft;      /* 1 (default): FP32 x- and y-derivative passes over
                         many lines (>= 512 x-rows, or y-lines of >= 16
@@ -142,6 +142,9 @@ typedef struct wt_options {
                         rate; the data stay FP64 in memory (measured operator
                         error 2e-15 of max |Ap| against 1e-15 in FP64).
                         0: FP64 arithmetic                                   */
+  int spectral_min;  /* smoother 1 or 2: levels with fewer unknowns than this
+                        smooth by block-Jacobi alone (their column blocks
+                        are built); 0 (default): every level spectral        */
 } wt_options;
 
 typedef struct wt_solve_info {

@@ -299,17 +299,20 @@ def coarse_solve(level, f):
 
 def vcycle(levels, l, x, f, nu1=2, nu2=2, smoother="jacobi", omega=0.4,
            bc_transfer="inject", omega_s=1.0, dref=None):
-    """Recursive V-cycle (Algorithm 1), level index l = 0 is the finest."""
+    """Recursive V-cycle (Algorithm 1), level index l = 0 is the finest.
+    smoother: one kind for every level, or a list of kinds by level index
+    (Algorithm 1 leaves the smoother of each level open)."""
     lev = levels[l]
     if l == len(levels) - 1:
         return coarse_solve(lev, f)
-    x = smooth(lev, x, f, nu1, smoother, omega, omega_s, dref)
+    kind = smoother[l] if isinstance(smoother, (list, tuple)) else smoother
+    x = smooth(lev, x, f, nu1, kind, omega, omega_s, dref)
     r = f - lev.apply(x)
     rc = restrict(lev.grid, levels[l + 1].grid, r, bc_transfer)
     ec = vcycle(levels, l + 1, np.zeros_like(rc), rc, nu1, nu2, smoother, omega, bc_transfer,
                 omega_s, dref)
     x = x + prolong(levels[l + 1].grid, lev.grid, ec)
-    x = smooth(lev, x, f, nu2, smoother, omega, omega_s, dref)
+    x = smooth(lev, x, f, nu2, kind, omega, omega_s, dref)
     return x
 
 

@@ -36,7 +36,8 @@ class wt_options(ctypes.Structure):
                 ("cycle", ctypes.c_int), ("smoother", ctypes.c_int), ("omega_s", ctypes.c_double),
                 ("warp_fft", ctypes.c_int),
                 ("pdl", ctypes.c_int),
-                ("df64", ctypes.c_int)]
+                ("df64", ctypes.c_int),
+                ("spectral_min", ctypes.c_int)]
 
 
 class wt_solve_info(ctypes.Structure):

@@ -444,6 +444,7 @@ int check_options(const wt_options& o) {
   if (o.warp_fft != 0 && o.warp_fft != 1) return fail(WT_EINVAL, "warp_fft must be 0 or 1");
   if (o.pdl != 0 && o.pdl != 1) return fail(WT_EINVAL, "pdl must be 0 or 1");
   if (o.df64 != 0 && o.df64 != 1) return fail(WT_EINVAL, "df64 must be 0 or 1");
+  if (o.spectral_min < 0) return fail(WT_EINVAL, "spectral_min must be >= 0");
   if ((o.filter != 0 && o.filter != 1) || (o.linear != 0 && o.linear != 1) ||
       (o.bc_transfer != 0 && o.bc_transfer != 1))
     return fail(WT_EINVAL, "filter, linear, bc_transfer are 0 or 1");
@@ -729,6 +730,7 @@ int wt_default_options(wt_options* o) {
   o->warp_fft = 1;
   o->pdl = 1;
   o->df64 = 1;
+  o->spectral_min = 0;
   return WT_OK;
 }
 

@@ -141,15 +141,27 @@ void setup_geometry(wt_tank& t, const double* ea, const double* eb, int precisio
 
 void setup_blocks(wt_tank& t, int precision, bool blocks, bool coarse, cudaStream_t s) {
   const int nl = (int)t.L64.size();
-  // the spectral smoother alone (smoother = 1) needs no column-block inverses
-  if (blocks && nl > 1 && t.opt.smoother != 1) {
-    // every level's column blocks in one launch
+  // the spectral smoother alone (smoother = 1) needs column-block inverses
+  // only on the levels that smooth by block-Jacobi (the one-launch tail and
+  // the levels below spectral_min unknowns), if any
+  int l0 = 0;
+  if (t.opt.smoother == 1) {
+    l0 = nl - 1;
+    for (int l = 0; l < nl - 1; ++l)
+      if ((t.opt.tail_max > 0 && t.L64[l].n <= t.opt.tail_max) || t.L64[l].n < t.opt.spectral_min) {
+        l0 = l;
+        break;
+      }
+  }
+  if (blocks && l0 < nl - 1) {
+    // the levels' column blocks in one launch
     auto fill = [&](auto& lev, auto tw, auto& m, double wbytes) {
       double bytes = 0.0, flops = 0.0;
-      m.nlev = nl - 1;
+      m.nlev = nl - 1 - l0;
       m.start[0] = 0;
-      for (int l = 0; l < nl - 1; ++l) {
-        auto& L = lev[l];
+      for (int i = 0; i < m.nlev; ++i) {
+        auto& L = lev[l0 + i];
+        const int l = i;
         m.L[l] = L.view(tw, t.logNtw, t.L);
         m.Binv[l] = L.Binv;
         m.nclass[l] = L.nclass;
@@ -303,7 +315,8 @@ static void smooth_bj(wt_tank& t, int l, T* x, const T* f, bool first, bool f_ha
 template <typename T>
 static void smooth(wt_tank& t, int l, T* x, const T* f, bool first, bool f_has_nyq, bool tr,
                    bool have_dx = false) {
-  const int kind = t.opt.smoother;
+  // levels below spectral_min unknowns smooth by block-Jacobi alone
+  const int kind = levels<T>(t)[l].n < t.opt.spectral_min ? 0 : t.opt.smoother;
   if (kind == 1) {
     spectral_sweep<T>(t, l, x, f, first, tr, have_dx);
     return;
@@ -394,9 +407,11 @@ template <> TailLevel<float>* tail_desc<float>(wt_tank& t) { return t.tl32; }
 
 // First level handled by the single-launch tail of the V-cycle (one CTA, or
 // one thread-block cluster with tail_cluster >= 2); -1: none.
+// The tail smooths by block-Jacobi; with the spectral smoother (1 or 2) the
+// levels above it keep the spectral sweeps.
 template <typename T>
 static int tail_level(wt_tank& t, bool tr) {
-  if (t.opt.tail_max <= 0 || tr || t.opt.smoother != 0) return -1;
+  if (t.opt.tail_max <= 0 || tr) return -1;
   auto& lev = levels<T>(t);
   for (size_t l = 0; l < lev.size(); ++l)
     if (lev[l].n <= t.opt.tail_max) return (int)l;

@@ -29,12 +29,24 @@ double now_ms() {
 }
 
 // Second stage on the winner: the refinement form with inner tolerances
-// 1e-4 and 1e-3, the spectral smoothers, the full-multigrid cycle instead of
+// 1e-4 and 1e-3, the spectral smoothers (on every level, or on the finest
+// one to three levels), the full-multigrid cycle instead of
 // the V-cycle, then the launch schedule of the V-cycles - the levels below
-// tail_max unknowns in one launch (one CTA, or a cluster of 16 CTAs), or the
-// whole cycle as one cooperative launch - each kept only where it is faster.
+// tail_max unknowns in one launch (one CTA, or a cluster of 16 CTAs), or (with
+// block-Jacobi alone) the whole cycle as one cooperative launch - each kept
+// only where it is faster.
+// Unknowns of each level of the tank's hierarchy, finest first.
+std::vector<long> level_sizes(const wt_tank* t) {
+  int nl = 0;
+  int dims[3 * 16] = {0};
+  std::vector<long> n;
+  if (wt_get_levels(t, &nl, dims) != WT_OK) return n;
+  for (int l = 0; l < nl; ++l) n.push_back((long)dims[3 * l] * dims[3 * l + 1] * (dims[3 * l + 2] + 1));
+  return n;
+}
+
 template <typename F>
-void refine_schedule(wt_options& bo, double& bms, F&& measure) {
+void refine_schedule(wt_options& bo, double& bms, F&& measure, const std::vector<long>& sizes) {
   if (bo.mode != WT_FP64) {
     // the literal refinement form with looser inner solves: each refinement
     // then costs fewer FP32 iterations, and the FP64 operator (the costly
@@ -73,6 +85,20 @@ void refine_schedule(wt_options& bo, double& bms, F&& measure) {
         }
       }
   }
+  if (bo.smoother != 0) {
+    // spectral sweeps on the finest one, two or three levels only,
+    // block-Jacobi below
+    const wt_options base = bo;
+    for (size_t k = 1; k <= 3 && k + 1 < sizes.size(); ++k) {
+      wt_options o = base;
+      o.spectral_min = (int)std::min<long>(sizes[k] + 1, 1L << 30);
+      const double ms = measure(o, bms);
+      if (ms > 0 && ms < bms) {
+        bms = ms;
+        bo = o;
+      }
+    }
+  }
   {
     // the full-multigrid cycle (Algorithm 2) as the preconditioner
     wt_options o = bo;
@@ -86,7 +112,8 @@ void refine_schedule(wt_options& bo, double& bms, F&& measure) {
       bo = o;
     }
   }
-  if (bo.smoother != 0) return;             // the one-launch schedules smooth by block-Jacobi only
+  // the levels at or below tail_max unknowns in one launch (block-Jacobi
+  // inside it; with the spectral smoother the finer levels keep theirs)
   const wt_options base = bo;
   const int tails[] = {2048, 8192};
   const int clusters[] = {0, 16};
@@ -102,6 +129,7 @@ void refine_schedule(wt_options& bo, double& bms, F&& measure) {
         bo = o;
       }
     }
+  if (base.smoother != 0) return;          // the cooperative cycle smooths by block-Jacobi only
   wt_options o = base;
   o.vcycle_grid = 1;
   o.tail_max = 0;
@@ -192,7 +220,7 @@ extern "C" int wt_autotune(wt_tank* t, const double* eta_a, const double* eta_b,
             bo = o;
           }
         }
-  if (bms < 1e300) refine_schedule(bo, bms, measure);
+  if (bms < 1e300) refine_schedule(bo, bms, measure, level_sizes(t));
   if (bms >= 1e300) {
     wt_set_options(t, &entry);
     return wt::set_error(WT_ENOCONV, "wt_autotune: no candidate reached the tolerance");
@@ -275,7 +303,7 @@ extern "C" int wt_autotune_step(wt_tank* t, double dt, int reps, wt_options* bes
             bo = o;
           }
         }
-  if (bms < 1e300) refine_schedule(bo, bms, measure);
+  if (bms < 1e300) refine_schedule(bo, bms, measure, level_sizes(t));
   if (bms >= 1e300) {
     wt_set_options(t, &entry);
     restore();

@@ -106,3 +106,50 @@ def test_spectral_tables_follow_the_bathymetry(wt):
     with pytest.raises(wt.WtError) as e:
         T.set_options(smoother=3)
     assert e.value.code == wt.WT_EINVAL
+
+
+@pytest.mark.parametrize("Nx,Ny,Nz,tail,cluster", [(64, 64, 16, 4352, 0), (64, 64, 16, 4352, 8),
+                                                    (32, 32, 12, 1000, 0), (1024, 1, 24, 2048, 0)])
+def test_spectral_vcycle_with_tail_parity(wt, Nx, Ny, Nz, tail, cluster):
+    # spectral smoother on the levels above tail_max unknowns, the one-launch
+    # tail (one CTA, or a cluster) with block-Jacobi sweeps on the rest:
+    # against the oracle's V-cycle with the same smoother kind by level
+    L = 2 * math.pi
+    g, h, ea, eb = curved(Nx, Ny, Nz, L)
+    r = np.random.default_rng(6).standard_normal(g.shape)
+    levels = pmg.build_levels(Nx, Ny, Nz, L, h, ea, eb, coarsest_max=64)
+    sizes = [lv.grid.Nx * lv.grid.Ny * (lv.grid.Nz + 1) for lv in levels]
+    kinds = ["spectral" if n > tail else "jacobi" for n in sizes]
+    assert "jacobi" in kinds[:-1] and kinds[0] == "spectral"
+    ref = pmg.vcycle(levels, 0, np.zeros(g.shape), r, 2, 2, kinds, 0.4, "inject", 1.0, float(h.min()))
+    T = wt.Tank(Nx, Ny, Nz, L, h, smoother=1, tail_max=tail, tail_cluster=cluster)
+    scale = np.abs(ref).max()
+    got = T.precondition(ea, eb, r, wt.WT_FP64)
+    assert np.abs(got - ref).max() <= 1e-9 * scale
+    got32 = T.precondition(ea, eb, r, wt.WT_FP32)
+    assert np.abs(got32 - ref).max() <= 5e-3 * scale
+    # and a mixed solve to the method's tolerance in the oracle's operator
+    T.set_options(mode=wt.WT_MIXED, tol=1e-10, max_it=300, nu1=1, nu2=1)
+    p, info = T.poisson_solve(ea, eb, r)
+    res = r - op.apply_A(g, op.Geometry(g, h, ea), op.Geometry(g, h, eb), p)
+    assert np.linalg.norm(res) <= 1.5e-9 * np.linalg.norm(r)
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+@pytest.mark.parametrize("Nx,Ny,Nz,smin", [(64, 64, 16, 8192), (1024, 1, 24, 3000)])
+def test_spectral_min_parity(wt, Nx, Ny, Nz, smin, kind):
+    # spectral sweeps (kind 1, or block-Jacobi then spectral, kind 2) on the
+    # levels of at least spectral_min unknowns, block-Jacobi below, launch
+    # per phase: against the oracle's V-cycle with those kinds by level
+    L = 2 * math.pi
+    g, h, ea, eb = curved(Nx, Ny, Nz, L)
+    r = np.random.default_rng(7).standard_normal(g.shape)
+    levels = pmg.build_levels(Nx, Ny, Nz, L, h, ea, eb, coarsest_max=64)
+    sizes = [lv.grid.Nx * lv.grid.Ny * (lv.grid.Nz + 1) for lv in levels]
+    kinds = [KINDS[kind] if n >= smin else "jacobi" for n in sizes]
+    assert "jacobi" in kinds[:-1] and kinds[0] == KINDS[kind]
+    ref = pmg.vcycle(levels, 0, np.zeros(g.shape), r, 2, 2, kinds, 0.4, "inject", 1.0, float(h.min()))
+    T = wt.Tank(Nx, Ny, Nz, L, h, smoother=kind, spectral_min=smin)
+    scale = np.abs(ref).max()
+    assert np.abs(T.precondition(ea, eb, r, wt.WT_FP64) - ref).max() <= 1e-9 * scale
+    assert np.abs(T.precondition(ea, eb, r, wt.WT_FP32) - ref).max() <= 5e-3 * scale

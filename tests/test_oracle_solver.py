@@ -178,3 +178,26 @@ def test_spectral_smoothers_solve_to_dense_lu(smoother):
     _, its_bj, _, _ = krylov.solve_pmg(32, 1, 10, g.L, h, ea, eb, b, tol=1e-13, coarsest_max=64, nu1=1, nu2=1)
     if smoother == "jacobi+spectral":
         assert its < its_bj
+
+
+def test_vcycle_smoother_by_level_list():
+    # a list of smoother kinds by level: the same kind everywhere reproduces
+    # the single-kind cycle, and a mixed list differs from both pure ones
+    N, Nz, L = 16, 8, 2 * math.pi
+    g = op.Grid(N, N, Nz, L)
+    X, Y = np.meshgrid(g.x, g.y, indexing="xy")
+    h = 1.0 - 0.2 * np.exp(-((X - 3) ** 2 + (Y - 3) ** 2))
+    ea = 0.05 * np.cos(X)
+    levels = pmg.build_levels(N, N, Nz, L, h, ea, ea, coarsest_max=64)
+    r = np.random.default_rng(1).standard_normal(g.shape)
+    nl = len(levels)
+    dref = float(h.min())
+    for kind in ("jacobi", "spectral"):
+        a = pmg.vcycle(levels, 0, np.zeros(g.shape), r, 1, 1, kind, 0.4, "inject", 1.0, dref)
+        b = pmg.vcycle(levels, 0, np.zeros(g.shape), r, 1, 1, [kind] * nl, 0.4, "inject", 1.0, dref)
+        assert np.array_equal(a, b)
+    mixed = pmg.vcycle(levels, 0, np.zeros(g.shape), r, 1, 1, ["spectral"] + ["jacobi"] * (nl - 1), 0.4,
+                       "inject", 1.0, dref)
+    for kind in ("jacobi", "spectral"):
+        pure = pmg.vcycle(levels, 0, np.zeros(g.shape), r, 1, 1, kind, 0.4, "inject", 1.0, dref)
+        assert np.abs(mixed - pure).max() > 1e-6 * np.abs(pure).max()
