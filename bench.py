@@ -453,7 +453,7 @@ def bench_sea3d(w, torch, args):
     # form that applies it once per refinement wins
     Tb, ms_bj, its_bj = run(omega=0.6)
     Tb.close()
-    T, ms, its = run(smoother=1, nu1=1, nu2=1, mode=w.WT_REFINE, inner_tol=1e-4)
+    T, ms, its = run(smoother=1, nu1=1, nu2=1, mode=w.WT_REFINE, inner_tol=1e-4, spectral_min=20000)
     eta_now = np.ascontiguousarray(T.get_state()[0])
     op_ms, op_launches = T.time_kernel(eta_now, eta_now, w.WT_TIME_OPERATOR, w.WT_FP32, reps=100)
     vc_ms, vc_launches = T.time_kernel(eta_now, eta_now, w.WT_TIME_VCYCLE, w.WT_FP32, reps=10)
@@ -462,7 +462,8 @@ def bench_sea3d(w, torch, args):
     dof1 = N * N * (Nz + 1)
     ach = 8.0 * dof1 / (op_ms / 1e3) / 1e9
     return {"workload": "3D directional JONSWAP sea, 256 x 256 x 16, L = 64, 4096 components, filter on, "
-                        "FP64 refinement (FP32 GMRES + FP32 V-cycle to 1e-4) to 1e-10, mean-depth spectral smoother V(1,1)",
+                        "FP64 refinement (FP32 GMRES + FP32 V-cycle to 1e-4) to 1e-10, mean-depth spectral smoother V(1,1) "
+                        "on the levels of >= 20,000 unknowns (block-Jacobi below), FP64 passes in double-float",
             "metric": "RK4 DOF-updates/s", "value": STAGES * dof1 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
             "solves_per_s": STAGES / (ms / 1e3),
             "krylov_iterations_per_solve": its, "steps": K,

@@ -66,38 +66,30 @@ void refine_schedule(wt_options& bo, double& bms, F&& measure, const std::vector
   }
   {
     // the mean-depth spectral smoother, alone or after block-Jacobi, with
-    // one or two sweeps each way
+    // one or two sweeps each way, on every level or on the finest one, two
+    // or three levels only (block-Jacobi below: spectral_min)
     const wt_options base = bo;
     const int kinds[] = {1, 2};
     const int nus[] = {1, 2};
+    std::vector<int> mins = {0};
+    for (size_t k = 1; k <= 3 && k + 1 < sizes.size(); ++k)
+      mins.push_back((int)std::min<long>(sizes[k] + 1, 1L << 30));
     for (int kind : kinds)
-      for (int nu : nus) {
-        wt_options o = base;
-        o.smoother = kind;
-        o.nu1 = o.nu2 = nu;
-        o.tail_max = 0;
-        o.tail_cluster = 0;
-        o.vcycle_grid = 0;
-        const double ms = measure(o, bms);
-        if (ms > 0 && ms < bms) {
-          bms = ms;
-          bo = o;
+      for (int nu : nus)
+        for (int mn : mins) {
+          wt_options o = base;
+          o.smoother = kind;
+          o.nu1 = o.nu2 = nu;
+          o.spectral_min = mn;
+          o.tail_max = 0;
+          o.tail_cluster = 0;
+          o.vcycle_grid = 0;
+          const double ms = measure(o, bms);
+          if (ms > 0 && ms < bms) {
+            bms = ms;
+            bo = o;
+          }
         }
-      }
-  }
-  if (bo.smoother != 0) {
-    // spectral sweeps on the finest one, two or three levels only,
-    // block-Jacobi below
-    const wt_options base = bo;
-    for (size_t k = 1; k <= 3 && k + 1 < sizes.size(); ++k) {
-      wt_options o = base;
-      o.spectral_min = (int)std::min<long>(sizes[k] + 1, 1L << 30);
-      const double ms = measure(o, bms);
-      if (ms > 0 && ms < bms) {
-        bms = ms;
-        bo = o;
-      }
-    }
   }
   {
     // the full-multigrid cycle (Algorithm 2) as the preconditioner
