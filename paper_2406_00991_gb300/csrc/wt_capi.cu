@@ -443,7 +443,7 @@ int check_options(const wt_options& o) {
   if (!(o.omega_s > 0) || !(o.omega_s < 2)) return fail(WT_EINVAL, "omega_s must be in (0, 2)");
   if (o.warp_fft != 0 && o.warp_fft != 1) return fail(WT_EINVAL, "warp_fft must be 0 or 1");
   if (o.pdl != 0 && o.pdl != 1) return fail(WT_EINVAL, "pdl must be 0 or 1");
-  if (o.df64 != 0 && o.df64 != 1) return fail(WT_EINVAL, "df64 must be 0 or 1");
+  if (o.df64 < 0 || o.df64 > 2) return fail(WT_EINVAL, "df64 must be 0, 1 or 2");
   if (o.spectral_min < 0) return fail(WT_EINVAL, "spectral_min must be >= 0");
   if ((o.filter != 0 && o.filter != 1) || (o.linear != 0 && o.linear != 1) ||
       (o.bc_transfer != 0 && o.bc_transfer != 1))

@@ -17,7 +17,7 @@
 // the error analysis of an FFT (a sum of such butterflies) needs.
 #pragma once
 
-#include "wt_internal.h"
+#include "wt_dev.cuh"
 
 namespace wt {
 
@@ -55,23 +55,43 @@ __device__ __forceinline__ ff operator*(ff a, ff b) {
   return ff_fast_two_sum(p, e);
 }
 
+template <> __device__ __forceinline__ ff2 mk<ff>(ff re, ff im) {
+  ff2 r;
+  r.x = re;
+  r.y = im;
+  return r;
+}
+
 // Conversions between the storage type T and the arithmetic type A (the
-// identity for float, double <-> double-float for the FP64 passes).
+// identity for float and double, double <-> double-float for the FP64
+// passes that run in double-float).
 template <typename A, typename T> __device__ __forceinline__ A to_arith(T v);
 template <> __device__ __forceinline__ float to_arith<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ double to_arith<double, double>(double v) { return v; }
 template <> __device__ __forceinline__ ff to_arith<ff, double>(double v) {
   const float h = __double2float_rn(v);
   return ff(h, __double2float_rn(v - (double)h));
 }
 template <typename T, typename A> __device__ __forceinline__ T from_arith(A v);
 template <> __device__ __forceinline__ float from_arith<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ double from_arith<double, double>(double v) { return v; }
 template <> __device__ __forceinline__ double from_arith<double, ff>(ff v) {
   return (double)v.hi + (double)v.lo;
 }
 
+// Constants in the arithmetic type.
 template <typename A> __device__ __forceinline__ A a_zero();
 template <> __device__ __forceinline__ float a_zero<float>() { return 0.f; }
+template <> __device__ __forceinline__ double a_zero<double>() { return 0.0; }
 template <> __device__ __forceinline__ ff a_zero<ff>() { return ff(0.f, 0.f); }
+template <typename A> __device__ __forceinline__ A a_half();
+template <> __device__ __forceinline__ float a_half<float>() { return 0.5f; }
+template <> __device__ __forceinline__ double a_half<double>() { return 0.5; }
+template <> __device__ __forceinline__ ff a_half<ff>() { return ff(0.5f, 0.f); }
+template <typename A> __device__ __forceinline__ A a_int(int v);             // exact for |v| < 2^24
+template <> __device__ __forceinline__ float a_int<float>(int v) { return (float)v; }
+template <> __device__ __forceinline__ double a_int<double>(int v) { return (double)v; }
+template <> __device__ __forceinline__ ff a_int<ff>(int v) { return ff(v); }
 
 __device__ __forceinline__ ff shfl_xor_a(ff v, int m) {
   return ff(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));

@@ -13,6 +13,7 @@
 // radix-2 stage for odd log2 N) Stockham self-sorting FFT with host-computed
 // FP64 twiddles staged in shared memory.
 #include "wt_dev.cuh"
+#include "wt_ff.cuh"
 
 #include <algorithm>
 
@@ -36,9 +37,10 @@ __global__ void __launch_bounds__(256) k_rowpass(RowPass<T> a, int ppc) {
 // then with H = Hout, W = exp(-2 pi i / Nout)
 //   C_m = (Y_m + conj Y_{H-m}) + i W^-m (Y_m - conj Y_{H-m})   (Y_{H-0} = Y_H),
 //   IDFT_H(C)_k = y_2k + i y_2k+1  (times Nin, removed by the epilogue scale).
-template <typename T>
+// T: the arithmetic type (the storage type S only for the filter table).
+template <typename T, typename S>
 __device__ c2_t<T>* real_spectral(c2_t<T>* A, c2_t<T>* B, int logNin, int logNout, int op, T kscale,
-                                  const T* filt, const c2_t<T>* tws, int logNt) {
+                                  const S* filt, const c2_t<T>* tws, int logNt) {
   using c2 = c2_t<T>;
   const int Hin = 1 << (logNin - 1), Hout = 1 << (logNout - 1);
   const int keep = (Hin < Hout ? Hin : Hout) * 2;          // resample: keep |m| < keep / 2
@@ -46,27 +48,27 @@ __device__ c2_t<T>* real_spectral(c2_t<T>* A, c2_t<T>* B, int logNin, int logNou
   c2* Z = fft_smem<T>(A, B, logNin - 1, 1, 0, tws, logNt, false);
   c2* Y = (Z == A) ? B : A;
   for (int m = threadIdx.x; m <= Hout; m += blockDim.x) {
-    c2 X = mk<T>(T(0), T(0));
+    c2 X = mk<T>(a_zero<T>(), a_zero<T>());
     if (m < Hin) {
       const c2 zm = Z[m], zc0 = Z[(Hin - m) & (Hin - 1)];
-      const c2 E = mk<T>(T(0.5) * (zm.x + zc0.x), T(0.5) * (zm.y - zc0.y));
-      const c2 Om = mk<T>(T(0.5) * (zm.y + zc0.y), -T(0.5) * (zm.x - zc0.x));   // (zm - conj zc) / 2i
+      const c2 E = mk<T>(a_half<T>() * (zm.x + zc0.x), a_half<T>() * (zm.y - zc0.y));
+      const c2 Om = mk<T>(a_half<T>() * (zm.y + zc0.y), -(a_half<T>() * (zm.x - zc0.x)));   // (zm - conj zc) / 2i
       const c2 WO = cmul<T>(tws[m << sin], Om);
       X = mk<T>(E.x + WO.x, E.y + WO.y);
     } else if (m == Hin) {
       const c2 z0 = Z[0];
-      X = mk<T>(z0.x - z0.y, T(0));                         // E_0 - O_0 (real)
+      X = mk<T>(z0.x - z0.y, a_zero<T>());                   // E_0 - O_0 (real)
     }
-    c2 v = mk<T>(T(0), T(0));
+    c2 v = mk<T>(a_zero<T>(), a_zero<T>());
     if (op == XOP_DERIV || op == XOP_RESAMPLE_DERIV) {
       if (m < Hout && 2 * m < keep) {
-        const T kap = kscale * T(m);
+        const T kap = kscale * a_int<T>(m);
         v = mk<T>(-kap * X.y, kap * X.x);
       }
     } else if (op == XOP_RESAMPLE) {
       if (2 * m < keep) v = X;
     } else if (op == XOP_FILTER) {
-      const T f = filt[m];
+      const T f = to_arith<T, S>(filt[m]);
       v = mk<T>(f * X.x, f * X.y);
     } else {
       v = X;                                                // XOP_NONE
@@ -90,11 +92,13 @@ __device__ c2_t<T>* real_spectral(c2_t<T>* A, c2_t<T>* B, int logNin, int logNou
 
 // One real x-row per CTA: the spectral operation of the pass, its epilogue
 // (store / add / residual / accumulate, boundary rows, Nyquist coefficient)
-// and the optional second transform of the result into out2.
-template <typename T>
+// and the optional second transform of the result into out2.  T: the
+// storage type; A: the arithmetic type of the transforms (T itself, or
+// double-float for FP64 data); epilogue in T.
+template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_rowpass_real(RowPass<T> a) {
   pdl_enter();
-  using c2 = c2_t<T>;
+  using c2 = c2_t<A>;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int Nin = a.Nin, Nout = a.Nout;
   const int logNt = a.Nin > a.Nout ? a.logNin : a.logNout;
@@ -103,13 +107,16 @@ __global__ void __launch_bounds__(256) k_rowpass_real(RowPass<T> a) {
   c2* P = reinterpret_cast<c2*>(smraw);
   c2* Q = P + Hb;
   c2* tws = Q + Hb;                                         // exp(-2 pi i t / Nt), t < Nt/2
-  for (int t = threadIdx.x; t < Nt / 2; t += blockDim.x) tws[t] = a.tw[t << (a.logNtw - logNt)];
+  for (int t = threadIdx.x; t < Nt / 2; t += blockDim.x) {
+    const c2_t<T> w = a.tw[t << (a.logNtw - logNt)];
+    tws[t] = mk<A>(to_arith<A, T>(w.x), to_arith<A, T>(w.y));
+  }
   const int r = blockIdx.x;
   const int Hin = Nin >> 1, Hout = Nout >> 1;
   const T* in = a.in + (long)r * Nin;
-  for (int k = threadIdx.x; k < Hin; k += blockDim.x) P[k] = mk<T>(in[2 * k], in[2 * k + 1]);
+  for (int k = threadIdx.x; k < Hin; k += blockDim.x) P[k] = mk<A>(to_arith<A, T>(in[2 * k]), to_arith<A, T>(in[2 * k + 1]));
   __syncthreads();
-  c2* R = real_spectral<T>(P, Q, a.logNin, a.logNout, a.op, a.kscale, a.filt, tws, logNt);
+  c2* R = real_spectral<A, T>(P, Q, a.logNin, a.logNout, a.op, to_arith<A, T>(a.kscale), a.filt, tws, logNt);
   const T sc = a.scale / T(Nin);
   const bool bc = bc_row(a, r);
   T alt = T(0);                                  // sum of (-1)^n out_n for the Nyquist coefficient
@@ -118,7 +125,7 @@ __global__ void __launch_bounds__(256) k_rowpass_real(RowPass<T> a) {
     T vv[2];
     for (int h = 0; h < 2; ++h) {
       const long o = (long)r * Nout + 2 * k + h;
-      T v = (h ? y.y : y.x) * sc;
+      T v = from_arith<T, A>(h ? y.y : y.x) * sc;
       if (bc) v = T(0);
       if (a.epi == EPI_ADD) v += a.add[o];
       else if (a.epi == EPI_RESID) v = a.rhs[o] - (a.add[o] + v);
@@ -127,7 +134,7 @@ __global__ void __launch_bounds__(256) k_rowpass_real(RowPass<T> a) {
       alt += h ? -v : v;
       vv[h] = v;
     }
-    if (a.out2) R[k] = mk<T>(vv[0], vv[1]);       // input of the second transform
+    if (a.out2) R[k] = mk<A>(to_arith<A, T>(vv[0]), to_arith<A, T>(vv[1]));   // input of the second transform
   }
   if (a.nyq) {
     __shared__ T red[32];
@@ -143,12 +150,12 @@ __global__ void __launch_bounds__(256) k_rowpass_real(RowPass<T> a) {
   if (a.out2) {
     __syncthreads();
     c2* O = (R == P) ? Q : P;
-    c2* R2 = real_spectral<T>(R, O, a.logNout, a.logNout2, a.op2, a.kscale, nullptr, tws, logNt);
+    c2* R2 = real_spectral<A, T>(R, O, a.logNout, a.logNout2, a.op2, to_arith<A, T>(a.kscale), (const T*)nullptr, tws, logNt);
     const T s2 = T(1) / T(Nout);
     for (int k = threadIdx.x; k < (a.Nout2 >> 1); k += blockDim.x) {
       const c2 y = R2[k];
-      a.out2[(long)r * a.Nout2 + 2 * k] = y.x * s2;
-      a.out2[(long)r * a.Nout2 + 2 * k + 1] = y.y * s2;
+      a.out2[(long)r * a.Nout2 + 2 * k] = from_arith<T, A>(y.x) * s2;
+      a.out2[(long)r * a.Nout2 + 2 * k + 1] = from_arith<T, A>(y.y) * s2;
     }
   }
 }
@@ -162,11 +169,21 @@ cudaError_t launch_rowpass(const RowPass<T>& a, cudaStream_t s) {
     const size_t smem = (size_t)(2 * (Nt / 2 + 1) + Nt / 2) * sizeof(c2_t<T>);
     // (the kernel's 32-word static reduction buffer counts against the
     // default 48 KB as well)
+    if constexpr (sizeof(T) == 8) {
+      if (a.df >= 2) {
+        // FP64 rows in double-float (the same shared-memory footprint)
+        if (smem > 32 * 1024) {
+          cudaError_t e = ensure_dyn_smem((const void*)k_rowpass_real<T, ff>, smem);
+          if (e != cudaSuccess) return e;
+        }
+        return launch_k(k_rowpass_real<T, ff>, dim3(a.nrows), dim3(256), smem, s, a);
+      }
+    }
     if (smem > 32 * 1024) {
-      cudaError_t e = ensure_dyn_smem((const void*)k_rowpass_real<T>, smem);
+      cudaError_t e = ensure_dyn_smem((const void*)k_rowpass_real<T, T>, smem);
       if (e != cudaSuccess) return e;
     }
-    return launch_k(k_rowpass_real<T>, dim3(a.nrows), dim3(256), smem, s, a);
+    return launch_k(k_rowpass_real<T, T>, dim3(a.nrows), dim3(256), smem, s, a);
   }
   const int Nmax = std::max(a.Nin, a.Nout);
   const int npairs = (a.nrows + 1) / 2;

@@ -28,18 +28,7 @@
 
 namespace wt {
 
-template <> __device__ __forceinline__ ff2 mk<ff>(ff re, ff im) {
-  ff2 r;
-  r.x = re;
-  r.y = im;
-  return r;
-}
-
 namespace {
-
-template <typename A> __device__ __forceinline__ A a_int(int v);
-template <> __device__ __forceinline__ float a_int<float>(int v) { return (float)v; }
-template <> __device__ __forceinline__ ff a_int<ff>(int v) { return ff(v); }
 
 template <int R>
 struct Log2 {

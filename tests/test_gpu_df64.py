@@ -107,3 +107,26 @@ def test_df64_stages_parity(wt):
     eta, u, v, w, tm = T.get_state()
     for got, ref in ((eta, st.eta), (u, st.u), (v, st.v), (w, st.w)):
         assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("shape", [(256, 1, 24), (64, 64, 12)])
+def test_df64_attainable_residual(wt, shape):
+    # the smallest relative residual an FP64 solve reaches (tolerance 1e-15,
+    # stopped by the iteration cap): FP64 arithmetic, double-float warp passes
+    # and columns (df64 = 1, the default), and double-float real-row passes
+    # too (df64 = 2); all well below the method's 1e-10
+    Nx, Ny, Nz = shape
+    L = 8.0
+    g, h, ea, eb = curved(Nx, Ny, Nz, L)
+    if Ny == 1:
+        h, ea, eb = (np.ascontiguousarray(a[:1]) for a in (h, ea, eb))
+    b = np.random.default_rng(11).standard_normal(g.shape)
+    floor = {}
+    for df in (0, 1, 2):
+        T = wt.Tank(Nx, Ny, Nz, L, h, mode=wt.WT_FP64, tol=1e-15, max_it=120, df64=df)
+        p, info = T.poisson_solve(ea, eb, b, raise_noconv=False)
+        floor[df] = info.rel_residual
+        T.close()
+    print("attainable FP64 relative residual %s: FP64 %.1e, df64=1 %.1e, df64=2 %.1e"
+          % (shape, floor[0], floor[1], floor[2]))
+    assert floor[0] <= 1e-12 and floor[1] <= 1e-11 and floor[2] <= 1e-11
