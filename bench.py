@@ -45,8 +45,8 @@ METRIC = "RK4 DOF-updates/s (mixed FP32/FP64 p-MG Poisson solves at 1e-10 residu
 # traffic summary under profiles/): 2D 1024 x 24, 3 launches; 3D 256 x 256 x 16,
 # 5 launches.  The writes read 0 there: each output stays dirty in L2 past the
 # end of its kernel.
-OP_TRAFFIC_2D = 154368 + 259072 + 256512
-OP_TRAFFIC_3D = 4488960 + 4491776 + 16568320 + 8944640 + 8947712
+OP_TRAFFIC_2D = 154624 + 259840 + 256768
+OP_TRAFFIC_3D = 4491008 + 4493568 + 16569344 + 8947200 + 8949504
 UNIT = "DOF-updates/s"
 SMOOTHERS = {0: "damped block-Jacobi", 1: "mean-depth spectral", 2: "block-Jacobi then mean-depth spectral"}
 STAGES = 5
