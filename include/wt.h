@@ -455,10 +455,9 @@ int wt_time_kernel(wt_tank* t, const double* eta_a, const double* eta_b, int wha
  *   h, eta_a, eta_b: device arrays [Nx]; p, Ap: device arrays [Nz+1][Nx]
  *   (host pointers return WT_EINVAL).  stream: cudaStream_t or NULL.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it: make that first call before any
- * stream capture.  All calls share the array and it keeps the last call's
- * contents, so calls that overlap on the GPU (different streams or threads)
- * race; serialise them.  Returns after Ap is complete; WT_EBREAK when
+ * (cudaGetSymbolAddress) and caches it.  All calls share the array and it
+ * keeps the last call's contents, so calls that overlap on the GPU
+ * (different streams or threads) race; serialise them.  Returns after Ap is complete; WT_EBREAK when
  * h + eta <= 0 or a value is not finite.
  */
 int wt_apply_operator_static(int Nx, int Nz, double L, const double* h, const double* eta_a,
