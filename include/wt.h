@@ -327,7 +327,8 @@ int wt_stream_function_wave(wt_tank* t, int nwaves, double H, int nmodes, double
  * warm-up solve plus the median of reps (1..100) timed solves each, and keeps
  * the fastest setting that reaches the tolerance; then, on that setting, the
  * WT_REFINE with inner_tol 1e-4 and 1e-3 (unless the tank is in WT_FP64),
- * the spectral smoothers (smoother 1 and 2, nu1 = nu2 in {1, 2}), the
+ * the spectral smoothers (smoother 1 and 2, nu1 = nu2 in {1, 2}, on every
+ * level or on the finest one, two or three levels: spectral_min), the
  * full-multigrid cycle (cycle = 1) and the V-cycle's launch schedule (tail_max 2048 or 8192 with tail_cluster 0 or
  * 16, or vcycle_grid = 1).  The paper leaves these
  * choices open (Sec. 4.1).  On success the tank uses the winner, *best holds
@@ -342,6 +343,15 @@ int wt_autotune(wt_tank* t, const double* eta_a, const double* eta_b, const doub
  * timed unit (the state, time included, is restored after every trial and on
  * return; solver statistics restart).  Needs a state (wt_set_state). */
 int wt_autotune_step(wt_tank* t, double dt, int reps, wt_options* best, double* best_ms, double* entry_ms);
+/* File of tuned options shared by wt_autotune and wt_autotune_step in this
+ * process: path, or NULL to stop using one (the default).  JSON lines, one
+ * search result per line, keyed by the kind of search ("solve" / "step"),
+ * the finest grid Nx x Ny x Nz, whether the tank runs WT_FP64, filter,
+ * linear and tol.  A search whose key is in the file applies the stored
+ * options without measuring (*best_ms, *entry_ms: the stored times); a
+ * completed search replaces its line (written to path.tmp, then renamed).
+ * WT_EINVAL for an empty path.  Thread-safe. */
+int wt_autotune_cache(const char* path);
 
 /*
  * Batches of independent 2D tanks of uneven size, advanced together by one

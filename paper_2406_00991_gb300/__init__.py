@@ -78,6 +78,7 @@ def _load():
         "wt_apply_operator_static": [I, I, D, P, P, P, P, P, P],
         "wt_autotune": [P, P, P, P, I, ctypes.POINTER(wt_options), ctypes.POINTER(D), ctypes.POINTER(D)],
         "wt_autotune_step": [P, D, I, ctypes.POINTER(wt_options), ctypes.POINTER(D), ctypes.POINTER(D)],
+        "wt_autotune_cache": [ctypes.c_char_p],
         "wt_set_bathymetry": [P, P],
         "wt_apply_operator_transposed": [P, P, P, P, P, I],
         "wt_adjoint_solve": [P, P, P, P, P, D, ctypes.POINTER(wt_solve_info)],
@@ -318,6 +319,11 @@ def wt_autotune_step(t, dt, reps=3):
     b, e = ctypes.c_double(), ctypes.c_double()
     st = _lib.wt_autotune_step(t, float(dt), int(reps), ctypes.byref(o), ctypes.byref(b), ctypes.byref(e))
     return st, o, b.value, e.value
+
+
+def wt_autotune_cache(path):
+    """File of tuned options for wt_autotune / wt_autotune_step (None: none)."""
+    return _lib.wt_autotune_cache(None if path is None else os.fsencode(path))
 
 
 def wt_create_batch(Nx, Nz, L, bathymetry, g=9.81, nu=0.0):

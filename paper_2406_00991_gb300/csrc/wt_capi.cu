@@ -534,6 +534,9 @@ void filter_field(wt_tank& t, double* q, int planes, bool cheb) {
 }
 
 int rk_stage(wt_tank& t, int k, double dt, AdjStage* rec = nullptr) {
+  static const char* const kStageNames[5] = {"wt stage 1", "wt stage 2", "wt stage 3", "wt stage 4",
+                                             "wt stage 5"};
+  NvtxRange range(kStageNames[k - 1]);
   enter(t);
   const double a = kAlpha[k - 1], b = kBeta[k - 1];
   const bool y = t.Ny > 1;
@@ -1337,6 +1340,7 @@ int wt_adjoint_step(wt_tank* t, double dt, const double* eta, const double* u, c
   if (!t || !eta || !u || !w || !lam_eta || !lam_u || !lam_w) return fail(WT_EINVAL, "NULL argument");
   if (t->Ny != 1) return fail(WT_ENOTSUP, "the adjoint step is 2D only");
   if (!(dt > 0) || !std::isfinite(dt)) return fail(WT_EINVAL, "dt must be positive");
+  NvtxRange range("wt adjoint step");
   return guarded_t(t, [&]() -> int {
     enter(*t);
     alloc_adj(*t);
@@ -1531,6 +1535,7 @@ int wt_batch_get_state(const wt_batch* b, int i, double* eta, double* u, double*
 int wt_batch_step(wt_batch* b, const double* dt, int nsteps) {
   if (!b || !dt) return fail(WT_EINVAL, "NULL argument");
   if (nsteps < 0) return fail(WT_EINVAL, "nsteps must be >= 0");
+  NvtxRange range("wt batch step");
   const int nt = (int)b->tanks.size();
   for (int i = 0; i < nt; ++i) {
     if (!(dt[i] > 0) || !std::isfinite(dt[i])) return fail(WT_EINVAL, "dt must be positive");

@@ -4,6 +4,8 @@
 #include "../../include/wt.h"
 #include "wt_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <array>
 #include <stdexcept>
 #include <string>
@@ -15,6 +17,15 @@ namespace wt {
 struct WtError {
   int code;
   std::string msg;
+};
+
+// NVTX range for the lifetime of the object (stage, solve, V-cycle level,
+// batch step): visible in a timeline profiler, no cost without one.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 #define WT_CK(call)                                                                         \

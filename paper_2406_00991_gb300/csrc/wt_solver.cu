@@ -424,6 +424,12 @@ static int tail_level(wt_tank& t, bool tr) {
 // this level.
 template <typename T>
 void vcycle(wt_tank& t, int l, const T* f, T* x, bool tr, bool x0_given) {
+  static const char* const kLevelNames[kMaxLevels] = {
+      "wt vcycle level 0",  "wt vcycle level 1",  "wt vcycle level 2",  "wt vcycle level 3",
+      "wt vcycle level 4",  "wt vcycle level 5",  "wt vcycle level 6",  "wt vcycle level 7",
+      "wt vcycle level 8",  "wt vcycle level 9",  "wt vcycle level 10", "wt vcycle level 11",
+      "wt vcycle level 12", "wt vcycle level 13", "wt vcycle level 14", "wt vcycle level 15"};
+  NvtxRange range(kLevelNames[l < kMaxLevels ? l : kMaxLevels - 1]);
   auto& lev = levels<T>(t);
   const int nl = (int)lev.size();
   auto& L = lev[l];
@@ -709,6 +715,7 @@ void write_barrier_limit(wt_tank& t) {
 // ------------------------------------------------------------------ solves
 int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_solve_info* info,
                          bool tr) {
+  NvtxRange range("wt poisson solve");
   const long n = t.n;
   const double bn = norm2<double>(t, b, n);
   int its_total = 0, refinements = 0;

@@ -12,9 +12,114 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <mutex>
+#include <sstream>
+#include <string>
 #include <vector>
 
 namespace {
+
+// ---- file of tuned options (JSON lines, one search result per line)
+//   {"key": "step 1024x1x24 fp64=0 filter=1 linear=0 tol=1e-10", "mode": 1, "omega": 0.5, ...}
+// keyed by the kind of search, the finest grid, whether the tank runs the
+// all-FP64 form, the filter, the linearised model and the tolerance.
+std::mutex g_cache_mu;
+std::string g_cache_path;
+
+struct CacheField {
+  const char* name;
+  double (*get)(const wt_options&);
+  void (*set)(wt_options&, double);
+};
+#define WT_CF(F) {#F, [](const wt_options& o) { return (double)o.F; }, [](wt_options& o, double v) { o.F = (decltype(o.F))v; }}
+const CacheField kCacheFields[] = {WT_CF(mode),        WT_CF(omega),     WT_CF(nu1),          WT_CF(nu2),
+                                   WT_CF(coarsest_max), WT_CF(inner_tol), WT_CF(smoother),     WT_CF(spectral_min),
+                                   WT_CF(cycle),        WT_CF(tail_max),  WT_CF(tail_cluster), WT_CF(vcycle_grid)};
+#undef WT_CF
+
+std::string cache_key(const char* kind, wt_tank* t, const wt_options& o) {
+  int nl = 0;
+  int dims[3 * 16] = {0};
+  wt_get_levels(t, &nl, dims);
+  char buf[200];
+  std::snprintf(buf, sizeof buf, "%s %dx%dx%d fp64=%d filter=%d linear=%d tol=%.3g", kind, dims[0], dims[1],
+                dims[2], o.mode == WT_FP64 ? 1 : 0, o.filter, o.linear, o.tol);
+  return buf;
+}
+
+bool json_number(const std::string& line, const char* name, double* v) {
+  const std::string pat = std::string("\"") + name + "\":";
+  const size_t at = line.find(pat);
+  if (at == std::string::npos) return false;
+  const char* p = line.c_str() + at + pat.size();
+  char* end = nullptr;
+  *v = std::strtod(p, &end);
+  return end != p;
+}
+
+std::string line_key(const std::string& line) {
+  const std::string pat = "\"key\": \"";
+  const size_t at = line.find(pat);
+  if (at == std::string::npos) return "";
+  const size_t b = at + pat.size(), e = line.find('"', b);
+  return e == std::string::npos ? "" : line.substr(b, e - b);
+}
+
+// The stored options for key on top of o (true if found).
+bool cache_lookup(const std::string& key, wt_options& o, double* best_ms, double* entry_ms) {
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  if (g_cache_path.empty()) return false;
+  std::ifstream in(g_cache_path);
+  std::string line;
+  while (std::getline(in, line)) {
+    if (line_key(line) != key) continue;
+    wt_options r = o;
+    for (const auto& f : kCacheFields) {
+      double v;
+      if (!json_number(line, f.name, &v)) return false;
+      f.set(r, v);
+    }
+    double b = 0.0, e = 0.0;
+    json_number(line, "best_ms", &b);
+    json_number(line, "entry_ms", &e);
+    o = r;
+    if (best_ms) *best_ms = b;
+    if (entry_ms) *entry_ms = e;
+    return true;
+  }
+  return false;
+}
+
+// Replace (or add) the line of key, written to a temporary file and renamed.
+void cache_store(const std::string& key, const wt_options& o, double best_ms, double entry_ms) {
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  if (g_cache_path.empty()) return;
+  std::vector<std::string> keep;
+  {
+    std::ifstream in(g_cache_path);
+    std::string line;
+    while (std::getline(in, line))
+      if (!line.empty() && line_key(line) != key) keep.push_back(line);
+  }
+  std::ostringstream os;
+  os.precision(17);
+  os << "{\"key\": \"" << key << "\"";
+  for (const auto& f : kCacheFields) os << ", \"" << f.name << "\": " << f.get(o);
+  os << ", \"best_ms\": " << best_ms << ", \"entry_ms\": " << entry_ms << "}";
+  keep.push_back(os.str());
+  const std::string tmp = g_cache_path + ".tmp";
+  {
+    std::ofstream out(tmp, std::ios::trunc);
+    if (!out) return;
+    for (const auto& l : keep) out << l << "\n";
+    if (!out) return;
+  }
+  std::rename(tmp.c_str(), g_cache_path.c_str());
+}
 
 struct DevBuf {
   double* p = nullptr;
@@ -141,6 +246,15 @@ extern "C" int wt_autotune(wt_tank* t, const double* eta_a, const double* eta_b,
   if (reps < 1 || reps > 100) return wt::set_error(WT_EINVAL, "wt_autotune: reps must be in [1, 100]");
   wt_options entry{};
   wt_get_options(t, &entry);
+  const std::string key = cache_key("solve", t, entry);
+  {
+    wt_options o = entry;
+    if (cache_lookup(key, o, best_ms, entry_ms)) {
+      const int st = wt_set_options(t, &o);
+      if (st == WT_OK && best) *best = o;
+      return st;
+    }
+  }
   int nl = 0;
   int dims[3 * 16];
   if (wt_get_levels(t, &nl, dims) != WT_OK) return WT_EINVAL;
@@ -219,6 +333,7 @@ extern "C" int wt_autotune(wt_tank* t, const double* eta_a, const double* eta_b,
   }
   const int st = wt_set_options(t, &bo);
   if (st != WT_OK) return st;
+  cache_store(key, bo, bms, e_ms);
   if (best) *best = bo;
   if (best_ms) *best_ms = bms;
   if (entry_ms) *entry_ms = e_ms;
@@ -235,6 +350,15 @@ extern "C" int wt_autotune_step(wt_tank* t, double dt, int reps, wt_options* bes
   if (!(dt > 0)) return wt::set_error(WT_EINVAL, "wt_autotune_step: dt must be positive");
   wt_options entry{};
   wt_get_options(t, &entry);
+  const std::string key = cache_key("step", t, entry);
+  {
+    wt_options o = entry;
+    if (cache_lookup(key, o, best_ms, entry_ms)) {
+      const int st = wt_set_options(t, &o);
+      if (st == WT_OK && best) *best = o;
+      return st;
+    }
+  }
   int nl = 0;
   int dims[3 * 16];
   if (wt_get_levels(t, &nl, dims) != WT_OK) return WT_EINVAL;
@@ -304,6 +428,7 @@ extern "C" int wt_autotune_step(wt_tank* t, double dt, int reps, wt_options* bes
   st = wt_set_options(t, &bo);
   if (st == WT_OK) st = restore();
   if (st != WT_OK) return st;
+  cache_store(key, bo, bms, e_ms);
   if (best) *best = bo;
   if (best_ms) *best_ms = bms;
   if (entry_ms) *entry_ms = e_ms;
@@ -402,5 +527,12 @@ extern "C" int wt_batch_autotune(wt_batch* b, const double* dt, int reps, wt_opt
   if (best) *best = bo;
   if (best_ms) *best_ms = bms;
   if (entry_ms) *entry_ms = e_ms;
+  return WT_OK;
+}
+
+extern "C" int wt_autotune_cache(const char* path) {
+  if (path && !*path) return wt::set_error(WT_EINVAL, "wt_autotune_cache: empty path");
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  g_cache_path = path ? path : "";
   return WT_OK;
 }

@@ -56,6 +56,10 @@ def test_argument_checks_without_gpu():
     code, msg = w.wt_last_error()
     assert code == w.WT_EINVAL and "nu" in msg
     assert w.wt_destroy(None) == w.WT_OK
+    # the tuned-options file: a path, none, and an empty path (rejected)
+    assert w.wt_autotune_cache("/nonexistent/dir/tuned.jsonl") == w.WT_OK
+    assert w.wt_autotune_cache(None) == w.WT_OK
+    assert w.wt_autotune_cache("") == w.WT_EINVAL
 
 
 def test_product_path_has_no_oracle_import():

@@ -65,3 +65,44 @@ def test_batch_autotune(wt, mode):
     for i in range(len(shapes)):
         assert B.stats(i)[2] <= 1e-10
     B.close()
+
+
+def test_autotune_cache(wt, tmp_path):
+    # a completed search is written to the file under its key; a second tank
+    # of the same grid and settings takes the stored options without
+    # measuring (no step runs: the solver statistics stay at zero)
+    import json
+    from test_gpu_parity import curved
+    path = tmp_path / "tuned.jsonl"
+    assert wt.wt_autotune_cache(str(path)) == wt.WT_OK
+    try:
+        Nx, Nz, L = 128, 12, 8.0
+        g, h, ea, eb = curved(Nx, 1, Nz, L)
+        z = np.zeros(g.shape)
+        eta = np.ascontiguousarray(0.01 * np.cos(2 * np.pi * g.x / L)[None, :])
+
+        def tank():
+            T = wt.Tank(Nx, 1, Nz, L, h, mode=1, tol=1e-10, filter=1)
+            T.set_state(eta, z, z, z)
+            return T
+
+        A = tank()
+        opts, best, entry = A.autotune_step(0.01, reps=1)
+        lines = path.read_text().splitlines()
+        assert len(lines) == 1
+        rec = json.loads(lines[0])
+        assert rec["key"].startswith("step 128x1x12 fp64=0 filter=1 linear=0")
+        assert (rec["omega"], rec["nu1"], rec["smoother"], rec["spectral_min"]) == \
+            (opts["omega"], opts["nu1"], opts["smoother"], opts["spectral_min"])
+        B = tank()
+        opts2, best2, entry2 = B.autotune_step(0.01, reps=1)
+        assert B.stats() == (0, 0)
+        assert opts2 == opts and (best2, entry2) == (pytest.approx(best), pytest.approx(entry))
+        # another grid is a different key: searched and appended
+        C = wt.Tank(64, 1, 12, L, np.ascontiguousarray(h[:, ::2]), mode=1, tol=1e-10, filter=1)
+        C.set_state(np.ascontiguousarray(eta[:, ::2]), np.zeros((13, 1, 64)), np.zeros((13, 1, 64)),
+                    np.zeros((13, 1, 64)))
+        C.autotune_step(0.01, reps=1)
+        assert len(path.read_text().splitlines()) == 2
+    finally:
+        wt.wt_autotune_cache(None)
