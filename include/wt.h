@@ -122,11 +122,12 @@ typedef struct wt_options {
                         tail_max (if set) run the one-launch tail with
                         block-Jacobi sweeps, the finer levels spectral ones */
   double omega_s;    /* damping of the spectral smoother (1.0)               */
-  int warp_fft;      /* 1 (default): FP32 x- and y-derivative passes over
-                        many lines (>= 512 x-rows, or y-lines of >= 16
-                        columns; 32..1024 points) run one warp per line pair
-                        with the transform in registers; 0: every pass one
-                        CTA per line (pair)                                  */
+  int warp_fft;      /* 1 (default): x- and y-derivative and filter passes
+                        over many lines (>= 512 x-rows, or y-lines of >= 16
+                        columns; FP32 32..1024 points, FP64 with df64
+                        32..256 points) run one warp per line pair with the
+                        transform in registers; 0: every pass one CTA per
+                        line (pair)                                          */
   int pdl;           /* 1 (default): kernels are launched with programmatic
                         dependent launch - the next kernel of the stream is
                         made resident while its predecessor runs and waits
