@@ -329,7 +329,8 @@ int wt_stream_function_wave(wt_tank* t, int nwaves, double H, int nmodes, double
  * the fastest setting that reaches the tolerance; then, on that setting, the
  * WT_REFINE with inner_tol 1e-4 and 1e-3 (unless the tank is in WT_FP64),
  * the spectral smoothers (smoother 1 and 2, nu1 = nu2 in {1, 2}, on every
- * level or on the finest one, two or three levels: spectral_min), the
+ * level or on the finest one, two or three levels: spectral_min; then
+ * omega_s 0.8 and 1.2), the
  * full-multigrid cycle (cycle = 1) and the V-cycle's launch schedule (tail_max 2048 or 8192 with tail_cluster 0 or
  * 16, or vcycle_grid = 1).  The paper leaves these
  * choices open (Sec. 4.1).  On success the tank uses the winner, *best holds

@@ -36,9 +36,10 @@ struct CacheField {
   void (*set)(wt_options&, double);
 };
 #define WT_CF(F) {#F, [](const wt_options& o) { return (double)o.F; }, [](wt_options& o, double v) { o.F = (decltype(o.F))v; }}
-const CacheField kCacheFields[] = {WT_CF(mode),        WT_CF(omega),     WT_CF(nu1),          WT_CF(nu2),
-                                   WT_CF(coarsest_max), WT_CF(inner_tol), WT_CF(smoother),     WT_CF(spectral_min),
-                                   WT_CF(cycle),        WT_CF(tail_max),  WT_CF(tail_cluster), WT_CF(vcycle_grid)};
+const CacheField kCacheFields[] = {WT_CF(mode),     WT_CF(omega),        WT_CF(nu1),      WT_CF(nu2),
+                                   WT_CF(coarsest_max), WT_CF(inner_tol), WT_CF(smoother), WT_CF(spectral_min),
+                                   WT_CF(omega_s),  WT_CF(cycle),        WT_CF(tail_max), WT_CF(tail_cluster),
+                                   WT_CF(vcycle_grid)};
 #undef WT_CF
 
 std::string cache_key(const char* kind, wt_tank* t, const wt_options& o) {
@@ -135,7 +136,7 @@ double now_ms() {
 
 // Second stage on the winner: the refinement form with inner tolerances
 // 1e-4 and 1e-3, the spectral smoothers (on every level, or on the finest
-// one to three levels), the full-multigrid cycle instead of
+// one to three levels; then their damping 0.8 / 1.2), the full-multigrid cycle instead of
 // the V-cycle, then the launch schedule of the V-cycles - the levels below
 // tail_max unknowns in one launch (one CTA, or a cluster of 16 CTAs), or (with
 // block-Jacobi alone) the whole cycle as one cooperative launch - each kept
@@ -195,6 +196,20 @@ void refine_schedule(wt_options& bo, double& bms, F&& measure, const std::vector
             bo = o;
           }
         }
+  }
+  if (bo.smoother != 0) {
+    // the spectral sweep's damping around the undamped exact flat solve
+    const wt_options base = bo;
+    const double oms[] = {0.8, 1.2};
+    for (double om : oms) {
+      wt_options o = base;
+      o.omega_s = om;
+      const double ms = measure(o, bms);
+      if (ms > 0 && ms < bms) {
+        bms = ms;
+        bo = o;
+      }
+    }
   }
   {
     // the full-multigrid cycle (Algorithm 2) as the preconditioner

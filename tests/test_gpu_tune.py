@@ -92,8 +92,8 @@ def test_autotune_cache(wt, tmp_path):
         assert len(lines) == 1
         rec = json.loads(lines[0])
         assert rec["key"].startswith("step 128x1x12 fp64=0 filter=1 linear=0")
-        assert (rec["omega"], rec["nu1"], rec["smoother"], rec["spectral_min"]) == \
-            (opts["omega"], opts["nu1"], opts["smoother"], opts["spectral_min"])
+        assert (rec["omega"], rec["nu1"], rec["smoother"], rec["spectral_min"], rec["omega_s"]) == \
+            (opts["omega"], opts["nu1"], opts["smoother"], opts["spectral_min"], opts["omega_s"])
         B = tank()
         opts2, best2, entry2 = B.autotune_step(0.01, reps=1)
         assert B.stats() == (0, 0)
