@@ -89,7 +89,7 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index, interval_ms=50, wait_s=3.0):
+    def __init__(self, gpu_index, interval_ms=20, wait_s=3.0):
         self.idx = gpu_index
         self.interval_ms = interval_ms
         self.wait_s = wait_s
