@@ -176,7 +176,7 @@ def test_gradient_workload_as_stated(wt):
     second seeded bathymetry.  The FP64 gradient (solves at 1e-12, the
     tightest relative residual the FP64 path reaches here) against central
     finite differences with step 1e-6 along a unit direction in the 64 b_k
-    and one in eta0 (spec: <= 1e-6 relative), and the mixed solver's
+    and one in eta0 (agreement to 1e-6 relative), and the mixed solver's
     gradient (1e-10 solves) against the FP64 one."""
     from paper_2406_00991_gb300.adjoint import gauge_series
     Nx, Nz, L, nsteps, every = 512, 20, 16.0, 400, 20
