@@ -55,7 +55,7 @@ enum wt_status {
                        the sigma map is invalid (e.g. a breaking wave)        */
   WT_ECUDA = 5,     /* a CUDA runtime call or kernel launch failed            */
   WT_ETIMEOUT = 6,  /* a bounded device-side wait gave up                     */
-  WT_ENOTSUP = 7    /* valid request that this build does not support        */
+  WT_ENOTSUP = 7    /* valid request that the library does not support      */
 };
 
 enum wt_precision { WT_FP64 = 0, WT_MIXED = 1, WT_FP32 = 2, WT_REFINE = 3 };
