@@ -290,8 +290,8 @@ def run_ours(args):
         copy_ms.append((time.perf_counter() - t0) * 1e3)
     bytes_io = 8 * (host[0].size + host[1].size + host[3].size)
 
-    # ---------------- plain FP64 solver on the same GPU
-    T.set_options(mode=w.WT_FP64)
+    # ---------------- plain FP64 solver on the same GPU (FP64 arithmetic throughout)
+    T.set_options(mode=w.WT_FP64, df64=0)
     T.set_state(*st0)
     T.step(p["dt"], 1)
     Kf = max(1, min(args.steps, 3))

@@ -134,19 +134,22 @@ typedef struct wt_options {
                         (griddepcontrol.wait) for the predecessor's completion
                         before touching memory, so results are unchanged and
                         only launch latency is hidden; 0: plain stream order */
-  int df64;          /* 1 (default): the FP64 x- and y-derivative and filter
-                        passes over many lines (32..256 points, 3D levels)
-                        and the FP64 sigma-column kernels over many columns
-                        run in double-float arithmetic (each value the
-                        unevaluated sum of two floats, about 48 significant
-                        bits, from error-free float transformations) on the
-                        FP32 units, which GB300 runs at 64 times its FP64
-                        rate; the data stay FP64 in memory (measured operator
-                        error 2e-15 .. 1e-14 of max |Ap| against 1e-15 in
-                        FP64).  2: the CTA-per-row FP64 passes (2D rows) too:
-                        faster, with a higher floor on the relative residual
-                        an FP64 solve can reach (tolerances near 1e-12 may
-                        end in WT_ENOCONV).  0: FP64 arithmetic             */
+  int df64;          /* 1 (default): the FP64 spectral passes and sigma-column
+                        kernels run in double-float arithmetic (each value
+                        the unevaluated sum of two floats, about 48
+                        significant bits, from error-free float
+                        transformations) on the FP32 units, which GB300 runs
+                        at 64 times its FP64 rate - the warp passes over many
+                        lines (32..256 points), the column kernels over many
+                        columns and the CTA-per-row passes - except that the
+                        solver's true residuals (the restart residual of the
+                        flexible GMRES, the refinement residual) keep the
+                        CTA-per-row passes in FP64, so an FP64 solve reaches
+                        FP64's attainable residual; the data stay FP64 in
+                        memory (measured operator error 2e-15 .. 1e-14 of
+                        max |Ap| against 1e-15 in FP64).  2: double-float in
+                        the true residuals too (attainable residual about
+                        1e-11 on 1,024-point rows).  0: FP64 arithmetic      */
   int spectral_min;  /* smoother 1 or 2: levels with fewer unknowns than this
                         smooth by block-Jacobi alone (their column blocks
                         are built); 0 (default): every level spectral        */

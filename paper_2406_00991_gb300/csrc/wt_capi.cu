@@ -503,7 +503,7 @@ RowPass<double> dpass(wt_tank& t, const double* in, double* out, int nrows, int 
   a.logNin = ilog2(N); a.logNout = ilog2(N); a.op = op;
   a.kscale = 2.0 * M_PI / t.L; a.tw = t.tw64; a.logNtw = t.logNtw;
   a.warp = t.opt.warp_fft;
-  a.df = t.opt.df64;
+  a.df = df_level(t);
   return a;
 }
 // d/dx of a field with `planes` sigma levels (planes = 1: a surface)

@@ -164,6 +164,7 @@ bool sf_solve(double k, double d, double H, double g, int N, SfWave& out);
 double sf_eta(const SfWave& W, double x, double t);
 // fixed-frame velocity at x, height z above the still water level, time t
 void sf_velocity(const SfWave& W, double x, double z, double t, double& u, double& w);
+
 }  // namespace wt
 
 struct wt_tank {
@@ -173,6 +174,10 @@ struct wt_tank {
   // hierarchy change
   std::vector<wt::IterGraph> graphs[6];
   bool use_graphs = true;
+  // > 0 while the solver evaluates a true residual (restart residual of the
+  // flexible GMRES, refinement residual): with df64 = 1 the FP64 real-row
+  // passes then stay in FP64 arithmetic (see df_level)
+  int residual_scope = 0;
   cudaStream_t own_stream = nullptr;
   cudaEvent_t order_ev = nullptr;
   cudaStream_t side = nullptr;                 // stage set-up overlapped with the forcing:
@@ -236,3 +241,28 @@ struct wt_tank {
   unsigned* tickets = nullptr;     // last-CTA counters of the one-launch Krylov reductions
   long solves = 0, iterations = 0;
 };
+
+namespace wt {
+
+// Double-float level of the FP64 kernels for the next launches (the
+// RowPass.df / column-kernel df argument): 0 FP64 arithmetic; 1 the warp
+// passes and sigma-column kernels over many lines / columns in double-float;
+// 2 also the CTA-per-row passes.  Option df64 = 1 (default) gives 2, and 1
+// inside a true-residual evaluation, so that the attainable residual of an
+// FP64 solve stays FP64's; df64 = 2 gives 2 everywhere.
+inline int df_level(const wt_tank& t) {
+  const int d = t.opt.df64;
+  if (d == 1) return t.residual_scope > 0 ? 1 : 2;
+  return d;
+}
+
+// Marks a true-residual evaluation for df_level while it lives.
+struct ResidualScope {
+  wt_tank& t;
+  explicit ResidualScope(wt_tank& tk) : t(tk) { ++t.residual_scope; }
+  ~ResidualScope() { --t.residual_scope; }
+  ResidualScope(const ResidualScope&) = delete;
+  ResidualScope& operator=(const ResidualScope&) = delete;
+};
+
+}  // namespace wt

@@ -40,7 +40,7 @@ static RowPass<T> xpass(wt_tank& t, const T* in, T* out, int nrows, int Nin, int
   a.tw = twiddles<T>(t);
   a.logNtw = t.logNtw;
   a.warp = t.opt.warp_fft;
-  a.df = t.opt.df64;
+  a.df = df_level(t);
   return a;
 }
 
@@ -223,7 +223,7 @@ void apply_op(wt_tank& t, int l, const T* x, T* out, const T* f, bool nyq, bool 
   }
   if (L.Ny == 1) {
     if (!ex.have_dx) run_rowpass(t, xpass<T>(t, x, L.t1, L.M1, L.Nx, L.Nx, XOP_DERIV));
-    WT_LAUNCH(t, K_OPCOLS, sizeof(T) * (4.0 * L.n + 7.0 * L.ncols), 6.0 * L.M1 * L.M1 * L.ncols, launch_op_cols<T>(V, x, L.t1, nullptr, L.t2, nullptr, L.t3, s, t.opt.df64));
+    WT_LAUNCH(t, K_OPCOLS, sizeof(T) * (4.0 * L.n + 7.0 * L.ncols), 6.0 * L.M1 * L.M1 * L.ncols, launch_op_cols<T>(V, x, L.t1, nullptr, L.t2, nullptr, L.t3, s, df_level(t)));
     RowPass<T> a = xpass<T>(t, L.t2, out, L.M1, L.Nx, L.Nx, XOP_DERIV);
     a.skip_bc = 1;
     a.Ny = 1;
@@ -237,7 +237,7 @@ void apply_op(wt_tank& t, int l, const T* x, T* out, const T* f, bool nyq, bool 
   } else {
     run_rowpass(t, xpass<T>(t, x, L.t1, L.M1 * L.Ny, L.Nx, L.Nx, XOP_DERIV));
     run_rowpass(t, ypass<T>(t, x, L.t4, L.M1, L.Nx, L.Ny, L.Ny, XOP_DERIV));
-    WT_LAUNCH(t, K_OPCOLS, sizeof(T) * (6.0 * L.n + 12.0 * L.ncols), 8.0 * L.M1 * L.M1 * L.ncols, launch_op_cols<T>(V, x, L.t1, L.t4, L.t2, L.t5, L.t3, s, t.opt.df64));
+    WT_LAUNCH(t, K_OPCOLS, sizeof(T) * (6.0 * L.n + 12.0 * L.ncols), 8.0 * L.M1 * L.M1 * L.ncols, launch_op_cols<T>(V, x, L.t1, L.t4, L.t2, L.t5, L.t3, s, df_level(t)));
     RowPass<T> a = xpass<T>(t, L.t2, L.t6, L.M1 * L.Ny, L.Nx, L.Nx, XOP_DERIV);
     a.skip_bc = 1;
     a.Ny = L.Ny;
@@ -676,7 +676,10 @@ double fgmres(wt_tank& t, const T* b, T* x, double bnorm, double tol, int maxit,
   int its = 0;
   double rel = 1.0;
   for (;;) {
-    apply_op<T>(t, 0, x, V, b, false, tr);                   // r = b - A x -> V_0
+    {
+      ResidualScope rs(t);                                     // the true residual
+      apply_op<T>(t, 0, x, V, b, false, tr);                   // r = b - A x -> V_0
+    }
     WT_LAUNCH(t, K_KRYLOV, sizeof(T) * (double)n, 2.0 * n,
               launch_dots<T>(V, nullptr, 0, 0, n, t.partial, t.nblk, 1, t.s));
     WT_LAUNCH(t, K_KRYLOV, 8.0 * t.nblk, 0.0,
@@ -735,7 +738,10 @@ int poisson_solve_device(wt_tank& t, const double* b, double* x, double tol, wt_
       // FP64 iterative refinement: r = b - A x (FP64); A e = r / |r| solved by
       // FP32 flexible GMRES with the FP32 V-cycle to inner_tol; x += |r| e.
       for (;;) {
-        apply_op<double>(t, 0, x, t.r64, b, false, tr);
+        {
+          ResidualScope rs(t);                                 // the true residual
+          apply_op<double>(t, 0, x, t.r64, b, false, tr);
+        }
         const double rn = norm2<double>(t, t.r64, n);      // |r| also left in stN[0]
         rel = rn / bn;
         if (rel <= tol || refinements >= t.opt.max_ir || its_total >= t.opt.max_it || !std::isfinite(rel))

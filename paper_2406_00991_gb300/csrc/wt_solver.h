@@ -62,7 +62,7 @@ template <typename T>
 inline void run_col_matrix(wt_tank& t, const T* M, int Mo, int Mi, const T* in, T* out, int ncols,
                            int acc) {
   WT_LAUNCH(t, K_COLMAT, (double)sizeof(T) * ncols * (Mi + Mo * (acc ? 2 : 1)),
-            2.0 * Mo * Mi * ncols, launch_col_matrix<T>(M, Mo, Mi, in, out, ncols, acc, t.s, t.opt.df64));
+            2.0 * Mo * Mi * ncols, launch_col_matrix<T>(M, Mo, Mi, in, out, ncols, acc, t.s, df_level(t)));
 }
 
 template <typename T> std::vector<Level<T>>& levels(wt_tank& t);

@@ -112,9 +112,10 @@ def test_df64_stages_parity(wt):
 @pytest.mark.parametrize("shape", [(256, 1, 24), (64, 64, 12)])
 def test_df64_attainable_residual(wt, shape):
     # the smallest relative residual an FP64 solve reaches (tolerance 1e-15,
-    # stopped by the iteration cap): FP64 arithmetic, double-float warp passes
-    # and columns (df64 = 1, the default), and double-float real-row passes
-    # too (df64 = 2); all well below the method's 1e-10
+    # stopped by the iteration cap): FP64 arithmetic; double-float kernels
+    # with the true residuals' row passes in FP64 (df64 = 1, the default:
+    # FP64's floor); double-float everywhere (df64 = 2); all well below the
+    # method's 1e-10
     Nx, Ny, Nz = shape
     L = 8.0
     g, h, ea, eb = curved(Nx, Ny, Nz, L)
@@ -129,4 +130,4 @@ def test_df64_attainable_residual(wt, shape):
         T.close()
     print("attainable FP64 relative residual %s: FP64 %.1e, df64=1 %.1e, df64=2 %.1e"
           % (shape, floor[0], floor[1], floor[2]))
-    assert floor[0] <= 1e-12 and floor[1] <= 1e-11 and floor[2] <= 1e-11
+    assert floor[0] <= 1e-12 and floor[1] <= 2e-12 and floor[2] <= 1e-11
