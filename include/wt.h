@@ -197,6 +197,17 @@ int wt_get_grid(const wt_tank* t, double* x, double* y, double* sigma);
  * (Nx, Ny, Nz) of level l, finest first (capacity >= 3 * 16). */
 int wt_get_levels(const wt_tank* t, int* nlevels, int* dims);
 
+/* The hierarchy wt_create would build for an Nx x Ny x Nz grid with the
+ * given coarsest_max (1..128), without a tank: host code only, no GPU or
+ * CUDA call, so a caller can size a problem before creating it.  Coarsening
+ * per Sec. 4.1 (Algorithm 1): halve Nx (and Ny) while Nx > Nz, halve Nz
+ * (rounding up, at least 2) while Nz > Nx, both when equal; stop at a level
+ * of at most coarsest_max unknowns or before Nx (Ny) < 4 or Nz < 2.  Output
+ * as wt_get_levels (capacity >= 3 * 16).  WT_EINVAL for sizes wt_create
+ * rejects; WT_ENOTSUP (levels still written) when the coarsest level has
+ * more than 128 unknowns, as wt_create reports. */
+int wt_levels_for(int Nx, int Ny, int Nz, int coarsest_max, int* nlevels, int* dims);
+
 /*
  * Model state: eta [Ny][Nx], u, v, w [Nz+1][Ny][Nx] (v ignored / returned as
  * zero when Ny = 1), time t.  wt_set_state also clears the 2N Runge-Kutta
@@ -321,6 +332,17 @@ int wt_relax(wt_tank* t, double x0, double x1, const double* eta_target, const d
  */
 int wt_stream_function_wave(wt_tank* t, int nwaves, double H, int nmodes, double time, double* eta,
                             double* u, double* w, double* c);
+/* The same stream-function solve without a tank: host code only, no GPU or
+ * CUDA call.  Wavenumber k, still depth d, height H, gravity g, nmodes
+ * (2..128), the same height limit and errors as wt_stream_function_wave.
+ * Host outputs (each may be NULL): params[3] = (c, Q, R) - phase speed
+ * (equal to the moving frame's current U), volume flux under the wave in
+ * that frame, Bernoulli constant; B[nmodes] = stream-function coefficients
+ * B_1..B_N of psi = -U y + sum_j B_j sinh(j k y) / cosh(j k d) cos(j k X),
+ * y the height above the bed; E[nmodes + 1] = cosine coefficients E_0..E_N
+ * of the surface, eta(X) = sum_j E_j cos(j k X) with X = x - c t. */
+int wt_stream_function_solve(double k, double d, double H, double g, int nmodes, double* params, double* B,
+                             double* E);
 
 /*
  * Solver autotuner.  Times wt_poisson_solve on this tank's problem

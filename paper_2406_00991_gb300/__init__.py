@@ -61,6 +61,7 @@ def _load():
         "wt_set_stream": [P, P],
         "wt_get_grid": [P, P, P, P],
         "wt_get_levels": [P, ctypes.POINTER(I), P],
+        "wt_levels_for": [I, I, I, I, ctypes.POINTER(I), P],
         "wt_set_state": [P, P, P, P, P, D],
         "wt_get_state": [P, P, P, P, P, ctypes.POINTER(D)],
         "wt_get_pressure": [P, P],
@@ -98,6 +99,7 @@ def _load():
         "wt_batch_autotune": [P, P, I, ctypes.POINTER(wt_options), ctypes.POINTER(D), ctypes.POINTER(D)],
         "wt_time_kernel": [P, P, P, I, I, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long)],
         "wt_stream_function_wave": [P, I, D, I, D, P, P, P, ctypes.POINTER(D)],
+        "wt_stream_function_solve": [D, D, D, D, I, P, P, P],
         "wt_relax": [P, D, D, P, P, P, P],
         "wt_last_error": [ctypes.c_char_p, ctypes.c_size_t],
     }
@@ -195,6 +197,14 @@ def wt_get_levels(t):
     return st, [tuple(dims[3 * l: 3 * l + 3]) for l in range(n.value)]
 
 
+def wt_levels_for(Nx, Ny, Nz, coarsest_max):
+    """Host only: the level sizes wt_create would build (no tank, no GPU)."""
+    n = ctypes.c_int()
+    dims = (ctypes.c_int * 48)()
+    st = _lib.wt_levels_for(int(Nx), int(Ny), int(Nz), int(coarsest_max), ctypes.byref(n), dims)
+    return st, [tuple(dims[3 * l: 3 * l + 3]) for l in range(n.value)]
+
+
 def wt_set_state(t, eta, u, v, w, time=0.0):
     return _lib.wt_set_state(t, _ptr(eta), _ptr(u), _ptr(v), _ptr(w), float(time))
 
@@ -269,6 +279,17 @@ def wt_stream_function_wave(t, nwaves, H, nmodes, time, eta, u, w):
     st = _lib.wt_stream_function_wave(t, int(nwaves), float(H), int(nmodes), float(time), _ptr(eta), _ptr(u),
                                       _ptr(w), ctypes.byref(c))
     return st, c.value
+
+
+def wt_stream_function_solve(k, d, H, g, nmodes):
+    """Host only: (status, (c, Q, R), B[nmodes], E[nmodes + 1]) of the
+    stream-function wave (no tank, no GPU)."""
+    params = np.zeros(3)
+    B = np.zeros(int(nmodes))
+    E = np.zeros(int(nmodes) + 1)
+    st = _lib.wt_stream_function_solve(float(k), float(d), float(H), float(g), int(nmodes),
+                                       params.ctypes.data, B.ctypes.data, E.ctypes.data)
+    return st, tuple(params), B, E
 
 
 def wt_relax(t, x0, x1, eta_target, u_target, v_target, w_target):

@@ -1280,6 +1280,50 @@ int wt_stream_function_wave(wt_tank* t, int nwaves, double H, int nmodes, double
   });
 }
 
+int wt_levels_for(int Nx, int Ny, int Nz, int coarsest_max, int* nlevels, int* dims) {
+  if (!nlevels) return fail(WT_EINVAL, "nlevels pointer is NULL");
+  if (!pow2(Nx) || Nx < 4 || Nx > 4096) return fail(WT_EINVAL, "Nx must be a power of two in [4, 4096]");
+  if (!(Ny == 1 || (pow2(Ny) && Ny >= 4 && Ny <= 1024)))
+    return fail(WT_EINVAL, "Ny must be 1 or a power of two in [4, 1024]");
+  if (Nz < 2 || Nz > 32) return fail(WT_EINVAL, "Nz must be in [2, 32]");
+  if (coarsest_max < 1 || coarsest_max > 128) return fail(WT_EINVAL, "coarsest_max must be in [1, 128]");
+  const auto lv = hierarchy(Nx, Ny, Nz, coarsest_max);
+  if ((int)lv.size() > kMaxLevels) return fail(WT_EINVAL, "too many multigrid levels");
+  *nlevels = (int)lv.size();
+  if (dims)
+    for (size_t l = 0; l < lv.size(); ++l)
+      for (int k = 0; k < 3; ++k) dims[3 * l + k] = lv[l][k];
+  const auto& c = lv.back();
+  const long nc = (long)c[0] * c[1] * (c[2] + 1);
+  if (nc > 128)
+    return fail(WT_ENOTSUP, "coarsest level has " + std::to_string(nc) +
+                                " unknowns; the dense FP64 solve takes at most 128");
+  return WT_OK;
+}
+
+int wt_stream_function_solve(double k, double d, double H, double g, int nmodes, double* params, double* B,
+                             double* E) {
+  if (!(k > 0) || !std::isfinite(k)) return fail(WT_EINVAL, "k must be positive");
+  if (!(d > 0) || !std::isfinite(d)) return fail(WT_EINVAL, "d must be positive");
+  if (!(g > 0) || !std::isfinite(g)) return fail(WT_EINVAL, "g must be positive");
+  if (nmodes < 2 || nmodes > 128) return fail(WT_EINVAL, "nmodes must be in [2, 128]");
+  if (!(H > 0) || !std::isfinite(H)) return fail(WT_EINVAL, "H must be positive");
+  if (H * k / (2.0 * M_PI) > 0.85 * 0.1401 * std::tanh(0.8863 * k * d))
+    return fail(WT_EINVAL, "H above 0.85 x the Battjes breaking steepness");
+  return guarded([&]() -> int {
+    SfWave W;
+    if (!sf_solve(k, d, H, g, nmodes, W)) return fail(WT_ENOCONV, "stream-function Newton iteration failed");
+    if (params) {
+      params[0] = W.c;
+      params[1] = W.Q;
+      params[2] = W.R;
+    }
+    if (B) std::copy(W.B.begin(), W.B.end(), B);
+    if (E) std::copy(W.E.begin(), W.E.end(), E);
+    return WT_OK;
+  });
+}
+
 int wt_apply_operator_transposed(wt_tank* t, const double* eta_a, const double* eta_b, const double* lam,
                                  double* out, int precision) {
   if (!t || !eta_a || !eta_b || !lam || !out) return fail(WT_EINVAL, "NULL argument");
