@@ -174,7 +174,10 @@ int wt_default_options(wt_options* opt);
  * the surface nodes (a stress-free surface), and the bed is no-slip
  * (Sec. 5.4): after every stage the velocity and its stage registers are
  * zero on the bottom nodes.  The
- * adjoint calls and the batched tanks cover nu = 0 only (WT_ENOTSUP).  On
+ * adjoint calls and the batched tanks cover nu = 0 only (WT_ENOTSUP).  The
+ * coarsest level must have at most 128 unknowns (WT_ENOTSUP otherwise): the
+ * coarsening halves Ny only together with Nx, so 3D tanks need Ny = Nx in
+ * practice (wt_levels_for shows the hierarchy without creating a tank).  On
  * success *out owns all device memory of the tank until wt_destroy.
  */
 int wt_create(int Nx, int Ny, int Nz, double L, double g, double nu,
