@@ -261,7 +261,7 @@ int wt_poisson_solve(wt_tank* t, const double* eta_a, const double* eta_b,
  */
 int wt_rk_stage(wt_tank* t, int k, double dt);
 
-/* nsteps full steps (5 stages each). */
+/* nsteps full steps of Eq. LSERK, five wt_rk_stage stages each. */
 int wt_step(wt_tank* t, double dt, int nsteps);
 
 /* Statistics of the last wt_rk_stage / wt_step: total Krylov iterations and
@@ -335,8 +335,8 @@ int wt_relax(wt_tank* t, double x0, double x1, const double* eta_target, const d
  */
 int wt_stream_function_wave(wt_tank* t, int nwaves, double H, int nmodes, double time, double* eta,
                             double* u, double* w, double* c);
-/* The same stream-function solve without a tank: host code only, no GPU or
- * CUDA call.  Wavenumber k, still depth d, height H, gravity g, nmodes
+/* The same stream-function solve (the Sec. 5.2 initial condition) without a
+ * tank: host code only, no GPU or CUDA call.  Wavenumber k, still depth d, height H, gravity g, nmodes
  * (2..128), the same height limit and errors as wt_stream_function_wave.
  * Host outputs (each may be NULL): params[3] = (c, Q, R) - phase speed
  * (equal to the moving frame's current U), volume flux under the wave in
@@ -384,7 +384,10 @@ int wt_autotune_step(wt_tank* t, double dt, int reps, wt_options* best, double* 
 int wt_autotune_cache(const char* path);
 
 /*
- * Batches of independent 2D tanks of uneven size, advanced together by one
+ * Batches of independent 2D tanks of uneven size.  The paper advances one
+ * tank at a time; the batch has no counterpart there, and each of its tanks
+ * takes the step of wt_step (Sec. 3.1-3.3, the solver of Sec. 4).  The tanks
+ * advance together by one
  * persistent kernel launch per wt_batch_step: one CTA owns one tank and runs
  * all of its Runge-Kutta stages (free surface, metric, smoother set-up,
  * forcing, mixed-stage Poisson solve - FP64 flexible GMRES with the FP32 or
