@@ -211,6 +211,19 @@ int wt_get_levels(const wt_tank* t, int* nlevels, int* dims);
  * more than 128 unknowns, as wt_create reports. */
 int wt_levels_for(int Nx, int Ny, int Nz, int coarsest_max, int* nlevels, int* dims);
 
+/* The sigma-direction matrices the library builds on the host for an
+ * (Nz+1)-node CGL column and a coarser Nzc (2 <= Nzc <= Nz <= 32), without a
+ * tank: host code only, no GPU or CUDA call.  Row-major host outputs (each
+ * may be NULL): D [Nz+1][Nz+1] = d/dsigma (Sec. 3.5, 2 x the CGL matrix on
+ * xi = 2 sigma - 1); F [Nz+1][Nz+1] = the Chebyshev exponential filter
+ * (Sec. 3.6: modal transform, mode m damped by exp(-36 ((m - Nc) / (Nz + 1
+ * - Nc))^2) above Nc = floor(0.9 Nz), evaluation); R [Nzc+1][Nz+1] = the
+ * restriction's Chebyshev truncation (Sec. 4.2; bc_transfer 0: surface and
+ * bottom rows injected, the library's default; 1: the whole column
+ * truncated); P [Nz+1][Nzc+1] = the prolongation (the coarse interpolant at
+ * the fine nodes).  Node m = 0 is the surface. */
+int wt_sigma_matrices(int Nz, int Nzc, int bc_transfer, double* D, double* F, double* R, double* P);
+
 /*
  * Model state: eta [Ny][Nx], u, v, w [Nz+1][Ny][Nx] (v ignored / returned as
  * zero when Ny = 1), time t.  wt_set_state also clears the 2N Runge-Kutta

@@ -62,6 +62,7 @@ def _load():
         "wt_get_grid": [P, P, P, P],
         "wt_get_levels": [P, ctypes.POINTER(I), P],
         "wt_levels_for": [I, I, I, I, ctypes.POINTER(I), P],
+        "wt_sigma_matrices": [I, I, I, P, P, P, P],
         "wt_set_state": [P, P, P, P, P, D],
         "wt_get_state": [P, P, P, P, P, ctypes.POINTER(D)],
         "wt_get_pressure": [P, P],
@@ -203,6 +204,17 @@ def wt_levels_for(Nx, Ny, Nz, coarsest_max):
     dims = (ctypes.c_int * 48)()
     st = _lib.wt_levels_for(int(Nx), int(Ny), int(Nz), int(coarsest_max), ctypes.byref(n), dims)
     return st, [tuple(dims[3 * l: 3 * l + 3]) for l in range(n.value)]
+
+
+def wt_sigma_matrices(Nz, Nzc, bc_transfer=0):
+    """Host only: (status, D, F, R, P), the library's sigma-direction
+    derivative, filter, restriction and prolongation matrices (no GPU)."""
+    M1, Mc = max(int(Nz) + 1, 1), max(int(Nzc) + 1, 1)     # sizes the library rejects write nothing
+    D, F = np.zeros((M1, M1)), np.zeros((M1, M1))
+    R, Pm = np.zeros((Mc, M1)), np.zeros((M1, Mc))
+    st = _lib.wt_sigma_matrices(int(Nz), int(Nzc), int(bc_transfer), D.ctypes.data, F.ctypes.data,
+                                R.ctypes.data, Pm.ctypes.data)
+    return st, D, F, R, Pm
 
 
 def wt_set_state(t, eta, u, v, w, time=0.0):

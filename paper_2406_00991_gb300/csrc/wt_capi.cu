@@ -122,6 +122,18 @@ double filter_resp(int i, int N, int Nc) {
   const double r = double(i - Nc) / double(N + 1 - Nc);
   return std::exp(-36.0 * r * r);
 }
+// Nodal matrix of the Chebyshev exponential filter (Sec. 3.6): modal
+// transform, damping of mode m by F_S(m, Nc = floor(0.9 Nz)), evaluation.
+std::vector<double> cheb_filter(int Nz) {
+  const int M1 = Nz + 1;
+  auto W = cheb_modal(Nz);
+  auto x = cgl_xi(Nz);
+  const int Nc = (int)std::floor(0.9 * Nz);
+  std::vector<double> VF(M1 * M1);
+  for (int i = 0; i < M1; ++i)
+    for (int k = 0; k < M1; ++k) VF[i * M1 + k] = chebT(k, x[i]) * filter_resp(k, Nz, Nc);
+  return matmul(VF, W, M1, M1, M1);
+}
 // Dense periodic first derivative (Nyquist coefficient zero) and its square.
 std::vector<double> fourier_D_and_DD(int N, double L) {
   std::vector<double> D(N * N, 0.0);
@@ -791,14 +803,7 @@ int wt_create(int Nx, int Ny, int Nz, double L, double g, double nu, const doubl
         for (int i = 0; i <= Ny / 2; ++i) fy[i] = filter_resp(i, Ny / 2, Ny / 4);
       t->filt_x = upload<double>(ar, fx);
       t->filt_y = upload<double>(ar, fy);
-      const int M1 = Nz + 1;
-      auto W = cheb_modal(Nz);
-      auto x = cgl_xi(Nz);
-      const int Nc = (int)std::floor(0.9 * Nz);
-      std::vector<double> VF(M1 * M1);
-      for (int i = 0; i < M1; ++i)
-        for (int k = 0; k < M1; ++k) VF[i * M1 + k] = chebT(k, x[i]) * filter_resp(k, Nz, Nc);
-      t->Fcheb = upload<double>(ar, matmul(VF, W, M1, M1, M1));
+      t->Fcheb = upload<double>(ar, cheb_filter(Nz));
     }
     // Krylov storage for restart <= 31, state and stage arrays
     t->V64 = ar.alloc<double>((size_t)32 * n);
@@ -1299,6 +1304,31 @@ int wt_levels_for(int Nx, int Ny, int Nz, int coarsest_max, int* nlevels, int* d
     return fail(WT_ENOTSUP, "coarsest level has " + std::to_string(nc) +
                                 " unknowns; the dense FP64 solve takes at most 128");
   return WT_OK;
+}
+
+int wt_sigma_matrices(int Nz, int Nzc, int bc_transfer, double* D, double* F, double* R, double* P) {
+  if (Nz < 2 || Nz > 32) return fail(WT_EINVAL, "Nz must be in [2, 32]");
+  if (Nzc < 2 || Nzc > Nz) return fail(WT_EINVAL, "Nzc must be in [2, Nz]");
+  if (bc_transfer != 0 && bc_transfer != 1) return fail(WT_EINVAL, "bc_transfer is 0 or 1");
+  return guarded([&]() -> int {
+    if (D) {
+      const auto m = cheb_D(Nz);
+      std::copy(m.begin(), m.end(), D);
+    }
+    if (F) {
+      const auto m = cheb_filter(Nz);
+      std::copy(m.begin(), m.end(), F);
+    }
+    if (R) {
+      const auto m = cheb_restrict(Nz, Nzc, bc_transfer == 0);
+      std::copy(m.begin(), m.end(), R);
+    }
+    if (P) {
+      const auto m = cheb_prolong(Nzc, Nz);
+      std::copy(m.begin(), m.end(), P);
+    }
+    return WT_OK;
+  });
 }
 
 int wt_stream_function_solve(double k, double d, double H, double g, int nmodes, double* params, double* B,

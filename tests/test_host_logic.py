@@ -148,3 +148,48 @@ def test_stream_function_solve_rejects(w):
                  (k, 1.0, 0.0, G, 16), (k, 1.0, 0.01, 0.0, 16)):
         st, *_ = w.wt_stream_function_solve(*args)
         assert st == w.WT_EINVAL, args
+
+
+SIGMA_CASES = [(Nz, Nzc) for Nz in (2, 3, 4, 6, 8, 12, 16, 17, 24, 32) for Nzc in sorted({2, (Nz + 1) // 2, Nz})
+               if 2 <= Nzc <= Nz]
+
+
+def test_sigma_matrices_match_the_oracle(w):
+    from oracle import spectral as sp
+    for Nz, Nzc in SIGMA_CASES:
+        for bc in (0, 1):
+            st, D, F, R, P = w.wt_sigma_matrices(Nz, Nzc, bc)
+            assert st == w.WT_OK, w.wt_last_error()
+            D0 = sp.cheb_diff_matrix_sigma(Nz)
+            assert np.abs(D - D0).max() <= 1e-12 * np.abs(D0).max(), (Nz, "D")
+            F0 = sp.cheb_filter_matrix(Nz)
+            assert np.abs(F - F0).max() <= 1e-12, (Nz, "F")
+            R0 = pmg.restrict_sigma_matrix(Nz, Nzc, "inject" if bc == 0 else "paper")
+            assert np.abs(R - R0).max() <= 1e-12, (Nz, Nzc, bc, "R")
+            P0 = sp.cheb_prolong_matrix(Nzc, Nz)
+            assert np.abs(P - P0).max() <= 1e-12, (Nz, Nzc, "P")
+
+
+def test_sigma_matrices_on_polynomials(w):
+    # independent of the oracle: d/dsigma is exact on polynomials of degree
+    # <= Nz; the filter keeps degrees <= floor(0.9 Nz); prolongation then
+    # restriction is the identity on the coarse nodes (both forms); the
+    # prolongation reproduces a coarse-degree polynomial at the fine nodes
+    for Nz, Nzc in SIGMA_CASES:
+        st, D, F, R, P = w.wt_sigma_matrices(Nz, Nzc, 0)
+        st1, _, _, R1, _ = w.wt_sigma_matrices(Nz, Nzc, 1)
+        assert st == st1 == w.WT_OK
+        s = 0.5 * (np.cos(np.pi * np.arange(Nz + 1) / Nz) + 1.0)
+        sc = 0.5 * (np.cos(np.pi * np.arange(Nzc + 1) / Nzc) + 1.0)
+        for deg in range(Nz + 1):
+            assert np.abs(D @ s ** deg - deg * s ** max(deg - 1, 0)).max() <= 1e-10 * max(1, deg * deg), (Nz, deg)
+        for deg in range(int(np.floor(0.9 * Nz)) + 1):
+            assert np.abs(F @ s ** deg - s ** deg).max() <= 1e-12, (Nz, deg)
+        assert np.abs(R @ P - np.eye(Nzc + 1)).max() <= 1e-12, (Nz, Nzc)
+        assert np.abs(R1 @ P - np.eye(Nzc + 1)).max() <= 1e-12, (Nz, Nzc)
+        for deg in range(Nzc + 1):
+            assert np.abs(P @ sc ** deg - s ** deg).max() <= 1e-12, (Nz, Nzc, deg)
+    assert w.wt_sigma_matrices(33, 8)[0] == w.WT_EINVAL
+    assert w.wt_sigma_matrices(16, 17)[0] == w.WT_EINVAL
+    assert w.wt_sigma_matrices(16, 1)[0] == w.WT_EINVAL
+    assert w.wt_sigma_matrices(16, 8, 2)[0] == w.WT_EINVAL
