@@ -590,11 +590,8 @@ void precondition<double>(wt_tank& t, const double* v, double* z, bool pre32, bo
   WT_LAUNCH(t, K_KRYLOV, 12.0 * n, 0.0, (launch_convert<float, double>(t.e32, z, n, nullptr, 0, t.s)));
 }
 
-// Right-preconditioned flexible GMRES(m) on the finest level of precision T:
-// x is the initial guess and the result; returns the last true relative
-// residual ||b - A x|| / bnorm computed in precision T.  With pre32 the
-// preconditioner is the FP32 V-cycle: every Arnoldi step then refines the
-// FP64 iterate with an FP32 correction (flexible Krylov iterative refinement).
+// Drop every captured Arnoldi-step graph (new options, possibly a new
+// hierarchy, or the tank's end): the next solve captures them again.
 void destroy_graphs(wt_tank& t) {
   for (auto& v : t.graphs) {
     for (auto& g : v)
