@@ -147,7 +147,10 @@ typedef struct wt_options {
                         CTA-per-row passes in FP64, so an FP64 solve reaches
                         FP64's attainable residual; the data stay FP64 in
                         memory (measured operator error 2e-15 .. 1e-14 of
-                        max |Ap| against 1e-15 in FP64).  2: double-float in
+                        max |Ap| against 1e-15 in FP64).  Double-float has
+                        float's exponent range: fields whose values are all
+                        below about 1e-30 or above 1e38 in magnitude need
+                        df64 = 0.  2: double-float in
                         the true residuals too (attainable residual about
                         1e-11 on 1,024-point rows).  0: FP64 arithmetic      */
   int spectral_min;  /* smoother 1 or 2: levels with fewer unknowns than this

@@ -14,7 +14,10 @@
 // double-float (about ten times the instructions of the FP64 one) still runs
 // several times faster than in FP64.  The addition is the "sloppy" form: its
 // error is bounded by about 2^-47 (|a| + |b|), a normwise bound, which is what
-// the error analysis of an FFT (a sum of such butterflies) needs.
+// the error analysis of an FFT (a sum of such butterflies) needs.  The
+// exponent range is float's: a field whose values all lie below about 1e-30
+// (where lo becomes subnormal) or above about 1e38 in magnitude loses its
+// precision or overflows; the fields of the method are of order one.
 #pragma once
 
 #include "wt_dev.cuh"
