@@ -38,7 +38,7 @@ def _t(a):
 
 
 class Grid2:
-    """2D grid: Nx Fourier nodes (x, last axis), Nz+1 CGL nodes (sigma, first axis)."""
+    """2D grid (Sec. 3.4): Nx Fourier nodes (x, last axis), Nz+1 CGL nodes (sigma, first axis)."""
 
     def __init__(self, Nx, Nz, L):
         self.Nx, self.Nz, self.L = int(Nx), int(Nz), float(L)
@@ -74,8 +74,9 @@ def div(g, m, Gx, Gz):
 
 
 def apply_A(g, ma, mb, p):
-    """A_{a,b} p for p of shape (..., M1, Nx): interior Div_a Grad_b p, surface
-    row p, bottom row h_x G_x + G_z."""
+    """A_{a,b} p (Eq. poissonp, bcpd, bcpdneu; Eq. 1_chain) for p of shape
+    (..., M1, Nx): interior Div_a Grad_b p, surface row p, bottom row
+    h_x G_x + G_z."""
     Gx, Gz = grad(g, mb, p)
     out = div(g, ma, Gx, Gz)
     bot = (mb["hx"] * Gx[..., -1, :] + Gz[..., -1, :]).unsqueeze(-2)
@@ -83,14 +84,15 @@ def apply_A(g, ma, mb, p):
 
 
 def assemble_A(g, ma, mb):
-    """Dense A_{a,b} (n x n, n = M1 Nx, row-major (m, x) ordering)."""
+    """Dense A_{a,b} of Eq. poissonp (n x n, n = M1 Nx, row-major (m, x) ordering)."""
     n = g.M1 * g.Nx
     E = torch.eye(n, dtype=F64).reshape(n, g.M1, g.Nx)
     return apply_A(g, ma, mb, E).reshape(n, n).T
 
 
 def apply_AT(g, ma, mb, lam):
-    """A_{a,b}^T lam through the dense matrix (the plain definition)."""
+    """A_{a,b}^T lam through the dense matrix (the plain definition; the paper
+    has no adjoint, this is the transpose of the Eq. poissonp operator)."""
     return (assemble_A(g, ma, mb).T @ lam.reshape(-1)).reshape(g.M1, g.Nx)
 
 
@@ -132,7 +134,8 @@ def stage(g, h, st, k, dt, grav=9.81, linear=False, filt=False):
 
 
 def step(g, h, eta, u, w, dt, **kw):
-    """One full step from (eta, u, w); the 2N registers start at zero (alpha_1 = 0)."""
+    """One full step of Eq. LSERK from (eta, u, w); the 2N registers start at
+    zero (alpha_1 = 0)."""
     st = (eta, u, w, torch.zeros_like(eta), torch.zeros_like(u), torch.zeros_like(w))
     for k in range(1, STAGES + 1):
         st = stage(g, h, st, k, dt, **kw)
@@ -140,7 +143,7 @@ def step(g, h, eta, u, w, dt, **kw):
 
 
 def run(g, h, eta, u, w, dt, nsteps, gauges, **kw):
-    """Gauge series: eta after steps 1..nsteps at the gauge node indices."""
+    """Gauge series: eta after steps 1..nsteps (Eq. LSERK) at the gauge node indices."""
     out = []
     for _ in range(nsteps):
         eta, u, w = step(g, h, eta, u, w, dt, **kw)
@@ -153,7 +156,9 @@ def gauge_loss(series, target, dt):
 
 
 def loss_and_gradient(g, h, eta0, u0, w0, dt, nsteps, gauges, target, **kw):
-    """J and dJ/dh, dJ/d(eta0, u0, w0) by reverse-mode differentiation."""
+    """J and dJ/dh, dJ/d(eta0, u0, w0) by reverse-mode differentiation of the
+    discrete steps (the paper has no adjoint: the derivative of Sec. 3.1-3.3
+    as discretised here)."""
     h = _t(h).requires_grad_(True)
     eta0 = _t(eta0).requires_grad_(True)
     u0 = _t(u0).requires_grad_(True)
@@ -165,8 +170,8 @@ def loss_and_gradient(g, h, eta0, u0, w0, dt, nsteps, gauges, target, **kw):
 
 
 def step_vjp(g, h, eta, u, w, dt, lam_eta, lam_u, lam_w, **kw):
-    """(d step / d(state, h))^T applied to (lam_eta, lam_u, lam_w): the
-    adjoint of one step, returning (lam_eta, lam_u, lam_w) at the step start
+    """(d step / d(state, h))^T applied to (lam_eta, lam_u, lam_w) (no paper
+    passage: the derivative of one Eq. LSERK step): the adjoint of one step, returning (lam_eta, lam_u, lam_w) at the step start
     and the contribution to dJ/dh."""
     h = _t(h).requires_grad_(True)
     s = [_t(a).requires_grad_(True) for a in (eta, u, w)]

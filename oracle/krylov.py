@@ -16,7 +16,8 @@ from . import pmg
 
 
 def gmres(apply_A, b, x0=None, precond=None, tol=1e-12, restart=30, maxit=1000):
-    """Right-preconditioned restarted GMRES; returns (x, iterations, relres_history)."""
+    """Right-preconditioned restarted GMRES (Sec. 4.4); returns (x, iterations,
+    relres_history)."""
     shape = b.shape
     bv = b.ravel()
     nb = np.linalg.norm(bv)
@@ -71,7 +72,8 @@ def gmres(apply_A, b, x0=None, precond=None, tol=1e-12, restart=30, maxit=1000):
 
 
 def solve_dense(level, b):
-    """Plain definition of the discrete solution: dense LU of A_{a,b} (tiny sizes)."""
+    """Plain definition of the discrete solution of Eq. poissonp: dense LU of
+    A_{a,b} (tiny sizes)."""
     return np.linalg.solve(level.dense, b.ravel()).reshape(level.grid.shape)
 
 

@@ -34,7 +34,8 @@ from . import spectral as sp
 
 
 class Grid:
-    """Tensor grid of one level: Nx (x) by Ny (y) Fourier nodes, Nz+1 CGL nodes."""
+    """Tensor grid of one level (Sec. 3.4): Nx (x) by Ny (y) Fourier nodes,
+    Nz+1 CGL nodes."""
 
     def __init__(self, Nx, Ny, Nz, L):
         self.Nx, self.Ny, self.Nz, self.L = int(Nx), int(Ny), int(Nz), float(L)
@@ -114,7 +115,8 @@ def apply_A(grid, geo_a, geo_b, p):
 
 
 def assemble_A(grid, geo_a, geo_b):
-    """Dense matrix of A_{a,b} by applying it to every unit vector (tiny sizes)."""
+    """Dense matrix of A_{a,b} (Eq. poissonp) by applying it to every unit
+    vector (tiny sizes)."""
     n = grid.n
     A = np.zeros((n, n))
     e = np.zeros(n)
@@ -126,7 +128,8 @@ def assemble_A(grid, geo_a, geo_b):
 
 
 def column_blocks(grid, geo_a, geo_b):
-    """Diagonal (Nz+1)x(Nz+1) block A_rr of A_{a,b} for every vertical column r.
+    """Diagonal (Nz+1)x(Nz+1) block A_rr of A_{a,b} for every vertical column r
+    (the blocks of the Sec. 4.3 block relaxation).
 
     Written out from the composite operator: the x- and y-derivative matrices
     have a zero diagonal, so within one column only the second-derivative

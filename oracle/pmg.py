@@ -55,7 +55,8 @@ def coarsen(Nx, Ny, Nz):
 
 
 def hierarchy(Nx, Ny, Nz, coarsest_max=256):
-    """Level sizes, finest first, ending at the coarsest (direct-solve) level."""
+    """Level sizes (Sec. 4.1 coarsening), finest first, ending at the coarsest
+    (direct-solve) level."""
     levels = [(Nx, Ny, Nz)]
     while True:
         nx, ny, nz = levels[-1]
@@ -69,7 +70,7 @@ def hierarchy(Nx, Ny, Nz, coarsest_max=256):
 
 
 def restrict_surface(f, Nx_c, Ny_c):
-    """Fourier truncation of a surface array (Ny, Nx) to (Ny_c, Nx_c)."""
+    """Fourier truncation (Sec. 4.2) of a surface array (Ny, Nx) to (Ny_c, Nx_c)."""
     g = sp.fourier_resample(f, Nx_c, axis=1)
     if g.shape[0] > 1:
         g = sp.fourier_resample(g, Ny_c, axis=0)
@@ -77,7 +78,7 @@ def restrict_surface(f, Nx_c, Ny_c):
 
 
 class Level:
-    """One grid of the hierarchy with its rediscretised operator A_{a,b}."""
+    """One grid of the hierarchy (Sec. 4.1) with its rediscretised operator A_{a,b}."""
 
     def __init__(self, Nx, Ny, Nz, L, h, eta_a, eta_b):
         self.grid = Grid(Nx, Ny, Nz, L)
@@ -129,7 +130,8 @@ def restrict_sigma_matrix(Nz_f, Nz_c, bc_transfer="inject"):
 
 
 def restrict(fine, coarse, r, bc_transfer="inject"):
-    """R: fine residual -> coarse grid (Fourier truncation, then Chebyshev)."""
+    """R (Sec. 4.2, Algorithm 1): fine residual -> coarse grid (Fourier
+    truncation, then Chebyshev)."""
     g = sp.fourier_resample(r, coarse.Nx, axis=2)
     if fine.Ny > 1:
         g = sp.fourier_resample(g, coarse.Ny, axis=1)
@@ -138,7 +140,8 @@ def restrict(fine, coarse, r, bc_transfer="inject"):
 
 
 def prolong(coarse, fine, e):
-    """P: coarse correction -> fine grid (Chebyshev interpolation, then Fourier zero-pad)."""
+    """P (Sec. 4.2, Algorithm 1): coarse correction -> fine grid (Chebyshev
+    interpolation, then Fourier zero-pad)."""
     P = sp.cheb_prolong_matrix(coarse.Nz, fine.Nz)
     g = np.tensordot(P, e, axes=(1, 0))
     if fine.Ny > 1:
@@ -147,7 +150,8 @@ def prolong(coarse, fine, e):
 
 
 def nyquist_parts(grid, r):
-    """Split r into parts by x- and y-Nyquist content: {(ix, iy): r_part}, where
+    """Split r into parts by x- and y-Nyquist content (for the Sec. 4.3 block
+    smoother with the Nyquist reading): {(ix, iy): r_part}, where
     ix = 1 marks the projection on (-1)^jx along x (likewise iy along y)."""
     def proj(f, axis):
         N = f.shape[axis]
@@ -171,7 +175,8 @@ def nyquist_parts(grid, r):
 
 
 def nyquist_blocks(level, ix, iy):
-    """Column blocks with the x- (ix=1) and/or y- (iy=1) diagonal term removed."""
+    """Column blocks (Sec. 4.3) with the x- (ix=1) and/or y- (iy=1) diagonal
+    term removed."""
     g = level.grid
     def diag2(N):
         if N == 1:
@@ -186,7 +191,8 @@ def nyquist_blocks(level, ix, iy):
 
 
 def block_jacobi(level, x, f, omega, nyquist_split=True):
-    """One damped block-Jacobi sweep: x <- x + omega A_rr^{-1} (f - A x)_r for all r
+    """One damped block-Jacobi sweep (Sec. 4.3 block relaxation, Jacobi form):
+    x <- x + omega A_rr^{-1} (f - A x)_r for all r
     (with ``nyquist_split`` the Nyquist parts use their own column blocks)."""
     r = f - level.apply(x)
     parts = nyquist_parts(level.grid, r) if nyquist_split else {(0, 0): r}
@@ -234,7 +240,8 @@ def reference_column_matrix(grid, kappa2, dref):
 
 
 def reference_kappa2(grid):
-    """kappa_x^2 + kappa_y^2 of every (y, x) Fourier mode, numpy FFT order,
+    """kappa_x^2 + kappa_y^2 (Sec. 3.4 wavenumbers) of every (y, x) Fourier mode,
+    numpy FFT order,
     with the Nyquist wavenumber of each axis counted as 0."""
     def k2(N):
         if N == 1:
@@ -273,7 +280,7 @@ def spectral_smooth(level, x, f, omega_s, dref, transpose=False):
 
 
 def smooth(level, x, f, sweeps, smoother, omega, omega_s=1.0, dref=None):
-    """``sweeps`` sweeps of the chosen smoother: "jacobi" (damped block-Jacobi
+    """``sweeps`` sweeps of the chosen smoother (Sec. 4.3): "jacobi" (damped block-Jacobi
     with the Nyquist split), "jacobi-plain", "gs" (forward block
     Gauss-Seidel), "spectral" (mean-depth spectral smoother of depth dref),
     "jacobi+spectral" (a block-Jacobi sweep then a spectral sweep)."""

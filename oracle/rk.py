@@ -62,7 +62,8 @@ STAGES = 5
 
 
 def butcher_from_2n(alpha, beta):
-    """Butcher tableau (a_ij, b_j, c_i) implied by the 2N-storage recursion.
+    """Butcher tableau (a_ij, b_j, c_i) implied by the 2N-storage recursion
+    (Eq. LSERK).
 
     K^k = sum_{j<=k} (prod_{l=j+1..k} alpha_l) dt f_j and
     y^(k) = y^n + sum_{i<=k} beta_i K^i, so stage k (evaluated at y^(k-1)) has
@@ -87,7 +88,7 @@ def butcher_from_2n(alpha, beta):
 
 
 class State:
-    """eta (Ny, Nx); u, v, w (Nz+1, Ny, Nx); the 2N registers K; last p_D."""
+    """eta (Ny, Nx); u, v, w (Nz+1, Ny, Nx); the 2N registers K of Eq. LSERK; last p_D."""
 
     def __init__(self, grid, eta, u, v, w):
         self.eta = np.array(eta, dtype=np.float64).reshape(grid.Ny, grid.Nx)
@@ -107,7 +108,8 @@ class State:
 
 
 class Tank:
-    """Problem definition: grid, bathymetry h(x, y) > 0, gravity, viscosity, options."""
+    """Problem definition (Sec. 2): grid, bathymetry h(x, y) > 0, gravity,
+    viscosity, options."""
 
     def __init__(self, Nx, Ny, Nz, L, h, g=9.81, nu=0.0, linear=False, filter=False,
                  tol=1e-12, solver="pmg", coarsest_max=256, nu1=2, nu2=2, omega=0.4,
@@ -211,7 +213,7 @@ def stage(tank, st, k, dt):
 
 
 def step(tank, st, dt):
-    """One full LSERK step (all five stages)."""
+    """One full step of Eq. LSERK (all five stages)."""
     for k in range(1, STAGES + 1):
         stage(tank, st, k, dt)
     st.t += dt
@@ -230,7 +232,8 @@ def relaxation_weight(x, x0, x1):
 
 
 def relax(tank, st, x0, x1, eta_t=None, u_t=None, v_t=None, w_t=None):
-    """q <- (1 - w) q + w q_target for the given targets (columns of the zone)."""
+    """Relaxation zone (Sec. 5.5): q <- (1 - w) q + w q_target for the given
+    targets (columns of the zone)."""
     wgt = relaxation_weight(tank.grid.x, x0, x1)[None, :]
     if eta_t is not None:
         st.eta = (1.0 - wgt) * st.eta + wgt * eta_t
@@ -242,7 +245,8 @@ def relax(tank, st, x0, x1, eta_t=None, u_t=None, v_t=None, w_t=None):
 
 
 def divergence_residual(tank, st):
-    """Interior Div u and bottom n . u of the current state (geometry of st.eta)."""
+    """Interior Div u and bottom n . u of the current state (geometry of st.eta):
+    the incompressibility and bed conditions the projection of Eq. rkforc1 enforces."""
     gr = tank.grid
     geo = Geometry(gr, tank.h, np.zeros_like(st.eta) if tank.linear else st.eta)
     dv = div(gr, geo, (st.u, st.v, st.w))

@@ -31,7 +31,7 @@ def fourier_nodes(N, L):
 
 
 def fourier_wavenumbers(N, L):
-    """Wavenumbers kappa_n = 2 pi n / L in numpy FFT order (n = 0, 1, .., -1)."""
+    """Wavenumbers kappa_n = 2 pi n / L (Sec. 3.4) in numpy FFT order (n = 0, 1, .., -1)."""
     return 2.0 * np.pi * np.fft.fftfreq(N, d=1.0 / N) / L
 
 
@@ -57,7 +57,7 @@ def fourier_derivative(f, L, axis, order=1):
 
 
 def fourier_diff_matrix(N, L):
-    """Dense first-derivative matrix of the periodic grid (closed form).
+    """Dense first-derivative matrix of the periodic grid (Sec. 3.5, closed form).
 
     D_ij = 1/2 (-1)^(i-j) cot((i-j) h / 2), D_ii = 0, h = 2 pi / N, scaled by
     2 pi / L.  For even N this is exactly the spectral derivative with the
@@ -116,7 +116,8 @@ def fourier_filter(f, axis, alpha=36.0, s=2):
 
 
 def filter_response(i, N, Nc, alpha=36.0, s=2):
-    """F_S(i, Nc, alpha, s): 1 for i <= Nc, exp(-alpha ((i-Nc)/(N+1-Nc))^s) above."""
+    """F_S(i, Nc, alpha, s) of Sec. 3.6 (damping sign): 1 for i <= Nc,
+    exp(-alpha ((i-Nc)/(N+1-Nc))^s) above."""
     i = np.asarray(i, dtype=np.float64)
     out = np.ones_like(i)
     hi = i > Nc
@@ -127,17 +128,17 @@ def filter_response(i, N, Nc, alpha=36.0, s=2):
 # ------------------------------------------------------------ Chebyshev (sigma)
 
 def cgl_xi(Nz):
-    """CGL nodes xi_m = cos(m pi / Nz), m = 0..Nz (xi_0 = 1)."""
+    """CGL nodes xi_m = cos(m pi / Nz), m = 0..Nz (xi_0 = 1) (Sec. 3.4, as read)."""
     return np.cos(np.pi * np.arange(Nz + 1) / Nz)
 
 
 def cgl_sigma(Nz):
-    """sigma_m = (xi_m + 1)/2 in [0, 1]; m = 0 is the free surface."""
+    """sigma_m = (xi_m + 1)/2 in [0, 1] (Sec. 3.4); m = 0 is the free surface."""
     return 0.5 * (cgl_xi(Nz) + 1.0)
 
 
 def cheb_diff_matrix_xi(Nz):
-    """Textbook CGL differentiation matrix on [-1, 1].
+    """Textbook CGL differentiation matrix on [-1, 1] (Sec. 3.5).
 
     D_ij = (c_i / c_j) (-1)^(i+j) / (xi_i - xi_j) for i != j, c_0 = c_Nz = 2,
     else 1; the diagonal is the negative row sum (exact on constants).
@@ -157,7 +158,7 @@ def cheb_diff_matrix_xi(Nz):
 
 
 def cheb_diff_matrix_sigma(Nz):
-    """d/dsigma on the CGL nodes: sigma = (xi+1)/2, so D_sigma = 2 D_xi."""
+    """d/dsigma on the CGL nodes (Sec. 3.5): sigma = (xi+1)/2, so D_sigma = 2 D_xi."""
     return 2.0 * cheb_diff_matrix_xi(Nz)
 
 
@@ -167,7 +168,7 @@ def cheb_T(m, xi):
 
 
 def cheb_vandermonde(Nz, xi=None):
-    """V[j, m] = T_m(xi_j) on the given points (default: the CGL nodes)."""
+    """V[j, m] = T_m(xi_j) (Sec. 3.4 basis) on the given points (default: the CGL nodes)."""
     if xi is None:
         xi = cgl_xi(Nz)
     m = np.arange(Nz + 1)[None, :]
@@ -175,7 +176,7 @@ def cheb_vandermonde(Nz, xi=None):
 
 
 def cheb_nodal_to_modal(f, axis=0):
-    """Modal Chebyshev coefficients from CGL nodal values (V^{-1} f)."""
+    """Modal Chebyshev coefficients (Sec. 3.4) from CGL nodal values (V^{-1} f)."""
     Nz = f.shape[axis] - 1
     V = cheb_vandermonde(Nz)
     fm = np.moveaxis(f, axis, 0)
@@ -221,7 +222,7 @@ def cheb_prolong_matrix(Nz_c, Nz_f):
 
 
 def cheb_filter_matrix(Nz, alpha=36.0, s=2):
-    """Nodal matrix of the Chebyshev exponential filter: V diag(F_S(m)) V^{-1}."""
+    """Nodal matrix of the Chebyshev exponential filter (Sec. 3.6): V diag(F_S(m)) V^{-1}."""
     V = cheb_vandermonde(Nz)
     resp = filter_response(np.arange(Nz + 1), Nz, int(np.floor(0.9 * Nz)), alpha, s)
     return V @ np.diag(resp) @ np.linalg.inv(V)

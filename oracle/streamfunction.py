@@ -35,7 +35,8 @@ import numpy as np
 
 
 class Wave:
-    """A solved stream-function wave: k, d, H, g, c, U, Q, R, B (1..N), eta_m."""
+    """A solved stream-function wave (the Sec. 5.2 initial condition): k, d, H,
+    g, c, U, Q, R, B (1..N), eta_m."""
 
     def __init__(self, k, d, H, g, N, U, Q, R, eta, B):
         self.k, self.d, self.H, self.g, self.N = k, d, H, g, N
@@ -59,8 +60,8 @@ class Wave:
         return np.cos(np.multiply.outer(X, j * self.k)) @ self.E
 
     def velocity(self, x, z, t=0.0):
-        """Fixed-frame (u, w) at horizontal position x and height z above the
-        still water level (broadcast together)."""
+        """Fixed-frame (u, w) of the Sec. 5.2 wave at horizontal position x and
+        height z above the still water level (broadcast together)."""
         X = np.asarray(x, dtype=np.float64) - self.c * t
         y = np.asarray(z, dtype=np.float64) + self.d
         X, y = np.broadcast_arrays(X, y)
@@ -107,8 +108,9 @@ def _residual(z, k, d, H, g, N):
 
 
 def solve(k, d, H, g=9.81, N=24, steps=None, tol=1e-13, maxit=60):
-    """Stream-function wave of wavenumber k, depth d, height H (Newton's method
-    with continuation in H).  Returns a ``Wave``."""
+    """Stream-function wave (Sec. 5.2; Rienecker & Fenton, cited there) of
+    wavenumber k, depth d, height H (Newton's method with continuation in H).
+    Returns a ``Wave``."""
     if steps is None:
         steep = H * k / (2 * math.pi)
         steps = max(1, int(math.ceil(steep / 0.005)))
